@@ -1,0 +1,467 @@
+"""CPU oracle for tensor-train contraction (Kisil et al., arXiv 2109.00626).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct float64
+reference that the CUDA library is checked against.  Only the test-suite, the
+smoke check and the benchmark's CPU-baseline leg may import it; the library
+itself never calls it and has no CPU fallback.
+
+Every function works on plain numpy float64 arrays and cites the passage of the
+paper it restates.  Library primitives (matmul, einsum, svd) serve as single
+steps; nothing is blocked, fused or reordered beyond the definitions.
+
+Conventions
+-----------
+* A TT of order N is a list of cores, core k shaped (R_k, I_k, R_{k+1}) with
+  R_0 = R_N = 1 (0-based bond index; the paper's G^(k) in R^{R_{k-1} x I_k x R_k},
+  Def. 7 / Eq. 9 and the rank conditions of Example 1).  Row-major storage:
+  the right rank is fastest.  (The paper's little-endian unfolding of Eq. 2 is
+  not used; all reshapes here are row-major, stated where they occur.)
+* Contracted set S: position k of X is contracted with position k of Y.  The
+  paper contracts one mode pair (Eq. 8); several pairs are contracted one
+  after the other, which gives the same result in any order because the sums
+  are over distinct indices.
+* Output mode order of a partial contraction follows Eq. 8: the free modes of
+  X ascending, then the free modes of Y ascending.  A layout whose modes come
+  in another order carries ``perm`` with Z_rho = Z.transpose(perm), i.e. axis p
+  of the emitted TT is axis perm[p] of Eq. 8's Z (the re-ordering of Step 6 of
+  Algorithm 2, kept as a relabelling in line with Remark 2).
+
+Functions
+---------
+tt_to_dense            Eq. 9
+tcp / tcp_nm           Eq. 8 (set of same-position pairs / one (n, m) pair)
+absorb_left            one contracted mode folded into the left environment
+                       (Example 1's K = A_x^T A_y generalised, Algorithm 2 step 4)
+absorb_right           the mirror image, right environment
+contract_full          all modes contracted -> scalar (Fig. 1b's full contraction)
+partial_chain          end-block S -> chain TT (Algorithm 2 steps 4-6)
+partial_merged         any S -> TT-matrix of merged cores
+chain_to_dense / merged_to_dense   dense reconstruction + un-permutation
+grad_sweep / grad_full / grad_partial_chain   gradients by the L/F formulas
+tt_svd                 Algorithm 1
+ttcp_alg2              Algorithm 2 on dense operands of different order
+tcp_ops / ttcp_ops     the operation counts of Section IV and Remark 3
+
+Parity status: every function here is pinned by a test in tests/ that does not
+re-use its formula (brute force, closed forms, invariants or finite
+differences); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import string
+
+import numpy as np
+
+__all__ = [
+    "tt_to_dense",
+    "tcp",
+    "tcp_nm",
+    "absorb_left",
+    "absorb_right",
+    "left_envs",
+    "right_envs",
+    "contract_full",
+    "end_block",
+    "partial_chain",
+    "partial_merged",
+    "chain_to_dense",
+    "merged_to_dense",
+    "grad_sweep",
+    "grad_full",
+    "grad_partial_chain",
+    "tt_svd",
+    "ttcp_alg2",
+    "tcp_ops",
+    "ttcp_ops",
+]
+
+
+def _f64(cores):
+    return [np.asarray(c, dtype=np.float64) for c in cores]
+
+
+# --------------------------------------------------------------------------
+# Dense semantics
+# --------------------------------------------------------------------------
+def tt_to_dense(cores):
+    """Eq. 9: X = G^(1) x_2^1 G^(2) x_3^1 ... x_3^1 G^(N).
+
+    Each step contracts the last (rank) mode of the running tensor with the
+    first (rank) mode of the next core, one TCP of Eq. 8 at a time.
+    """
+    cores = _f64(cores)
+    z = cores[0].reshape(cores[0].shape[1], cores[0].shape[2])  # R_0 = 1
+    for g in cores[1:]:
+        z = np.tensordot(z, g, axes=([z.ndim - 1], [0]))
+    return z.reshape(z.shape[:-1])  # R_N = 1
+
+
+def tcp(x, y, contracted):
+    """Eq. 8 for several same-position pairs: Z = sum over i_S of X[..] Y[..].
+
+    ``contracted`` lists 0-based positions k; position k of X is summed
+    against position k of Y.  Result axes: free modes of X ascending, then
+    free modes of Y ascending (Eq. 8's ordering).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = x.ndim
+    assert y.ndim == n
+    letters = string.ascii_letters
+    xs = [letters[k] for k in range(n)]
+    ys = [letters[k] if k in contracted else letters[n + k] for k in range(n)]
+    out = [xs[k] for k in range(n) if k not in contracted] + [ys[k] for k in range(n) if k not in contracted]
+    return np.einsum("".join(xs) + "," + "".join(ys) + "->" + "".join(out), x, y)
+
+
+def tcp_nm(x, y, n, m):
+    """Eq. 8 literally: the (n, m)-contraction of tensors of any orders (0-based n, m)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    assert x.shape[n] == y.shape[m]
+    letters = string.ascii_letters
+    xs = [letters[k] for k in range(x.ndim)]
+    ys = [letters[x.ndim + k] for k in range(y.ndim)]
+    ys[m] = xs[n]
+    out = [xs[k] for k in range(x.ndim) if k != n] + [ys[k] for k in range(y.ndim) if k != m]
+    return np.einsum("".join(xs) + "," + "".join(ys) + "->" + "".join(out), x, y)
+
+
+# --------------------------------------------------------------------------
+# Environment sweep (Algorithm 2 step 4, generalised to many modes)
+# --------------------------------------------------------------------------
+def absorb_left(e, gx, gy):
+    """E'[a',b'] = sum_{a,b,i} E[a,b] Gx[a,i,a'] Gy[b,i,b'].
+
+    With E = [[1]] and one mode this is Example 1's K = A_x^T A_y.  Written as
+    a sum over the mode index i of Gx[:,i,:]^T E Gy[:,i,:].
+    """
+    gx = np.asarray(gx, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    assert gx.shape[1] == gy.shape[1]
+    out = np.zeros((gx.shape[2], gy.shape[2]))
+    for i in range(gx.shape[1]):
+        out += gx[:, i, :].T @ e @ gy[:, i, :]
+    return out
+
+
+def absorb_right(f, gx, gy):
+    """F[a,b] = sum_{a',b',i} Gx[a,i,a'] F'[a',b'] Gy[b,i,b'] (mirror of absorb_left)."""
+    gx = np.asarray(gx, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    assert gx.shape[1] == gy.shape[1]
+    out = np.zeros((gx.shape[0], gy.shape[0]))
+    for i in range(gx.shape[1]):
+        out += gx[:, i, :] @ f @ gy[:, i, :].T
+    return out
+
+
+def left_envs(xc, yc, start=None):
+    """L_0 = start (default [[1]]), L_{k+1} = absorb_left(L_k, Gx_k, Gy_k); returns L_0..L_N."""
+    xc, yc = _f64(xc), _f64(yc)
+    e = np.ones((1, 1)) if start is None else np.asarray(start, dtype=np.float64)
+    envs = [e]
+    for gx, gy in zip(xc, yc):
+        e = absorb_left(e, gx, gy)
+        envs.append(e)
+    return envs
+
+
+def right_envs(xc, yc, end=None):
+    """F_N = end (default [[1]]), F_k = absorb_right(F_{k+1}, Gx_k, Gy_k); returns F_0..F_N."""
+    xc, yc = _f64(xc), _f64(yc)
+    f = np.ones((1, 1)) if end is None else np.asarray(end, dtype=np.float64)
+    envs = [f]
+    for gx, gy in zip(reversed(xc), reversed(yc)):
+        f = absorb_right(f, gx, gy)
+        envs.append(f)
+    return envs[::-1]
+
+
+def contract_full(xc, yc):
+    """<X, Y>: every position contracted (Fig. 1b's all-mode contraction to a scalar)."""
+    assert len(xc) == len(yc)
+    return float(left_envs(xc, yc)[-1][0, 0])
+
+
+# --------------------------------------------------------------------------
+# Partial contraction, chain layout (Algorithm 2 steps 4-6)
+# --------------------------------------------------------------------------
+def end_block(mask):
+    """Classify a contracted set: ("lead", s) if S = {0..s-1}, ("trail", s) if
+    S = {N-s..N-1}, else None.  The empty set counts as leading."""
+    n = len(mask)
+    s = int(sum(1 for v in mask if v))
+    if all(bool(mask[k]) == (k < s) for k in range(n)):
+        return ("lead", s)
+    if all(bool(mask[k]) == (k >= n - s) for k in range(n)):
+        return ("trail", s)
+    return None
+
+
+def _swap_rank_legs(g):
+    """The paper's (.)^{T[1;3]}: exchange the first and third modes of a core."""
+    return np.ascontiguousarray(np.transpose(g, (2, 1, 0)))
+
+
+def partial_chain(xc, yc, mask):
+    """Partial contraction over an end block S, returned as one TT (chain layout).
+
+    Leading S = {0..s-1} (the case of Algorithm 2 after its step-1 permutation):
+      K = L_s, the left environment over S (step 4 generalised);
+      C[a',i,b] = sum_a Gx_s[a,i,a'] K[a,b];
+      cores = Gx_{N-1}^T, ..., Gx_{s+1}^T, C, Gy_s, ..., Gy_{N-1}   (step 5,
+      X's cores walked backwards with their rank legs exchanged);
+      perm: axis p < m is X-free mode m-1-p, axis m+q is Y-free mode q.
+    Trailing S = {m..N-1}, m = N - s (the mirror image):
+      K = F_m, the right environment over S;
+      C[a,i,b] = sum_{a'} Gx_{m-1}[a,i,a'] K[a',b];
+      cores = Gx_0, ..., Gx_{m-2}, C, Gy_{m-1}^T, ..., Gy_0^T;
+      perm: axis p < m is X-free mode p, axis m+q is Y-free mode m-1-q.
+    Returns (cores, perm) with Z_rho = Z.transpose(perm) (step 6 as a relabelling).
+    """
+    xc, yc = _f64(xc), _f64(yc)
+    n = len(xc)
+    blk = end_block(mask)
+    if blk is None:
+        raise ValueError("chain layout needs the contracted modes to form a leading or trailing block")
+    side, s = blk
+    if s == n:
+        raise ValueError("all modes contracted: use contract_full")
+    m = n - s
+    if side == "lead":
+        k = left_envs(xc[:s], yc[:s])[-1]
+        gx = xc[s]
+        c = np.einsum("aiu,ab->uib", gx, k)
+        cores = [_swap_rank_legs(xc[j]) for j in range(n - 1, s, -1)] + [c] + [yc[j].copy() for j in range(s, n)]
+        perm = [m - 1 - p for p in range(m)] + [m + q for q in range(m)]
+    else:
+        k = right_envs(xc[m:], yc[m:])[0]
+        gx = xc[m - 1]
+        c = np.einsum("aiu,ub->aib", gx, k)
+        cores = [xc[j].copy() for j in range(m - 1)] + [c] + [_swap_rank_legs(yc[j]) for j in range(m - 1, -1, -1)]
+        perm = list(range(m)) + [m + (m - 1 - q) for q in range(m)]
+    return cores, perm
+
+
+def chain_to_dense(cores, perm):
+    """Dense Z in Eq. 8 order from a chain-layout TT and its perm."""
+    zr = tt_to_dense(cores)
+    return np.transpose(zr, np.argsort(perm))
+
+
+# --------------------------------------------------------------------------
+# Partial contraction, merged (TT-matrix) layout, any S
+# --------------------------------------------------------------------------
+def partial_merged(xc, yc, mask):
+    """Partial contraction over any S as a TT over the free positions.
+
+    Free positions f_0 < ... < f_{m-1}.  Core t is the Kronecker pair
+      W_t[(a,b), i, j, (a',b')] = Gx_{f_t}[a,i,a'] Gy_{f_t}[b,j,b']
+    (pair index a*R^y + b).  The left environment of the contracted modes
+    before f_0 is absorbed on the left of W_0; the contracted modes between f_t
+    and f_{t+1} (and after f_{m-1}) are absorbed on the right of W_t by running
+    the left-environment step on every row (r, i, j) of W_t.  Core t is returned
+    shaped (r_t, I_{f_t}, J_{f_t}, r_{t+1}); axes of the represented tensor
+    interleave (i_{f_0}, j_{f_0}, i_{f_1}, j_{f_1}, ...), so perm[2t] = t and
+    perm[2t+1] = m + t.
+    """
+    xc, yc = _f64(xc), _f64(yc)
+    n = len(xc)
+    free = [k for k in range(n) if not mask[k]]
+    if not free:
+        raise ValueError("all modes contracted: use contract_full")
+    m = len(free)
+    el = left_envs(xc[: free[0]], yc[: free[0]])[-1]
+    cores = []
+    for t, f in enumerate(free):
+        gx, gy = xc[f], yc[f]
+        rx, i_dim, rx2 = gx.shape
+        ry, j_dim, ry2 = gy.shape
+        w = np.einsum("aiu,bjv->abijuv", gx, gy).reshape(rx * ry, i_dim, j_dim, rx2, ry2)
+        if t == 0:
+            w = np.einsum("ab,abijuv->ijuv", el, w.reshape(rx, ry, i_dim, j_dim, rx2, ry2))[None]
+        nxt = free[t + 1] if t + 1 < m else n
+        run = range(f + 1, nxt)
+        rows = w.reshape(-1, rx2, ry2)
+        out_rows = []
+        for e in rows:
+            for k in run:
+                e = absorb_left(e, xc[k], yc[k])
+            out_rows.append(e.reshape(-1))
+        r_left = w.shape[0]
+        w = np.stack(out_rows).reshape(r_left, i_dim, j_dim, -1)
+        cores.append(w)
+    perm = []
+    for t in range(m):
+        perm += [t, m + t]
+    return cores, perm
+
+
+def merged_to_dense(cores, perm):
+    """Dense Z in Eq. 8 order from merged cores (r, I, J, r')."""
+    acc = None
+    dims = []
+    for w in cores:
+        r, i_dim, j_dim, r2 = w.shape
+        dims += [i_dim, j_dim]
+        g = np.asarray(w, dtype=np.float64).reshape(r, i_dim * j_dim, r2)
+        acc = g.reshape(i_dim * j_dim, r2) if acc is None else np.tensordot(acc, g, axes=([acc.ndim - 1], [0]))
+    zr = acc.reshape(dims)
+    return np.transpose(zr, np.argsort(perm))
+
+
+# --------------------------------------------------------------------------
+# Gradients
+# --------------------------------------------------------------------------
+def grad_sweep(xc, yc, start=None, end=None):
+    """Gradients of z = <start | sweep over all modes | end> w.r.t. every core.
+
+    With L_k the left environments from ``start`` and F_k the right ones from
+    ``end``, z is linear in each core and
+      dz/dGx_k[:, i, :] = L_k Gy_k[:, i, :] F_{k+1}^T,
+      dz/dGy_k[:, i, :] = L_k^T Gx_k[:, i, :] F_{k+1}.
+    """
+    xc, yc = _f64(xc), _f64(yc)
+    le = left_envs(xc, yc, start)
+    fe = right_envs(xc, yc, end)
+    gx_out, gy_out = [], []
+    for k, (gx, gy) in enumerate(zip(xc, yc)):
+        dgx = np.zeros_like(gx)
+        dgy = np.zeros_like(gy)
+        for i in range(gx.shape[1]):
+            dgx[:, i, :] = le[k] @ gy[:, i, :] @ fe[k + 1].T
+            dgy[:, i, :] = le[k].T @ gx[:, i, :] @ fe[k + 1]
+        gx_out.append(dgx)
+        gy_out.append(dgy)
+    return gx_out, gy_out
+
+
+def grad_full(xc, yc, cot=1.0):
+    """d(cot * <X,Y>)/dG for every core of X and Y."""
+    gx, gy = grad_sweep(xc, yc)
+    return [cot * g for g in gx], [cot * g for g in gy]
+
+
+def grad_partial_chain(xc, yc, mask, dz):
+    """Back-propagate cotangents ``dz`` of the chain-layout cores to X and Y.
+
+    The emitted cores are copies (or leg-swapped copies) of free cores, plus C,
+    which is bilinear in the boundary core and K; K is the environment over S,
+    so its cotangent dK seeds ``grad_sweep`` on the contracted block.
+    """
+    xc, yc = _f64(xc), _f64(yc)
+    dz = _f64(dz)
+    n = len(xc)
+    side, s = end_block(mask)
+    m = n - s
+    gx = [np.zeros_like(g) for g in xc]
+    gy = [np.zeros_like(g) for g in yc]
+    if side == "lead":
+        k = left_envs(xc[:s], yc[:s])[-1]
+        for p, j in enumerate(range(n - 1, s, -1)):
+            gx[j] = _swap_rank_legs(dz[p])
+        dc = dz[m - 1]  # C[a',i,b] = sum_a Gx_s[a,i,a'] K[a,b]
+        gx[s] = np.einsum("ab,uib->aiu", k, dc)
+        dk = np.einsum("aiu,uib->ab", xc[s], dc)
+        for q, j in enumerate(range(s, n)):
+            gy[j] = dz[m + q].copy()
+        if s > 0:
+            sx, sy = grad_sweep(xc[:s], yc[:s], None, dk)
+            gx[:s], gy[:s] = sx, sy
+    else:
+        k = right_envs(xc[m:], yc[m:])[0]
+        for j in range(m - 1):
+            gx[j] = dz[j].copy()
+        dc = dz[m - 1]  # C[a,i,b] = sum_u Gx_{m-1}[a,i,u] K[u,b]
+        gx[m - 1] = np.einsum("aib,ub->aiu", dc, k)
+        dk = np.einsum("aiu,aib->ub", xc[m - 1], dc)
+        for q, j in enumerate(range(m - 1, -1, -1)):
+            gy[j] = _swap_rank_legs(dz[m + q])
+        sx, sy = grad_sweep(xc[m:], yc[m:], dk, None)
+        gx[m:], gy[m:] = sx, sy
+    return gx, gy
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 (TT-SVD) and Algorithm 2 (TTCP) on dense operands
+# --------------------------------------------------------------------------
+def tt_svd(x, eps=0.0):
+    """Algorithm 1: sequential delta-truncated SVDs.
+
+    delta = eps / sqrt(N-1) * ||X||_F; at step n the running matrix is
+    reshaped (row-major) to (R_{n-1} I_n) x rest, its truncated SVD keeps the
+    fewest singular values whose discarded tail has 2-norm <= delta, U becomes
+    core n and S V^T carries on.  The last core is what remains.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    dims = x.shape
+    n = len(dims)
+    if n == 1:
+        return [x.reshape(1, dims[0], 1).copy()]
+    delta = eps / np.sqrt(n - 1) * np.linalg.norm(x)
+    cores = []
+    r_prev = 1
+    z = x.reshape(-1)
+    for k in range(n - 1):
+        z = z.reshape(r_prev * dims[k], -1)
+        u, sv, vt = np.linalg.svd(z, full_matrices=False)
+        tail = np.sqrt(np.cumsum((sv**2)[::-1]))[::-1]  # tail[r] = ||sv[r:]||
+        r = len(sv)
+        for cand in range(1, len(sv) + 1):
+            rest = tail[cand] if cand < len(sv) else 0.0
+            if rest <= delta:
+                r = cand
+                break
+        cores.append(u[:, :r].reshape(r_prev, dims[k], r))
+        z = sv[:r, None] * vt[:r]
+        r_prev = r
+    cores.append(z.reshape(r_prev, dims[n - 1], 1))
+    return cores
+
+
+def ttcp_alg2(x, y, n, m, eps=0.0):
+    """Algorithm 2 (TTCP) for dense X (order N) and Y (order M), 0-based (n, m).
+
+    Steps: move mode n of X to the front (step 1) and decompose with
+    Algorithm 1 (step 2); the same for Y (step 3); K = A_x^T A_y (step 4);
+    join X's remaining cores, walked backwards with their rank legs exchanged,
+    through K to Y's remaining cores (step 5; K is absorbed into the last X core
+    of the walk, G_x^(2)); re-order the axes into Eq. 8's order (step 6).
+    Returns (dense Z, chain cores of Z_rho, perm).  Needs N, M >= 2.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    nx, ny = x.ndim, y.ndim
+    assert nx >= 2 and ny >= 2
+    xr = np.moveaxis(x, n, 0)
+    yr = np.moveaxis(y, m, 0)
+    gx = tt_svd(xr, eps)
+    gy = tt_svd(yr, eps)
+    ax = gx[0][0]  # (I_n, R_1)
+    ay = gy[0][0]  # (J_m, P_1)
+    k = ax.T @ ay
+    xrev = [_swap_rank_legs(g) for g in gx[:0:-1]]  # B_x^T, ..., G_x^(2)T
+    xrev[-1] = np.einsum("uia,ab->uib", xrev[-1], k)
+    cores = xrev + [g.copy() for g in gy[1:]]
+    # axis bookkeeping: X^rho's cores 2..N hold X's modes except n, ascending
+    x_modes = [k2 for k2 in range(nx) if k2 != n]
+    y_modes = [k2 for k2 in range(ny) if k2 != m]
+    zr_axes_x = list(reversed(x_modes))
+    # Eq. 8 position of each Z_rho axis
+    perm = [x_modes.index(a) for a in zr_axes_x] + [len(x_modes) + y_modes.index(b) for b in y_modes]
+    z = chain_to_dense(cores, perm)
+    return z, cores, perm
+
+
+# --------------------------------------------------------------------------
+# Operation counts of Section IV
+# --------------------------------------------------------------------------
+def tcp_ops(i_dim, order):
+    """Standard TCP of two order-N tensors with all modes I: I^(2N-1) (Section IV)."""
+    return i_dim ** (2 * order - 1)
+
+
+def ttcp_ops(i_dim, rank):
+    """TTCP cost of one contracted mode at the front: K = A_x^T A_y, I R_1 P_1 with R_1 = P_1 = R."""
+    return i_dim * rank * rank

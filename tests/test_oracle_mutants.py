@@ -1,0 +1,103 @@
+"""Planted slips in the oracle (on the CPU) must be caught by the pins.
+
+Each mutant patches one oracle function with a plausible mistake; the test
+then evaluates the independent check used in test_oracle_pins.py and asserts
+that it now fails.  This shows that the pins constrain every part they cover.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import tt_oracle as T
+from paper_2109_00626_gb300 import inputs as G
+
+
+def _dense_by_entries(cores):
+    shape = tuple(g.shape[1] for g in cores)
+    out = np.empty(shape)
+    for idx in itertools.product(*[range(s) for s in shape]):
+        m = np.ones((1, 1))
+        for g, i in zip(cores, idx):
+            m = m @ g[:, i, :]
+        out[idx] = m[0, 0]
+    return out
+
+
+def _absorb_drop_first_slice(e, gx, gy):
+    out = np.zeros((gx.shape[2], gy.shape[2]))
+    for i in range(1, gx.shape[1]):
+        out += gx[:, i, :].T @ e @ gy[:, i, :]
+    return out
+
+
+def _absorb_transposed_env(e, gx, gy):
+    out = np.zeros((gx.shape[2], gy.shape[2]))
+    for i in range(gx.shape[1]):
+        out += gx[:, i, :].T @ e.T @ gy[:, i, :]
+    return out
+
+
+def _absorb_sign(e, gx, gy):
+    out = np.zeros((gx.shape[2], gy.shape[2]))
+    for i in range(gx.shape[1]):
+        out += (-1) ** i * (gx[:, i, :].T @ e @ gy[:, i, :])
+    return out
+
+
+@pytest.mark.parametrize("mutant", [_absorb_drop_first_slice, _absorb_transposed_env, _absorb_sign])
+def test_full_pin_catches_absorb_mutants(mutant, monkeypatch):
+    x, y = G.pair(11, [3, 4, 3], [1, 3, 3, 1], [1, 3, 3, 1], np.float64)
+    ref = math.fsum((_dense_by_entries(x) * _dense_by_entries(y)).ravel())
+    assert abs(O.contract_full(x, y) - ref) < 1e-14
+    monkeypatch.setattr(T, "absorb_left", mutant)
+    assert abs(T.contract_full(x, y) - ref) > 1e-6
+
+
+def test_chain_pin_catches_unswapped_legs(monkeypatch):
+    x, y = G.pair(12, [2, 3, 2, 3], [1, 2, 2, 2, 1], [1, 2, 2, 2, 1], np.float64)
+    want = O.tcp(_dense_by_entries(x), _dense_by_entries(y), [0])
+    monkeypatch.setattr(T, "_swap_rank_legs", lambda g: np.ascontiguousarray(g))
+    try:
+        cores, perm = T.partial_chain(x, y, [1, 0, 0, 0])
+        got = T.chain_to_dense(cores, perm)
+        assert got.shape != want.shape or np.abs(got - want).max() > 1e-6
+    except ValueError:
+        pass  # leg sizes no longer join: caught as well
+
+
+def test_chain_pin_catches_wrong_perm(monkeypatch):
+    x, y = G.pair(13, [2, 3, 4, 2], [1, 2, 3, 2, 1], [1, 3, 2, 2, 1], np.float64)
+    want = O.tcp(_dense_by_entries(x), _dense_by_entries(y), [0, 1])
+    cores, perm = O.partial_chain(x, y, [1, 1, 0, 0])
+    np.testing.assert_allclose(O.chain_to_dense(cores, perm), want, atol=1e-14)
+    bad = list(perm)
+    bad[0], bad[1] = bad[1], bad[0]
+    got = O.chain_to_dense(cores, bad)
+    assert got.shape != want.shape or np.abs(got - want).max() > 1e-6
+
+
+def test_grad_pin_catches_shifted_env(monkeypatch):
+    x, y = G.pair(14, [3, 3, 3], [1, 2, 2, 1], [1, 2, 2, 1], np.float64)
+    z = O.contract_full(x, y)
+
+    def bad_grad_sweep(xc, yc, start=None, end=None):
+        le = T.left_envs(xc, yc, start)
+        fe = T.right_envs(xc, yc, end)
+        gx = []
+        for k, (a, b) in enumerate(zip(xc, yc)):
+            d = np.zeros_like(a)
+            f = fe[min(k + 2, len(fe) - 1)]
+            for i in range(a.shape[1]):
+                if f.shape[0] != a.shape[2]:
+                    f = fe[k + 1] * 1.5
+                d[:, i, :] = le[k] @ b[:, i, :] @ f.T
+            gx.append(d)
+        return gx, [np.zeros_like(b) for b in yc]
+
+    monkeypatch.setattr(T, "grad_sweep", bad_grad_sweep)
+    gx, _ = T.grad_full(x, y)
+    # Euler's identity <G_k, dz/dG_k> = z fails for at least one core
+    assert max(abs(np.sum(g * c) - z) for g, c in zip(gx, x)) > 1e-6
