@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the tensor-train contraction library on GB300.
+
+Workload (one "step"): the order-10 TT pair with mode sizes 16 and internal
+ranks 64 in float32 (seeded Gaussian cores, sigma = 1/sqrt(I R)); one full
+contraction <X, Y> and one partial contraction over modes 1-6 (chain layout).
+Metric: contractions per second (2 per step), with GFLOP/s and the roofline
+fraction of the dominant kernel (the environment sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica of the pair (the path has no
+exchange step: replicas only); rank 0 prints one JSON line.  The reference arm
+times the float64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2109_00626_gb300 import inputs as G  # noqa: E402
+from paper_2109_00626_gb300 import workload as W  # noqa: E402
+
+METRIC = "TT contractions/s (order-10, I=16, R=64, fp32: full + partial over modes 1-6)"
+UNIT = "contractions/s"
+MASK = [1] * 6 + [0] * 4
+WORKLOAD = "order-10 TT pair, modes 16, internal ranks 64, float32; full contraction + partial contraction over modes 1-6 (chain layout)"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp32_simt_peak_tflops():
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz maximum SM clock."""
+    sm_mhz = _peaks().get("sm_max_mhz", 2070.0)
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def work_per_step():
+    modes = [16] * 10
+    r = G.tt_ranks(10, 64)
+    f_full = W.full_flops(modes, r, r)
+    f_part = W.partial_chain_flops(modes, r, r, MASK)
+    b_full = W.full_bytes(modes, r, r, 4)
+    b_part = W.partial_chain_bytes(modes, r, r, MASK, 4)
+    return f_full, f_part, b_full, b_part
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.lines = []
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL,
+                text=True,
+            )
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = []
+        for ln in out.strip().splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(
+                    {
+                        "sm": float(parts[1]),
+                        "max": float(parts[2]),
+                        "hw": parts[5],
+                        "hwt": parts[6],
+                        "swt": parts[7],
+                        "pcap": parts[8],
+                    }
+                )
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"] == "Active":
+                reasons.add("sw_power_cap")
+        return {
+            "sm_mhz": statistics.median(r["sm"] for r in rows),
+            "sm_max_mhz": max(r["max"] for r in rows),
+            "reasons": sorted(reasons),
+            "samples": len(rows),
+        }
+
+
+def cpu_baseline(seconds=10.0):
+    """The float64 oracle, as it stands, on the same pair (one host thread)."""
+    import oracle as O
+
+    x, y = G.order10_r64(0, np.float64)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        O.contract_full(x, y)
+        O.partial_chain(x, y, MASK)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {
+        "value": 2 * n / dt,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{n} steps (full + partial over modes 1-6 of the same order-10 pair) in {dt:.1f} s, numpy float64, OPENBLAS_NUM_THREADS=1",
+    }
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    x, y = G.order10_r64(0, np.float64)
+    for _ in range(args.warmup):
+        O.contract_full(x, y)
+        O.partial_chain(x, y, MASK)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.contract_full(x, y)
+        O.partial_chain(x, y, MASK)
+    dt = time.perf_counter() - t0
+    val = 2 * args.steps / dt
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": val,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "seed": 0},
+        "cpu_baseline": {
+            "value": val,
+            "unit": UNIT,
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"{args.steps} steps of the full workload, numpy float64 oracle, one host thread",
+        },
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2109_00626_gb300 as T
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    x, y = G.order10_r64(0, np.float32)
+    xd = [torch.from_numpy(c).to(dev) for c in x]
+    yd = [torch.from_numpy(c).to(dev) for c in y]
+    full = T.FullContraction(xd, yd)
+    part = T.PartialContraction(xd, yd, MASK)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        full()
+        part()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = T.launch_count()
+    for k in range(K):
+        flush.fill_(float(k))  # L2 flush between timed steps (256 MiB write, untimed)
+        ev[k][0].record(stream)
+        full()
+        ev[k][1].record(stream)
+        part()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = T.launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    t_full = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    tot_ms = sum(t_step)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms = tot_ms / K
+    value = 2 * K * world / (tot_ms / 1e3)
+
+    f_full, f_part, b_full, b_part = work_per_step()
+    full_ms = statistics.mean(t_full)
+    achieved = f_full / (full_ms / 1e3) / 1e12
+    peak = fp32_simt_peak_tflops()
+
+    # end to end through the C ABI with host buffers: H2D of every core,
+    # both contractions, D2H of z and of the partial result's cores.
+    xh = [torch.from_numpy(c).pin_memory() for c in x]
+    yh = [torch.from_numpy(c).pin_memory() for c in y]
+    zh = [torch.empty(c.shape, dtype=c.dtype).pin_memory() for c in part.z]
+    outh = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = sum(c.numel() * 4 for c in xh + yh)
+    d2h = 8 + sum(c.numel() * 4 for c in zh)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K2 = max(1, K // 2)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(K2):
+        for d, h in zip(xd + yd, xh + yh):
+            d.copy_(h, non_blocking=True)
+        full()
+        part()
+        outh.copy_(full.out, non_blocking=True)
+        for h, d in zip(zh, part.z):
+            h.copy_(d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / K2
+
+    status = int(full.status.item()) | int(part.status.item())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOAD,
+                "seed": 0,
+                "l2": "flushed between timed steps (256 MiB write)",
+                "parallelism": "replicas" if world > 1 else "single GPU",
+            },
+            "gflops": (f_full + f_part) / (ms / 1e3) / 1e9,
+            "roofline": {
+                "kernel": "sweep_cluster_kernel<float,64> (full contraction)",
+                "bound": "alu",
+                "achieved": achieved,
+                "peak": peak,
+                "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": None,
+                "note": "fp32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz (derived); single latency-bound contraction",
+            },
+            "e2e": {
+                "value": 2 / (e2e_ms / 1e3) * world,
+                "unit": UNIT,
+                "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+            },
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "device_status": status,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,244 @@
+/*
+ * ttc.h -- C ABI of the GB300 (sm_103a) tensor-train contraction library.
+ *
+ * The library contracts two tensors held in tensor-train (TT) format along a
+ * set of common modes, as in the Tensor-Train Contraction Product (TTCP) of
+ * Kisil, Calvi, Konstantinidis, Xu and Mandic, "Reducing Computational
+ * Complexity of Tensor Contractions via Tensor-Train Networks"
+ * (arXiv 2109.00626).
+ *
+ * Data model (Def. 7 / Eq. 9): a TT of order N is N cores; core k holds
+ *   G_k[r][i][r'],  r < R_k, i < I_k, r' < R_{k+1},  R_0 = R_N = 1,
+ * contiguous and row-major in device memory (right rank fastest), and
+ *   X[i_0..i_{N-1}] = G_0[:,i_0,:] G_1[:,i_1,:] ... G_{N-1}[:,i_{N-1},:].
+ *
+ * Conventions common to every call
+ *   - Mode k of X is contracted with mode k of Y (same position).  The paper's
+ *     TCP (Eq. 8) contracts one mode pair; a set S of pairs is contracted pair
+ *     after pair, which is order independent.
+ *   - Descriptors (tt_desc) and masks live in HOST memory; core pointers are
+ *     DEVICE pointers.  The caller owns every buffer; the library allocates
+ *     nothing on any call below except tt_batch_plan (host memory, released by
+ *     tt_plan_free) and never synchronises the stream.
+ *   - Every compute call is asynchronous on `stream` (NULL = legacy default
+ *     stream) and returns a tt_error synchronously: argument and shape errors
+ *     are detected on the host before anything is enqueued.
+ *   - Conditions found on the device (non-finite values, overflow of the
+ *     output after undoing the scaling, a wait that ran out) are OR-ed into the
+ *     int32 word `*status_dev` (TT_STATUS_* bits).  The library never clears
+ *     it: zero it before the call.  No call traps or faults on bad data.
+ *   - Scaling.  Environments are kept as mantissa * 2^e with an exact power of
+ *     two folded out whenever their largest entry leaves [2^-s, 2^s]
+ *     (s = 32 for float32/bfloat16 arithmetic, 256 for float64), so long
+ *     contractions neither overflow nor underflow.  Results may be returned
+ *     split as (mantissa, int64 log2 scale).
+ */
+#ifndef TTC_H
+#define TTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* tt_stream;
+
+/* Storage type of TT cores. */
+typedef enum { TT_F64 = 0, TT_F32 = 1, TT_BF16 = 2 } tt_dtype;
+
+/* Arithmetic used for the core products.
+ *   TT_P_NATIVE  products and sums in the storage type (float64 or float32;
+ *                for bfloat16 storage: bfloat16 products, float32 sums).
+ *   TT_P_BF16    float32 operands rounded to bfloat16, float32 sums (tensor cores).
+ *   TT_P_BF16X3  float32 operands split as hi + lo bfloat16 pairs; the
+ *                products hi*hi + hi*lo + lo*hi are summed in float32 (tensor
+ *                cores), the lo*lo term is dropped.
+ *   TT_P_TF32X3  the same split with tf32 pieces. */
+typedef enum { TT_P_NATIVE = 0, TT_P_TF32X3 = 1, TT_P_BF16 = 2, TT_P_BF16X3 = 3 } tt_prec;
+
+/* Layout of a partial contraction's result (see tt_partial_shape). */
+typedef enum { TT_LAYOUT_CHAIN = 0, TT_LAYOUT_MERGED = 1 } tt_layout;
+
+/* Return codes. */
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_ARG = -1,         /* NULL pointer, bad enum, order <= 0 or > TT_MAX_ORDER     */
+  TT_ERR_SHAPE = -2,       /* ranks do not chain, R_0/R_N != 1, I_k != J_k on S,      */
+                           /* orders differ, output shape differs from tt_partial_shape */
+  TT_ERR_DTYPE = -3,       /* dtype / precision combination not provided              */
+  TT_ERR_LAYOUT = -4,      /* chain layout asked for a contracted set that is not an */
+                           /* end block                                              */
+  TT_ERR_TOO_LARGE = -5,   /* a rank, mode size or merged core exceeds a stated cap  */
+  TT_ERR_WS = -6,          /* workspace smaller than tt_workspace_bytes              */
+  TT_ERR_CUDA = -7,        /* a CUDA runtime call failed (launch, attribute query)   */
+  TT_ERR_UNSUPPORTED = -8  /* valid request outside what this build implements       */
+} tt_error;
+
+/* Bits OR-ed into *status_dev by kernels. */
+enum {
+  TT_STATUS_NONFINITE = 1, /* an environment or result held Inf/NaN                  */
+  TT_STATUS_OVERFLOW = 2,  /* undoing the power-of-two scaling left the float range  */
+  TT_STATUS_TIMEOUT = 4    /* a bounded device-side wait gave up                     */
+};
+
+#define TT_MAX_ORDER 64
+
+/* One TT operand.  All arrays are host memory; cores[k] is a device pointer to
+ * R_k * I_k * R_{k+1} elements of `dtype`, contiguous, row-major. */
+typedef struct {
+  int32_t order;          /* N >= 1                                              */
+  const int32_t* modes;   /* [N]   I_k >= 1                                      */
+  const int32_t* ranks;   /* [N+1] R_0 = R_N = 1, R_k >= 1                       */
+  void* const* cores;     /* [N]   device pointers                               */
+  int32_t dtype;          /* tt_dtype                                           */
+} tt_desc;
+
+/* Operation selectors for tt_workspace_bytes. */
+enum { TT_OP_FULL = 0, TT_OP_PARTIAL = 1, TT_OP_BACKWARD = 2 };
+
+/* Bytes of device workspace `op` needs for these operands (0 is possible).
+ * `mask` (host, [N], 1 = contracted) is ignored for TT_OP_FULL and may be NULL
+ * there; for TT_OP_BACKWARD a NULL mask means the full contraction.
+ * Returns TT_OK and sets *bytes, or an error code. */
+int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
+                       int prec, size_t* bytes);
+
+/* Full contraction z = <X, Y> = sum over all indices of X[i] Y[i]
+ * (Fig. 1b: contraction along every mode to a scalar; the all-mode
+ * generalisation of Algorithm 2 step 4).  X and Y have the same order and mode
+ * sizes; ranks are independent.
+ *   out_dev      device double.  If out_log2_dev is NULL it receives z;
+ *                otherwise it receives a mantissa m and *out_log2_dev an int64 e
+ *                with z = m * 2^e (use this form when |z| may leave the double
+ *                range).
+ *   status_dev   device int32, see TT_STATUS_*.
+ * Precision: TT_P_NATIVE for F64/F32/BF16 storage; TT_P_BF16 and TT_P_BF16X3
+ * for F32 storage.  The final sum of the last mode is accumulated in float64. */
+int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_dev,
+                     int64_t* out_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
+                     tt_stream stream);
+
+/* Shape of the result of a partial contraction over S = {k : mask[k] != 0}
+ * (host only, synchronous).  Z has the free modes of X ascending, then the
+ * free modes of Y ascending (Eq. 8's order); m = number of free modes >= 1.
+ *
+ * TT_LAYOUT_CHAIN (S a leading block {0..s-1} or a trailing block
+ *   {N-s..N-1}; Algorithm 2 steps 4-6): a TT of order 2m.
+ *   leading : cores Gx_{N-1}^T .. Gx_{s+1}^T, C, Gy_s .. Gy_{N-1}
+ *             with K = left environment over S and
+ *             C[a'][i][b] = sum_a Gx_s[a][i][a'] K[a][b];
+ *   trailing: cores Gx_0 .. Gx_{m-2}, C, Gy_{m-1}^T .. Gy_0^T
+ *             with K = right environment over S and
+ *             C[a][i][b] = sum_a' Gx_{m-1}[a][i][a'] K[a'][b];
+ *   G^T exchanges the two rank legs of a core (the paper's T[1;3]).
+ * TT_LAYOUT_MERGED (any S): a TT of m cores over the free positions
+ *   f_0 < .. < f_{m-1}; core t is [r_t][I_{f_t}][J_{f_t}][r_{t+1}] (stored as
+ *   [r_t][I*J][r_{t+1}], i major) holding Gx_{f_t} (x) Gy_{f_t} with pair rank
+ *   index a*R^y + b, the environments of the contracted modes folded in.
+ *
+ * Outputs (host): *z_order = number of cores; z_modes[z_order] = mode size of
+ * each core (I*J for merged); z_ranks[z_order+1]; z_perm[2m]: axis p of the
+ * represented tensor is axis z_perm[p] of Eq. 8's Z (chain axes follow the
+ * cores; merged axes are i_{f_0}, j_{f_0}, i_{f_1}, ...).  Arrays must hold
+ * 2*N (+1 for ranks) entries. */
+int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
+                     int32_t* z_order, int32_t* z_modes, int32_t* z_ranks, int32_t* z_perm);
+
+/* Partial contraction Z = X x_S Y (Eq. 8 over every pair in S; Algorithm 2
+ * steps 4-6 for the chain layout).  `z` describes caller-allocated output
+ * cores of exactly the shape tt_partial_shape reports, same dtype as X.
+ * An output core may alias the input core it is a plain copy of (chain: the
+ * Gy_k of a leading block, the Gx_k of a trailing block); then nothing is
+ * copied for it.
+ *   z_log2_dev  optional device int64: if non-NULL the power-of-two scale of
+ *               the environment is stored there and left out of C (Z = Z_stored
+ *               * 2^e); if NULL it is folded into C.
+ * Precision: TT_P_NATIVE (F64/F32). */
+int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
+                        int prec, const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev,
+                        void* ws, size_t ws_bytes, tt_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched contraction of many independent pairs in one persistent launch.
+ * ------------------------------------------------------------------------- */
+typedef struct tt_plan tt_plan;
+
+typedef struct {
+  int32_t n_pairs;
+  const tt_desc* x;              /* [n_pairs]                                       */
+  const tt_desc* y;              /* [n_pairs]                                       */
+  const uint8_t* const* mask;    /* [n_pairs]; NULL entry (or NULL array) = full    */
+  const tt_desc* z;              /* [n_pairs] chain-layout outputs of partial pairs */
+                                 /* (entries of full pairs are ignored; may be NULL */
+                                 /* when every pair is full)                        */
+  int32_t prec;                  /* TT_P_NATIVE                                     */
+} tt_batch;
+
+/* Validate every pair, order the work longest-first, choose a tile
+ * configuration per pair and size the device tables.  Host only, synchronous,
+ * allocates host memory (freed by tt_plan_free).  Returns the bytes of the
+ * packed device table (*packed_bytes) and of the workspace (*ws_bytes). */
+int tt_batch_plan(const tt_batch* batch, tt_plan** plan, size_t* packed_bytes, size_t* ws_bytes);
+
+/* Write the packed table into host memory `packed_host` (packed_bytes long);
+ * the caller copies it to device memory once and passes that copy below. */
+int tt_batch_pack(const tt_plan* plan, void* packed_host, size_t packed_bytes);
+
+/* Enqueue the batched contraction.  out_dev: device double[n_pairs], the value
+ * of each full pair (mantissa if out_log2_dev is non-NULL, which then receives
+ * int64[n_pairs] scales); entries of partial pairs are set to 0.  Partial
+ * pairs write their chain-layout cores into the batch's z descriptors (scale
+ * folded in).  No allocation, no synchronisation: the call can be captured in
+ * a CUDA graph and replayed. */
+int tt_contract_batched(const tt_plan* plan, const void* packed_dev, double* out_dev,
+                        int64_t* out_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
+                        tt_stream stream);
+
+/* Number of pairs and the tile configuration chosen for pair p (for tests and
+ * reports); returns TT_ERR_ARG for p out of range. */
+int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile_config);
+
+void tt_plan_free(tt_plan* plan);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint.
+ * ------------------------------------------------------------------------- */
+/* Gradients of a full or partial contraction with respect to every core of
+ * both operands.
+ *   mask == NULL     full contraction; cot_dev = device double, the cotangent
+ *                    of z; dz ignored.
+ *   mask != NULL     chain-layout partial contraction; dz describes the
+ *                    cotangent of every output core (device, same shapes as
+ *                    the output), cot_dev ignored.
+ *   gx, gy           caller-allocated gradient cores, shapes of x and y.
+ *   ckpt_stride      left environments are stored every `ckpt_stride` modes
+ *                    and recomputed inside each segment during the backward
+ *                    sweep (0 = choose ceil(sqrt(N))).
+ * For a full contraction, dz/dGx_k[:,i,:] = L_k Gy_k[:,i,:] F_{k+1}^T and
+ * dz/dGy_k[:,i,:] = L_k^T Gx_k[:,i,:] F_{k+1}, where L_k / F_{k+1} are the left
+ * / right environments; a chain-layout partial contraction reduces to this with
+ * the cotangent of its K as the boundary environment.
+ * Precision: TT_P_NATIVE (F64/F32). */
+int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
+                         int prec, const double* cot_dev, const tt_desc* dz, const tt_desc* gx,
+                         const tt_desc* gy, int32_t ckpt_stride, int32_t* status_dev, void* ws,
+                         size_t ws_bytes, tt_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Misc.
+ * ------------------------------------------------------------------------- */
+/* Static text for a tt_error code. */
+const char* tt_error_string(int code);
+
+/* Number of kernel launches the library has enqueued since load (all calls,
+ * all threads); used to report how many of this library's kernels ran. */
+uint64_t tt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTC_H */

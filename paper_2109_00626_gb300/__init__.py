@@ -1,0 +1,25 @@
+"""GB300 (sm_103a) tensor-train contraction library.
+
+Contracts two tensors held in tensor-train format along a set of common modes
+(the Tensor-Train Contraction Product of Kisil et al., arXiv 2109.00626).  The
+compute path is the C-ABI library ``libttc.so`` (``include/ttc.h``, CUDA
+kernels under ``csrc/``); this package only marshals arguments.
+
+``inputs`` (seeded synthetic TTs) is numpy-only and imports nothing else.
+"""
+from ._binding import (  # noqa: F401
+    EXPORTS,
+    LAYOUT,
+    PREC,
+    Desc,
+    FullContraction,
+    PartialContraction,
+    TTError,
+    contract_full,
+    contract_partial,
+    error_string,
+    launch_count,
+    lib,
+    partial_shape,
+    workspace_bytes,
+)

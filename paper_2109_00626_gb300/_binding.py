@@ -1,0 +1,302 @@
+"""ctypes binding of libttc.so (include/ttc.h).
+
+Argument marshalling only: every step of a contraction runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  There
+is no CPU fallback: if the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_int, c_int32, c_size_t, c_uint8, c_uint64, c_void_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttc.so")
+
+TT_F64, TT_F32, TT_BF16 = 0, 1, 2
+TT_P_NATIVE, TT_P_TF32X3, TT_P_BF16, TT_P_BF16X3 = 0, 1, 2, 3
+TT_LAYOUT_CHAIN, TT_LAYOUT_MERGED = 0, 1
+TT_OP_FULL, TT_OP_PARTIAL, TT_OP_BACKWARD = 0, 1, 2
+TT_STATUS_NONFINITE, TT_STATUS_OVERFLOW, TT_STATUS_TIMEOUT = 1, 2, 4
+TT_MAX_ORDER = 64
+
+PREC = {"native": TT_P_NATIVE, "tf32x3": TT_P_TF32X3, "bf16": TT_P_BF16, "bf16x3": TT_P_BF16X3}
+LAYOUT = {"chain": TT_LAYOUT_CHAIN, "merged": TT_LAYOUT_MERGED}
+
+# Every symbol include/ttc.h declares (checked by the CPU test-suite).
+EXPORTS = [
+    "tt_workspace_bytes",
+    "tt_contract_full",
+    "tt_partial_shape",
+    "tt_contract_partial",
+    "tt_batch_plan",
+    "tt_batch_pack",
+    "tt_contract_batched",
+    "tt_plan_info",
+    "tt_plan_free",
+    "tt_contract_backward",
+    "tt_error_string",
+    "tt_launch_count",
+]
+
+
+class TTDesc(ctypes.Structure):
+    _fields_ = [
+        ("order", c_int32),
+        ("modes", POINTER(c_int32)),
+        ("ranks", POINTER(c_int32)),
+        ("cores", POINTER(c_void_p)),
+        ("dtype", c_int32),
+    ]
+
+
+class TTBatch(ctypes.Structure):
+    _fields_ = [
+        ("n_pairs", c_int32),
+        ("x", POINTER(TTDesc)),
+        ("y", POINTER(TTDesc)),
+        ("mask", POINTER(POINTER(c_uint8))),
+        ("z", POINTER(TTDesc)),
+        ("prec", c_int32),
+    ]
+
+
+class TTError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (code {code})")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libttc.so is not built; run paper_2109_00626_gb300.build.build() (needs nvcc)"
+        )
+    L = ctypes.CDLL(LIB_PATH)
+    D = POINTER(TTDesc)
+    U8 = POINTER(c_uint8)
+    I32 = POINTER(c_int32)
+    L.tt_workspace_bytes.argtypes = [c_int, D, D, U8, c_int, c_int, POINTER(c_size_t)]
+    L.tt_contract_full.argtypes = [D, D, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.tt_partial_shape.argtypes = [D, D, U8, c_int, I32, I32, I32, I32]
+    L.tt_contract_partial.argtypes = [D, D, U8, c_int, c_int, D, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.tt_batch_plan.argtypes = [POINTER(TTBatch), POINTER(c_void_p), POINTER(c_size_t), POINTER(c_size_t)]
+    L.tt_batch_pack.argtypes = [c_void_p, c_void_p, c_size_t]
+    L.tt_contract_batched.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.tt_plan_info.argtypes = [c_void_p, c_int32, I32, I32]
+    L.tt_plan_free.argtypes = [c_void_p]
+    L.tt_plan_free.restype = None
+    L.tt_contract_backward.argtypes = [
+        D, D, U8, c_int, c_int, c_void_p, D, D, D, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
+    ]
+    L.tt_error_string.argtypes = [c_int]
+    L.tt_error_string.restype = ctypes.c_char_p
+    L.tt_launch_count.argtypes = []
+    L.tt_launch_count.restype = c_uint64
+    _lib = L
+    return L
+
+
+def error_string(code: int) -> str:
+    try:
+        return lib().tt_error_string(int(code)).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def launch_count() -> int:
+    return int(lib().tt_launch_count())
+
+
+def check(rc, where):
+    if rc != 0:
+        raise TTError(rc, where)
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float64:
+        return TT_F64
+    if t.dtype == torch.float32:
+        return TT_F32
+    if t.dtype == torch.bfloat16:
+        return TT_BF16
+    raise TypeError(f"unsupported core dtype {t.dtype}")
+
+
+class Desc:
+    """A tt_desc over a list of device tensors (kept alive by this object)."""
+
+    def __init__(self, cores, modes=None, ranks=None, dtype=None):
+        n = len(cores)
+        if n < 1 or n > TT_MAX_ORDER:
+            raise ValueError("TT order must be in [1, 64]")
+        self.tensors = list(cores)
+        if modes is None:
+            for c in cores:
+                if c.dim() != 3:
+                    raise ValueError("cores must be 3-D (R, I, R')")
+            modes = [int(c.shape[1]) for c in cores]
+            ranks = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
+        for c in cores:
+            if not c.is_cuda or not c.is_contiguous():
+                raise ValueError("cores must be contiguous CUDA tensors")
+        self.modes = list(modes)
+        self.ranks = list(ranks)
+        self.dtype = _dtype_code(cores[0]) if dtype is None else dtype
+        self._modes = (c_int32 * n)(*self.modes)
+        self._ranks = (c_int32 * (n + 1))(*self.ranks)
+        self._cores = (c_void_p * n)(*[c.data_ptr() for c in cores])
+        self.desc = TTDesc(n, self._modes, self._ranks, self._cores, self.dtype)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.desc)
+
+
+def _mask_arr(mask):
+    return (c_uint8 * len(mask))(*[1 if v else 0 for v in mask])
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def workspace_bytes(op, xd, yd, mask=None, layout="chain", prec="native"):
+    nb = c_size_t(0)
+    m = _mask_arr(mask) if mask is not None else None
+    check(
+        lib().tt_workspace_bytes(op, xd.ref, yd.ref, m, LAYOUT[layout], PREC[prec], ctypes.byref(nb)),
+        "tt_workspace_bytes",
+    )
+    return int(nb.value)
+
+
+def partial_shape(xd, yd, mask, layout="chain"):
+    n = xd.desc.order
+    order = c_int32(0)
+    modes = (c_int32 * (2 * n))()
+    ranks = (c_int32 * (2 * n + 1))()
+    perm = (c_int32 * (2 * n))()
+    check(
+        lib().tt_partial_shape(xd.ref, yd.ref, _mask_arr(mask), LAYOUT[layout], ctypes.byref(order), modes, ranks, perm),
+        "tt_partial_shape",
+    )
+    o = order.value
+    nfree = sum(1 for v in mask if not v)
+    return list(modes[:o]), list(ranks[: o + 1]), list(perm[: 2 * nfree])
+
+
+def status_tensor(device=None):
+    import torch
+
+    return torch.zeros(1, dtype=torch.int32, device=device or "cuda")
+
+
+class FullContraction:
+    """Pre-marshalled full contraction <X, Y> (re-usable, graph-capturable)."""
+
+    def __init__(self, x, y, prec="native", split=False):
+        import torch
+
+        self.xd, self.yd = Desc(x), Desc(y)
+        dev = x[0].device
+        self.out = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.log2 = torch.zeros(1, dtype=torch.int64, device=dev) if split else None
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.prec = PREC[prec]
+        nb = workspace_bytes(TT_OP_FULL, self.xd, self.yd, None, "chain", prec)
+        self.ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+        self.ws_bytes = nb
+
+    def __call__(self, stream=None):
+        rc = lib().tt_contract_full(
+            self.xd.ref,
+            self.yd.ref,
+            self.prec,
+            c_void_p(self.out.data_ptr()),
+            c_void_p(self.log2.data_ptr()) if self.log2 is not None else None,
+            c_void_p(self.status.data_ptr()),
+            c_void_p(self.ws.data_ptr()),
+            c_size_t(self.ws_bytes),
+            _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_full")
+        return self.out
+
+
+class PartialContraction:
+    """Pre-marshalled partial contraction; output cores allocated once."""
+
+    def __init__(self, x, y, mask, layout="chain", prec="native", split=False, out=None):
+        import torch
+
+        self.xd, self.yd = Desc(x), Desc(y)
+        self.mask = list(mask)
+        self._mask = _mask_arr(mask)
+        self.layout = LAYOUT[layout]
+        self.prec = PREC[prec]
+        dev = x[0].device
+        modes, ranks, perm = partial_shape(self.xd, self.yd, mask, layout)
+        self.perm = perm
+        if out is None:
+            out = [
+                torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=dev)
+                for t in range(len(modes))
+            ]
+        self.z = out
+        self.zd = Desc(out)
+        self.log2 = torch.zeros(1, dtype=torch.int64, device=dev) if split else None
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        nb = workspace_bytes(TT_OP_PARTIAL, self.xd, self.yd, mask, layout, prec)
+        self.ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+        self.ws_bytes = nb
+
+    def __call__(self, stream=None):
+        rc = lib().tt_contract_partial(
+            self.xd.ref,
+            self.yd.ref,
+            self._mask,
+            self.layout,
+            self.prec,
+            self.zd.ref,
+            c_void_p(self.log2.data_ptr()) if self.log2 is not None else None,
+            c_void_p(self.status.data_ptr()),
+            c_void_p(self.ws.data_ptr()),
+            c_size_t(self.ws_bytes),
+            _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_partial")
+        return self.z
+
+
+def contract_full(x, y, prec="native", split=False, stream=None):
+    """<X, Y> on the device.  Returns a float64 CUDA tensor of shape (1,), or
+    (mantissa, log2) tensors with split=True.  Raises on argument errors;
+    device status bits are returned by ``contract_full_status``."""
+    op = FullContraction(x, y, prec, split)
+    op(stream)
+    if split:
+        return op.out, op.log2
+    return op.out
+
+
+def contract_partial(x, y, mask, layout="chain", prec="native", split=False, stream=None):
+    """Partial contraction over S = {k: mask[k]}.  Returns (cores, perm) or
+    (cores, perm, log2) with split=True."""
+    op = PartialContraction(x, y, mask, layout, prec, split)
+    op(stream)
+    if split:
+        return op.z, op.perm, op.log2
+    return op.z, op.perm

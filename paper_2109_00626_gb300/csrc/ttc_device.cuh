@@ -1,0 +1,113 @@
+// Device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace ttc {
+
+// Load N consecutive elements (16-byte aligned when N * sizeof(T) >= 16).
+template <typename T, int N>
+__device__ __forceinline__ void ld_vec(T (&r)[N], const T* __restrict__ p) {
+  if constexpr (std::is_same<T, float>::value && N % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + j);
+      r[j] = v.x;
+      r[j + 1] = v.y;
+      r[j + 2] = v.z;
+      r[j + 3] = v.w;
+    }
+  } else if constexpr (std::is_same<T, float>::value && N % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p + j);
+      r[j] = v.x;
+      r[j + 1] = v.y;
+    }
+  } else if constexpr (std::is_same<T, double>::value && N % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < N; j += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(p + j);
+      r[j] = v.x;
+      r[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) r[j] = p[j];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, int bits) {
+  if (status != nullptr && bits != 0) atomicOr(status, bits);
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v) {
+  return isfinite(v);
+}
+
+// Exact multiplication by 2^e for |e| well inside the exponent range of T.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
+}
+template <typename T>
+__device__ __forceinline__ T pow2(int e);
+template <>
+__device__ __forceinline__ float pow2<float>(int e) {
+  return pow2f(e);
+}
+template <>
+__device__ __forceinline__ double pow2<double>(int e) {
+  return pow2d(e);
+}
+
+// x * 2^e, exact for |e| up to about twice the exponent range of T (two steps).
+template <typename T>
+__device__ __forceinline__ T mul_pow2(T x, int e) {
+  const int e1 = e / 2;
+  return x * pow2<T>(e1) * pow2<T>(e - e1);
+}
+
+// s * 2^e saturated to +-Inf / signed zero outside the range of T.
+template <typename T>
+__device__ __forceinline__ T scale_pow2_sat(T s, int64_t e) {
+  constexpr int64_t lim = sizeof(T) == 4 ? 250 : 2000;
+  if (s == T(0) || !isfinite(s)) return s;
+  if (e > lim) return s > T(0) ? T(INFINITY) : T(-INFINITY);
+  if (e < -lim) return s * T(0);
+  return mul_pow2<T>(s, static_cast<int>(e));
+}
+
+// Binary exponent e with 2^(e-1) <= |v| < 2^e (v finite, non-zero).
+__device__ __forceinline__ int exp2_of(double v) {
+  int e;
+  frexp(v, &e);
+  return e;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_or(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace ttc

@@ -1,0 +1,90 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/ttc.h"
+
+namespace ttc {
+
+constexpr int kMaxOrder = TT_MAX_ORDER;
+
+// Power-of-two renormalisation thresholds: an environment whose largest
+// magnitude leaves [2^-s, 2^s] is rescaled by an exact power of two.
+constexpr int kRenormBitsF32 = 32;
+constexpr int kRenormBitsF64 = 256;
+
+// One step of an environment sweep.  The generic step is
+//   E'[u][v] = sum_i sum_{p,q} A_i[p][u] E[p][q] B_i[q][v]
+// where, for a left-to-right sweep over core k (ranks R_k -> R_{k+1}),
+//   A_i[p][u] = Gx_k[p][i][u],  B_i[q][v] = Gy_k[q][i][v],
+// and for a right-to-left sweep (ranks R_{k+1} -> R_k)
+//   A_i[p][u] = Gx_k[u][i][p],  B_i[q][v] = Gy_k[v][i][q].
+struct SweepStep {
+  const void* gx;
+  const void* gy;
+  int I;
+  int rin_x, rout_x;  // p range, u range
+  int rin_y, rout_y;  // q range, v range
+};
+
+struct SweepParams {
+  int n_steps;
+  int transposed;         // 1 = right-to-left (slices read with swapped legs)
+  int final_scalar;       // 1 = the last step ends at a 1x1 environment summed in float64
+  int renorm_bits;
+  SweepStep step[kMaxOrder];
+  const void* e_in;       // optional start environment [rin_x(0)][rin_y(0)], row-major
+  const int64_t* e_in_log2;
+  void* e_out;            // optional final environment [rout_x][rout_y], row-major
+  int64_t* e_out_log2;    // scale of e_out (always written when e_out is set)
+  double* z_out;          // final scalar (final_scalar == 1)
+  int64_t* z_out_log2;    // optional; if NULL the scale is folded into *z_out
+  int32_t* status;
+};
+
+// Copy / leg-swap of free cores and the boundary core with K absorbed
+// (chain layout of a partial contraction).
+constexpr int kMaxCopies = 2 * kMaxOrder;
+struct CopyTask {
+  const void* src;
+  void* dst;
+  int r0, I, r1;  // source core shape
+  int swap;       // 1: dst[r1][I][r0] = src[r0][I][r1]
+};
+struct CopyParams {
+  int n_tasks;
+  CopyTask task[kMaxCopies];
+  int64_t block_start[kMaxCopies + 1];  // prefix sum of blocks per task
+};
+
+struct EmitCParams {
+  const void* gx;   // boundary core of X
+  int ra, I, rb;    // its shape [ra][I][rb]
+  int lead;         // 1: C[rb][I][ry] = sum_a gx[a][i][rb'] K[a][y]; 0: C[ra][I][ry] = sum_b gx[ra][i][b] K[b][y]
+  const void* k;    // K, row-major [(lead ? ra : rb)][ry]
+  const int64_t* k_log2;
+  int ry;
+  void* c_out;
+  int64_t* z_log2_out;  // optional; when NULL the scale of K is folded into C
+  int32_t* status;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
+cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
+cudaError_t launch_copy(const CopyParams& p, int elem_bytes, cudaStream_t s);
+cudaError_t launch_emit_c_f32(const EmitCParams& p, cudaStream_t s);
+cudaError_t launch_emit_c_f64(const EmitCParams& p, cudaStream_t s);
+cudaError_t launch_fill_identity(void* k, int64_t* k_log2, int elem_bytes, cudaStream_t s);
+
+// Largest cluster size (<= want) the sweep kernel for this rank tile can run with.
+int sweep_cluster_size(int rmax, int elem_bytes, int want);
+
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace ttc

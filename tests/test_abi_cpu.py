@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol include/ttc.h declares, and rejects bad arguments before it
+enqueues anything (fake device pointers are never dereferenced)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2109_00626_gb300 as T
+from paper_2109_00626_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2109_00626_gb300 import build
+
+    build.build()
+    return T.lib()
+
+
+def test_header_symbols_exported(L):
+    hdr = open(os.path.join(ROOT, "include", "ttc.h")).read()
+    declared = set(re.findall(r"\b(tt_[a-z0-9_]+)\s*\(", hdr))
+    declared -= {"tt_desc", "tt_batch"}
+    assert declared == set(B.EXPORTS), declared ^ set(B.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+class FakeDesc:
+    """tt_desc with non-NULL fake device pointers (host validation only)."""
+
+    def __init__(self, modes, ranks, dtype=B.TT_F32):
+        n = len(modes)
+        self._modes = (ctypes.c_int32 * n)(*modes)
+        self._ranks = (ctypes.c_int32 * (n + 1))(*ranks)
+        self._cores = (ctypes.c_void_p * n)(*[0x1000 * (k + 1) for k in range(n)])
+        self.desc = B.TTDesc(n, self._modes, self._ranks, self._cores, dtype)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.desc)
+
+
+def _mask(m):
+    return (ctypes.c_uint8 * len(m))(*m)
+
+
+def test_shape_errors(L):
+    x = FakeDesc([4, 4, 4], [1, 3, 3, 1])
+    y = FakeDesc([4, 5, 4], [1, 2, 2, 1])
+    out = ctypes.c_void_p(0x2000)
+    assert L.tt_contract_full(x.ref, y.ref, 0, out, None, None, None, 0, None) == -2
+    bad = FakeDesc([4, 4], [2, 3, 1])
+    assert L.tt_contract_full(bad.ref, bad.ref, 0, out, None, None, None, 0, None) == -2
+    z8 = FakeDesc([4, 4, 4], [1, 3, 3, 1], dtype=B.TT_F64)
+    assert L.tt_contract_full(x.ref, z8.ref, 0, out, None, None, None, 0, None) == -3
+    assert L.tt_contract_full(x.ref, x.ref, 0, None, None, None, None, 0, None) == -1
+
+
+def test_partial_shape_chain_and_merged(L):
+    x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
+    y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
+    modes, ranks, perm = B.partial_shape(x, y, [1, 1, 0, 0], "chain")
+    assert modes == [5, 4, 4, 5] and ranks == [1, 8, 10, 11, 1] and perm == [1, 0, 2, 3]
+    modes, ranks, perm = B.partial_shape(x, y, [0, 0, 1, 1], "chain")
+    assert modes == [2, 3, 3, 2] and ranks == [1, 6, 10, 9, 1] and perm == [0, 1, 3, 2]
+    modes, ranks, perm = B.partial_shape(x, y, [0, 1, 0, 1], "merged")
+    assert modes == [4, 16] and ranks == [1, 70, 1] and perm == [0, 2, 1, 3]
+    with pytest.raises(B.TTError) as e:
+        B.partial_shape(x, y, [0, 1, 1, 0], "chain")
+    assert e.value.code == -4
+    with pytest.raises(B.TTError) as e:
+        B.partial_shape(x, y, [1, 1, 1, 1], "chain")
+    assert e.value.code == -1
+
+
+def test_partial_validation(L):
+    x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
+    y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
+    zbad = FakeDesc([5, 4, 3, 5], [1, 8, 10, 11, 1])
+    nb = B.workspace_bytes(B.TT_OP_PARTIAL, x, y, [1, 1, 0, 0], "chain")
+    assert nb >= 7 * 10 * 4
+    # wrong output shape (the third core's mode is 4, not 3)
+    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, zbad.ref, None, None,
+                               ctypes.c_void_p(0x3000), nb, None)
+    assert rc == -2
+    # too small workspace is reported before any launch
+    modes, ranks, _ = B.partial_shape(x, y, [1, 1, 0, 0], "chain")
+    z = FakeDesc(modes, ranks)
+    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, z.ref, None, None,
+                               ctypes.c_void_p(0x3000), 8, None)
+    assert rc == -6
+
+
+def test_error_strings(L):
+    for code in range(0, -9, -1):
+        assert isinstance(T.error_string(code), str) and T.error_string(code)

@@ -1,0 +1,188 @@
+"""GPU parity of the full and chain-layout partial contractions against the
+float64 oracle, element by element, through the C ABI.
+
+Tolerances (normalised error eps = |z - z*| / (||X||_F ||Y||_F)):
+  float64 storage: 1e-12      float32 storage: 1e-5
+Partial results: every emitted core is compared; copied cores bit-exactly,
+the boundary core C entrywise with the Cauchy-Schwarz scale of K.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import cs_bound, norm_scale, to_dev, to_host
+from paper_2109_00626_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2109_00626_gb300 as T  # noqa: E402
+
+TOL = {np.float64: 1e-12, np.float32: 1e-5}
+TDT = {np.float64: torch.float64, np.float32: torch.float32}
+
+
+def _full(x, y, split=False):
+    op = T.FullContraction(to_dev(x), to_dev(y), split=split)
+    op()
+    torch.cuda.synchronize()
+    st = int(op.status.item())
+    if split:
+        return float(op.out.item()), int(op.log2.item()), st
+    return float(op.out.item()), st
+
+
+def _check_full(x, y, dt):
+    z, st = _full(x, y)
+    assert st == 0
+    want = O.contract_full(x, y)
+    eps = abs(z - want) / norm_scale(x, y)
+    assert eps <= TOL[dt], (z, want, eps)
+    return z, want
+
+
+def test_full_small_fp64():
+    x, y = G.small_fp64(0)
+    z, want = _check_full(x, y, np.float64)
+    # kappa is modest here, so the plain relative error holds as well
+    assert abs(z - want) <= 1e-12 * abs(want) * 1e3
+
+
+def test_full_order10_r64_fp32():
+    x, y = G.order10_r64(0)
+    _check_full(x, y, np.float32)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_full_ragged_fp32(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = [1, 2, 3, 5][seed]
+    modes = [int(v) for v in rng.choice([1, 2, 31, 7, 16], size=n)]
+    rx = [1] + [int(v) for v in rng.choice([1, 3, 17, 33, 127], size=n - 1)] + [1]
+    ry = [1] + [int(v) for v in rng.choice([1, 3, 17, 33, 127], size=n - 1)] + [1]
+    x = G.random_tt(rng, modes, rx, np.float32)
+    y = G.random_tt(rng, modes, ry, np.float32)
+    _check_full(x, y, np.float32)
+
+
+@pytest.mark.parametrize("r", [1, 3, 17, 33, 64])
+def test_full_ragged_fp64(r):
+    rng = np.random.default_rng(r)
+    modes = [3, 31, 2, 5]
+    rx = [1, r, max(1, r // 2), r, 1]
+    ry = [1, max(1, r - 1), r, 2, 1]
+    x = G.random_tt(rng, modes, rx, np.float64)
+    y = G.random_tt(rng, modes, ry, np.float64)
+    _check_full(x, y, np.float64)
+
+
+def test_full_rank1_closed_form_fp64():
+    rng = np.random.default_rng(9)
+    xs = [rng.standard_normal(16) for _ in range(12)]
+    ys = [rng.standard_normal(16) for _ in range(12)]
+    want = float(np.prod([np.dot(a, b) for a, b in zip(xs, ys)]))
+    z, st = _full(G.rank1_tt(xs), G.rank1_tt(ys))
+    assert st == 0 and abs(z - want) <= 1e-12 * abs(want)
+
+
+def test_full_renormalisation_split_scale():
+    """Cores scaled by 2^40 each: z = 2^(40*2N) <X0,Y0> leaves float32's range
+    long before the end; the split result (mantissa, log2) must still match."""
+    x, y = G.pair(21, [8] * 6, G.tt_ranks(6, 16), G.tt_ranks(6, 16), np.float32)
+    xs = [c * np.float32(2.0**40) for c in x]
+    ys = [c * np.float32(2.0**40) for c in y]
+    m, e, st = _full(xs, ys, split=True)
+    assert st == 0
+    want = O.contract_full(x, y)
+    got = np.ldexp(m, e - 2 * 6 * 40)
+    assert abs(got - want) / norm_scale(x, y) <= 1e-5
+    # unsplit: 2^480 * z fits in double
+    z, st = _full(xs, ys)
+    assert st == 0 and abs(np.ldexp(z, -480) - want) / norm_scale(x, y) <= 1e-5
+
+
+def test_full_overflow_status_without_split():
+    x, y = G.pair(22, [4] * 4, G.tt_ranks(4, 4), G.tt_ranks(4, 4), np.float64)
+    xs = [c * 2.0**300 for c in x]
+    ys = [c * 2.0**300 for c in y]
+    z, st = _full(xs, ys)
+    assert st & 2 and np.isinf(z)
+
+
+def test_full_nonfinite_status():
+    x, y = G.small_fp64(1)
+    x[1] = x[1].copy()
+    x[1][0, 0, 0] = np.nan
+    z, st = _full(x, y)
+    assert st & 1
+
+
+def _check_chain(x, y, mask, dt):
+    xd, yd = to_dev(x), to_dev(y)
+    op = T.PartialContraction(xd, yd, mask)
+    op()
+    torch.cuda.synchronize()
+    assert int(op.status.item()) == 0
+    got = to_host(op.z)
+    want, perm = O.partial_chain(x, y, mask)
+    assert perm == op.perm
+    assert [g.shape for g in got] == [w.shape for w in want]
+    side, s = O.end_block(mask)
+    m = len(x) - s
+    for p, (g, w) in enumerate(zip(got, want)):
+        if p == m - 1:
+            # C = boundary core joined with K: scale by |Gx| and the CS bound of K
+            kb = cs_bound(x, y, side, s) if s > 0 else np.ones((1, 1))
+            gxb = x[s] if side == "lead" else x[m - 1]
+            scale = np.abs(gxb).max() * kb.max() * np.sqrt(gxb.shape[0] if side == "lead" else gxb.shape[2])
+            assert np.abs(g - w).max() <= TOL[dt] * scale, (np.abs(g - w).max(), scale)
+        else:
+            np.testing.assert_array_equal(g, w)
+    return got, want
+
+
+def test_partial_small_fp64_dense():
+    x, y = G.small_fp64(0)
+    mask = [0, 0, 1, 1]
+    got, _ = _check_chain(x, y, mask, np.float64)
+    dense_want = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [2, 3])
+    _, perm = O.partial_chain(x, y, mask)
+    dense_got = O.chain_to_dense(got, perm)
+    assert np.abs(dense_got - dense_want).max() <= 1e-12 * norm_scale(x, y)
+
+
+def test_partial_order10_leading6_fp32():
+    x, y = G.order10_r64(0)
+    _check_chain(x, y, [1] * 6 + [0] * 4, np.float32)
+
+
+@pytest.mark.parametrize("mask", [[1, 0, 0, 0, 0], [0, 0, 0, 1, 1], [1, 1, 1, 1, 0], [0, 1, 1, 1, 1], [0, 0, 0, 0, 0]])
+def test_partial_ragged_fp64(mask):
+    rng = np.random.default_rng(sum(mask) + 7 * mask[0])
+    modes = [3, 2, 31, 2, 5]
+    x = G.random_tt(rng, modes, [1, 3, 17, 33, 2, 1], np.float64)
+    y = G.random_tt(rng, modes, [1, 5, 1, 9, 4, 1], np.float64)
+    got, _ = _check_chain(x, y, mask, np.float64)
+    dense_want = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [k for k in range(5) if mask[k]])
+    _, perm = O.partial_chain(x, y, mask)
+    assert np.abs(O.chain_to_dense(got, perm) - dense_want).max() <= 1e-12 * norm_scale(x, y)
+
+
+def test_partial_split_scale_fp32():
+    x, y = G.pair(31, [4] * 6, G.tt_ranks(6, 8), G.tt_ranks(6, 8), np.float32)
+    xs = [c * np.float32(2.0**30) for c in x]
+    ys = [c * np.float32(2.0**30) for c in y]
+    mask = [1, 1, 1, 1, 0, 0]
+    op = T.PartialContraction(to_dev(xs), to_dev(ys), mask, split=True)
+    op()
+    torch.cuda.synchronize()
+    assert int(op.status.item()) == 0
+    e = int(op.log2.item())
+    got = to_host(op.z)
+    want, perm = O.partial_chain(x, y, mask)
+    # undo: C carries 2^e and the input scaling of 4 X cores (K) and 1 X core (C) and 4 Y cores (K)
+    c = got[1] * 2.0 ** (e - 30 * 9)
+    assert np.abs(c - want[1]).max() <= 1e-5 * np.abs(want[1]).max() * 10
