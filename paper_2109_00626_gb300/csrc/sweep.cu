@@ -27,6 +27,8 @@ namespace cg = cooperative_groups;
 
 namespace ttc {
 
+constexpr int kNoExp = -(1 << 30);  // exponent marker of an all-zero environment
+
 template <typename T, int RM>
 struct SweepCfg {
   static constexpr int NT = 256;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_cons
       if (crank == 0 && tid == 0) {
         double z = 0.0;
         for (int r = 0; r < C; ++r) z += *cluster.map_shared_rank(red + 32, r);
-        int st_bits = isfinite(z) ? 0 : TT_STATUS_NONFINITE;
+        int st_bits = (isfinite(z) && !bad) ? 0 : TT_STATUS_NONFINITE;
         if (p.z_out_log2 != nullptr) {
           *p.z_out = z;
           *p.z_out_log2 = log2s;
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_cons
     const int nu = st.rout_x, nv = st.rout_y;
     const int chunk = (nu + C - 1) / C;
     const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
-    float lmax = 0.f;
+    int lexp = kNoExp;  // largest binary exponent among the entries this CTA reduced
     int lbad = 0;
     for (int idx = tid; idx < (ue - ub) * nv; idx += NT) {
       const int u = ub + idx / nv, v = idx % nv;
@@ -229,43 +231,40 @@ __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_cons
       for (int r = 0; r < C; ++r) s += *cluster.map_shared_rank(Ts + u * LD + v, r);
       for (int r = 0; r < C; ++r) *cluster.map_shared_rank(Es + v * LD + u, r) = s;
       if (!isfinite(s)) lbad = 1;
-      lmax = fmaxf(lmax, static_cast<float>(fabs(s)));
+      else if (s != T(0)) lexp = max(lexp, exp2_of(static_cast<double>(s)));
     }
-    lmax = warp_max(lmax);
-    lbad = warp_or(lbad);
-    float* fred = reinterpret_cast<float*>(red);
+    lexp = __reduce_max_sync(0xffffffffu, lexp);
+    lbad = __reduce_or_sync(0xffffffffu, lbad);
+    int* ired = reinterpret_cast<int*>(red);
     if (lane == 0) {
-      fred[warp] = lmax;
-      fred[16 + warp] = lbad ? 1.f : 0.f;
+      ired[warp] = lexp;
+      ired[16 + warp] = lbad;
     }
     __syncthreads();
     if (tid == 0) {
-      float m = 0.f, bb = 0.f;
+      int m = kNoExp, bb = 0;
       for (int w = 0; w < NT / 32; ++w) {
-        m = fmaxf(m, fred[w]);
-        bb = fmaxf(bb, fred[16 + w]);
+        m = max(m, ired[w]);
+        bb |= ired[16 + w];
       }
       for (int r = 0; r < C; ++r) {
-        *cluster.map_shared_rank(fred + 32 + crank, r) = m;
-        *cluster.map_shared_rank(fred + 64 + crank, r) = bb;
+        *cluster.map_shared_rank(ired + 32 + crank, r) = m;
+        *cluster.map_shared_rank(ired + 64 + crank, r) = bb;
       }
     }
     cluster.sync();
-    float gmax = 0.f, gbad = 0.f;
+    int gexp = kNoExp, gbad = 0;
     for (int r = 0; r < C; ++r) {
-      gmax = fmaxf(gmax, fred[32 + r]);
-      gbad = fmaxf(gbad, fred[64 + r]);
+      gexp = max(gexp, ired[32 + r]);
+      gbad |= ired[64 + r];
     }
-    if (gbad != 0.f) bad = 1;
-    if (gmax > 0.f && isfinite(gmax)) {
-      const int e = exp2_of(static_cast<double>(gmax));
-      if (e > p.renorm_bits || e < -p.renorm_bits) {
-        for (int idx = tid; idx < nu * nv; idx += NT) {
-          const int u = idx / nv, v = idx % nv;
-          Es[v * LD + u] = mul_pow2<T>(Es[v * LD + u], -e);
-        }
-        log2s += e;
+    if (gbad) bad = 1;
+    if (gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits)) {
+      for (int idx = tid; idx < nu * nv; idx += NT) {
+        const int u = idx / nv, v = idx % nv;
+        Es[v * LD + u] = mul_pow2<T>(Es[v * LD + u], -gexp);
       }
+      log2s += gexp;
     }
     __syncthreads();
   }
