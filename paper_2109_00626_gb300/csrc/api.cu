@@ -112,15 +112,17 @@ static void fill_right(SweepParams& p, const tt_desc* x, const tt_desc* y, int k
 }
 
 static int sweep_max_rank(const SweepParams& p) {
-  int r = 1;
+  int r = std::max(p.rx0, p.ry0);
   for (int j = 0; j < p.n_steps; ++j)
     r = std::max({r, p.step[j].rin_x, p.step[j].rout_x, p.step[j].rin_y, p.step[j].rout_y});
+  if (p.emit.enabled) r = std::max({r, p.emit.ra, p.emit.rb, p.emit.ry});
   return r;
 }
 
 static int sweep_max_mode(const SweepParams& p) {
   int m = 1;
   for (int j = 0; j < p.n_steps; ++j) m = std::max(m, p.step[j].I);
+  if (p.emit.enabled) m = std::max(m, p.emit.I);
   return m;
 }
 
@@ -237,7 +239,7 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
     ChainPlan cp;
     rc = chain_plan(x, y, mask, &cp);
     if (rc != TT_OK) return rc;
-    *bytes = align256(static_cast<size_t>(cp.kx) * cp.ky * elem_bytes(x->dtype)) + 256;
+    *bytes = 0;  // the environment K stays in shared memory
     return TT_OK;
   }
   (void)prec;
@@ -321,87 +323,67 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
   if (z->order != cp.order || z->dtype != x->dtype) return TT_ERR_SHAPE;
   for (int p = 0; p < cp.order; ++p)
     if (z->modes[p] != cp.modes[p] || z->ranks[p] != cp.ranks[p]) return TT_ERR_SHAPE;
-  const int eb = elem_bytes(x->dtype);
-  const size_t kbytes = align256(static_cast<size_t>(cp.kx) * cp.ky * eb);
-  if (ws == nullptr || ws_bytes < kbytes + 256) return TT_ERR_WS;
-  if (std::max(max_rank(x), max_rank(y)) > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
+  (void)ws;
+  (void)ws_bytes;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  void* kbuf = ws;
-  int64_t* klog2 = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + kbytes);
   const int n = cp.n, m = cp.m, sS = cp.s;
 
-  // 1. K = environment over the contracted block
-  if (sS == 0) {
-    if (launch_fill_identity(kbuf, klog2, eb, s) != cudaSuccess) return TT_ERR_CUDA;
-  } else {
-    SweepParams p;
-    memset(&p, 0, sizeof(p));
+  SweepParams p;
+  memset(&p, 0, sizeof(p));
+  // 1. K = environment over the contracted block (empty block: K = [1])
+  if (sS > 0) {
     if (cp.side == 0) fill_left(p, x, y, 0, sS);
     else fill_right(p, x, y, m, n);
-    p.final_scalar = 0;
-    p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
-    p.e_out = kbuf;
-    p.e_out_log2 = klog2;
-    p.status = status_dev;
-    rc = launch_sweep(p, x->dtype, s);
-    if (rc != TT_OK) return rc;
   }
+  p.rx0 = 1;
+  p.ry0 = 1;
+  p.final_scalar = 0;
+  p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+  p.status = status_dev;
 
-  // 2. boundary core C
-  EmitCParams ep;
-  memset(&ep, 0, sizeof(ep));
+  // 2. boundary core C, fused behind the sweep
+  EmitParams& ep = p.emit;
+  ep.enabled = 1;
   const int kb = cp.side == 0 ? sS : m - 1;
   ep.gx = x->cores[kb];
   ep.ra = x->ranks[kb];
   ep.I = x->modes[kb];
   ep.rb = x->ranks[kb + 1];
   ep.lead = cp.side == 0 ? 1 : 0;
-  ep.k = kbuf;
-  ep.k_log2 = klog2;
   ep.ry = cp.ky;
   ep.c_out = z->cores[m - 1];
   ep.z_log2_out = z_log2_dev;
-  ep.status = status_dev;
-  cudaError_t err = x->dtype == TT_F64 ? launch_emit_c_f64(ep, s) : launch_emit_c_f32(ep, s);
-  if (err != cudaSuccess) return TT_ERR_CUDA;
 
   // 3. free cores
-  CopyParams c;
-  memset(&c, 0, sizeof(c));
-  auto add = [&](const void* src, void* dst, int r0, int I, int r1, int swap) {
-    if (!swap && src == dst) return;
-    CopyTask& t = c.task[c.n_tasks];
+  auto add = [&](const void* src, void* dst, int r0, int I, int r1, int swap) -> int {
+    if (!swap && src == dst) return TT_OK;
+    if (swap && src == dst) return TT_ERR_ARG;
+    CopyTask& t = ep.copy[ep.n_copies++];
     t.src = src;
     t.dst = dst;
     t.r0 = r0;
     t.I = I;
     t.r1 = r1;
     t.swap = swap;
-    const int64_t elems = static_cast<int64_t>(r0) * I * r1;
-    c.block_start[c.n_tasks + 1] = c.block_start[c.n_tasks] + (elems + 4095) / 4096;
-    c.n_tasks++;
+    return TT_OK;
   };
   if (cp.side == 0) {
-    for (int p = 0; p < m - 1; ++p) {
-      const int k = n - 1 - p;
-      add(x->cores[k], z->cores[p], x->ranks[k], x->modes[k], x->ranks[k + 1], 1);
+    for (int q = 0; q < m - 1; ++q) {
+      const int k = n - 1 - q;
+      if (add(x->cores[k], z->cores[q], x->ranks[k], x->modes[k], x->ranks[k + 1], 1) != TT_OK) return TT_ERR_ARG;
     }
     for (int q = 0; q < m; ++q) {
       const int k = sS + q;
       add(y->cores[k], z->cores[m + q], y->ranks[k], y->modes[k], y->ranks[k + 1], 0);
     }
   } else {
-    for (int p = 0; p < m - 1; ++p) add(x->cores[p], z->cores[p], x->ranks[p], x->modes[p], x->ranks[p + 1], 0);
+    for (int q = 0; q < m - 1; ++q) add(x->cores[q], z->cores[q], x->ranks[q], x->modes[q], x->ranks[q + 1], 0);
     for (int q = 0; q < m; ++q) {
       const int k = m - 1 - q;
-      add(y->cores[k], z->cores[m + q], y->ranks[k], y->modes[k], y->ranks[k + 1], 1);
+      if (add(y->cores[k], z->cores[m + q], y->ranks[k], y->modes[k], y->ranks[k + 1], 1) != TT_OK) return TT_ERR_ARG;
     }
   }
-  if (c.n_tasks > 0) {
-    err = launch_copy(c, eb, s);
-    if (err != cudaSuccess) return TT_ERR_CUDA;
-  }
-  return TT_OK;
+  return launch_sweep(p, x->dtype, s);
 }
 
 int tt_batch_plan(const tt_batch* batch, tt_plan** plan, size_t* packed_bytes, size_t* ws_bytes) {

@@ -31,55 +31,51 @@ struct SweepStep {
   int rin_y, rout_y;  // q range, v range
 };
 
+// Copy / leg-swap of one free core into the chain-layout output.
+struct CopyTask {
+  const void* src;
+  void* dst;
+  int r0, I, r1;  // source core shape [r0][I][r1]
+  int swap;       // 1: dst[r1][I][r0] = src[r0][I][r1]
+};
+constexpr int kMaxCopies = 2 * kMaxOrder;
+
+// Boundary core of a chain-layout partial contraction, C = (core of X) joined
+// with the environment K of the contracted block.
+//   lead : C[u][i][y] = sum_a gx[a][i][u] K[a][y]   (gx is [ra][I][rb], u < rb)
+//   trail: C[u][i][y] = sum_b gx[u][i][b] K[b][y]   (gx is [ra][I][rb], u < ra)
+struct EmitParams {
+  int enabled;
+  const void* gx;
+  int ra, I, rb;
+  int lead;
+  int ry;               // columns of K
+  void* c_out;
+  int64_t* z_log2_out;  // optional: scale of K stored here instead of folded into C
+  int n_copies;
+  CopyTask copy[kMaxCopies];
+};
+
 struct SweepParams {
-  int n_steps;
+  int n_steps;            // contracted modes in the sweep (may be 0 for an emission only)
   int transposed;         // 1 = right-to-left (slices read with swapped legs)
   int final_scalar;       // 1 = the last step ends at a 1x1 environment summed in float64
   int renorm_bits;
   SweepStep step[kMaxOrder];
-  const void* e_in;       // optional start environment [rin_x(0)][rin_y(0)], row-major
+  const void* e_in;       // optional start environment [rx0][ry0], row-major
   const int64_t* e_in_log2;
-  void* e_out;            // optional final environment [rout_x][rout_y], row-major
-  int64_t* e_out_log2;    // scale of e_out (always written when e_out is set)
+  int rx0, ry0;           // shape of the start environment (1x1 when e_in is NULL)
+  void* e_out;            // optional final environment [rx][ry], row-major
+  int64_t* e_out_log2;    // scale of e_out (written when e_out is set)
   double* z_out;          // final scalar (final_scalar == 1)
   int64_t* z_out_log2;    // optional; if NULL the scale is folded into *z_out
   int32_t* status;
-};
-
-// Copy / leg-swap of free cores and the boundary core with K absorbed
-// (chain layout of a partial contraction).
-constexpr int kMaxCopies = 2 * kMaxOrder;
-struct CopyTask {
-  const void* src;
-  void* dst;
-  int r0, I, r1;  // source core shape
-  int swap;       // 1: dst[r1][I][r0] = src[r0][I][r1]
-};
-struct CopyParams {
-  int n_tasks;
-  CopyTask task[kMaxCopies];
-  int64_t block_start[kMaxCopies + 1];  // prefix sum of blocks per task
-};
-
-struct EmitCParams {
-  const void* gx;   // boundary core of X
-  int ra, I, rb;    // its shape [ra][I][rb]
-  int lead;         // 1: C[rb][I][ry] = sum_a gx[a][i][rb'] K[a][y]; 0: C[ra][I][ry] = sum_b gx[ra][i][b] K[b][y]
-  const void* k;    // K, row-major [(lead ? ra : rb)][ry]
-  const int64_t* k_log2;
-  int ry;
-  void* c_out;
-  int64_t* z_log2_out;  // optional; when NULL the scale of K is folded into C
-  int32_t* status;
+  EmitParams emit;        // fused chain emission after the sweep (partial contractions)
 };
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
-cudaError_t launch_copy(const CopyParams& p, int elem_bytes, cudaStream_t s);
-cudaError_t launch_emit_c_f32(const EmitCParams& p, cudaStream_t s);
-cudaError_t launch_emit_c_f64(const EmitCParams& p, cudaStream_t s);
-cudaError_t launch_fill_identity(void* k, int64_t* k_log2, int elem_bytes, cudaStream_t s);
 
 // Largest cluster size (<= want) the sweep kernel for this rank tile can run with.
 int sweep_cluster_size(int rmax, int elem_bytes, int want);

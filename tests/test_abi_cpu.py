@@ -82,18 +82,20 @@ def test_partial_validation(L):
     x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
     y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
     zbad = FakeDesc([5, 4, 3, 5], [1, 8, 10, 11, 1])
-    nb = B.workspace_bytes(B.TT_OP_PARTIAL, x, y, [1, 1, 0, 0], "chain")
-    assert nb >= 7 * 10 * 4
+    # the environment stays on chip: a partial contraction needs no workspace
+    assert B.workspace_bytes(B.TT_OP_PARTIAL, x, y, [1, 1, 0, 0], "chain") == 0
     # wrong output shape (the third core's mode is 4, not 3)
-    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, zbad.ref, None, None,
-                               ctypes.c_void_p(0x3000), nb, None)
+    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, zbad.ref, None, None, None, 0, None)
     assert rc == -2
-    # too small workspace is reported before any launch
+    # interior contracted block with the chain layout
     modes, ranks, _ = B.partial_shape(x, y, [1, 1, 0, 0], "chain")
     z = FakeDesc(modes, ranks)
-    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, z.ref, None, None,
-                               ctypes.c_void_p(0x3000), 8, None)
-    assert rc == -6
+    rc = L.tt_contract_partial(x.ref, y.ref, _mask([0, 1, 1, 0]), 0, 0, z.ref, None, None, None, 0, None)
+    assert rc == -4
+    # output dtype differs from the operands
+    z64 = FakeDesc(modes, ranks, dtype=B.TT_F64)
+    rc = L.tt_contract_partial(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, 0, z64.ref, None, None, None, 0, None)
+    assert rc == -2
 
 
 def test_error_strings(L):
