@@ -203,6 +203,16 @@ int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile
 
 void tt_plan_free(tt_plan* plan);
 
+/* Tile autotuner for the batched launch.  For every (rank bucket <= 32, <= 64,
+ * <= 128) x (mode-size bucket <= 8, <= 16, <= 32, > 32) it times each rank
+ * tile that fits on a synthetic batch of order-6 pairs filling the GPU, and
+ * writes the fastest as text lines "dtype rank_bucket mode_bucket tile" to
+ * `cache_path`.  tt_batch_plan reads the file named by the environment
+ * variable TTC_AUTOTUNE_CACHE (without it, the smallest tile that fits is
+ * used).  Synchronous; unlike every other call it allocates (and frees)
+ * device memory and must not be called during stream capture. */
+int tt_autotune(int dtype, const char* cache_path);
+
 /* ---------------------------------------------------------------------------
  * Adjoint.
  * ------------------------------------------------------------------------- */

@@ -9,6 +9,8 @@ kernels under ``csrc/``); this package only marshals arguments.
 """
 from ._binding import (  # noqa: F401
     EXPORTS,
+    BatchedContraction,
+    autotune,
     LAYOUT,
     PREC,
     Desc,

@@ -34,6 +34,7 @@ EXPORTS = [
     "tt_contract_batched",
     "tt_plan_info",
     "tt_plan_free",
+    "tt_autotune",
     "tt_contract_backward",
     "tt_error_string",
     "tt_launch_count",
@@ -96,6 +97,7 @@ def lib():
     L.tt_contract_backward.argtypes = [
         D, D, U8, c_int, c_int, c_void_p, D, D, D, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
     ]
+    L.tt_autotune.argtypes = [c_int, ctypes.c_char_p]
     L.tt_error_string.argtypes = [c_int]
     L.tt_error_string.restype = ctypes.c_char_p
     L.tt_launch_count.argtypes = []
@@ -300,3 +302,116 @@ def contract_partial(x, y, mask, layout="chain", prec="native", split=False, str
     if split:
         return op.z, op.perm, op.log2
     return op.z, op.perm
+
+
+class BatchedContraction:
+    """Many independent contractions in one persistent launch.
+
+    ``pairs`` is a list of (x_cores, y_cores, mask) with mask None for a full
+    contraction or a 0/1 list selecting an end block (chain layout).  Output
+    cores of partial pairs are allocated here (``self.z[p]``); ``self.out``
+    holds the value of every full pair.  The plan (tile per pair, LPT order) is
+    built once; ``__call__`` only enqueues a memset and one kernel, so it can
+    be captured with :meth:`graph`.
+    """
+
+    def __init__(self, pairs, prec="native", split=False):
+        import torch
+
+        n = len(pairs)
+        if n < 1:
+            raise ValueError("empty batch")
+        dev = pairs[0][0][0].device
+        self.xd = [Desc(p[0]) for p in pairs]
+        self.yd = [Desc(p[1]) for p in pairs]
+        self.masks = [None if p[2] is None else list(p[2]) for p in pairs]
+        self.z = []
+        self.zd = []
+        self.perm = []
+        for i, (x, y, mask) in enumerate(pairs):
+            if mask is None:
+                self.z.append(None)
+                self.zd.append(None)
+                self.perm.append(None)
+                continue
+            modes, ranks, perm = partial_shape(self.xd[i], self.yd[i], mask, "chain")
+            z = [torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=dev) for t in range(len(modes))]
+            self.z.append(z)
+            self.zd.append(Desc(z))
+            self.perm.append(perm)
+        self._xarr = (TTDesc * n)(*[d.desc for d in self.xd])
+        self._yarr = (TTDesc * n)(*[d.desc for d in self.yd])
+        dummy = self.xd[0].desc
+        self._zarr = (TTDesc * n)(*[(d.desc if d is not None else dummy) for d in self.zd])
+        self._mask_bufs = [(_mask_arr(m) if m is not None else None) for m in self.masks]
+        mp = (POINTER(c_uint8) * n)(
+            *[(ctypes.cast(b, POINTER(c_uint8)) if b is not None else POINTER(c_uint8)()) for b in self._mask_bufs]
+        )
+        self._mp = mp
+        batch = TTBatch(n, self._xarr, self._yarr, mp, self._zarr, PREC[prec])
+        plan = c_void_p()
+        pb = c_size_t(0)
+        wb = c_size_t(0)
+        check(lib().tt_batch_plan(ctypes.byref(batch), ctypes.byref(plan), ctypes.byref(pb), ctypes.byref(wb)), "tt_batch_plan")
+        self.plan = plan
+        host = torch.empty(pb.value, dtype=torch.uint8).pin_memory()
+        check(lib().tt_batch_pack(plan, c_void_p(host.data_ptr()), pb), "tt_batch_pack")
+        self.packed = host.to(dev)
+        self.ws = torch.zeros(max(wb.value, 256), dtype=torch.uint8, device=dev)
+        self.ws_bytes = self.ws.numel()
+        self.n = n
+        self.out = torch.zeros(n, dtype=torch.float64, device=dev)
+        self.log2 = torch.zeros(n, dtype=torch.int64, device=dev) if split else None
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def tiles(self):
+        t = c_int32(0)
+        out = []
+        for p in range(self.n):
+            check(lib().tt_plan_info(self.plan, p, None, ctypes.byref(t)), "tt_plan_info")
+            out.append(int(t.value))
+        return out
+
+    def __call__(self, stream=None):
+        rc = lib().tt_contract_batched(
+            self.plan,
+            c_void_p(self.packed.data_ptr()),
+            c_void_p(self.out.data_ptr()),
+            c_void_p(self.log2.data_ptr()) if self.log2 is not None else None,
+            c_void_p(self.status.data_ptr()),
+            c_void_p(self.ws.data_ptr()),
+            c_size_t(self.ws_bytes),
+            _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_batched")
+        return self.out
+
+    def graph(self):
+        """Capture one launch in a CUDA graph; returns the torch CUDAGraph."""
+        import torch
+
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self()  # warm-up outside capture (sets kernel attributes)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self()
+        return g
+
+    def __del__(self):
+        try:
+            if getattr(self, "plan", None) is not None and self.plan.value:
+                lib().tt_plan_free(self.plan)
+                self.plan = None
+        except Exception:
+            pass
+
+
+def autotune(dtype="f32", cache_path=None):
+    """Run the batched-tile autotuner and write its cache file (see tt_autotune)."""
+    code = {"f32": TT_F32, "f64": TT_F64}[dtype]
+    path = cache_path or os.path.join(_HERE, f"autotune_{dtype}.txt")
+    check(lib().tt_autotune(code, path.encode()), "tt_autotune")
+    return path

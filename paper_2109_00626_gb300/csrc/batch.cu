@@ -1,0 +1,262 @@
+// Host side of the batched contraction: plan (validation, LPT order, tile
+// choice), packing of the device table, launch, and the tile autotuner.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "host_plan.h"
+
+struct tt_plan {
+  int n_pairs = 0;
+  int dtype = TT_F32;
+  std::vector<ttc::SweepParams> table;
+  std::vector<int32_t> order;
+  std::vector<int32_t> tile;
+  std::vector<double> cost;
+  size_t off_order = 0, off_tile = 0, packed_bytes = 0;
+};
+
+namespace ttc {
+
+// Autotuned tile per (dtype, rank bucket, mode bucket); -1 = not tuned.
+struct TuneTable {
+  int tile[2][3][4];
+  bool loaded = false;
+};
+
+static int rank_bucket(int r) { return r <= 32 ? 0 : (r <= 64 ? 1 : 2); }
+static int mode_bucket(int I) { return I <= 8 ? 0 : (I <= 16 ? 1 : (I <= 32 ? 2 : 3)); }
+
+static TuneTable& tune_table() {
+  static TuneTable t;
+  if (!t.loaded) {
+    for (auto& a : t.tile)
+      for (auto& b : a)
+        for (int& c : b) c = -1;
+    const char* path = getenv("TTC_AUTOTUNE_CACHE");
+    if (path != nullptr) {
+      FILE* f = fopen(path, "r");
+      if (f != nullptr) {
+        int d, rb, ib, tl;
+        while (fscanf(f, "%d %d %d %d", &d, &rb, &ib, &tl) == 4)
+          if (d >= 0 && d < 2 && rb >= 0 && rb < 3 && ib >= 0 && ib < 4 && tl >= 0 && tl < 3) t.tile[d][rb][ib] = tl;
+        fclose(f);
+      }
+    }
+    t.loaded = true;
+  }
+  return t;
+}
+
+static int choose_tile(const SweepParams& p, int dtype) {
+  const int rmax = sweep_max_rank(p);
+  const int need = rank_bucket(rmax);
+  const int d = dtype == TT_F64 ? 1 : 0;
+  const int tuned = tune_table().tile[d][need][mode_bucket(sweep_max_mode(p))];
+  const int maxt = dtype == TT_F64 ? 1 : 2;
+  return std::min(maxt, std::max(need, tuned));
+}
+
+}  // namespace ttc
+
+using namespace ttc;
+
+extern "C" {
+
+int tt_batch_plan(const tt_batch* b, tt_plan** plan_out, size_t* packed_bytes, size_t* ws_bytes) {
+  if (b == nullptr || plan_out == nullptr || packed_bytes == nullptr || ws_bytes == nullptr) return TT_ERR_ARG;
+  if (b->n_pairs < 1 || b->x == nullptr || b->y == nullptr) return TT_ERR_ARG;
+  if (b->prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+  const int n = b->n_pairs;
+  tt_plan* plan = new tt_plan();
+  plan->n_pairs = n;
+  plan->dtype = b->x[0].dtype;
+  plan->table.resize(n);
+  plan->tile.resize(n);
+  plan->cost.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const tt_desc* x = &b->x[i];
+    const tt_desc* y = &b->y[i];
+    const uint8_t* mask = b->mask != nullptr ? b->mask[i] : nullptr;
+    int rc = check_pair(x, y, mask);
+    if (rc == TT_OK && x->dtype != plan->dtype) rc = TT_ERR_DTYPE;
+    if (rc == TT_OK && x->dtype == TT_BF16) rc = TT_ERR_UNSUPPORTED;
+    if (rc == TT_OK) {
+      if (mask == nullptr) {
+        build_full(x, y, nullptr, nullptr, nullptr, &plan->table[i]);
+      } else {
+        ChainPlan cp;
+        rc = chain_plan(x, y, mask, &cp);
+        if (rc == TT_OK && b->z == nullptr) rc = TT_ERR_ARG;
+        if (rc == TT_OK) rc = check_chain_output(x, cp, &b->z[i]);
+        if (rc == TT_OK) rc = build_partial(x, y, cp, &b->z[i], nullptr, nullptr, &plan->table[i]);
+      }
+    }
+    if (rc == TT_OK && sweep_max_rank(plan->table[i]) > rank_cap(plan->dtype)) rc = TT_ERR_TOO_LARGE;
+    if (rc != TT_OK) {
+      delete plan;
+      return rc;
+    }
+    plan->tile[i] = choose_tile(plan->table[i], plan->dtype);
+    plan->cost[i] = sweep_flops(plan->table[i]);
+  }
+  // longest processing time first
+  plan->order.resize(n);
+  std::iota(plan->order.begin(), plan->order.end(), 0);
+  std::stable_sort(plan->order.begin(), plan->order.end(),
+                   [&](int a, int c) { return plan->cost[a] > plan->cost[c]; });
+  plan->off_order = align256(sizeof(SweepParams) * n);
+  plan->off_tile = plan->off_order + align256(sizeof(int32_t) * n);
+  plan->packed_bytes = plan->off_tile + align256(sizeof(int32_t) * n);
+  *packed_bytes = plan->packed_bytes;
+  *ws_bytes = 256;  // work-queue counter
+  *plan_out = plan;
+  return TT_OK;
+}
+
+int tt_batch_pack(const tt_plan* plan, void* packed_host, size_t packed_bytes) {
+  if (plan == nullptr || packed_host == nullptr || packed_bytes < plan->packed_bytes) return TT_ERR_ARG;
+  char* base = static_cast<char*>(packed_host);
+  memset(base, 0, plan->packed_bytes);
+  memcpy(base, plan->table.data(), sizeof(SweepParams) * plan->n_pairs);
+  memcpy(base + plan->off_order, plan->order.data(), sizeof(int32_t) * plan->n_pairs);
+  memcpy(base + plan->off_tile, plan->tile.data(), sizeof(int32_t) * plan->n_pairs);
+  return TT_OK;
+}
+
+int tt_contract_batched(const tt_plan* plan, const void* packed_dev, double* out_dev, int64_t* out_log2_dev,
+                        int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+  if (plan == nullptr || packed_dev == nullptr || out_dev == nullptr) return TT_ERR_ARG;
+  if (ws == nullptr || ws_bytes < 256) return TT_ERR_WS;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const char* base = static_cast<const char*>(packed_dev);
+  if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(out_dev, 0, sizeof(double) * plan->n_pairs, s) != cudaSuccess) return TT_ERR_CUDA;
+  const cudaError_t err =
+      launch_batched(base, reinterpret_cast<const int32_t*>(base + plan->off_order),
+                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs, static_cast<int*>(ws),
+                     out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
+  return err == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile_config) {
+  if (plan == nullptr) return TT_ERR_ARG;
+  if (n_pairs != nullptr) *n_pairs = plan->n_pairs;
+  if (p < 0 || p >= plan->n_pairs) return TT_ERR_ARG;
+  if (tile_config != nullptr) *tile_config = plan->tile[p];
+  return TT_OK;
+}
+
+void tt_plan_free(tt_plan* plan) { delete plan; }
+
+int tt_autotune(int dtype, const char* cache_path) {
+  if (cache_path == nullptr) return TT_ERR_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_DTYPE;
+  const int d = dtype == TT_F64 ? 1 : 0;
+  const int eb = dtype == TT_F64 ? 8 : 4;
+  const int ntiles = dtype == TT_F64 ? 2 : 3;
+  const int rank_of[3] = {32, 64, 128};
+  const int mode_of[4] = {8, 16, 32, 48};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int order = 6;
+  const int npairs = 2 * sms;
+  FILE* f = fopen(cache_path, "w");
+  if (f == nullptr) return TT_ERR_ARG;
+  int rc = TT_OK;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void* cores = nullptr;
+  void* dev_table = nullptr;
+  int* counter = nullptr;
+  double* out = nullptr;
+  if (cudaStreamCreate(&s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    fclose(f);
+    return TT_ERR_CUDA;
+  }
+  for (int rb = 0; rb < 3 && rc == TT_OK; ++rb) {
+    if (rb >= ntiles) break;
+    for (int ib = 0; ib < 4 && rc == TT_OK; ++ib) {
+      const int R = dtype == TT_F64 ? std::min(rank_of[rb], 64) : rank_of[rb];
+      const int I = mode_of[ib];
+      // one synthetic pair (zeros: the timing does not depend on values)
+      const size_t core_elems = static_cast<size_t>(R) * I * R;
+      const size_t bytes = core_elems * eb * order;
+      if (cudaMalloc(&cores, bytes) != cudaSuccess || cudaMemset(cores, 0, bytes) != cudaSuccess) {
+        rc = TT_ERR_CUDA;
+        break;
+      }
+      int32_t modes[order], ranks[order + 1];
+      void* ptrs[order];
+      for (int k = 0; k < order; ++k) {
+        modes[k] = I;
+        ranks[k] = k == 0 ? 1 : R;
+        ptrs[k] = static_cast<char*>(cores) + k * core_elems * eb;
+      }
+      ranks[order] = 1;
+      tt_desc x{order, modes, ranks, ptrs, dtype};
+      SweepParams p;
+      build_full(&x, &x, nullptr, nullptr, nullptr, &p);
+      std::vector<SweepParams> tab(npairs, p);
+      std::vector<int32_t> ord(npairs), tl(npairs);
+      std::iota(ord.begin(), ord.end(), 0);
+      if (cudaMalloc(&dev_table, sizeof(SweepParams) * npairs + 8 * npairs + 256) != cudaSuccess ||
+          cudaMalloc(&counter, 256) != cudaSuccess || cudaMalloc(&out, sizeof(double) * npairs) != cudaSuccess) {
+        rc = TT_ERR_CUDA;
+        break;
+      }
+      char* tb = static_cast<char*>(dev_table);
+      cudaMemcpy(tb, tab.data(), sizeof(SweepParams) * npairs, cudaMemcpyHostToDevice);
+      cudaMemcpy(tb + sizeof(SweepParams) * npairs, ord.data(), 4 * npairs, cudaMemcpyHostToDevice);
+      float best_ms = 1e30f;
+      int best = rb;
+      for (int t = rb; t < ntiles; ++t) {
+        std::fill(tl.begin(), tl.end(), t);
+        cudaMemcpy(tb + sizeof(SweepParams) * npairs + 4 * npairs, tl.data(), 4 * npairs, cudaMemcpyHostToDevice);
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaMemsetAsync(counter, 0, 4, s);
+          cudaEventRecord(e0, s);
+          launch_batched(tb, reinterpret_cast<int32_t*>(tb + sizeof(SweepParams) * npairs),
+                         reinterpret_cast<int32_t*>(tb + sizeof(SweepParams) * npairs + 4 * npairs), npairs, counter,
+                         out, nullptr, nullptr, dtype, 0, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) ms_sum += ms;
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+          rc = TT_ERR_CUDA;
+          break;
+        }
+        if (ms_sum < best_ms) {
+          best_ms = ms_sum;
+          best = t;
+        }
+      }
+      fprintf(f, "%d %d %d %d\n", d, rb, ib, best);
+      cudaFree(cores);
+      cudaFree(dev_table);
+      cudaFree(counter);
+      cudaFree(out);
+      cores = dev_table = nullptr;
+      counter = nullptr;
+      out = nullptr;
+    }
+  }
+  fclose(f);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  tune_table().loaded = false;  // pick the new cache up on the next plan
+  return rc;
+}
+
+}  // extern "C"

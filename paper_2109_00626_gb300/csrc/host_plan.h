@@ -1,0 +1,310 @@
+// Host-side helpers shared by the C-ABI translation units: descriptor
+// validation, sweep parameter filling and the chain-layout plan.
+#pragma once
+
+#include <string.h>
+
+#include <algorithm>
+
+#include "ttc_internal.h"
+
+namespace ttc {
+
+inline int elem_bytes(int dtype) {
+  switch (dtype) {
+    case TT_F64: return 8;
+    case TT_F32: return 4;
+    case TT_BF16: return 2;
+    default: return 0;
+  }
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+inline int check_desc(const tt_desc* d) {
+  if (d == nullptr || d->order < 1 || d->order > kMaxOrder || d->modes == nullptr || d->ranks == nullptr ||
+      d->cores == nullptr)
+    return TT_ERR_ARG;
+  if (elem_bytes(d->dtype) == 0) return TT_ERR_DTYPE;
+  if (d->ranks[0] != 1 || d->ranks[d->order] != 1) return TT_ERR_SHAPE;
+  for (int k = 0; k < d->order; ++k) {
+    if (d->modes[k] < 1 || d->ranks[k + 1] < 1) return TT_ERR_SHAPE;
+    if (d->cores[k] == nullptr) return TT_ERR_ARG;
+  }
+  return TT_OK;
+}
+
+// Same order and dtype; equal mode sizes wherever mask is set (mask NULL = all).
+inline int check_pair(const tt_desc* x, const tt_desc* y, const uint8_t* mask) {
+  int rc = check_desc(x);
+  if (rc != TT_OK) return rc;
+  rc = check_desc(y);
+  if (rc != TT_OK) return rc;
+  if (x->order != y->order) return TT_ERR_SHAPE;
+  if (x->dtype != y->dtype) return TT_ERR_DTYPE;
+  for (int k = 0; k < x->order; ++k)
+    if ((mask == nullptr || mask[k]) && x->modes[k] != y->modes[k]) return TT_ERR_SHAPE;
+  return TT_OK;
+}
+
+// Classify the contracted set: 0 = leading block {0..s-1}, 1 = trailing block
+// {N-s..N-1}, -1 = neither (the empty set counts as leading); *s_out = |S|.
+inline int end_block(const uint8_t* mask, int n, int* s_out) {
+  int s = 0;
+  for (int k = 0; k < n; ++k) s += mask[k] ? 1 : 0;
+  *s_out = s;
+  bool lead = true, trail = true;
+  for (int k = 0; k < n; ++k) {
+    if ((mask[k] != 0) != (k < s)) lead = false;
+    if ((mask[k] != 0) != (k >= n - s)) trail = false;
+  }
+  if (lead) return 0;
+  if (trail) return 1;
+  return -1;
+}
+
+inline int max_rank(const tt_desc* d) {
+  int r = 1;
+  for (int k = 0; k <= d->order; ++k) r = std::max(r, d->ranks[k]);
+  return r;
+}
+
+inline int rank_cap(int dtype) { return dtype == TT_F64 ? 64 : 128; }
+
+inline int pow2_floor(int v) {
+  int c = 1;
+  while (c * 2 <= v) c *= 2;
+  return c;
+}
+
+// Fill a left-to-right sweep over modes [k0, k1) of (x, y).
+inline void fill_left(SweepParams& p, const tt_desc* x, const tt_desc* y, int k0, int k1) {
+  p.n_steps = k1 - k0;
+  p.transposed = 0;
+  for (int j = 0; j < p.n_steps; ++j) {
+    const int k = k0 + j;
+    SweepStep& st = p.step[j];
+    st.gx = x->cores[k];
+    st.gy = y->cores[k];
+    st.I = x->modes[k];
+    st.rin_x = x->ranks[k];
+    st.rout_x = x->ranks[k + 1];
+    st.rin_y = y->ranks[k];
+    st.rout_y = y->ranks[k + 1];
+  }
+}
+
+// Fill a right-to-left sweep over modes k1-1 down to k0.
+inline void fill_right(SweepParams& p, const tt_desc* x, const tt_desc* y, int k0, int k1) {
+  p.n_steps = k1 - k0;
+  p.transposed = 1;
+  for (int j = 0; j < p.n_steps; ++j) {
+    const int k = k1 - 1 - j;
+    SweepStep& st = p.step[j];
+    st.gx = x->cores[k];
+    st.gy = y->cores[k];
+    st.I = x->modes[k];
+    st.rin_x = x->ranks[k + 1];
+    st.rout_x = x->ranks[k];
+    st.rin_y = y->ranks[k + 1];
+    st.rout_y = y->ranks[k];
+  }
+}
+
+inline int sweep_max_rank(const SweepParams& p) {
+  int r = std::max(p.rx0, p.ry0);
+  for (int j = 0; j < p.n_steps; ++j)
+    r = std::max({r, p.step[j].rin_x, p.step[j].rout_x, p.step[j].rin_y, p.step[j].rout_y});
+  if (p.emit.enabled) r = std::max({r, p.emit.ra, p.emit.rb, p.emit.ry});
+  return r;
+}
+
+inline int sweep_max_mode(const SweepParams& p) {
+  int m = 1;
+  for (int j = 0; j < p.n_steps; ++j) m = std::max(m, p.step[j].I);
+  if (p.emit.enabled) m = std::max(m, p.emit.I);
+  return m;
+}
+
+inline int launch_sweep(const SweepParams& p, int dtype, cudaStream_t s) {
+  const int rmax = sweep_max_rank(p);
+  if (rmax > rank_cap(dtype)) return TT_ERR_TOO_LARGE;
+  const int eb = elem_bytes(dtype);
+  const int want = pow2_floor(std::min(16, sweep_max_mode(p)));
+  const int C = sweep_cluster_size(rmax, eb, want);
+  if (C < 1) return TT_ERR_CUDA;
+  cudaError_t err = dtype == TT_F64 ? launch_sweep_f64(p, rmax, C, s) : launch_sweep_f32(p, rmax, C, s);
+  return err == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+struct ChainPlan {
+  int side;  // 0 lead, 1 trail
+  int s, m;
+  int n;
+  // output cores
+  int order;
+  int modes[2 * kMaxOrder];
+  int ranks[2 * kMaxOrder + 1];
+  int perm[2 * kMaxOrder];
+  // K shape
+  int kx, ky;
+};
+
+inline int chain_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, ChainPlan* cp) {
+  const int n = x->order;
+  int s = 0;
+  const int side = end_block(mask, n, &s);
+  if (s == n) return TT_ERR_ARG;
+  if (side < 0) return TT_ERR_LAYOUT;
+  const int m = n - s;
+  cp->side = side;
+  cp->s = s;
+  cp->m = m;
+  cp->n = n;
+  cp->order = 2 * m;
+  if (side == 0) {
+    // Gx_{N-1}^T .. Gx_{s+1}^T, C, Gy_s .. Gy_{N-1}
+    for (int p = 0; p < m - 1; ++p) {
+      const int k = n - 1 - p;
+      cp->modes[p] = x->modes[k];
+      cp->ranks[p] = x->ranks[k + 1];
+    }
+    cp->modes[m - 1] = x->modes[s];
+    cp->ranks[m - 1] = x->ranks[s + 1];
+    for (int q = 0; q < m; ++q) {
+      cp->modes[m + q] = y->modes[s + q];
+      cp->ranks[m + q] = y->ranks[s + q];
+    }
+    cp->ranks[2 * m] = 1;
+    for (int p = 0; p < m; ++p) cp->perm[p] = m - 1 - p;
+    for (int q = 0; q < m; ++q) cp->perm[m + q] = m + q;
+    cp->kx = x->ranks[s];
+    cp->ky = y->ranks[s];
+  } else {
+    // Gx_0 .. Gx_{m-2}, C, Gy_{m-1}^T .. Gy_0^T
+    for (int p = 0; p < m; ++p) {
+      cp->modes[p] = x->modes[p];
+      cp->ranks[p] = x->ranks[p];
+    }
+    for (int q = 0; q < m; ++q) {
+      const int k = m - 1 - q;
+      cp->modes[m + q] = y->modes[k];
+      cp->ranks[m + q] = y->ranks[k + 1];
+    }
+    cp->ranks[2 * m] = 1;
+    for (int p = 0; p < m; ++p) cp->perm[p] = p;
+    for (int q = 0; q < m; ++q) cp->perm[m + q] = m + (m - 1 - q);
+    cp->kx = x->ranks[m];
+    cp->ky = y->ranks[m];
+  }
+  return TT_OK;
+}
+
+// Check that z describes exactly the chain-layout output of cp.
+inline int check_chain_output(const tt_desc* x, const ChainPlan& cp, const tt_desc* z) {
+  const int rc = check_desc(z);
+  if (rc != TT_OK) return rc;
+  if (z->order != cp.order || z->dtype != x->dtype) return TT_ERR_SHAPE;
+  for (int q = 0; q < cp.order; ++q)
+    if (z->modes[q] != cp.modes[q] || z->ranks[q] != cp.ranks[q]) return TT_ERR_SHAPE;
+  return TT_OK;
+}
+
+// Sweep parameters of a chain-layout partial contraction: the sweep over the
+// contracted block followed by the fused emission of C and the free cores.
+inline int build_partial(const tt_desc* x, const tt_desc* y, const ChainPlan& cp, const tt_desc* z,
+                         int64_t* z_log2_dev, int32_t* status_dev, SweepParams* out) {
+  SweepParams& p = *out;
+  memset(&p, 0, sizeof(p));
+  const int n = cp.n, m = cp.m, sS = cp.s;
+  if (sS > 0) {
+    if (cp.side == 0) fill_left(p, x, y, 0, sS);
+    else fill_right(p, x, y, m, n);
+  }
+  p.rx0 = 1;
+  p.ry0 = 1;
+  p.final_scalar = 0;
+  p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+  p.status = status_dev;
+  EmitParams& ep = p.emit;
+  ep.enabled = 1;
+  const int kb = cp.side == 0 ? sS : m - 1;
+  ep.gx = x->cores[kb];
+  ep.ra = x->ranks[kb];
+  ep.I = x->modes[kb];
+  ep.rb = x->ranks[kb + 1];
+  ep.lead = cp.side == 0 ? 1 : 0;
+  ep.ry = cp.ky;
+  ep.c_out = z->cores[m - 1];
+  ep.z_log2_out = z_log2_dev;
+  auto add = [&](const void* src, void* dst, int r0, int I, int r1, int swap) -> int {
+    if (!swap && src == dst) return TT_OK;  // output aliases its input: nothing to copy
+    if (swap && src == dst) return TT_ERR_ARG;
+    if (static_cast<int64_t>(r0) * I * r1 >= (int64_t(1) << 31)) return TT_ERR_TOO_LARGE;
+    CopyTask& t = ep.copy[ep.n_copies++];
+    t.src = src;
+    t.dst = dst;
+    t.r0 = r0;
+    t.I = I;
+    t.r1 = r1;
+    t.swap = swap;
+    return TT_OK;
+  };
+  int rc = TT_OK;
+  if (cp.side == 0) {
+    for (int q = 0; q < m - 1 && rc == TT_OK; ++q) {
+      const int k = n - 1 - q;
+      rc = add(x->cores[k], z->cores[q], x->ranks[k], x->modes[k], x->ranks[k + 1], 1);
+    }
+    for (int q = 0; q < m && rc == TT_OK; ++q) {
+      const int k = sS + q;
+      rc = add(y->cores[k], z->cores[m + q], y->ranks[k], y->modes[k], y->ranks[k + 1], 0);
+    }
+  } else {
+    for (int q = 0; q < m - 1 && rc == TT_OK; ++q)
+      rc = add(x->cores[q], z->cores[q], x->ranks[q], x->modes[q], x->ranks[q + 1], 0);
+    for (int q = 0; q < m && rc == TT_OK; ++q) {
+      const int k = m - 1 - q;
+      rc = add(y->cores[k], z->cores[m + q], y->ranks[k], y->modes[k], y->ranks[k + 1], 1);
+    }
+  }
+  return rc;
+}
+
+// Sweep parameters of a full contraction.
+inline void build_full(const tt_desc* x, const tt_desc* y, double* out_dev, int64_t* out_log2_dev,
+                       int32_t* status_dev, SweepParams* out) {
+  SweepParams& p = *out;
+  memset(&p, 0, sizeof(p));
+  fill_left(p, x, y, 0, x->order);
+  p.rx0 = 1;
+  p.ry0 = 1;
+  p.final_scalar = 1;
+  p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+  p.z_out = out_dev;
+  p.z_out_log2 = out_log2_dev;
+  p.status = status_dev;
+}
+
+// Flops of one contracted mode, the cheaper of the two evaluation orders.
+inline double mode_flops(int rx, int rx2, int ry, int ry2, int I) {
+  const double a = double(rx) * ry * I * ry2 + double(rx) * I * rx2 * ry2;
+  const double b = double(rx) * ry * I * rx2 + double(ry) * I * rx2 * ry2;
+  return 2.0 * std::min(a, b);
+}
+
+inline double sweep_flops(const SweepParams& p) {
+  double f = 0.0;
+  for (int j = 0; j < p.n_steps; ++j) {
+    const SweepStep& s = p.step[j];
+    f += mode_flops(s.rin_x, s.rout_x, s.rin_y, s.rout_y, s.I);
+  }
+  if (p.emit.enabled) {
+    const EmitParams& e = p.emit;
+    f += 2.0 * e.ra * e.I * e.rb * e.ry;
+    for (int t = 0; t < e.n_copies; ++t) f += 0.25 * e.copy[t].r0 * e.copy[t].I * e.copy[t].r1;  // copy cost proxy
+  }
+  return f;
+}
+
+}  // namespace ttc

@@ -1,0 +1,580 @@
+// Environment sweep over contracted modes, as a device body shared by the
+// single-contraction cluster kernel and the batched persistent kernel.
+//
+// One contracted mode folds the core pair into the running environment
+// (the generalisation of Algorithm 2 step 4 / Example 1's K = A_x^T A_y):
+//   E'[u][v] = sum_i  (A_i^T E B_i)[u][v]
+// with A_i, B_i the i-th slices of the two cores (see SweepStep).  The sum
+// over the mode index i is split across the CTAs of a cluster: CTA c owns
+// slices i = c, c + C, ...  Per slice a CTA computes T = E B_i and
+// P += A_i^T T out of shared memory with a register-blocked outer-product
+// loop.  Core slices stream in 32-row chunks through a ring of NST stages
+// filled by cp.async, NST-1 chunks ahead of the one being consumed; the loads
+// do not depend on E, so the next mode's chunks land while the cluster is
+// still reducing the current mode.  The cluster adds the partial P's through
+// distributed shared memory: CTA c sums its share of rows over all peers
+// (fixed order: deterministic), and every CTA pulls the reduced rows back into
+// its own copy of E'.
+//
+// Scaling: after each mode the largest binary exponent of E' is compared with
+// +-s; outside that band E' is multiplied by an exact power of two and the
+// exponent is accumulated in an int64, so long sweeps neither overflow nor
+// underflow.
+//
+// The last step of a full contraction (both right ranks 1) is summed in
+// float64: t_i[p] = sum_q E[p][q] B_i[q] in the storage type, then
+// z = sum_{i,p} A_i[p] t_i[p] in double, cluster-reduced in double.
+//
+// Partial contractions (Algorithm 2 steps 5-6, chain layout) continue in the
+// same launch: K = E is joined into the boundary core of X, slice by slice
+// across the cluster, and the free cores are copied (leg-swapped where the
+// chain walks X backwards).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "ttc_device.cuh"
+#include "ttc_internal.h"
+
+namespace ttc {
+
+namespace cg = cooperative_groups;
+
+constexpr int kNoExp = -(1 << 30);  // exponent marker of an all-zero environment
+constexpr int KC = 32;               // rows per pipeline chunk
+
+// Shared-memory plan of the sweep for element type T and rank tile RM.
+//   CL: cluster mode (a reduction buffer of RM/2 rows is needed)
+template <typename T, int RM, bool CL>
+struct SweepCfg {
+  static constexpr int NT = 256;
+  static constexpr int NW = NT / 32;
+  static constexpr int TM = RM / 16;               // thread tile is TM x TM
+  static constexpr int V = 16 / sizeof(T);         // elements per 16-byte vector
+  static constexpr int LD = RM + V;                // row stride (elements), 16-byte padded
+  static constexpr int TILE = RM * LD;
+  static constexpr int RS_ROWS = CL ? RM / 2 : 0;  // a CTA of a cluster (C >= 2) reduces <= RM/2 rows
+  static constexpr int STAGE = KC * LD;
+  static constexpr size_t kBudget = 232448 - 1024;
+  static constexpr size_t FIXED = (2 * TILE + RS_ROWS * LD) * sizeof(T) + 128 * sizeof(int);
+  static constexpr int NST_FIT = static_cast<int>((kBudget - FIXED) / (STAGE * sizeof(T)));
+  static constexpr int NST = NST_FIT >= 4 ? 4 : NST_FIT;
+  static_assert(NST >= 2, "sweep tile does not fit in shared memory");
+  static constexpr size_t SMEM = FIXED + static_cast<size_t>(NST) * STAGE * sizeof(T);
+};
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static __device__ __forceinline__ float get(const float4& v, int j) {
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+  }
+  static __device__ __forceinline__ float4 add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+  }
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static __device__ __forceinline__ double get(const double2& v, int j) { return j == 0 ? v.x : v.y; }
+  static __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+};
+
+// Asynchronously copy rows [r0, r0 + nr) of slice i of a core into dst[r - r0][c]
+// (row stride LD).
+//   transposed == 0: core is [rows][I][cols], dst[r][c] = core[r][i][c]
+//   transposed == 1: core is [cols][I][rows], dst[r][c] = core[c][i][r]
+template <typename T, int LD, int NT>
+__device__ __forceinline__ void load_rows_async(T* __restrict__ dst, const T* __restrict__ core, int i, int I,
+                                                int rows, int cols, int transposed, int r0, int nr) {
+  if (!transposed) {
+    constexpr int V = 16 / sizeof(T);
+    if ((cols % V) == 0 && (reinterpret_cast<uintptr_t>(core) & 15) == 0) {
+      const int cv = cols / V;
+      for (int idx = threadIdx.x; idx < nr * cv; idx += NT) {
+        const int r = idx / cv, c = (idx - r * cv) * V;
+        cp_async16(dst + r * LD + c, core + (static_cast<int64_t>(r0 + r) * I + i) * cols + c);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < nr * cols; idx += NT) {
+        const int r = idx / cols, c = idx - r * cols;
+        cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(r0 + r) * I + i) * cols + c);
+      }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nr * cols; idx += NT) {
+      const int c = idx / nr, r = idx - c * nr;
+      cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(c) * I + i) * rows + r0 + r);
+    }
+  }
+}
+
+// acc[a][b] += sum_{k<K} A[k][m0+a] * B[k][n0+b]   (A, B row stride LD)
+template <typename T, int TM, int LD>
+__device__ __forceinline__ void outer_product(T (&acc)[TM][TM], const T* __restrict__ A, const T* __restrict__ B,
+                                              int K, int m0, int n0) {
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    T av[TM], bv[TM];
+    ld_vec<T, TM>(av, A + k * LD + m0);
+    ld_vec<T, TM>(bv, B + k * LD + n0);
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void track(int& lexp, int& lbad, T s) {
+  if (!isfinite(s)) lbad = 1;
+  else if (s != T(0)) lexp = max(lexp, exp2_of(static_cast<double>(s)));
+}
+
+// Block-wide max exponent / or of bad flags; every thread gets the result.
+template <int NW>
+__device__ __forceinline__ void block_exp(int& lexp, int& lbad, int* ired) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  lexp = __reduce_max_sync(0xffffffffu, lexp);
+  lbad = __reduce_or_sync(0xffffffffu, lbad);
+  if (lane == 0) {
+    ired[warp] = lexp;
+    ired[16 + warp] = lbad;
+  }
+  __syncthreads();
+  int m = kNoExp, b = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    m = max(m, ired[w]);
+    b |= ired[16 + w];
+  }
+  lexp = m;
+  lbad = b;
+}
+
+// Position in the stream of chunk loads of one CTA: job (mode j, slice i),
+// operand which = 0 (B_i, rin_y rows) or 1 (A_i, rin_x rows), chunk c of nch.
+struct ChunkIt {
+  int j, i, which, c, nch;
+  bool valid;
+};
+
+__device__ __forceinline__ int nchunks(int rows) { return (rows + KC - 1) / KC; }
+
+__device__ __forceinline__ void it_settle(ChunkIt& it, const SweepParams& p, int n_pipe, int crank) {
+  while (it.j < n_pipe && it.i >= p.step[it.j].I) {
+    ++it.j;
+    it.i = crank;
+  }
+  it.valid = it.j < n_pipe;
+  if (it.valid) it.nch = nchunks(p.step[it.j].rin_y);
+}
+__device__ __forceinline__ void it_first(ChunkIt& it, const SweepParams& p, int n_pipe, int crank) {
+  it.j = 0;
+  it.i = crank;
+  it.which = 0;
+  it.c = 0;
+  it_settle(it, p, n_pipe, crank);
+}
+__device__ __forceinline__ void it_next(ChunkIt& it, const SweepParams& p, int n_pipe, int crank, int C) {
+  if (++it.c < it.nch) return;
+  it.c = 0;
+  if (it.which == 0) {
+    it.which = 1;
+    it.nch = nchunks(p.step[it.j].rin_x);
+    return;
+  }
+  it.which = 0;
+  it.i += C;
+  it_settle(it, p, n_pipe, crank);
+}
+
+// Where results and device status go (per call; the batched kernel points
+// these at its per-pair slots).
+struct SweepOut {
+  double* z_out;
+  int64_t* z_out_log2;
+  int32_t* status;
+};
+
+// Result of a sweep that is not a full contraction: E (in Es, transposed) and
+// its scale; the caller continues with the environment output / emission.
+template <typename T, int RM, bool CL>
+struct SweepState {
+  int64_t log2s;
+  int bad;
+};
+
+// The sweep itself.  Returns false when it handled a final scalar (full
+// contraction) and nothing is left to do.
+template <typename T, int RM, bool CL>
+__device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut& o, unsigned char* smem, int C,
+                                           int crank, SweepState<T, RM, CL>& out) {
+  using Cfg = SweepCfg<T, RM, CL>;
+  using VT = typename Vec16<T>::type;
+  constexpr int NT = Cfg::NT, NW = Cfg::NW, TM = Cfg::TM, LD = Cfg::LD, V = Cfg::V, NST = Cfg::NST;
+  T* Es = reinterpret_cast<T*>(smem);  // E transposed: Es[q][p] = E[p][q]
+  T* Ts = Es + Cfg::TILE;              // T = E B_i; the partial P at a mode's end
+  T* Rs = Ts + Cfg::TILE;              // reduced rows of this CTA (cluster mode)
+  T* stage0 = Rs + Cfg::RS_ROWS * LD;
+  int* ired = reinterpret_cast<int*>(stage0 + NST * Cfg::STAGE);
+
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int n_pipe = p.final_scalar ? p.n_steps - 1 : p.n_steps;
+
+  int64_t log2s = 0;
+  int bad = 0;
+
+  // ---- start environment ----
+  if (p.e_in == nullptr) {
+    if (tid == 0) Es[0] = T(1);
+  } else {
+    const T* e = static_cast<const T*>(p.e_in);
+    for (int idx = tid; idx < p.rx0 * p.ry0; idx += NT) {
+      const int a = idx / p.ry0, b = idx - a * p.ry0;
+      Es[b * LD + a] = e[idx];
+    }
+    if (p.e_in_log2 != nullptr) log2s = *p.e_in_log2;
+  }
+
+  // ---- chunk pipeline ----
+  ChunkIt prod, cons;
+  it_first(prod, p, n_pipe, crank);
+  it_first(cons, p, n_pipe, crank);
+  int Lp = 0, Lc = 0;
+  auto produce = [&]() {
+    if (prod.valid) {
+      const SweepStep& st = p.step[prod.j];
+      T* dst = stage0 + (Lp % NST) * Cfg::STAGE;
+      const int rows = prod.which == 0 ? st.rin_y : st.rin_x;
+      const int cols = prod.which == 0 ? st.rout_y : st.rout_x;
+      const T* core = static_cast<const T*>(prod.which == 0 ? st.gy : st.gx);
+      const int r0 = prod.c * KC;
+      load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, p.transposed, r0, min(KC, rows - r0));
+      ++Lp;
+      it_next(prod, p, n_pipe, crank, C);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < NST - 1; ++s) produce();
+  __syncthreads();
+
+  const int p0 = ty * TM, v0 = tx * TM;
+  for (int j = 0; j < n_pipe; ++j) {
+    const SweepStep st = p.step[j];
+    T acc[TM][TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+
+    while (cons.valid && cons.j == j) {
+      // ---- T = E B_i over chunks of q ----
+      T t[TM][TM];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) t[a][b] = T(0);
+      const bool act1 = p0 < st.rin_x && v0 < st.rout_y;
+      while (true) {
+        cp_async_wait<NST - 2>();
+        __syncthreads();
+        produce();
+        const T* Bs = stage0 + (Lc % NST) * Cfg::STAGE;
+        ++Lc;
+        const int q0 = cons.c * KC, kc = min(KC, st.rin_y - q0);
+        if (act1) outer_product<T, TM, LD>(t, Es + q0 * LD, Bs, kc, p0, v0);
+        const bool last = cons.c + 1 == cons.nch;
+        it_next(cons, p, n_pipe, crank, C);
+        if (last) break;
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a) {
+        T* row = Ts + (p0 + a) * LD + v0;
+#pragma unroll
+        for (int b = 0; b < TM; ++b) row[b] = t[a][b];
+      }
+      // ---- P += A_i^T T over chunks of p ----
+      const bool act2 = p0 < st.rout_x && v0 < st.rout_y;
+      while (true) {
+        cp_async_wait<NST - 2>();
+        __syncthreads();
+        produce();
+        const T* As = stage0 + (Lc % NST) * Cfg::STAGE;
+        ++Lc;
+        const int r0 = cons.c * KC, kc = min(KC, st.rin_x - r0);
+        if (act2) outer_product<T, TM, LD>(acc, As, Ts + r0 * LD, kc, p0, v0);
+        const bool last = cons.c + 1 == cons.nch;
+        it_next(cons, p, n_pipe, crank, C);
+        if (last) break;
+      }
+    }
+    __syncthreads();  // every thread is done reading Es / Ts of this mode
+
+    const int nu = st.rout_x, nv = st.rout_y;
+    if (!CL || C == 1) {
+      int lexp = kNoExp, lbad = 0;
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b)
+          if (p0 + a < nu && v0 + b < nv) track(lexp, lbad, acc[a][b]);
+      block_exp<NW>(lexp, lbad, ired);
+      if (lbad) bad = 1;
+      const bool rescale = lexp != kNoExp && (lexp > p.renorm_bits || lexp < -p.renorm_bits);
+      if (rescale) log2s += lexp;
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b)
+          Es[(v0 + b) * LD + p0 + a] = rescale ? mul_pow2<T>(acc[a][b], -lexp) : acc[a][b];
+      __syncthreads();
+      continue;
+    }
+
+    if constexpr (CL) {
+      cg::cluster_group cluster = cg::this_cluster();
+      // ---- cluster reduction: E'[u][v] = sum over CTAs of P_c[u][v] ----
+#pragma unroll
+      for (int a = 0; a < TM; ++a) {
+        T* row = Ts + (p0 + a) * LD + v0;
+#pragma unroll
+        for (int b = 0; b < TM; ++b) row[b] = acc[a][b];
+      }
+      cluster.sync();
+      const int nvv = (nv + V - 1) / V;
+      const int chunk = (nu + C - 1) / C;
+      const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
+      int lexp = kNoExp, lbad = 0;
+      for (int idx = tid; idx < (ue - ub) * nvv; idx += NT) {
+        const int u = ub + idx / nvv, c = (idx % nvv) * V;
+        VT part[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (r < C) part[r] = *reinterpret_cast<const VT*>(cluster.map_shared_rank(Ts + u * LD + c, r));
+        VT s = Vec16<T>::zero();
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          if (r < C) s = Vec16<T>::add(s, part[r]);
+        *reinterpret_cast<VT*>(Rs + (u - ub) * LD + c) = s;
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+          if (c + q < nv) track(lexp, lbad, Vec16<T>::get(s, q));
+      }
+      lexp = __reduce_max_sync(0xffffffffu, lexp);
+      lbad = __reduce_or_sync(0xffffffffu, lbad);
+      if (lane == 0) {
+        ired[warp] = lexp;
+        ired[16 + warp] = lbad;
+      }
+      __syncthreads();
+      if (tid < C) {
+        int m = kNoExp, bb = 0;
+        for (int w = 0; w < NW; ++w) {
+          m = max(m, ired[w]);
+          bb |= ired[16 + w];
+        }
+        *cluster.map_shared_rank(ired + 32 + crank, tid) = m;
+        *cluster.map_shared_rank(ired + 64 + crank, tid) = bb;
+      }
+      cluster.sync();
+      int gexp = kNoExp, gbad = 0;
+      for (int r = 0; r < C; ++r) {
+        gexp = max(gexp, ired[32 + r]);
+        gbad |= ired[64 + r];
+      }
+      if (gbad) bad = 1;
+      const bool rescale = gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits);
+      if (rescale) log2s += gexp;
+      for (int idx = tid; idx < nu * nvv; idx += NT) {
+        const int u = idx / nvv, c = (idx % nvv) * V;
+        const int owner = u / chunk;
+        const VT v =
+            *reinterpret_cast<const VT*>(cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + c, owner));
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const T e = Vec16<T>::get(v, q);
+          Es[(c + q) * LD + u] = rescale ? mul_pow2<T>(e, -gexp) : e;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- last mode of a full contraction: float64 sum ----
+  if (p.final_scalar) {
+    const SweepStep st = p.step[p.n_steps - 1];
+    const T* gx = static_cast<const T*>(st.gx);
+    const T* gy = static_cast<const T*>(st.gy);
+    const int I = st.I;
+    T* bvec = Ts;       // B_i[q][0]
+    T* avec = Ts + LD;  // A_i[p][0]
+    double part = 0.0;
+    for (int i = crank; i < I; i += C) {
+      for (int q = tid; q < st.rin_y; q += NT)
+        bvec[q] = p.transposed ? ldg(gy + static_cast<int64_t>(i) * st.rin_y + q)
+                               : ldg(gy + static_cast<int64_t>(q) * I + i);
+      for (int a = tid; a < st.rin_x; a += NT)
+        avec[a] = p.transposed ? ldg(gx + static_cast<int64_t>(i) * st.rin_x + a)
+                               : ldg(gx + static_cast<int64_t>(a) * I + i);
+      __syncthreads();
+      for (int a = tid; a < st.rin_x; a += NT) {
+        T t = T(0);
+        for (int q = 0; q < st.rin_y; ++q) t = fma(Es[q * LD + a], bvec[q], t);
+        part = fma(static_cast<double>(avec[a]), static_cast<double>(t), part);
+      }
+      __syncthreads();
+    }
+    part = warp_sum(part);
+    double* dred = reinterpret_cast<double*>(ired + 96);  // 16 doubles (ired has 128 ints)
+    if (lane == 0) dred[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += dred[w];
+      dred[8] = s;
+    }
+    double z = 0.0;
+    if constexpr (CL) {
+      cg::cluster_group cluster = cg::this_cluster();
+      cluster.sync();
+      if (crank == 0 && tid == 0)
+        for (int r = 0; r < C; ++r) z += *cluster.map_shared_rank(dred + 8, r);
+    } else {
+      __syncthreads();
+      z = dred[8];
+    }
+    if (crank == 0 && tid == 0) {
+      int st_bits = (isfinite(z) && !bad) ? 0 : TT_STATUS_NONFINITE;
+      if (o.z_out_log2 != nullptr) {
+        *o.z_out = z;
+        *o.z_out_log2 = log2s;
+      } else {
+        double v = z;
+        if (z != 0.0 && isfinite(z)) {
+          const int64_t tot = static_cast<int64_t>(exp2_of(z)) + log2s;
+          if (tot > 1024) {
+            v = z > 0 ? INFINITY : -INFINITY;
+            st_bits |= TT_STATUS_OVERFLOW;
+          } else if (tot < -1074) {
+            v = 0.0;
+          } else {
+            v = ldexp(z, static_cast<int>(log2s));
+          }
+        }
+        *o.z_out = v;
+      }
+      set_status(o.status, st_bits);
+    }
+    if constexpr (CL) cg::this_cluster().sync();  // peers' shared memory stays alive until CTA 0 has read it
+    return false;
+  }
+  out.log2s = log2s;
+  out.bad = bad;
+  return true;
+}
+
+// Environment output and chain emission after a sweep (see EmitParams).
+template <typename T, int RM, bool CL>
+__device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut& o, unsigned char* smem, int C,
+                                           int crank, const SweepState<T, RM, CL>& s) {
+  using Cfg = SweepCfg<T, RM, CL>;
+  constexpr int NT = Cfg::NT, TM = Cfg::TM, LD = Cfg::LD;
+  T* Es = reinterpret_cast<T*>(smem);
+  T* Ts = Es + Cfg::TILE;
+  T* stage0 = Ts + Cfg::TILE + Cfg::RS_ROWS * LD;
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  const int64_t log2s = s.log2s;
+
+  const int kx = p.n_steps > 0 ? p.step[p.n_steps - 1].rout_x : p.rx0;
+  const int ky = p.n_steps > 0 ? p.step[p.n_steps - 1].rout_y : p.ry0;
+  if (crank == 0 && p.e_out != nullptr) {
+    T* e = static_cast<T*>(p.e_out);
+    for (int idx = tid; idx < kx * ky; idx += NT) {
+      const int u = idx / ky, v = idx - u * ky;
+      e[idx] = Es[v * LD + u];
+    }
+    if (tid == 0 && p.e_out_log2 != nullptr) *p.e_out_log2 = log2s;
+  }
+
+  if (p.emit.enabled) {
+    const EmitParams& em = p.emit;
+    // K row-major into Ts: Ts[a][y] = K[a][y] = Es[y][a]
+    for (int idx = tid; idx < kx * ky; idx += NT) {
+      const int a = idx / ky, y = idx - a * ky;
+      Ts[a * LD + y] = Es[y * LD + a];
+    }
+    const T* gx = static_cast<const T*>(em.gx);
+    T* cout = static_cast<T*>(em.c_out);
+    const int nu = em.lead ? em.rb : em.ra;
+    const bool fold = em.z_log2_out == nullptr && log2s != 0;
+    int ebits = 0;
+    const int u0 = ty * TM, y0 = tx * TM;
+    for (int i = crank; i < em.I; i += C) {
+      T acc[TM][TM];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+      for (int r0 = 0; r0 < kx; r0 += KC) {
+        const int kc = min(KC, kx - r0);
+        __syncthreads();
+        if (em.lead) load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.ra, em.rb, 0, r0, kc);
+        else load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.rb, em.ra, 1, r0, kc);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        if (u0 < nu && y0 < em.ry) outer_product<T, TM, LD>(acc, stage0, Ts + r0 * LD, kc, u0, y0);
+      }
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) {
+          const int u = u0 + a, y = y0 + b;
+          if (u < nu && y < em.ry) {
+            T v = acc[a][b];
+            if (fold) {
+              const T v0 = v;
+              v = scale_pow2_sat<T>(v, log2s);
+              if (isfinite(v0) && !isfinite(v)) ebits |= TT_STATUS_OVERFLOW;
+            }
+            if (!isfinite(v)) ebits |= TT_STATUS_NONFINITE;
+            cout[(static_cast<int64_t>(u) * em.I + i) * em.ry + y] = v;
+          }
+        }
+    }
+    if (ebits) set_status(o.status, ebits);
+    if (crank == 0 && tid == 0 && em.z_log2_out != nullptr) *em.z_log2_out = log2s;
+    // free cores: plain or leg-swapped copies, grid-stride over the cluster
+    const int64_t g = static_cast<int64_t>(crank) * NT + tid, gs = static_cast<int64_t>(C) * NT;
+    for (int t = 0; t < em.n_copies; ++t) {
+      const CopyTask& tk = em.copy[t];
+      const T* __restrict__ src = static_cast<const T*>(tk.src);
+      T* __restrict__ dst = static_cast<T*>(tk.dst);
+      const int64_t n = static_cast<int64_t>(tk.r0) * tk.I * tk.r1;
+      if (!tk.swap) {
+        for (int64_t e = g; e < n; e += gs) dst[e] = ldg(src + e);
+      } else {
+        // dst is [r1][I][r0]; element e of dst = (c1, i, c0); 32-bit index math
+        const unsigned r0 = tk.r0, ii = tk.I, r1 = tk.r1;
+        for (int64_t e = g; e < n; e += gs) {
+          const unsigned ee = static_cast<unsigned>(e);
+          const unsigned c0 = ee % r0, rest = ee / r0;
+          const unsigned i2 = rest % ii, c1 = rest / ii;
+          dst[e] = ldg(src + (static_cast<int64_t>(c0) * ii + i2) * r1 + c1);
+        }
+      }
+    }
+  }
+  if (tid == 0 && crank == 0 && s.bad) set_status(o.status, TT_STATUS_NONFINITE);
+}
+
+}  // namespace ttc

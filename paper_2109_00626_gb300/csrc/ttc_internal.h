@@ -77,6 +77,9 @@ struct SweepParams {
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 
+cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n, int* counter,
+                           double* out, int64_t* out_log2, int32_t* status, int dtype, int grid, cudaStream_t s);
+
 // Largest cluster size (<= want) the sweep kernel for this rank tile can run with.
 int sweep_cluster_size(int rmax, int elem_bytes, int want);
 

@@ -1,0 +1,160 @@
+"""GPU parity of the batched persistent contraction (one launch over many
+uneven pairs) against the float64 oracle, against the single-pair calls, and
+between a captured CUDA graph and eager launches."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import cs_bound, norm_scale, to_dev, to_host
+from paper_2109_00626_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2109_00626_gb300 as T  # noqa: E402
+
+
+def _uneven_pairs(n, seed, rmax=48, nmax=6, dtype=np.float32):
+    """Uneven batch in the shape of the 4096-pair workload, scaled down so the
+    oracle finishes quickly: order U{1..nmax}, modes U{1..20}, ranks U{1..rmax}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for p in range(n):
+        order = int(rng.integers(1, nmax + 1))
+        modes = [int(v) for v in rng.integers(1, 21, size=order)]
+        rx = [1] + [int(v) for v in rng.integers(1, rmax + 1, size=order - 1)] + [1]
+        ry = [1] + [int(v) for v in rng.integers(1, rmax + 1, size=order - 1)] + [1]
+        x = G.random_tt(rng, modes, rx, dtype)
+        y = G.random_tt(rng, modes, ry, dtype)
+        mask = None
+        if p % 2 == 1 and order >= 2:
+            s = int(rng.integers(0, order))
+            lead = bool(rng.integers(0, 2))
+            mask = [0] * order
+            for k in range(s):
+                mask[k if lead else order - 1 - k] = 1
+        out.append((x, y, mask))
+    return out
+
+
+def _check(pairs, bat, tol):
+    for p, (x, y, mask) in enumerate(pairs):
+        if mask is None:
+            want = O.contract_full(x, y)
+            got = float(bat.out[p].item())
+            assert abs(got - want) <= tol * norm_scale(x, y), (p, got, want)
+        else:
+            want, perm = O.partial_chain(x, y, mask)
+            got = to_host(bat.z[p])
+            assert perm == bat.perm[p]
+            side, s = O.end_block(mask)
+            m = len(x) - s
+            for q, (g, w) in enumerate(zip(got, want)):
+                if q == m - 1:
+                    kb = cs_bound(x, y, side, s).max() if s > 0 else 1.0
+                    gxb = x[s] if side == "lead" else x[m - 1]
+                    scale = np.abs(gxb).max() * kb * np.sqrt(gxb.shape[0] if side == "lead" else gxb.shape[2])
+                    assert np.abs(g - w).max() <= tol * scale, (p, q)
+                else:
+                    np.testing.assert_array_equal(g, w)
+
+
+def test_batched_uneven_fp32():
+    pairs = _uneven_pairs(48, 1)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, 1e-5)
+
+
+def test_batched_high_rank_fp32():
+    """Pairs that need the 128-rank tile."""
+    pairs = _uneven_pairs(6, 2, rmax=128, nmax=3)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    assert max(bat.tiles()) == 2
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, 1e-5)
+
+
+def test_batched_fp64():
+    pairs = _uneven_pairs(24, 3, rmax=40, dtype=np.float64)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, 1e-12)
+
+
+def test_batched_matches_single_calls_and_graph_replay():
+    pairs = _uneven_pairs(32, 4)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    eager = bat.out.clone()
+    eager_z = [None if z is None else [c.clone() for c in z] for z in bat.z]
+    for p, (x, y, m) in enumerate(dev):
+        if m is None:
+            one = T.FullContraction(x, y)
+            one()
+            torch.cuda.synchronize()
+            a, b = float(one.out.item()), float(eager[p].item())
+            assert abs(a - b) <= 1e-5 * norm_scale(pairs[p][0], pairs[p][1])
+    g = bat.graph()
+    bat.out.zero_()
+    for z in bat.z:
+        if z is not None:
+            for c in z:
+                c.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(bat.out, eager)
+    for z, ez in zip(bat.z, eager_z):
+        if z is not None:
+            for c, e in zip(z, ez):
+                assert torch.equal(c, e)
+
+
+def test_batched_lpt_and_generator_shapes():
+    """A slice of the 4096-pair workload itself (shapes from its generator)."""
+    specs = G.batch4096_spec(64)
+    assert sum(1 for s in specs if s["kind"] == "full") == 32
+    pairs = []
+    for p in (0, 1, 2, 3):
+        spec, x, y = G.batch_pair(p)
+        pairs.append((x, y, None if spec["kind"] == "full" else spec["mask"]))
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, 1e-5)
+
+
+def test_autotune_cache(tmp_path, monkeypatch):
+    path = str(tmp_path / "tune.txt")
+    monkeypatch.setenv("TTC_AUTOTUNE_CACHE", path)
+    T.autotune("f32", path)
+    lines = open(path).read().split("\n")
+    rows = [list(map(int, ln.split())) for ln in lines if ln.strip()]
+    assert len(rows) == 12
+    for d, rb, ib, tile in rows:
+        assert d == 0 and tile >= rb
+    pairs = _uneven_pairs(8, 5)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    _check(pairs, bat, 1e-5)
