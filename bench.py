@@ -229,15 +229,29 @@ def run_ours(args):
     full = T.FullContraction(xd, yd)
     part = T.PartialContraction(xd, yd, MASK)
     stream = torch.cuda.current_stream(dev)
+    side = torch.cuda.Stream(dev)  # the full and the partial contraction are independent: run them side by side
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    def step(evs=None):
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        side.wait_event(fork)
+        if evs is not None:
+            evs[0].record(side)
+        full(side)
+        if evs is not None:
+            evs[1].record(side)
+        part(stream)
+        join = torch.cuda.Event()
+        join.record(side)
+        stream.wait_event(join)
+
     for _ in range(args.warmup):
-        full()
-        part()
+        step()
     torch.cuda.synchronize(dev)
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -248,17 +262,15 @@ def run_ours(args):
     for k in range(K):
         flush.fill_(float(k))  # L2 flush between timed steps (256 MiB write, untimed)
         ev[k][0].record(stream)
-        full()
+        step(ev[k][2:4])
         ev[k][1].record(stream)
-        part()
-        ev[k][2].record(stream)
     torch.cuda.synchronize(dev)
     launches = T.launch_count() - l0
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    t_step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
-    t_full = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    t_step = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    t_full = [ev[k][2].elapsed_time(ev[k][3]) for k in range(K)]
     tot_ms = sum(t_step)
     if world > 1:
         t = torch.tensor([tot_ms], device=dev)
@@ -288,8 +300,7 @@ def run_ours(args):
     for _ in range(K2):
         for d, h in zip(xd + yd, xh + yh):
             d.copy_(h, non_blocking=True)
-        full()
-        part()
+        step()
         outh.copy_(full.out, non_blocking=True)
         for h, d in zip(zh, part.z):
             h.copy_(d, non_blocking=True)
@@ -298,6 +309,9 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / K2
 
     status = int(full.status.item()) | int(part.status.item())
+    forms = {}
+    if not args.no_forms:
+        forms["batched"] = bench_batched(T, dev, args)
 
     if rank == 0:
         line = {
@@ -339,6 +353,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "device_status": status,
+            "forms": forms,
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -346,6 +361,70 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_batched(T, dev, args):
+    """4096 uneven pairs in one graph-captured persistent launch (inputs 15 GB,
+    larger than L2: no flush needed)."""
+    import torch
+
+    t0 = time.perf_counter()
+    specs, pairs = G.batch4096_device(4096, 0, dev)
+    bat = T.BatchedContraction(pairs)
+    g = bat.graph()
+    setup_s = time.perf_counter() - t0
+    flops = 0
+    nbytes = 0
+    for sp in specs:
+        m, rx, ry = sp["modes"], sp["ranks_x"], sp["ranks_y"]
+        if sp["kind"] == "full":
+            flops += W.full_flops(m, rx, ry)
+            nbytes += W.full_bytes(m, rx, ry, 4)
+        else:
+            flops += W.partial_chain_flops(m, rx, ry, sp["mask"])
+            nbytes += W.partial_chain_bytes(m, rx, ry, sp["mask"], 4)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup // 4)):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    K = max(3, args.steps // 20)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = fp32_simt_peak_tflops()
+    hbm = _peaks().get("hbm_gbs", 6683.2)
+    out = {
+        "workload": "4096 TT pairs, order U{4..12}, modes U{2..32}, ranks U{4..128}, float32; even pairs full, odd pairs partial over an end block of floor(N/2) modes; one CUDA-graph replay of one persistent launch",
+        "value": 4096 / (ms / 1e3),
+        "unit": "contractions/s",
+        "ms_per_launch": ms,
+        "launches": K,
+        "gflops": flops / (ms / 1e3) / 1e9,
+        "alg_flops": flops,
+        "alg_bytes": nbytes,
+        "roofline": {
+            "kernel": "batched_kernel<float>",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "hbm_gbs": nbytes / (ms / 1e3) / 1e9,
+            "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+        },
+        "tiles": {str(int(t)): int(c) for t, c in zip(*np.unique(bat.tiles(), return_counts=True))},
+        "setup_s": setup_s,
+        "device_status": int(bat.status.item()),
+        "gpu_launches_per_replay": 1,
+    }
+    del g, bat, pairs
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -356,6 +435,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

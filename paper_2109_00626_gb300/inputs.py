@@ -17,7 +17,10 @@ Workloads (names give their sizes):
   * ``batch4096``      4096 pairs: order U{4..12}, I_k U{2..32} shared by the
                        pair, ranks U{4..128} per bond and per operand, float32;
                        even pairs full, odd pairs partial over an end block of
-                       floor(N/2) modes (leading or trailing by a coin)
+                       floor(N/2) modes (leading or trailing by a coin).  Its
+                       15 GB of cores are drawn on the device
+                       (:func:`batch4096_device`); :func:`batch_pair` draws
+                       host cores of the same shapes for small tests.
   * ``order16_r256``   order 16, I=32, internal ranks 256, log-normal core
                        scales exp(N(0,1)); float32 master copy (BF16 forms
                        round it)
@@ -40,6 +43,7 @@ __all__ = [
     "batch4096_spec",
     "batch_pair",
     "to_bf16_f32",
+    "batch4096_device",
 ]
 
 
@@ -194,3 +198,43 @@ def to_bf16_f32(a: np.ndarray) -> np.ndarray:
         out = out.copy()
         out[nan] = np.nan
     return out
+
+
+def batch4096_device(n_pairs: int = 4096, seed: int = 0, device="cuda", dtype=None):
+    """Cores of the uneven batch drawn on the device (the shapes are those of
+    :func:`batch4096_spec`).  Core k of X (Y) of pair p is filled from a
+    torch CUDA generator seeded with (seed, p, side, k), N(0, 1/(I_k R_k)).
+    All cores of the batch live in one arena (16-byte aligned views), so the
+    whole 15 GB batch is drawn in a few seconds.  Returns (specs, pairs) with
+    pairs[p] = (x_cores, y_cores, mask or None)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    specs = batch4096_spec(n_pairs, seed)
+    esize = torch.tensor([], dtype=dtype).element_size()
+    align = max(1, 16 // esize)
+    sizes = []
+    for s in specs:
+        for ranks in (s["ranks_x"], s["ranks_y"]):
+            for k, I in enumerate(s["modes"]):
+                n = ranks[k] * I * ranks[k + 1]
+                sizes.append((n + align - 1) // align * align)
+    arena = torch.empty(sum(sizes), dtype=dtype, device=device)
+    gen = torch.Generator(device=device)
+    off = 0
+    pairs = []
+    for p, s in enumerate(specs):
+        sides = []
+        for side, ranks in enumerate((s["ranks_x"], s["ranks_y"])):
+            cores = []
+            for k, I in enumerate(s["modes"]):
+                shape = (ranks[k], I, ranks[k + 1])
+                n = shape[0] * shape[1] * shape[2]
+                view = arena[off : off + n].view(shape)
+                gen.manual_seed(((seed * 1_000_003 + p) * 2 + side) * 64 + k)
+                view.normal_(0.0, 1.0 / float(np.sqrt(I * ranks[k + 1])), generator=gen)
+                cores.append(view)
+                off += (n + align - 1) // align * align
+            sides.append(cores)
+        pairs.append((sides[0], sides[1], None if s["kind"] == "full" else s["mask"]))
+    return specs, pairs

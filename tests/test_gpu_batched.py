@@ -158,3 +158,48 @@ def test_autotune_cache(tmp_path, monkeypatch):
     bat()
     torch.cuda.synchronize()
     _check(pairs, bat, 1e-5)
+
+
+def test_batched_full_size_sampled():
+    """The full 4096-pair workload in the launch configuration the benchmark
+    times; sampled pairs (the cheapest full and partial ones, plus one of the
+    largest) are checked against the oracle one by one."""
+    from paper_2109_00626_gb300 import workload as W
+
+    specs, pairs = G.batch4096_device(4096)
+    bat = T.BatchedContraction(pairs)
+    g = bat.graph()
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    cost = []
+    for s in specs:
+        f = W.full_flops(s["modes"], s["ranks_x"], s["ranks_y"]) if s["kind"] == "full" else \
+            W.partial_chain_flops(s["modes"], s["ranks_x"], s["ranks_y"], s["mask"])
+        cost.append(f)
+    full_ids = sorted([p for p in range(4096) if specs[p]["kind"] == "full"], key=lambda p: cost[p])
+    part_ids = sorted([p for p in range(4096) if specs[p]["kind"] == "partial"], key=lambda p: cost[p])
+    sample = full_ids[:2] + part_ids[:2] + [full_ids[len(full_ids) // 2]]
+    for p in sample:
+        x = [c.cpu().double().numpy() for c in pairs[p][0]]
+        y = [c.cpu().double().numpy() for c in pairs[p][1]]
+        mask = pairs[p][2]
+        if mask is None:
+            want = O.contract_full(x, y)
+            got = float(bat.out[p].item())
+            assert abs(got - want) <= 1e-5 * norm_scale(x, y), (p, got, want)
+        else:
+            want, perm = O.partial_chain(x, y, mask)
+            got = to_host(bat.z[p])
+            side, s = O.end_block(mask)
+            m = len(x) - s
+            for q, (gq, wq) in enumerate(zip(got, want)):
+                if q == m - 1:
+                    kb = cs_bound(x, y, side, s).max() if s > 0 else 1.0
+                    gxb = x[s] if side == "lead" else x[m - 1]
+                    scale = np.abs(gxb).max() * kb * np.sqrt(gxb.shape[0] if side == "lead" else gxb.shape[2])
+                    assert np.abs(gq - wq).max() <= 1e-5 * scale, (p, q)
+                else:
+                    np.testing.assert_array_equal(gq, wq)
+    del bat, pairs
+    torch.cuda.empty_cache()
