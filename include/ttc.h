@@ -197,6 +197,24 @@ int tt_contract_batched(const tt_plan* plan, const void* packed_dev, double* out
                         int64_t* out_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
                         tt_stream stream);
 
+/* The same batched contraction for callers that cannot allocate device
+ * memory where they contract -- a plugin inside a framework that owns every
+ * device allocation, or a loop that must not allocate once running -- and so
+ * have no workspace to pass.  (The paper has no counterpart to this call.)
+ * The work-queue counter lives in a fixed array inside the library instead:
+ * TT_NOALLOC_SCRATCH_BYTES bytes of static device memory that every GPU which
+ * loads the library holds until the process exits.  Plans whose workspace
+ * (tt_batch_plan's *ws_bytes) exceeds that size are rejected with
+ * TT_ERR_WS.  The call allocates and frees nothing; it zeroes what must
+ * start at zero and otherwise behaves like tt_contract_batched.  The first
+ * call on a device looks up the array's device address with that device
+ * current (make that first call before any stream capture).  Every call
+ * shares the one array, which keeps the last call's contents: calls whose
+ * executions overlap on the GPU race with each other. */
+#define TT_NOALLOC_SCRATCH_BYTES 256
+int tt_contract_batched_noalloc(const tt_plan* plan, const void* packed_dev, double* out_dev,
+                                int64_t* out_log2_dev, int32_t* status_dev, tt_stream stream);
+
 /* Number of pairs and the tile configuration chosen for pair p (for tests and
  * reports); returns TT_ERR_ARG for p out of range. */
 int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile_config);

@@ -32,6 +32,7 @@ EXPORTS = [
     "tt_batch_plan",
     "tt_batch_pack",
     "tt_contract_batched",
+    "tt_contract_batched_noalloc",
     "tt_plan_info",
     "tt_plan_free",
     "tt_autotune",
@@ -91,6 +92,7 @@ def lib():
     L.tt_batch_plan.argtypes = [POINTER(TTBatch), POINTER(c_void_p), POINTER(c_size_t), POINTER(c_size_t)]
     L.tt_batch_pack.argtypes = [c_void_p, c_void_p, c_size_t]
     L.tt_contract_batched.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.tt_contract_batched_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.tt_plan_info.argtypes = [c_void_p, c_int32, I32, I32]
     L.tt_plan_free.argtypes = [c_void_p]
     L.tt_plan_free.restype = None
@@ -384,6 +386,20 @@ class BatchedContraction:
             _stream_ptr(stream),
         )
         check(rc, "tt_contract_batched")
+        return self.out
+
+    def call_noalloc(self, stream=None):
+        """The same launch through tt_contract_batched_noalloc: no workspace,
+        the work-queue counter lives in the library's static device array."""
+        rc = lib().tt_contract_batched_noalloc(
+            self.plan,
+            c_void_p(self.packed.data_ptr()),
+            c_void_p(self.out.data_ptr()),
+            c_void_p(self.log2.data_ptr()) if self.log2 is not None else None,
+            c_void_p(self.status.data_ptr()),
+            _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_batched_noalloc")
         return self.out
 
     def graph(self):

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -18,6 +19,7 @@ struct tt_plan {
   std::vector<int32_t> tile;
   std::vector<double> cost;
   size_t off_order = 0, off_tile = 0, packed_bytes = 0;
+  size_t ws_bytes = 256;  // device workspace the launch needs (the work-queue counter)
 };
 
 namespace ttc {
@@ -260,3 +262,60 @@ int tt_autotune(int dtype, const char* cache_path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched contraction without a caller-provided workspace.
+//
+// Some callers cannot hand this library a device buffer at the point where
+// they contract: a plugin inside a framework that owns every device
+// allocation, or a loop that must not allocate once it is running.  For them
+// the work-queue counter lives in a fixed array inside the library instead of
+// in `ws`.  The array is static device memory: every GPU that loads the library
+// holds one copy of kNoAllocScratchBytes bytes until the process exits.
+// ---------------------------------------------------------------------------
+namespace ttc {
+
+constexpr size_t kNoAllocScratchBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in; the address is looked up once per
+// device, with that device current.
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return TT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return TT_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TT_OK;
+}
+
+}  // namespace ttc
+
+extern "C" int tt_contract_batched_noalloc(const tt_plan* plan, const void* packed_dev, double* out_dev,
+                                           int64_t* out_log2_dev, int32_t* status_dev, tt_stream stream) {
+  if (plan == nullptr || packed_dev == nullptr || out_dev == nullptr) return TT_ERR_ARG;
+  if (plan->ws_bytes > kNoAllocScratchBytes) return TT_ERR_WS;  // plan needs more than the fixed array
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc != TT_OK) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const char* base = static_cast<const char*>(packed_dev);
+  // the counter must start at zero on every call; the array keeps the last call's contents
+  if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(out_dev, 0, sizeof(double) * plan->n_pairs, s) != cudaSuccess) return TT_ERR_CUDA;
+  const cudaError_t err =
+      launch_batched(base, reinterpret_cast<const int32_t*>(base + plan->off_order),
+                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs, static_cast<int*>(scratch),
+                     out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
+  return err == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
