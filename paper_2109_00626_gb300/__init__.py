@@ -11,6 +11,10 @@ from ._binding import (  # noqa: F401
     EXPORTS,
     BatchedContraction,
     autotune,
+    backward,
+    tt_full,
+    tt_partial,
+    tt_sum,
     LAYOUT,
     PREC,
     Desc,

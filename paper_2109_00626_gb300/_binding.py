@@ -431,3 +431,130 @@ def autotune(dtype="f32", cache_path=None):
     path = cache_path or os.path.join(_HERE, f"autotune_{dtype}.txt")
     check(lib().tt_autotune(code, path.encode()), "tt_autotune")
     return path
+
+
+def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, layout="chain"):
+    """Gradients of a full (mask None; ``cot`` = float64 device scalar) or a
+    chain-layout partial contraction (``dz`` = cotangents of the output cores)
+    with respect to every core of x and y.  Returns (gx, gy, status)."""
+    import torch
+
+    xd, yd = Desc(x), Desc(y)
+    gx = [torch.empty_like(c) for c in x]
+    gy = [torch.empty_like(c) for c in y]
+    gxd, gyd = Desc(gx), Desc(gy)
+    dev = x[0].device
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    nb = workspace_bytes(TT_OP_BACKWARD, xd, yd, mask, layout)
+    if ckpt_stride:
+        nb = max(nb, (len(x) + 1 + 4) * _env_bytes(x, y) + 8192)
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+    m = _mask_arr(mask) if mask is not None else None
+    dzd = Desc(dz) if dz is not None else None
+    if cot is not None:
+        cot = cot.detach().to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    rc = lib().tt_contract_backward(
+        xd.ref,
+        yd.ref,
+        m,
+        LAYOUT[layout],
+        TT_P_NATIVE,
+        c_void_p(cot.data_ptr()) if cot is not None else None,
+        dzd.ref if dzd is not None else None,
+        gxd.ref,
+        gyd.ref,
+        int(ckpt_stride),
+        c_void_p(status.data_ptr()),
+        c_void_p(ws.data_ptr()),
+        c_size_t(ws.numel()),
+        _stream_ptr(stream),
+    )
+    check(rc, "tt_contract_backward")
+    return gx, gy, status
+
+
+def _env_bytes(x, y):
+    rx = max([int(c.shape[0]) for c in x] + [int(c.shape[2]) for c in x])
+    ry = max([int(c.shape[0]) for c in y] + [int(c.shape[2]) for c in y])
+    return rx * ry * x[0].element_size()
+
+
+def _autograd():
+    import torch
+
+    class TTFull(torch.autograd.Function):
+        """z = <X, Y> with a hand-written adjoint (tt_contract_backward)."""
+
+        @staticmethod
+        def forward(ctx, nx, *cores):
+            x = [c.contiguous() for c in cores[:nx]]
+            y = [c.contiguous() for c in cores[nx:]]
+            op = FullContraction(x, y)
+            op()
+            ctx.nx = nx
+            ctx.save_for_backward(*x, *y)
+            return op.out.reshape(())
+
+        @staticmethod
+        def backward(ctx, g):
+            saved = ctx.saved_tensors
+            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx :])
+            gx, gy, _ = backward(x, y, None, cot=g)
+            return (None, *gx, *gy)
+
+    class TTPartial(torch.autograd.Function):
+        """Chain-layout partial contraction with a hand-written adjoint."""
+
+        @staticmethod
+        def forward(ctx, nx, mask, *cores):
+            x = [c.contiguous() for c in cores[:nx]]
+            y = [c.contiguous() for c in cores[nx:]]
+            op = PartialContraction(x, y, mask)
+            op()
+            ctx.nx = nx
+            ctx.mask = list(mask)
+            ctx.save_for_backward(*x, *y)
+            return tuple(op.z)
+
+        @staticmethod
+        def backward(ctx, *gz):
+            saved = ctx.saved_tensors
+            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx :])
+            xd, yd = Desc(x), Desc(y)
+            modes, ranks, _ = partial_shape(xd, yd, ctx.mask, "chain")
+            dz = []
+            for t, g in enumerate(gz):
+                if g is None:
+                    g = torch.zeros((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
+                dz.append(g.contiguous())
+            gx, gy, _ = backward(x, y, ctx.mask, dz=dz)
+            return (None, None, *gx, *gy)
+
+    return TTFull, TTPartial
+
+
+_fns = None
+
+
+def tt_full(x, y):
+    """Differentiable <X, Y> (float64 scalar)."""
+    global _fns
+    if _fns is None:
+        _fns = _autograd()
+    return _fns[0].apply(len(x), *x, *y)
+
+
+def tt_partial(x, y, mask):
+    """Differentiable chain-layout partial contraction; returns the output cores."""
+    global _fns
+    if _fns is None:
+        _fns = _autograd()
+    return list(_fns[1].apply(len(x), list(mask), *x, *y))
+
+
+def tt_sum(cores):
+    """Sum of all entries of a TT (= <Z, all-ones rank-1 TT>), differentiable."""
+    import torch
+
+    ones = [torch.ones((1, int(c.shape[1]), 1), dtype=c.dtype, device=c.device) for c in cores]
+    return tt_full(list(cores), ones)

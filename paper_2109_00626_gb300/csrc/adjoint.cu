@@ -1,0 +1,560 @@
+// Adjoint of the environment sweep: gradients of a contraction with respect
+// to every core of both operands.
+//
+// For z = <L_seed | sweep over modes k0..k1-1 | F_seed> (a full contraction
+// has both seeds [1]; a chain-layout partial contraction seeds one side with
+// the cotangent of its K), z is linear in each core and, with L_k the left and
+// F_{k+1} the right environments,
+//   dGx_k[:, i, :] = L_k  Gy_k[:, i, :] F_{k+1}^T,
+//   dGy_k[:, i, :] = L_k^T Gx_k[:, i, :] F_{k+1}.
+// Per slice i this is evaluated as U = L Gy_i, dGx_i = U F^T, W = Gx_i F,
+// dGy_i = L^T W, and the next right environment gets W Gy_i^T.
+//
+// Memory: the left environments are not all kept.  A forward sweep stores L
+// every c modes (checkpoints) in the workspace; the backward walk then goes
+// segment by segment from the right, recomputing the c left environments of
+// the segment from its checkpoint before walking it backwards.  Workspace is
+// (ceil(n/c) + c) environments instead of n, for one extra forward sweep.
+//
+// Work split: like the forward sweep, the slices i of every mode are spread
+// over the CTAs of one cluster and the environment sums are reduced through
+// distributed shared memory.
+#include <cooperative_groups.h>
+
+#include "ttc_device.cuh"
+#include "ttc_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ttc {
+
+namespace {
+
+constexpr int kNoExpA = -(1 << 30);
+
+template <typename T, int RM>
+struct AdjCfg {
+  static constexpr int NT = 256;
+  static constexpr int NW = NT / 32;
+  static constexpr int TM = RM / 16;
+  static constexpr int V = 16 / sizeof(T);
+  static constexpr int LD = RM + V;
+  static constexpr int TILE = RM * LD;
+  // Ls, LT, F, FT, GyS, GyT, Gx, X1, W, Rs (half)
+  static constexpr int NBUF_FULL = 9;
+  static constexpr size_t SMEM = (NBUF_FULL * TILE + (RM / 2) * LD) * sizeof(T) + 128 * sizeof(int);
+};
+
+// acc[a][b] += sum_{k<K} A[k][m0+a] * B[k][n0+b]
+template <typename T, int TM, int LD>
+__device__ __forceinline__ void op_acc(T (&acc)[TM][TM], const T* __restrict__ A, const T* __restrict__ B, int K, int m0,
+                                       int n0) {
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    T av[TM], bv[TM];
+    ld_vec<T, TM>(av, A + k * LD + m0);
+    ld_vec<T, TM>(bv, B + k * LD + n0);
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+}
+
+template <typename T, int TM>
+__device__ __forceinline__ void zero(T (&acc)[TM][TM]) {
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+}
+
+// Slice i of a core into dst (row stride LD), asynchronously.
+//   tr == 0: dst[r][c] = core[r][i][c]   (core [rows][I][cols])
+//   tr == 1: dst[r][c] = core[c][i][r]   (core [cols][I][rows])
+template <typename T, int LD, int NT>
+__device__ __forceinline__ void slice_async(T* dst, const T* core, int i, int I, int rows, int cols, int tr) {
+  for (int idx = threadIdx.x; idx < rows * cols; idx += NT) {
+    if (!tr) {
+      const int r = idx / cols, c = idx - r * cols;
+      cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(r) * I + i) * cols + c);
+    } else {
+      const int c = idx / rows, r = idx - c * rows;
+      cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(c) * I + i) * rows + r);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void track_e(int& lexp, int& lbad, T s) {
+  if (!isfinite(s)) lbad = 1;
+  else if (s != T(0)) lexp = max(lexp, exp2_of(static_cast<double>(s)));
+}
+
+// Sum the thread tiles acc (tile at (u0, v0) of an nu x nv matrix) over the
+// cluster; every CTA writes the sum into Dn[u][v] and Dt[v][u], rescaled by an
+// exact power of two when its largest exponent leaves [-s, s].  Returns the
+// exponent folded out (0 when none).  Ps / Rs: scratch tiles.
+template <typename T, int RM>
+__device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, int nv, T* Ps, T* Rs, T* Dn, T* Dt,
+                          int* ired, int C, int crank, int renorm_bits, int& bad) {
+  using Cfg = AdjCfg<T, RM>;
+  constexpr int TM = Cfg::TM, LD = Cfg::LD, NT = Cfg::NT, NW = Cfg::NW;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __syncthreads();  // all readers of Dn / Dt / Ps are done
+  if (C == 1) {
+    int lexp = kNoExpA, lbad = 0;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b)
+        if (u0 + a < nu && v0 + b < nv) track_e(lexp, lbad, acc[a][b]);
+    lexp = __reduce_max_sync(0xffffffffu, lexp);
+    lbad = __reduce_or_sync(0xffffffffu, lbad);
+    if (lane == 0) {
+      ired[warp] = lexp;
+      ired[16 + warp] = lbad;
+    }
+    __syncthreads();
+    int g = kNoExpA, gb = 0;
+    for (int w = 0; w < NW; ++w) {
+      g = max(g, ired[w]);
+      gb |= ired[16 + w];
+    }
+    if (gb) bad = 1;
+    const int sh = (g != kNoExpA && (g > renorm_bits || g < -renorm_bits)) ? g : 0;
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TM; ++b) {
+        const T v = sh ? mul_pow2<T>(acc[a][b], -sh) : acc[a][b];
+        Dn[(u0 + a) * LD + v0 + b] = v;
+        Dt[(v0 + b) * LD + u0 + a] = v;
+      }
+    __syncthreads();
+    return sh;
+  }
+  cg::cluster_group cluster = cg::this_cluster();
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) Ps[(u0 + a) * LD + v0 + b] = acc[a][b];
+  cluster.sync();
+  const int chunk = (nu + C - 1) / C;
+  const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
+  int lexp = kNoExpA, lbad = 0;
+  for (int idx = tid; idx < (ue - ub) * nv; idx += NT) {
+    const int u = ub + idx / nv, v = idx % nv;
+    T part[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      if (r < C) part[r] = *cluster.map_shared_rank(Ps + u * LD + v, r);
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      if (r < C) s += part[r];
+    Rs[(u - ub) * LD + v] = s;
+    track_e(lexp, lbad, s);
+  }
+  lexp = __reduce_max_sync(0xffffffffu, lexp);
+  lbad = __reduce_or_sync(0xffffffffu, lbad);
+  if (lane == 0) {
+    ired[warp] = lexp;
+    ired[16 + warp] = lbad;
+  }
+  __syncthreads();
+  if (tid < C) {
+    int m = kNoExpA, bb = 0;
+    for (int w = 0; w < NW; ++w) {
+      m = max(m, ired[w]);
+      bb |= ired[16 + w];
+    }
+    *cluster.map_shared_rank(ired + 32 + crank, tid) = m;
+    *cluster.map_shared_rank(ired + 64 + crank, tid) = bb;
+  }
+  cluster.sync();
+  int g = kNoExpA, gb = 0;
+  for (int r = 0; r < C; ++r) {
+    g = max(g, ired[32 + r]);
+    gb |= ired[64 + r];
+  }
+  if (gb) bad = 1;
+  const int sh = (g != kNoExpA && (g > renorm_bits || g < -renorm_bits)) ? g : 0;
+  for (int idx = tid; idx < nu * nv; idx += NT) {
+    const int u = idx / nv, v = idx % nv;
+    const int owner = u / chunk;
+    T e = *cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + v, owner);
+    if (sh) e = mul_pow2<T>(e, -sh);
+    Dn[u * LD + v] = e;
+    Dt[v * LD + u] = e;
+  }
+  cluster.sync();  // peers are done reading Rs / Ps before they are reused
+  return sh;
+}
+
+// Load an environment (row-major [nu][nv] in global memory) into Dn / Dt.
+template <typename T, int LD, int NT>
+__device__ void load_env(const T* src, int nu, int nv, T* Dn, T* Dt) {
+  for (int idx = threadIdx.x; idx < nu * nv; idx += NT) {
+    const int u = idx / nv, v = idx - u * nv;
+    const T e = src[idx];
+    Dn[u * LD + v] = e;
+    Dt[v * LD + u] = e;
+  }
+}
+
+template <typename T, int LD, int NT>
+__device__ void store_env(T* dst, int nu, int nv, const T* Dn) {
+  for (int idx = threadIdx.x; idx < nu * nv; idx += NT) {
+    const int u = idx / nv, v = idx - u * nv;
+    dst[idx] = Dn[u * LD + v];
+  }
+}
+
+}  // namespace
+
+template <typename T, int RM>
+__global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__ AdjointParams p) {
+  using Cfg = AdjCfg<T, RM>;
+  constexpr int NT = Cfg::NT, TM = Cfg::TM, LD = Cfg::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // L[a][b]
+  T* LT = Ls + Cfg::TILE;                  // L[b][a]
+  T* Fs = LT + Cfg::TILE;                  // F[a'][b']
+  T* FT = Fs + Cfg::TILE;                  // F[b'][a']
+  T* GyS = FT + Cfg::TILE;                 // Gy_i[b][b']
+  T* GyT = GyS + Cfg::TILE;                // Gy_i[b'][b]
+  T* Gx = GyT + Cfg::TILE;                 // Gx_i[a][a'] (forward) or [a'][a] (backward)
+  T* X1 = Gx + Cfg::TILE;                  // U^T, W^T, partial sums
+  T* Wn = X1 + Cfg::TILE;                  // W[a][b'] / T[a][b']
+  T* Rs = Wn + Cfg::TILE;                  // reduced rows (RM/2 x LD)
+  int* ired = reinterpret_cast<int*>(Rs + (RM / 2) * LD);
+
+  const bool cl = p.cluster > 1;
+  int C = 1, crank = 0;
+  if (cl) {
+    cg::cluster_group cluster = cg::this_cluster();
+    C = static_cast<int>(cluster.num_blocks());
+    crank = static_cast<int>(cluster.block_rank());
+  }
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  const int u0 = ty * TM, v0 = tx * TM;
+  const int n = p.n;
+  const int c = p.stride;
+  int bad = 0, sbits = 0;
+  T* ckpt = static_cast<T*>(p.ckpt);
+  T* seg = static_cast<T*>(p.seg);
+  const int64_t env_elems = p.env_elems;
+
+  // One forward step L_{k+1} = sum_i Gx_i^T (L_k Gy_i); L in Ls/LT, result back in Ls/LT.
+  auto forward = [&](int k, int64_t& lg) {
+    const AdjStep& st = p.step[k];
+    T pacc[TM][TM];
+    zero<T, TM>(pacc);
+    for (int i = crank; i < st.I; i += C) {
+      __syncthreads();
+      slice_async<T, LD, NT>(GyS, static_cast<const T*>(st.gy), i, st.I, st.ry, st.ry2, 0);
+      slice_async<T, LD, NT>(Gx, static_cast<const T*>(st.gx), i, st.I, st.rx, st.rx2, 0);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      T t[TM][TM];
+      zero<T, TM>(t);
+      if (u0 < st.rx && v0 < st.ry2) op_acc<T, TM, LD>(t, LT, GyS, st.ry, u0, v0);  // T[a][b'] = L Gy_i
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) Wn[(u0 + a) * LD + v0 + b] = t[a][b];
+      __syncthreads();
+      if (u0 < st.rx2 && v0 < st.ry2) op_acc<T, TM, LD>(pacc, Gx, Wn, st.rx, u0, v0);  // P[a'][b'] += Gx_i^T T
+    }
+    lg += reduce_env<T, RM>(pacc, u0, v0, st.rx2, st.ry2, X1, Rs, Ls, LT, ired, C, crank, p.renorm_bits, bad);
+  };
+
+  // ---- phase 1: forward sweep storing checkpoints L_{jc} ----
+  int64_t lg = 0;
+  {
+    const int rx0 = p.step[0].rx, ry0 = p.step[0].ry;
+    if (p.l_seed != nullptr) {
+      load_env<T, LD, NT>(static_cast<const T*>(p.l_seed), rx0, ry0, Ls, LT);
+      if (p.l_seed_log2 != nullptr) lg = *p.l_seed_log2;
+    } else if (tid == 0) {
+      Ls[0] = T(1);
+      LT[0] = T(1);
+    }
+    __syncthreads();
+  }
+  const int nseg = (n + c - 1) / c;
+  const int last_ck = (nseg - 1) * c;
+  for (int k = 0; k <= last_ck; ++k) {
+    if (k % c == 0 && crank == 0) {
+      store_env<T, LD, NT>(ckpt + (k / c) * env_elems, p.step[k].rx, p.step[k].ry, Ls);
+      if (tid == 0) p.ckpt_log2[k / c] = lg;
+    }
+    if (k < last_ck) forward(k, lg);
+  }
+  __threadfence();
+  if (cl) cg::this_cluster().sync();
+  else __syncthreads();
+
+  // ---- phase 2: backward walk, segment by segment from the right ----
+  int64_t fl = 0;
+  {
+    const int rxn = p.step[n - 1].rx2, ryn = p.step[n - 1].ry2;
+    if (p.f_seed != nullptr) {
+      load_env<T, LD, NT>(static_cast<const T*>(p.f_seed), rxn, ryn, Fs, FT);
+      if (p.f_seed_log2 != nullptr) fl = *p.f_seed_log2;
+    } else if (tid == 0) {
+      Fs[0] = T(1);
+      FT[0] = T(1);
+    }
+  }
+  const double gbar = p.cot != nullptr ? *p.cot : 1.0;
+  for (int g = nseg - 1; g >= 0; --g) {
+    const int k0 = g * c, k1 = min(n, k0 + c);
+    // recompute L_{k0..k1-1} from the checkpoint into the segment buffer
+    __syncthreads();
+    load_env<T, LD, NT>(ckpt + g * env_elems, p.step[k0].rx, p.step[k0].ry, Ls, LT);
+    int64_t l = p.ckpt_log2[g];
+    __syncthreads();
+    if (crank == 0) {
+      store_env<T, LD, NT>(seg, p.step[k0].rx, p.step[k0].ry, Ls);
+      if (tid == 0) p.seg_log2[0] = l;
+    }
+    for (int k = k0; k + 1 < k1; ++k) {
+      forward(k, l);
+      if (crank == 0) {
+        store_env<T, LD, NT>(seg + (k + 1 - k0) * env_elems, p.step[k + 1].rx, p.step[k + 1].ry, Ls);
+        if (tid == 0) p.seg_log2[k + 1 - k0] = l;
+      }
+    }
+    __threadfence();
+    if (cl) cg::this_cluster().sync();
+    else __syncthreads();
+    // walk the segment backwards
+    for (int k = k1 - 1; k >= k0; --k) {
+      const AdjStep& st = p.step[k];
+      __syncthreads();
+      load_env<T, LD, NT>(seg + (k - k0) * env_elems, st.rx, st.ry, Ls, LT);
+      const int64_t lk = p.seg_log2[k - k0];
+      // gradient scale: gbar * 2^(lk + fl)
+      int64_t esum = lk + fl;
+      esum = esum < -4000 ? -4000 : (esum > 4000 ? 4000 : esum);
+      const double fac = ldexp(gbar, static_cast<int>(esum));
+      T facc[TM][TM];
+      zero<T, TM>(facc);
+      T* dgx = static_cast<T*>(st.dgx);
+      T* dgy = static_cast<T*>(st.dgy);
+      for (int i = crank; i < st.I; i += C) {
+        __syncthreads();
+        slice_async<T, LD, NT>(GyS, static_cast<const T*>(st.gy), i, st.I, st.ry, st.ry2, 0);   // [b][b']
+        slice_async<T, LD, NT>(GyT, static_cast<const T*>(st.gy), i, st.I, st.ry2, st.ry, 1);   // [b'][b]
+        slice_async<T, LD, NT>(Gx, static_cast<const T*>(st.gx), i, st.I, st.rx2, st.rx, 1);    // [a'][a]
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        T t[TM][TM];
+        // U[a][b'] = L Gy_i  -> X1 as U^T[b'][a]
+        zero<T, TM>(t);
+        if (u0 < st.rx && v0 < st.ry2) op_acc<T, TM, LD>(t, LT, GyS, st.ry, u0, v0);
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TM; ++b) X1[(v0 + b) * LD + u0 + a] = t[a][b];
+        __syncthreads();
+        // dGx[a][a'] = U F^T : A = U^T[b'][a], B = F^T[b'][a']
+        zero<T, TM>(t);
+        if (u0 < st.rx && v0 < st.rx2) op_acc<T, TM, LD>(t, X1, FT, st.ry2, u0, v0);
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TM; ++b)
+            if (u0 + a < st.rx && v0 + b < st.rx2) {
+              const double v = static_cast<double>(t[a][b]) * fac;
+              const T o = static_cast<T>(v);
+              if (!isfinite(o)) sbits |= isfinite(v) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+              dgx[(static_cast<int64_t>(u0 + a) * st.I + i) * st.rx2 + v0 + b] = o;
+            }
+        // W[a][b'] = Gx_i F : A = Gx^T[a'][a], B = F[a'][b']
+        zero<T, TM>(t);
+        if (u0 < st.rx && v0 < st.ry2) op_acc<T, TM, LD>(t, Gx, Fs, st.rx2, u0, v0);
+        __syncthreads();  // X1 (U^T) is read by everyone before it becomes W^T
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TM; ++b) {
+            Wn[(u0 + a) * LD + v0 + b] = t[a][b];
+            X1[(v0 + b) * LD + u0 + a] = t[a][b];
+          }
+        __syncthreads();
+        // dGy[b][b'] = L^T W : A = L[a][b], B = W[a][b']
+        zero<T, TM>(t);
+        if (u0 < st.ry && v0 < st.ry2) op_acc<T, TM, LD>(t, Ls, Wn, st.rx, u0, v0);
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TM; ++b)
+            if (u0 + a < st.ry && v0 + b < st.ry2) {
+              const double v = static_cast<double>(t[a][b]) * fac;
+              const T o = static_cast<T>(v);
+              if (!isfinite(o)) sbits |= isfinite(v) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+              dgy[(static_cast<int64_t>(u0 + a) * st.I + i) * st.ry2 + v0 + b] = o;
+            }
+        // F_k[a][b] += W Gy_i^T : A = W^T[b'][a], B = Gy^T[b'][b]
+        if (u0 < st.rx && v0 < st.ry) op_acc<T, TM, LD>(facc, X1, GyT, st.ry2, u0, v0);
+      }
+      if (k > 0 || p.need_f0) fl += reduce_env<T, RM>(facc, u0, v0, st.rx, st.ry, X1, Rs, Fs, FT, ired, C, crank,
+                                                      p.renorm_bits, bad);
+    }
+  }
+  if (sbits) set_status(p.status, sbits);
+  if (bad && tid == 0 && crank == 0) set_status(p.status, TT_STATUS_NONFINITE);
+  if (cl) cg::this_cluster().sync();
+}
+
+// ---------------------------------------------------------------------------
+// Chain-layout partial contraction: cotangents of the emitted cores -> the
+// gradient of the boundary core, the cotangent dK of the environment K, and
+// the gradients of the free cores (plain or leg-swapped copies).
+//   lead : C[u][i][y] = sum_a Gx[a][i][u] K[a][y]
+//          dGx[a][i][u] = sum_y K[a][y] dC[u][i][y],  dK[a][y] = sum_{u,i} Gx[a][i][u] dC[u][i][y]
+//   trail: C[u][i][y] = sum_b Gx[u][i][b] K[b][y]
+//          dGx[u][i][b] = sum_y dC[u][i][y] K[b][y],  dK[b][y] = sum_{u,i} Gx[u][i][b] dC[u][i][y]
+// Blocks 0..I-1 compute the gradient slice i; block I computes dK; every
+// block then helps with the copies.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) chain_adjoint_kernel(const __grid_constant__ ChainAdjParams p) {
+  const int i = blockIdx.x;
+  const T* gx = static_cast<const T*>(p.gx);
+  const T* k = static_cast<const T*>(p.k);
+  const T* dc = static_cast<const T*>(p.dc);
+  const int64_t klg = p.k_log2 != nullptr ? *p.k_log2 : 0;
+  const int ra = p.ra, rb = p.rb, I = p.I, ry = p.ry;
+  int bits = 0;
+  if (i < I) {
+    T* dg = static_cast<T*>(p.dgx);
+    if (p.lead) {
+      for (int idx = threadIdx.x; idx < ra * rb; idx += blockDim.x) {
+        const int a = idx / rb, u = idx - a * rb;
+        T s = T(0);
+        for (int y = 0; y < ry; ++y) s = fma(k[a * ry + y], dc[(static_cast<int64_t>(u) * I + i) * ry + y], s);
+        const T o = scale_pow2_sat<T>(s, klg);
+        if (!isfinite(o)) bits |= isfinite(s) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+        dg[(static_cast<int64_t>(a) * I + i) * rb + u] = o;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < ra * rb; idx += blockDim.x) {
+        const int u = idx / rb, b = idx - u * rb;
+        T s = T(0);
+        for (int y = 0; y < ry; ++y) s = fma(dc[(static_cast<int64_t>(u) * I + i) * ry + y], k[b * ry + y], s);
+        const T o = scale_pow2_sat<T>(s, klg);
+        if (!isfinite(o)) bits |= isfinite(s) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+        dg[(static_cast<int64_t>(u) * I + i) * rb + b] = o;
+      }
+    }
+  } else if (i == I && p.dk != nullptr) {
+    T* dk = static_cast<T*>(p.dk);
+    const int nk = p.lead ? ra : rb;
+    for (int idx = threadIdx.x; idx < nk * ry; idx += blockDim.x) {
+      const int a = idx / ry, y = idx - a * ry;
+      T s = T(0);
+      for (int ii = 0; ii < I; ++ii) {
+        if (p.lead) {
+          for (int u = 0; u < rb; ++u)
+            s = fma(gx[(static_cast<int64_t>(a) * I + ii) * rb + u], dc[(static_cast<int64_t>(u) * I + ii) * ry + y], s);
+        } else {
+          for (int u = 0; u < ra; ++u)
+            s = fma(gx[(static_cast<int64_t>(u) * I + ii) * rb + a], dc[(static_cast<int64_t>(u) * I + ii) * ry + y], s);
+        }
+      }
+      dk[idx] = s;
+    }
+  }
+  // copies: grid-stride over all blocks
+  const int64_t g0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int t = 0; t < p.n_copies; ++t) {
+    const CopyTask& tk = p.copy[t];
+    const T* src = static_cast<const T*>(tk.src);
+    T* dst = static_cast<T*>(tk.dst);
+    const int64_t nn = static_cast<int64_t>(tk.r0) * tk.I * tk.r1;
+    if (!tk.swap) {
+      for (int64_t e = g0; e < nn; e += gs) dst[e] = src[e];
+    } else {
+      for (int64_t e = g0; e < nn; e += gs) {
+        const int64_t c0 = e % tk.r0, rest = e / tk.r0;
+        const int64_t ii = rest % tk.I, c1 = rest / tk.I;
+        dst[e] = src[(c0 * tk.I + ii) * tk.r1 + c1];
+      }
+    }
+  }
+  if (bits) set_status(p.status, bits);
+}
+
+template <typename T, int RM>
+static cudaError_t adjoint_launch_impl(const AdjointParams& p, cudaStream_t s) {
+  const size_t smem = AdjCfg<T, RM>::SMEM;
+  cudaError_t err =
+      cudaFuncSetAttribute(adjoint_kernel<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(adjoint_kernel<T, RM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err != cudaSuccess) return err;
+  int C = p.cluster;
+  // the largest cluster (<= requested) that can be resident
+  for (; C >= 2; C /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nact = 0;
+    if (cudaOccupancyMaxActiveClusters(&nact, adjoint_kernel<T, RM>, &cfg) == cudaSuccess && nact >= 1) break;
+    cudaGetLastError();
+  }
+  AdjointParams q = p;
+  q.cluster = C < 1 ? 1 : C;
+  count_launch();
+  if (q.cluster == 1) {
+    adjoint_kernel<T, RM><<<1, 256, smem, s>>>(q);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(q.cluster, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = q.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, adjoint_kernel<T, RM>, q);
+}
+
+cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStream_t s) {
+  if (dtype == TT_F64) {
+    if (rmax <= 16) return adjoint_launch_impl<double, 16>(p, s);
+    return adjoint_launch_impl<double, 32>(p, s);
+  }
+  if (rmax <= 32) return adjoint_launch_impl<float, 32>(p, s);
+  return adjoint_launch_impl<float, 64>(p, s);
+}
+
+cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s) {
+  count_launch();
+  if (dtype == TT_F64) chain_adjoint_kernel<double><<<p.I + 1, 256, 0, s>>>(p);
+  else chain_adjoint_kernel<float><<<p.I + 1, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace ttc

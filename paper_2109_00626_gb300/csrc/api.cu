@@ -53,8 +53,14 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
     *bytes = 0;  // the environment K stays in shared memory
     return TT_OK;
   }
-  (void)prec;
-  return TT_ERR_UNSUPPORTED;
+  if (op == TT_OP_BACKWARD) {
+    BackwardPlan bp;
+    const int rc = backward_plan(x, y, mask, layout, prec, 0, &bp);
+    if (rc != TT_OK) return rc;
+    *bytes = bp.ws_bytes;
+    return TT_OK;
+  }
+  return TT_ERR_ARG;
 }
 
 int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_dev, int64_t* out_log2_dev,
@@ -137,21 +143,135 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
 int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
                          const double* cot_dev, const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
                          int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
-  (void)x;
-  (void)y;
-  (void)mask;
-  (void)layout;
-  (void)prec;
-  (void)cot_dev;
-  (void)dz;
-  (void)gx;
-  (void)gy;
-  (void)ckpt_stride;
-  (void)status_dev;
-  (void)ws;
-  (void)ws_bytes;
-  (void)stream;
-  return TT_ERR_UNSUPPORTED;
+  BackwardPlan bp;
+  int rc = backward_plan(x, y, mask, layout, prec, ckpt_stride, &bp);
+  if (rc != TT_OK) return rc;
+  rc = check_same_shape(x, gx);
+  if (rc == TT_OK) rc = check_same_shape(y, gy);
+  if (rc != TT_OK) return rc;
+  if (ws_bytes < bp.ws_bytes || (bp.ws_bytes > 0 && ws == nullptr)) return TT_ERR_WS;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const int eb = elem_bytes(x->dtype);
+  const int n = x->order;
+
+  AdjointParams ap;
+  memset(&ap, 0, sizeof(ap));
+  ap.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+  ap.status = status_dev;
+  ap.env_elems = bp.env_elems;
+  ap.ckpt = w + bp.off_ckpt;
+  ap.seg = w + bp.off_seg;
+  ap.ckpt_log2 = reinterpret_cast<int64_t*>(w + bp.off_ckpt_log2);
+  ap.seg_log2 = reinterpret_cast<int64_t*>(w + bp.off_seg_log2);
+  auto fill_block = [&](int k0, int k1) {
+    ap.n = k1 - k0;
+    ap.stride = bp.stride_for(ap.n);
+    int mi = 1;
+    for (int j = 0; j < ap.n; ++j) {
+      const int k = k0 + j;
+      AdjStep& st = ap.step[j];
+      st.gx = x->cores[k];
+      st.gy = y->cores[k];
+      st.dgx = gx->cores[k];
+      st.dgy = gy->cores[k];
+      st.I = x->modes[k];
+      st.rx = x->ranks[k];
+      st.rx2 = x->ranks[k + 1];
+      st.ry = y->ranks[k];
+      st.ry2 = y->ranks[k + 1];
+      mi = std::max(mi, st.I);
+    }
+    ap.cluster = pow2_floor(std::min(16, mi));
+  };
+
+  if (mask == nullptr) {
+    if (cot_dev == nullptr) return TT_ERR_ARG;
+    fill_block(0, n);
+    ap.cot = cot_dev;
+    return launch_adjoint(ap, x->dtype, bp.rmax, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
+
+  const ChainPlan& cp = bp.cp;
+  rc = check_chain_output(x, cp, dz);
+  if (rc != TT_OK) return rc;
+  const int m = cp.m, sS = cp.s;
+  void* kbuf = w + bp.off_k;
+  int64_t* klog2 = reinterpret_cast<int64_t*>(w + bp.off_klog2);
+  void* dkbuf = w + bp.off_dk;
+
+  // 1. K again (the environment over the contracted block)
+  {
+    SweepParams p;
+    memset(&p, 0, sizeof(p));
+    if (sS > 0) {
+      if (cp.side == 0) fill_left(p, x, y, 0, sS);
+      else fill_right(p, x, y, m, n);
+    }
+    p.rx0 = 1;
+    p.ry0 = 1;
+    p.renorm_bits = ap.renorm_bits;
+    p.e_out = kbuf;
+    p.e_out_log2 = klog2;
+    p.status = status_dev;
+    rc = launch_sweep(p, x->dtype, s);
+    if (rc != TT_OK) return rc;
+  }
+  // 2. boundary-core gradient, dK, free-core gradients
+  ChainAdjParams cap;
+  memset(&cap, 0, sizeof(cap));
+  const int kb = cp.side == 0 ? sS : m - 1;
+  cap.gx = x->cores[kb];
+  cap.ra = x->ranks[kb];
+  cap.I = x->modes[kb];
+  cap.rb = x->ranks[kb + 1];
+  cap.lead = cp.side == 0 ? 1 : 0;
+  cap.ry = cp.ky;
+  cap.k = kbuf;
+  cap.k_log2 = klog2;
+  cap.dc = dz->cores[m - 1];
+  cap.dgx = gx->cores[kb];
+  cap.dk = sS > 0 ? dkbuf : nullptr;
+  cap.status = status_dev;
+  auto add = [&](const void* src, void* dst, int r0, int I, int r1, int swap) {
+    CopyTask& t = cap.copy[cap.n_copies++];
+    t.src = src;
+    t.dst = dst;
+    t.r0 = r0;
+    t.I = I;
+    t.r1 = r1;
+    t.swap = swap;
+  };
+  if (cp.side == 0) {
+    for (int q = 0; q < m - 1; ++q) {
+      const int k = n - 1 - q;  // dz[q] is [R_{k+1}][I_k][R_k]
+      add(dz->cores[q], gx->cores[k], x->ranks[k + 1], x->modes[k], x->ranks[k], 1);
+    }
+    for (int q = 0; q < m; ++q) {
+      const int k = sS + q;
+      add(dz->cores[m + q], gy->cores[k], y->ranks[k], y->modes[k], y->ranks[k + 1], 0);
+    }
+  } else {
+    for (int q = 0; q < m - 1; ++q) add(dz->cores[q], gx->cores[q], x->ranks[q], x->modes[q], x->ranks[q + 1], 0);
+    for (int q = 0; q < m; ++q) {
+      const int k = m - 1 - q;  // dz[m+q] is [R^y_{k+1}][I_k][R^y_k]
+      add(dz->cores[m + q], gy->cores[k], y->ranks[k + 1], y->modes[k], y->ranks[k], 1);
+    }
+  }
+  if (launch_chain_adjoint(cap, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+  (void)eb;
+  // 3. adjoint of the sweep over the contracted block, seeded with dK
+  if (sS > 0) {
+    if (cp.side == 0) {
+      fill_block(0, sS);
+      ap.f_seed = dkbuf;
+    } else {
+      fill_block(m, n);
+      ap.l_seed = dkbuf;
+    }
+    if (launch_adjoint(ap, x->dtype, bp.rmax, s) != cudaSuccess) return TT_ERR_CUDA;
+  }
+  return TT_OK;
 }
 
 }  // extern "C"

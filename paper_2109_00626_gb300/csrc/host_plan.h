@@ -286,6 +286,84 @@ inline void build_full(const tt_desc* x, const tt_desc* y, double* out_dev, int6
   p.status = status_dev;
 }
 
+inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
+  const int rc = check_desc(g);
+  if (rc != TT_OK) return rc;
+  if (g->order != a->order || g->dtype != a->dtype) return TT_ERR_SHAPE;
+  for (int k = 0; k < a->order; ++k)
+    if (g->modes[k] != a->modes[k] || g->ranks[k] != a->ranks[k]) return TT_ERR_SHAPE;
+  return TT_OK;
+}
+
+inline int isqrt_ceil(int n) {
+  int c = 1;
+  while (c * c < n) ++c;
+  return c;
+}
+
+// Workspace layout of tt_contract_backward.
+struct BackwardPlan {
+  ChainPlan cp;
+  int partial = 0;
+  int rmax = 1;
+  int user_stride = 0;
+  int64_t env_elems = 1;
+  size_t off_k = 0, off_klog2 = 0, off_dk = 0, off_ckpt = 0, off_seg = 0, off_ckpt_log2 = 0, off_seg_log2 = 0;
+  size_t ws_bytes = 0;
+  int stride_for(int nmodes) const {
+    int c = user_stride > 0 ? user_stride : isqrt_ceil(nmodes);
+    return std::max(1, std::min(c, nmodes));
+  }
+};
+
+inline int adjoint_rank_cap(int dtype) { return dtype == TT_F64 ? 32 : 64; }
+
+inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec, int stride,
+                         BackwardPlan* bp) {
+  int rc = check_pair(x, y, mask);
+  if (rc != TT_OK) return rc;
+  if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+  if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
+  if (stride < 0) return TT_ERR_ARG;
+  const int n = x->order;
+  bp->user_stride = stride;
+  bp->partial = mask != nullptr;
+  int nblock = n;
+  if (mask != nullptr) {
+    if (layout != TT_LAYOUT_CHAIN) return TT_ERR_UNSUPPORTED;
+    rc = chain_plan(x, y, mask, &bp->cp);
+    if (rc != TT_OK) return rc;
+    nblock = std::max(1, bp->cp.s);
+  }
+  const int rmax = std::max(max_rank(x), max_rank(y));
+  bp->rmax = rmax;
+  if (rmax > adjoint_rank_cap(x->dtype) && (mask == nullptr || bp->cp.s > 0)) return TT_ERR_TOO_LARGE;
+  if (mask != nullptr && rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
+  const int eb = elem_bytes(x->dtype);
+  bp->env_elems = static_cast<int64_t>(max_rank(x)) * max_rank(y);
+  const int c = bp->stride_for(nblock);
+  const int nseg = (nblock + c - 1) / c;
+  size_t off = 0;
+  if (mask != nullptr) {
+    bp->off_k = off;
+    off += align256(static_cast<size_t>(bp->cp.kx) * bp->cp.ky * eb);
+    bp->off_klog2 = off;
+    off += 256;
+    bp->off_dk = off;
+    off += align256(static_cast<size_t>(bp->cp.kx) * bp->cp.ky * eb);
+  }
+  bp->off_ckpt = off;
+  off += align256(static_cast<size_t>(nseg) * bp->env_elems * eb);
+  bp->off_seg = off;
+  off += align256(static_cast<size_t>(c) * bp->env_elems * eb);
+  bp->off_ckpt_log2 = off;
+  off += align256(sizeof(int64_t) * nseg);
+  bp->off_seg_log2 = off;
+  off += align256(sizeof(int64_t) * c);
+  bp->ws_bytes = off;
+  return TT_OK;
+}
+
 // Flops of one contracted mode, the cheaper of the two evaluation orders.
 inline double mode_flops(int rx, int rx2, int ry, int ry2, int I) {
   const double a = double(rx) * ry * I * ry2 + double(rx) * I * rx2 * ry2;

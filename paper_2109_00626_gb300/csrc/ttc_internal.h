@@ -73,7 +73,56 @@ struct SweepParams {
   EmitParams emit;        // fused chain emission after the sweep (partial contractions)
 };
 
+// One mode of an adjoint block (left-to-right orientation): core k of X is
+// [rx][I][rx2], of Y [ry][I][ry2]; dgx / dgy receive the gradients.
+struct AdjStep {
+  const void* gx;
+  const void* gy;
+  void* dgx;
+  void* dgy;
+  int I, rx, rx2, ry, ry2;
+};
+
+struct AdjointParams {
+  int n;                 // modes in the block
+  int stride;            // checkpoint stride c
+  int cluster;           // requested cluster size
+  int renorm_bits;
+  int need_f0;           // 1 = also reduce the right environment left of the block
+  AdjStep step[kMaxOrder];
+  const void* l_seed;    // optional left seed [rx(0)][ry(0)] (NULL = [1])
+  const int64_t* l_seed_log2;
+  const void* f_seed;    // optional right seed [rx2(n-1)][ry2(n-1)] (NULL = [1])
+  const int64_t* f_seed_log2;
+  const double* cot;     // optional scalar multiplier (device)
+  void* ckpt;            // ceil(n/c) environments
+  int64_t* ckpt_log2;
+  void* seg;             // c environments
+  int64_t* seg_log2;
+  int64_t env_elems;     // elements per stored environment
+  int32_t* status;
+};
+
+// Cotangents of a chain-layout output -> boundary-core gradient, dK and the
+// free-core gradients (see adjoint.cu).
+struct ChainAdjParams {
+  const void* gx;
+  int ra, I, rb;
+  int lead;
+  int ry;
+  const void* k;
+  const int64_t* k_log2;
+  const void* dc;
+  void* dgx;
+  void* dk;  // NULL when the contracted block is empty
+  int n_copies;
+  CopyTask copy[kMaxCopies];
+  int32_t* status;
+};
+
 // Launchers (return cudaError_t of the launch).
+cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStream_t s);
+cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 

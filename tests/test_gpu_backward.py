@@ -1,0 +1,145 @@
+"""GPU parity of the hand-written adjoint (tt_contract_backward) against the
+oracle's gradients, against central finite differences of the GPU forward in
+float64, and through torch.autograd (TTFull / TTPartial)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import to_dev, to_host
+from paper_2109_00626_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2109_00626_gb300 as T  # noqa: E402
+
+
+def _rel(got, want):
+    """max |got - want| over all cores / max |want| over all cores."""
+    num = max(float(np.abs(g - w).max()) for g, w in zip(got, want))
+    den = max(float(np.abs(w).max()) for w in want)
+    return num / den
+
+
+def test_full_grad_fd_fp64():
+    """Finite-difference size: order 5, mode 4, ranks 3, float64.  z is linear
+    in every core, so central differences of the GPU forward are exact up to
+    rounding for any step; h = 1."""
+    x, y = G.pair(5, [4] * 5, G.tt_ranks(5, 3), G.tt_ranks(5, 3), np.float64)
+    xd, yd = to_dev(x), to_dev(y)
+    cot = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+    gx, gy, st = T.backward(xd, yd, None, cot=cot)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    gxh, gyh = to_host(gx), to_host(gy)
+    wx, wy = O.grad_full(x, y)
+    assert _rel(gxh + gyh, wx + wy) <= 1e-12
+
+    def z_of(xc, yc):
+        op = T.FullContraction(xc, yc)
+        op()
+        return float(op.out.item())
+
+    for k in range(5):
+        for side in (0, 1):
+            cores = xd if side == 0 else yd
+            grad = gxh[k] if side == 0 else gyh[k]
+            fd = np.zeros_like(grad)
+            base = cores[k].clone()
+            for idx in np.ndindex(*grad.shape):
+                for sgn in (+1, -1):
+                    cores[k] = base.clone()
+                    cores[k][idx] += sgn * 1.0
+                    val = z_of(xd, yd)
+                    fd[idx] += sgn * val / 2.0
+            cores[k] = base
+            assert np.abs(fd - grad).max() <= 1e-12 * max(1.0, np.abs(grad).max())
+
+
+def test_full_grad_cotangent_scaling_and_euler():
+    x, y = G.pair(6, [6, 3, 5, 4], [1, 5, 7, 3, 1], [1, 2, 9, 4, 1], np.float64)
+    xd, yd = to_dev(x), to_dev(y)
+    cot = torch.tensor([-2.5], dtype=torch.float64, device="cuda")
+    gx, gy, _ = T.backward(xd, yd, None, cot=cot)
+    torch.cuda.synchronize()
+    z = O.contract_full(x, y)
+    for g, c in zip(to_host(gx) + to_host(gy), x + y):
+        # Euler: <G_k, dz/dG_k> = z for every core
+        assert abs(np.sum(g * c) / -2.5 - z) <= 1e-12 * max(1.0, abs(z))
+
+
+@pytest.mark.parametrize("stride", [1, 2, 3, 10])
+def test_full_grad_order10_fp32_checkpoint_strides(stride):
+    x, y = G.order10_r64(0)
+    xd, yd = to_dev(x), to_dev(y)
+    cot = torch.tensor([1.0], dtype=torch.float64, device="cuda")
+    gx, gy, st = T.backward(xd, yd, None, cot=cot, ckpt_stride=stride)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    wx, wy = O.grad_full(x, y)
+    assert _rel(to_host(gx) + to_host(gy), wx + wy) <= 2e-5
+
+
+def _sum_cotangents(zc):
+    """Cotangents of the output cores for loss = sum of all entries of Z."""
+    ones = [np.ones((1, c.shape[1], 1)) for c in zc]
+    dz, _ = O.grad_full(zc, ones)
+    return dz
+
+
+@pytest.mark.parametrize("mask", [[1, 1, 1, 0, 0], [0, 0, 1, 1, 1], [1, 0, 0, 0, 0], [0, 0, 0, 0, 0]])
+def test_partial_grad_fp64(mask):
+    rng = np.random.default_rng(sum(mask) * 3 + mask[0])
+    modes = [3, 4, 2, 3, 2]
+    x = G.random_tt(rng, modes, [1, 2, 3, 4, 2, 1], np.float64)
+    y = G.random_tt(rng, modes, [1, 3, 2, 2, 3, 1], np.float64)
+    zc, _ = O.partial_chain(x, y, mask)
+    dz = [rng.standard_normal(c.shape) for c in zc]
+    gx, gy, st = T.backward(to_dev(x), to_dev(y), mask, dz=to_dev(dz))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    wx, wy = O.grad_partial_chain(x, y, mask, dz)
+    assert _rel(to_host(gx) + to_host(gy), wx + wy) <= 1e-12
+
+
+def test_partial_grad_order12_sum_fp32():
+    """Loss = sum of the partial contraction over modes 1-8 of the order-12,
+    mode 16, rank 64 pair; gradients for all 24 cores."""
+    x, y = G.order12_r64(0)
+    mask = [1] * 8 + [0] * 4
+    zc, _ = O.partial_chain(x, y, mask)
+    dz = _sum_cotangents(zc)
+    gx, gy, st = T.backward(to_dev(x), to_dev(y), mask, dz=to_dev(dz, torch.float32))
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    wx, wy = O.grad_partial_chain(x, y, mask, dz)
+    assert _rel(to_host(gx) + to_host(gy), wx + wy) <= 2e-5
+
+
+def test_autograd_sum_of_partial_fp32():
+    """torch.autograd through TTPartial and TTFull: loss = sum(Z)."""
+    x, y = G.order12_r64(1)
+    mask = [1] * 8 + [0] * 4
+    xd = [c.requires_grad_(True) for c in to_dev(x)]
+    yd = [c.requires_grad_(True) for c in to_dev(y)]
+    zc = T.tt_partial(xd, yd, mask)
+    loss = T.tt_sum(zc)
+    loss.backward()
+    zo, _ = O.partial_chain(x, y, mask)
+    ones = [np.ones((1, c.shape[1], 1)) for c in zo]
+    want_loss = O.contract_full(zo, ones)
+    assert abs(float(loss.detach()) - want_loss) <= 1e-5 * max(1.0, abs(want_loss))
+    dz = _sum_cotangents(zo)
+    wx, wy = O.grad_partial_chain(x, y, mask, dz)
+    got = [c.grad.detach().cpu().double().numpy() for c in xd + yd]
+    assert _rel(got, wx + wy) <= 2e-5
+
+
+def test_autograd_gradcheck_full_fp64():
+    x, y = G.pair(8, [3, 2, 3], [1, 2, 2, 1], [1, 3, 2, 1], np.float64)
+    xd = [c.requires_grad_(True) for c in to_dev(x)]
+    yd = [c.requires_grad_(True) for c in to_dev(y)]
+    assert torch.autograd.gradcheck(lambda *c: T.tt_full(list(c[:3]), list(c[3:])), (*xd, *yd), eps=1e-6, atol=1e-9)
