@@ -15,6 +15,92 @@ std::atomic<uint64_t> g_launches{0};
 
 using namespace ttc;
 
+namespace ttc {
+
+static int contract_merged(const tt_desc* x, const tt_desc* y, const uint8_t* mask, const tt_desc* z,
+                           int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+  MergedPlan mp;
+  int rc = merged_plan(x, y, mask, &mp);
+  if (rc != TT_OK) return rc;
+  rc = check_desc(z);
+  if (rc != TT_OK) return rc;
+  if (z->order != mp.m || z->dtype != x->dtype) return TT_ERR_SHAPE;
+  {
+    int32_t order = 0, modes[2 * kMaxOrder], ranks[2 * kMaxOrder + 1], perm[2 * kMaxOrder];
+    rc = tt_partial_shape(x, y, mask, TT_LAYOUT_MERGED, &order, modes, ranks, perm);
+    if (rc != TT_OK) return rc;
+    for (int t = 0; t < order; ++t)
+      if (z->modes[t] != modes[t] || z->ranks[t] != ranks[t]) return TT_ERR_SHAPE;
+  }
+  if (ws_bytes < mp.ws_bytes || ws == nullptr) return TT_ERR_WS;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const int eb = elem_bytes(x->dtype);
+  const int f0 = mp.free_pos[0];
+  // 1. left environment of the contracted modes before f_0 (E_L = [1] when none)
+  {
+    SweepParams p;
+    memset(&p, 0, sizeof(p));
+    if (f0 > 0) fill_left(p, x, y, 0, f0);
+    p.rx0 = 1;
+    p.ry0 = 1;
+    p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+    p.e_out = w + mp.off_el;
+    p.e_out_log2 = reinterpret_cast<int64_t*>(w + mp.off_ellog2);
+    p.status = status_dev;
+    rc = launch_sweep(p, x->dtype, s);
+    if (rc != TT_OK) return rc;
+  }
+  for (int t = 0; t < mp.m; ++t) {
+    const int f = mp.free_pos[t];
+    const bool run = mp.run_k1[t] > mp.run_k0[t];
+    void* dest = run ? static_cast<void*>(w + mp.off_pre) : z->cores[t];
+    KronParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.gx = x->cores[f];
+    kp.gy = y->cores[f];
+    kp.rx = x->ranks[f];
+    kp.ry = y->ranks[f];
+    kp.I = x->modes[f];
+    kp.J = y->modes[f];
+    kp.rx2 = x->ranks[f + 1];
+    kp.ry2 = y->ranks[f + 1];
+    kp.out = dest;
+    kp.status = status_dev;
+    if (t == 0) {
+      kp.el = w + mp.off_el;
+      kp.el_log2 = reinterpret_cast<int64_t*>(w + mp.off_ellog2);
+      kp.tmp = w + mp.off_v;
+      if (launch_kron(kp, 1, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+      if (launch_kron(kp, 2, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    } else {
+      if (launch_kron(kp, 0, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    }
+    if (run) {
+      SweepParams p;
+      memset(&p, 0, sizeof(p));
+      fill_left(p, x, y, mp.run_k0[t], mp.run_k1[t]);
+      p.rx0 = x->ranks[f + 1];
+      p.ry0 = y->ranks[f + 1];
+      p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+      p.status = status_dev;
+      const int nxt = mp.run_k1[t];
+      const int64_t r_next = t + 1 < mp.m ? static_cast<int64_t>(x->ranks[nxt]) * y->ranks[nxt] : 1;
+      RowIO io;
+      io.in = dest;
+      io.in_stride_bytes = mp.pre_cols[t] * eb;
+      io.out = z->cores[t];
+      io.out_stride_bytes = r_next * eb;
+      io.n_rows = mp.rows[t];
+      if (launch_rows_sweep(p, io, x->dtype, mp.rmax, s) != cudaSuccess) return TT_ERR_CUDA;
+    }
+  }
+  if (z_log2_dev != nullptr && cudaMemsetAsync(z_log2_dev, 0, sizeof(int64_t), s) != cudaSuccess) return TT_ERR_CUDA;
+  return TT_OK;
+}
+
+}  // namespace ttc
+
 extern "C" {
 
 const char* tt_error_string(int code) {
@@ -46,7 +132,14 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
     if (mask == nullptr) return TT_ERR_ARG;
     int rc = check_pair(x, y, mask);
     if (rc != TT_OK) return rc;
-    if (layout != TT_LAYOUT_CHAIN) return TT_ERR_UNSUPPORTED;
+    if (layout == TT_LAYOUT_MERGED) {
+      MergedPlan mp;
+      rc = merged_plan(x, y, mask, &mp);
+      if (rc != TT_OK) return rc;
+      *bytes = mp.ws_bytes;
+      return TT_OK;
+    }
+    if (layout != TT_LAYOUT_CHAIN) return TT_ERR_ARG;
     ChainPlan cp;
     rc = chain_plan(x, y, mask, &cp);
     if (rc != TT_OK) return rc;
@@ -125,7 +218,8 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
   if (rc != TT_OK) return rc;
   if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
   if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
-  if (layout != TT_LAYOUT_CHAIN) return TT_ERR_UNSUPPORTED;
+  if (layout == TT_LAYOUT_MERGED) return contract_merged(x, y, mask, z, z_log2_dev, status_dev, ws, ws_bytes, stream);
+  if (layout != TT_LAYOUT_CHAIN) return TT_ERR_ARG;
   ChainPlan cp;
   rc = chain_plan(x, y, mask, &cp);
   if (rc != TT_OK) return rc;

@@ -364,6 +364,61 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   return TT_OK;
 }
 
+// Plan of a merged-layout partial contraction (see merged.cu).
+struct MergedPlan {
+  int m = 0;
+  int free_pos[kMaxOrder];
+  int64_t pre_cols[kMaxOrder];   // R^x_{f+1} R^y_{f+1}: row length before the run
+  int64_t rows[kMaxOrder];       // r_t I J
+  int run_k0[kMaxOrder], run_k1[kMaxOrder];
+  int rmax = 1;
+  size_t off_el = 0, off_ellog2 = 0, off_v = 0, off_pre = 0, ws_bytes = 0;
+};
+
+constexpr int64_t kMergedCoreCap = int64_t(1) << 30;  // elements per merged core
+
+inline int merged_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, MergedPlan* mp) {
+  const int n = x->order;
+  int m = 0;
+  for (int k = 0; k < n; ++k)
+    if (!mask[k]) mp->free_pos[m++] = k;
+  if (m == 0) return TT_ERR_ARG;
+  mp->m = m;
+  const int eb = elem_bytes(x->dtype);
+  int rmax = 1;
+  const int f0 = mp->free_pos[0];
+  for (int k = 0; k <= f0; ++k) rmax = std::max({rmax, x->ranks[k], y->ranks[k]});
+  int64_t max_pre = 0;
+  int64_t r_t = 1;
+  for (int t = 0; t < m; ++t) {
+    const int f = mp->free_pos[t];
+    const int nxt = t + 1 < m ? mp->free_pos[t + 1] : n;
+    mp->run_k0[t] = f + 1;
+    mp->run_k1[t] = nxt;
+    mp->pre_cols[t] = static_cast<int64_t>(x->ranks[f + 1]) * y->ranks[f + 1];
+    mp->rows[t] = r_t * x->modes[f] * y->modes[f];
+    const int64_t r_next = t + 1 < m ? static_cast<int64_t>(x->ranks[nxt]) * y->ranks[nxt] : 1;
+    if (mp->rows[t] * mp->pre_cols[t] > kMergedCoreCap || mp->rows[t] * r_next > kMergedCoreCap) return TT_ERR_TOO_LARGE;
+    if (nxt > f + 1) max_pre = std::max(max_pre, mp->rows[t] * mp->pre_cols[t]);
+    for (int k = f + 1; k <= nxt && k <= n; ++k) rmax = std::max({rmax, x->ranks[k], y->ranks[k]});
+    r_t = r_next;
+  }
+  mp->rmax = rmax;
+  if (rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
+  const int kx = x->ranks[f0], ky = y->ranks[f0];
+  size_t off = 0;
+  mp->off_el = off;
+  off += align256(static_cast<size_t>(kx) * ky * eb);
+  mp->off_ellog2 = off;
+  off += 256;
+  mp->off_v = off;
+  off += align256(static_cast<size_t>(kx) * y->modes[f0] * y->ranks[f0 + 1] * eb);
+  mp->off_pre = off;
+  off += align256(static_cast<size_t>(max_pre) * eb);
+  mp->ws_bytes = off;
+  return TT_OK;
+}
+
 // Flops of one contracted mode, the cheaper of the two evaluation orders.
 inline double mode_flops(int rx, int rx2, int ry, int ry2, int I) {
   const double a = double(rx) * ry * I * ry2 + double(rx) * I * rx2 * ry2;

@@ -120,7 +120,30 @@ struct ChainAdjParams {
   int32_t* status;
 };
 
+// Kronecker expansion of one free core pair (merged layout, see merged.cu).
+struct KronParams {
+  const void* gx;
+  const void* gy;
+  int rx, ry, I, J, rx2, ry2;
+  void* out;
+  const void* el;           // left environment folded into the first core
+  const int64_t* el_log2;
+  void* tmp;                // V = E_L Gy
+  int32_t* status;
+};
+
+// Rows of a merged core swept through a contracted run.
+struct RowIO {
+  const void* in;
+  int64_t in_stride_bytes;
+  void* out;
+  int64_t out_stride_bytes;
+  int64_t n_rows;
+};
+
 // Launchers (return cudaError_t of the launch).
+cudaError_t launch_kron(const KronParams& p, int which, int dtype, cudaStream_t s);
+cudaError_t launch_rows_sweep(const SweepParams& p, const RowIO& io, int dtype, int rmax, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStream_t s);
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
