@@ -17,6 +17,12 @@ using namespace ttc;
 
 namespace ttc {
 
+struct TcPlan;
+int tc_full_plan(const tt_desc* x, const tt_desc* y, int prec, TcPlan* tp);
+int tc_full_launch(const tt_desc* x, const tt_desc* y, int prec, double* out, int64_t* out_log2, int32_t* status,
+                   void* ws, size_t ws_bytes, cudaStream_t s);
+size_t tc_full_ws(const tt_desc* x, const tt_desc* y, int prec, int* rc);
+
 static int contract_merged(const tt_desc* x, const tt_desc* y, const uint8_t* mask, const tt_desc* z,
                            int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
   MergedPlan mp;
@@ -125,8 +131,13 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
   if (bytes == nullptr) return TT_ERR_ARG;
   *bytes = 0;
   if (op == TT_OP_FULL) {
-    const int rc = check_pair(x, y, nullptr);
-    return rc;
+    int rc = check_pair(x, y, nullptr);
+    if (rc != TT_OK) return rc;
+    if (x->dtype == TT_BF16 || prec == TT_P_BF16 || prec == TT_P_BF16X3) {
+      *bytes = tc_full_ws(x, y, prec, &rc);
+      return rc;
+    }
+    return TT_OK;
   }
   if (op == TT_OP_PARTIAL) {
     if (mask == nullptr) return TT_ERR_ARG;
@@ -158,13 +169,13 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
 
 int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_dev, int64_t* out_log2_dev,
                      int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
-  (void)ws;
-  (void)ws_bytes;
   int rc = check_pair(x, y, nullptr);
   if (rc != TT_OK) return rc;
   if (out_dev == nullptr) return TT_ERR_ARG;
+  if (x->dtype == TT_BF16 || prec == TT_P_BF16 || prec == TT_P_BF16X3)
+    return tc_full_launch(x, y, prec, out_dev, out_log2_dev, status_dev, ws, ws_bytes,
+                          reinterpret_cast<cudaStream_t>(stream));
   if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
-  if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
   SweepParams p;
   build_full(x, y, out_dev, out_log2_dev, status_dev, &p);
   return launch_sweep(p, x->dtype, reinterpret_cast<cudaStream_t>(stream));

@@ -6,6 +6,9 @@
 
 #include <atomic>
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "../../include/ttc.h"
 
 namespace ttc {
@@ -140,6 +143,32 @@ struct RowIO {
   int64_t out_stride_bytes;
   int64_t n_rows;
 };
+
+// One interior mode of the tensor-core full contraction (see tc_sweep.cu).
+struct TcModeParams {
+  CUtensorMap gx_hi, gx_lo, gy_hi, gy_lo;  // 3D maps over [R][I][R'] bfloat16 cores, box (64, 1, 64)
+  int x3;
+  int rx, rx2, ry, ry2, I;
+  const __nv_bfloat16* e_hi;  // input environment: ry/64 K-major panels of rx rows x 128 bytes
+  const __nv_bfloat16* e_lo;
+  const int* bmax_in;         // binary-exponent maxima of the input environment, per producing block
+  int n_bmax_in;
+  const int64_t* l_in;        // log2 scale of the input environment
+  __nv_bfloat16* eo_hi;       // output environment panels (ry2/64 panels of rx2 rows)
+  __nv_bfloat16* eo_lo;
+  float* eo_f32;              // output environment, float32 row-major [rx2][ry2]
+  int* bmax_out;              // [gridDim.x]
+  int64_t* l_out;
+  int32_t* status;
+};
+
+cudaError_t tc_split(const float* src, void* hi, void* lo, int64_t n, cudaStream_t s);
+cudaError_t tc_first(const void* x0, const void* y0, bool f32_in, int I, int rx2, int ry2, float* eo_f32, void* eo_hi,
+                     void* eo_lo, int* bmax_out, int64_t* l_out, int32_t* status, cudaStream_t s);
+cudaError_t tc_last(const float* e, const void* x, const void* y, bool f32_in, int I, int rx, int ry, double* parts,
+                    const int64_t* l_in, double* out, int64_t* out_log2, int32_t* status, cudaStream_t s);
+cudaError_t tc_mode(const TcModeParams& p, int cluster, cudaStream_t s);
+int tc_cluster_size(bool x3, int want);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_kron(const KronParams& p, int which, int dtype, cudaStream_t s);
