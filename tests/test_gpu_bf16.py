@@ -100,6 +100,30 @@ def test_order16_r256_lognormal_both_forms():
     assert st == 0
     eps16 = abs(np.ldexp(zb, eb) - want16) / norm_scale(xb, yb)
     eps16_e2e = abs(np.ldexp(zb, eb) - want32) / scale32
-    print(f"order16 r256: bf16 eps={eps16:.3e} (vs fp32 cores {eps16_e2e:.3e}); bf16x3 eps={eps3:.3e}")
+    z16, zx3 = np.ldexp(zb, eb), np.ldexp(z3, e3)
+    print(f"order16 r256: bf16 eps={eps16:.3e} (vs fp32 cores {eps16_e2e:.3e}); bf16x3 eps={eps3:.3e}; "
+          f"z* fp32={want32:.6e} bf16={want16:.6e} got bf16={z16:.6e} x3={zx3:.6e} kappa={scale32 / abs(want32):.2e}")
+    # the results are not trivially small: they agree with the oracle to a fraction of |z*|
+    assert abs(zx3 - want32) <= 1e-3 * abs(want32)
     assert eps16 <= 2 * 16 * 2.0**-8
     assert eps3 <= 2 * 16 * 2.0**-15
+
+
+@pytest.mark.parametrize("prec", ["native", "bf16x3"])
+def test_order16_r256_norm_invariant(prec):
+    """<X, X> = ||X||_F^2 (condition number 1) at the full order-16, rank-256
+    size: the plain relative error is meaningful here."""
+    x, _ = G.order16_r256(1)
+    if prec == "native":
+        xb = _bf16(x)
+        want = O.contract_full(xb, xb)
+        z, e, st = _run(to_dev(xb, torch.bfloat16), to_dev(xb, torch.bfloat16), "native", split=True)
+        bound = 2 * 16 * 2.0**-8
+    else:
+        want = O.contract_full(x, x)
+        z, e, st = _run(to_dev(x), to_dev(x), "bf16x3", split=True)
+        bound = 2 * 16 * 2.0**-15
+    assert st == 0
+    rel = abs(np.ldexp(z, e) - want) / want
+    print(f"order16 r256 <X,X> {prec}: rel={rel:.3e} z={np.ldexp(z, e):.6e} want={want:.6e}")
+    assert rel <= bound
