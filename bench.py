@@ -312,6 +312,9 @@ def run_ours(args):
     forms = {}
     if not args.no_forms:
         forms["batched"] = bench_batched(T, dev, args)
+        forms["bf16"] = bench_bf16(T, dev, args, "native")
+        forms["bf16x3"] = bench_bf16(T, dev, args, "bf16x3")
+        forms["backward"] = bench_backward(T, dev, args)
 
     if rank == 0:
         line = {
@@ -427,6 +430,154 @@ def bench_batched(T, dev, args):
     return out
 
 
+def _bf16_peak():
+    pk = _peaks()
+    return pk.get("bf16_tflops", 1933.5), pk.get("bf16_tflops_sustained", 1747.6)
+
+
+def bench_bf16(T, dev, args, prec):
+    """Order 16, modes 32, ranks 256, log-normal core scales; full contraction
+    on the tensor cores: bfloat16 cores with float32 sums ("native"), or the
+    split-bfloat16 x3 products on the float32 cores ("bf16x3")."""
+    import torch
+
+    x, y = G.order16_r256(0)
+    if prec == "native":
+        xd = [torch.from_numpy(c).to(dev).bfloat16() for c in x]
+        yd = [torch.from_numpy(c).to(dev).bfloat16() for c in y]
+        ebytes = 2
+    else:
+        xd = [torch.from_numpy(c).to(dev) for c in x]
+        yd = [torch.from_numpy(c).to(dev) for c in y]
+        ebytes = 4
+    op = T.FullContraction(xd, yd, prec=prec, split=True)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup // 4)):
+        op()
+    torch.cuda.synchronize(dev)
+    K = max(5, args.steps // 10)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        flush.fill_(1.0)
+        a.record(stream)
+        op()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    modes, r = [32] * 16, G.tt_ranks(16, 256)
+    flops = W.full_flops(modes, r, r)
+    nprod = 3 if prec == "bf16x3" else 1
+    burst, sustained = _bf16_peak()
+    achieved = flops * nprod / (ms / 1e3) / 1e12
+    del op, xd, yd, flush
+    torch.cuda.empty_cache()
+    return {
+        "workload": "order-16 TT pair, modes 32, ranks 256, log-normal core scales (sigma 1); full contraction on tcgen05 tensor cores" + (", bf16 cores, fp32 sums, fp64 final sum" if prec == "native" else ", fp32 cores split into hi+lo bf16, 3 products per step"),
+        "value": 1.0 / (ms / 1e3),
+        "unit": "contractions/s",
+        "ms_per_contraction": ms,
+        "gflops": flops / (ms / 1e3) / 1e9,
+        "alg_flops": flops,
+        "alg_bytes": W.full_bytes(modes, r, r, ebytes),
+        "roofline": {
+            "kernel": "tc_mode_kernel<%s>" % ("true" if prec == "bf16x3" else "false"),
+            "bound": "tensor",
+            "achieved": achieved,
+            "peak": burst,
+            "unit": "TFLOP/s",
+            "frac": achieved / burst,
+            "note": "tensor products counted (x3 for the split variant); peak = measured bf16 burst",
+        },
+        "l2": "flushed before each contraction",
+    }
+
+
+def bench_backward(T, dev, args):
+    """Gradients of loss = sum(Z), Z = partial contraction over modes 1-8 of the
+    order-12, mode 16, rank 64 float32 pair, with respect to all 24 cores."""
+    import torch
+
+    x, y = G.order12_r64(0)
+    xd = [torch.from_numpy(c).to(dev).requires_grad_(True) for c in x]
+    yd = [torch.from_numpy(c).to(dev).requires_grad_(True) for c in y]
+    mask = [1] * 8 + [0] * 4
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for c in xd + yd:
+            c.grad = None
+        zc = T.tt_partial(xd, yd, mask)
+        loss = T.tt_sum(zc)
+        loss.backward()
+
+    for _ in range(max(3, args.warmup // 4)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = max(5, args.steps // 10)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / K
+    modes, r = [16] * 12, G.tt_ranks(12, 64)
+    fwd = W.partial_chain_flops(modes, r, r, mask)
+    # adjoint: five products per contracted mode (U, dGx, W, dGy, next F), counted without recompute
+    bwd = sum(5 * W.mode_flops(r[k], r[k + 1], r[k], r[k + 1], modes[k]) // 2 for k in range(8))
+    return {
+        "workload": "order-12 TT pair, modes 16, ranks 64, float32; loss = sum of the partial contraction over modes 1-8; gradients of all 24 cores through torch.autograd (TTPartial, TTFull)",
+        "value": 1.0 / (ms / 1e3),
+        "unit": "gradient evaluations/s",
+        "ms_per_step": ms,
+        "gflops": (fwd + bwd) / (ms / 1e3) / 1e9,
+        "alg_flops": fwd + bwd,
+        "roofline": {
+            "kernel": "adjoint_kernel<float,64>",
+            "bound": "alu",
+            "achieved": (fwd + bwd) / (ms / 1e3) / 1e12,
+            "peak": fp32_simt_peak_tflops(),
+            "unit": "TFLOP/s",
+            "frac": (fwd + bwd) / (ms / 1e3) / 1e12 / fp32_simt_peak_tflops(),
+            "note": "latency-bound single instance (one cluster of 16 SMs); forward + adjoint products, recompute not counted",
+        },
+    }
+
+
+def run_profile_case(case):
+    """Small cases for ncu captures (a few GB at most on the device)."""
+    import torch
+
+    import paper_2109_00626_gb300 as T
+
+    dev = torch.device("cuda", 0)
+    if case in ("tc_native", "tc_x3"):
+        x, y = G.order16_r256(0)
+        conv = (lambda c: torch.from_numpy(c).to(dev).bfloat16()) if case == "tc_native" else (lambda c: torch.from_numpy(c).to(dev))
+        op = T.FullContraction([conv(c) for c in x], [conv(c) for c in y],
+                               prec="native" if case == "tc_native" else "bf16x3", split=True)
+        for _ in range(2):
+            op()
+        status = op.status
+    elif case == "batched512":
+        _, pairs = G.batch4096_device(512, 0, dev)
+        op = T.BatchedContraction(pairs)
+        for _ in range(2):
+            op()
+        status = op.status
+    else:
+        x, y = G.order10_r64(0, np.float32)
+        op = T.FullContraction([torch.from_numpy(c).to(dev) for c in x], [torch.from_numpy(c).to(dev) for c in y])
+        for _ in range(2):
+            op()
+        status = op.status
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_case": case, "device_status": int(status.item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,11 +587,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10"], default=None,
+                    help="run a small case twice for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     return run_ours(args)
 
 
