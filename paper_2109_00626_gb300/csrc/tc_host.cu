@@ -1,8 +1,10 @@
 // Host orchestration of the tensor-core full contraction (tc_sweep.cu):
 // operand conversion, tensor maps, and the chain of per-mode launches.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "host_plan.h"
@@ -76,12 +78,29 @@ int tc_full_plan(const tt_desc* x, const tt_desc* y, int prec, TcPlan* tp) {
   return TT_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so the
+// library does not link libcuda (it loads on machines without a driver).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 static int make_map(CUtensorMap* m, const void* ptr, int r0, int I, int r1) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (enc == nullptr) return TT_ERR_CUDA;
   cuuint64_t gdim[3] = {static_cast<cuuint64_t>(r1), static_cast<cuuint64_t>(I), static_cast<cuuint64_t>(r0)};
   cuuint64_t gstride[2] = {static_cast<cuuint64_t>(r1) * 2, static_cast<cuuint64_t>(I) * r1 * 2};
   cuuint32_t box[3] = {64, 1, 64};
   cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), gdim,
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), gdim,
                                             gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
