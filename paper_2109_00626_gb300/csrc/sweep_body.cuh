@@ -49,7 +49,9 @@ template <typename T, int RM, bool CL>
 struct SweepCfg {
   static constexpr int NT = 256;
   static constexpr int NW = NT / 32;
-  static constexpr int TM = RM / 16;               // thread tile is TM x TM
+  static constexpr int TM = RM / 16;               // thread tile of the chain emission (TM x TM)
+  // sweep GEMMs: 4x4 sub-tiles dealt round-robin, at most NS per thread
+  static constexpr int NS = (RM / 4) * (RM / 4) / NT > 0 ? (RM / 4) * (RM / 4) / NT : 1;
   static constexpr int V = 16 / sizeof(T);         // elements per 16-byte vector
   static constexpr int LD = RM + V;                // row stride (elements), 16-byte padded
   static constexpr int TILE = RM * LD;
@@ -127,6 +129,26 @@ __device__ __forceinline__ void outer_product(T (&acc)[TM][TM], const T* __restr
 #pragma unroll
       for (int b = 0; b < TM; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
   }
+}
+
+// Sub-tile j of the calling thread in an M x N output covered by 4x4
+// sub-tiles in row-major order: consecutive threads take consecutive column
+// blocks, so their 16-byte operand reads are contiguous (no bank conflicts)
+// and every thread has work whatever the ranks of the mode.
+struct Sub {
+  int m0, n0;
+  bool on;
+};
+template <int NT>
+__device__ __forceinline__ Sub sub_tile(int j, int M, int N) {
+  const int ncb = (N + 3) >> 2;
+  const int s = static_cast<int>(threadIdx.x) + j * NT;
+  Sub t;
+  t.on = s < ((M + 3) >> 2) * ncb;
+  const int r = s / ncb;
+  t.m0 = r * 4;
+  t.n0 = (s - r * ncb) * 4;
+  return t;
 }
 
 template <typename T>
@@ -273,23 +295,26 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   for (int s = 0; s < NST - 1; ++s) produce();
   __syncthreads();
 
-  const int p0 = ty * TM, v0 = tx * TM;
+  constexpr int NS = Cfg::NS;
   for (int j = 0; j < n_pipe; ++j) {
     const SweepStep st = p.step[j];
-    T acc[TM][TM];
+    T acc[NS][4][4];
 #pragma unroll
-    for (int a = 0; a < TM; ++a)
+    for (int u = 0; u < NS; ++u)
 #pragma unroll
-      for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[u][a][b] = T(0);
 
     while (cons.valid && cons.j == j) {
       // ---- T = E B_i over chunks of q ----
-      T t[TM][TM];
+      T t[NS][4][4];
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+      for (int u = 0; u < NS; ++u)
 #pragma unroll
-        for (int b = 0; b < TM; ++b) t[a][b] = T(0);
-      const bool act1 = p0 < st.rin_x && v0 < st.rout_y;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) t[u][a][b] = T(0);
       while (true) {
         cp_async_wait<NST - 2>();
         __syncthreads();
@@ -297,19 +322,28 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         const T* Bs = stage0 + (Lc % NST) * Cfg::STAGE;
         ++Lc;
         const int q0 = cons.c * KC, kc = min(KC, st.rin_y - q0);
-        if (act1) outer_product<T, TM, LD>(t, Es + q0 * LD, Bs, kc, p0, v0);
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const Sub sb = sub_tile<NT>(u, st.rin_x, st.rout_y);
+          if (sb.on) outer_product<T, 4, LD>(t[u], Es + q0 * LD, Bs, kc, sb.m0, sb.n0);
+        }
         const bool last = cons.c + 1 == cons.nch;
         it_next(cons, p, n_pipe, crank, C);
         if (last) break;
       }
 #pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        T* row = Ts + (p0 + a) * LD + v0;
+      for (int u = 0; u < NS; ++u) {
+        const Sub sb = sub_tile<NT>(u, st.rin_x, st.rout_y);
+        if (sb.on) {
 #pragma unroll
-        for (int b = 0; b < TM; ++b) row[b] = t[a][b];
+          for (int a = 0; a < 4; ++a) {
+            T* row = Ts + (sb.m0 + a) * LD + sb.n0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) row[b] = t[u][a][b];
+          }
+        }
       }
       // ---- P += A_i^T T over chunks of p ----
-      const bool act2 = p0 < st.rout_x && v0 < st.rout_y;
       while (true) {
         cp_async_wait<NST - 2>();
         __syncthreads();
@@ -317,7 +351,11 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         const T* As = stage0 + (Lc % NST) * Cfg::STAGE;
         ++Lc;
         const int r0 = cons.c * KC, kc = min(KC, st.rin_x - r0);
-        if (act2) outer_product<T, TM, LD>(acc, As, Ts + r0 * LD, kc, p0, v0);
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const Sub sb = sub_tile<NT>(u, st.rout_x, st.rout_y);
+          if (sb.on) outer_product<T, 4, LD>(acc[u], As, Ts + r0 * LD, kc, sb.m0, sb.n0);
+        }
         const bool last = cons.c + 1 == cons.nch;
         it_next(cons, p, n_pipe, crank, C);
         if (last) break;
@@ -329,19 +367,31 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
     if (!CL || C == 1) {
       int lexp = kNoExp, lbad = 0;
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+      for (int u = 0; u < NS; ++u) {
+        const Sub sb = sub_tile<NT>(u, nu, nv);
+        if (sb.on) {
 #pragma unroll
-        for (int b = 0; b < TM; ++b)
-          if (p0 + a < nu && v0 + b < nv) track(lexp, lbad, acc[a][b]);
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (sb.m0 + a < nu && sb.n0 + b < nv) track(lexp, lbad, acc[u][a][b]);
+        }
+      }
       block_exp<NW>(lexp, lbad, ired);
       if (lbad) bad = 1;
       const bool rescale = lexp != kNoExp && (lexp > p.renorm_bits || lexp < -p.renorm_bits);
       if (rescale) log2s += lexp;
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+      for (int u = 0; u < NS; ++u) {
+        const Sub sb = sub_tile<NT>(u, nu, nv);
+        if (sb.on) {
 #pragma unroll
-        for (int b = 0; b < TM; ++b)
-          Es[(v0 + b) * LD + p0 + a] = rescale ? mul_pow2<T>(acc[a][b], -lexp) : acc[a][b];
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              Es[(sb.n0 + b) * LD + sb.m0 + a] = rescale ? mul_pow2<T>(acc[u][a][b], -lexp) : acc[u][a][b];
+        }
+      }
       __syncthreads();
       continue;
     }
@@ -350,10 +400,16 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       cg::cluster_group cluster = cg::this_cluster();
       // ---- cluster reduction: E'[u][v] = sum over CTAs of P_c[u][v] ----
 #pragma unroll
-      for (int a = 0; a < TM; ++a) {
-        T* row = Ts + (p0 + a) * LD + v0;
+      for (int u = 0; u < NS; ++u) {
+        const Sub sb = sub_tile<NT>(u, nu, nv);
+        if (sb.on) {
 #pragma unroll
-        for (int b = 0; b < TM; ++b) row[b] = acc[a][b];
+          for (int a = 0; a < 4; ++a) {
+            T* row = Ts + (sb.m0 + a) * LD + sb.n0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
+          }
+        }
       }
       cluster.sync();
       const int nvv = (nv + V - 1) / V;
