@@ -23,6 +23,9 @@ struct BatchKernelParams {
   int32_t* status;
 };
 
+constexpr int kBatchThreads = SweepCfg<float, 128, false>::NT;
+static_assert(SweepCfg<double, 64, false>::NT == kBatchThreads, "one block size for every tile");
+
 template <typename T, int RM>
 __device__ __forceinline__ void run_pair(const SweepParams& p, const SweepOut& o, unsigned char* smem) {
   SweepState<T, RM, false> st;
@@ -36,7 +39,7 @@ struct BatchSmem {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 1) batched_kernel(const __grid_constant__ BatchKernelParams bp) {
+__global__ void __launch_bounds__(512, 1) batched_kernel(const __grid_constant__ BatchKernelParams bp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   for (;;) {
@@ -70,13 +73,13 @@ static cudaError_t launch_batched_impl(const BatchKernelParams& bp, int grid, cu
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<T>, 256, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<T>, kBatchThreads, smem);
     if (err != cudaSuccess) return err;
     grid = sms * std::max(per, 1);
   }
   grid = std::min(grid, std::max(bp.n, 1));
   count_launch();
-  batched_kernel<T><<<grid, 256, smem, s>>>(bp);
+  batched_kernel<T><<<grid, kBatchThreads, smem, s>>>(bp);
   return cudaGetLastError();
 }
 

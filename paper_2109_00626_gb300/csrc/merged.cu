@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) kron0_w_kernel(const __grid_constant__ Kr
 
 // Every row of a merged core swept through a contracted run (C = 1 per row).
 template <typename T, int RM>
-__global__ void __launch_bounds__(256, 1) rows_sweep_kernel(const __grid_constant__ SweepParams p, RowIO io) {
+__global__ void __launch_bounds__(512, 1) rows_sweep_kernel(const __grid_constant__ SweepParams p, RowIO io) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (int64_t row = blockIdx.x; row < io.n_rows; row += gridDim.x) {
     SweepOut o{nullptr, nullptr, p.status};
@@ -123,12 +123,12 @@ static cudaError_t rows_impl(const SweepParams& p, const RowIO& io, cudaStream_t
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rows_sweep_kernel<T, RM>, 256, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rows_sweep_kernel<T, RM>, SweepCfg<T, RM, false>::NT, smem);
   if (err != cudaSuccess) return err;
   int64_t grid = static_cast<int64_t>(sms) * std::max(per, 1);
   grid = std::min<int64_t>(grid, io.n_rows);
   count_launch();
-  rows_sweep_kernel<T, RM><<<static_cast<unsigned>(grid), 256, smem, s>>>(p, io);
+  rows_sweep_kernel<T, RM><<<static_cast<unsigned>(grid), SweepCfg<T, RM, false>::NT, smem, s>>>(p, io);
   return cudaGetLastError();
 }
 

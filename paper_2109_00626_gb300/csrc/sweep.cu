@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_cons
 }
 
 template <typename T, int RM>
-__global__ void __launch_bounds__(256, 1) sweep_cta_kernel(const __grid_constant__ SweepParams p) {
+__global__ void __launch_bounds__(512, 1) sweep_cta_kernel(const __grid_constant__ SweepParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   SweepState<T, RM, false> st;
   const SweepOut o{p.z_out, p.z_out_log2, p.status};

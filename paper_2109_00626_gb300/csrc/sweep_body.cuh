@@ -47,8 +47,11 @@ constexpr int KC = 32;               // rows per pipeline chunk
 //   CL: cluster mode (a reduction buffer of RM/2 rows is needed)
 template <typename T, int RM, bool CL>
 struct SweepCfg {
-  static constexpr int NT = 256;
+  // a CTA of a cluster runs 256 threads; a CTA working alone runs 512, so a
+  // single SM still has 16 warps to hide the latency of its small GEMMs
+  static constexpr int NT = CL ? 256 : 512;
   static constexpr int NW = NT / 32;
+  static constexpr int IRED = 192;                 // ints of reduction scratch
   static constexpr int TM = RM / 16;               // thread tile of the chain emission (TM x TM)
   // sweep GEMMs: 4x4 sub-tiles dealt round-robin, at most NS per thread
   static constexpr int NS = (RM / 4) * (RM / 4) / NT > 0 ? (RM / 4) * (RM / 4) / NT : 1;
@@ -58,7 +61,8 @@ struct SweepCfg {
   static constexpr int RS_ROWS = CL ? RM / 2 : 0;  // a CTA of a cluster (C >= 2) reduces <= RM/2 rows
   static constexpr int STAGE = KC * LD;
   static constexpr size_t kBudget = 232448 - 1024;
-  static constexpr size_t FIXED = (2 * TILE + RS_ROWS * LD) * sizeof(T) + 128 * sizeof(int);
+  static constexpr size_t FIXED = (2 * TILE + RS_ROWS * LD) * sizeof(T) + IRED * sizeof(int) +
+                                  kMaxOrder * sizeof(SweepStep);
   static constexpr int NST_FIT = static_cast<int>((kBudget - FIXED) / (STAGE * sizeof(T)));
   static constexpr int NST = NST_FIT >= 4 ? 4 : NST_FIT;
   static_assert(NST >= 2, "sweep tile does not fit in shared memory");
@@ -187,32 +191,32 @@ struct ChunkIt {
 
 __device__ __forceinline__ int nchunks(int rows) { return (rows + KC - 1) / KC; }
 
-__device__ __forceinline__ void it_settle(ChunkIt& it, const SweepParams& p, int n_pipe, int crank) {
-  while (it.j < n_pipe && it.i >= p.step[it.j].I) {
+__device__ __forceinline__ void it_settle(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank) {
+  while (it.j < n_pipe && it.i >= steps[it.j].I) {
     ++it.j;
     it.i = crank;
   }
   it.valid = it.j < n_pipe;
-  if (it.valid) it.nch = nchunks(p.step[it.j].rin_y);
+  if (it.valid) it.nch = nchunks(steps[it.j].rin_y);
 }
-__device__ __forceinline__ void it_first(ChunkIt& it, const SweepParams& p, int n_pipe, int crank) {
+__device__ __forceinline__ void it_first(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank) {
   it.j = 0;
   it.i = crank;
   it.which = 0;
   it.c = 0;
-  it_settle(it, p, n_pipe, crank);
+  it_settle(it, steps, n_pipe, crank);
 }
-__device__ __forceinline__ void it_next(ChunkIt& it, const SweepParams& p, int n_pipe, int crank, int C) {
+__device__ __forceinline__ void it_next(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank, int C) {
   if (++it.c < it.nch) return;
   it.c = 0;
   if (it.which == 0) {
     it.which = 1;
-    it.nch = nchunks(p.step[it.j].rin_x);
+    it.nch = nchunks(steps[it.j].rin_x);
     return;
   }
   it.which = 0;
   it.i += C;
-  it_settle(it, p, n_pipe, crank);
+  it_settle(it, steps, n_pipe, crank);
 }
 
 // Where results and device status go (per call; the batched kernel points
@@ -250,6 +254,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   T* Rs = Ts + Cfg::TILE;              // reduced rows of this CTA (cluster mode)
   T* stage0 = Rs + Cfg::RS_ROWS * LD;
   int* ired = reinterpret_cast<int*>(stage0 + NST * Cfg::STAGE);
+  SweepStep* sst = reinterpret_cast<SweepStep*>(ired + Cfg::IRED);  // step table cached on chip
 
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
@@ -272,14 +277,17 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
     if (p.e_in_log2 != nullptr) log2s = *p.e_in_log2;
   }
 
+  for (int q = tid; q < p.n_steps; q += NT) sst[q] = p.step[q];
+  __syncthreads();
+
   // ---- chunk pipeline ----
   ChunkIt prod, cons;
-  it_first(prod, p, n_pipe, crank);
-  it_first(cons, p, n_pipe, crank);
+  it_first(prod, sst, n_pipe, crank);
+  it_first(cons, sst, n_pipe, crank);
   int Lp = 0, Lc = 0;
   auto produce = [&]() {
     if (prod.valid) {
-      const SweepStep& st = p.step[prod.j];
+      const SweepStep& st = sst[prod.j];
       T* dst = stage0 + (Lp % NST) * Cfg::STAGE;
       const int rows = prod.which == 0 ? st.rin_y : st.rin_x;
       const int cols = prod.which == 0 ? st.rout_y : st.rout_x;
@@ -287,7 +295,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       const int r0 = prod.c * KC;
       load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, p.transposed, r0, min(KC, rows - r0));
       ++Lp;
-      it_next(prod, p, n_pipe, crank, C);
+      it_next(prod, sst, n_pipe, crank, C);
     }
     cp_async_commit();
   };
@@ -297,7 +305,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 
   constexpr int NS = Cfg::NS;
   for (int j = 0; j < n_pipe; ++j) {
-    const SweepStep st = p.step[j];
+    const SweepStep st = sst[j];
     T acc[NS][4][4];
 #pragma unroll
     for (int u = 0; u < NS; ++u)
@@ -328,7 +336,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
           if (sb.on) outer_product<T, 4, LD>(t[u], Es + q0 * LD, Bs, kc, sb.m0, sb.n0);
         }
         const bool last = cons.c + 1 == cons.nch;
-        it_next(cons, p, n_pipe, crank, C);
+        it_next(cons, sst, n_pipe, crank, C);
         if (last) break;
       }
 #pragma unroll
@@ -357,7 +365,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
           if (sb.on) outer_product<T, 4, LD>(acc[u], As, Ts + r0 * LD, kc, sb.m0, sb.n0);
         }
         const bool last = cons.c + 1 == cons.nch;
-        it_next(cons, p, n_pipe, crank, C);
+        it_next(cons, sst, n_pipe, crank, C);
         if (last) break;
       }
     }
@@ -496,23 +504,23 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       __syncthreads();
     }
     part = warp_sum(part);
-    double* dred = reinterpret_cast<double*>(ired + 96);  // 16 doubles (ired has 128 ints)
+    double* dred = reinterpret_cast<double*>(ired + 128);  // 32 doubles: per-warp sums, total in [16]
     if (lane == 0) dred[warp] = part;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
       for (int w = 0; w < NW; ++w) s += dred[w];
-      dred[8] = s;
+      dred[16] = s;
     }
     double z = 0.0;
     if constexpr (CL) {
       cg::cluster_group cluster = cg::this_cluster();
       cluster.sync();
       if (crank == 0 && tid == 0)
-        for (int r = 0; r < C; ++r) z += *cluster.map_shared_rank(dred + 8, r);
+        for (int r = 0; r < C; ++r) z += *cluster.map_shared_rank(dred + 16, r);
     } else {
       __syncthreads();
-      z = dred[8];
+      z = dred[16];
     }
     if (crank == 0 && tid == 0) {
       int st_bits = (isfinite(z) && !bad) ? 0 : TT_STATUS_NONFINITE;
@@ -549,12 +557,11 @@ template <typename T, int RM, bool CL>
 __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut& o, unsigned char* smem, int C,
                                            int crank, const SweepState<T, RM, CL>& s) {
   using Cfg = SweepCfg<T, RM, CL>;
-  constexpr int NT = Cfg::NT, TM = Cfg::TM, LD = Cfg::LD;
+  constexpr int NT = Cfg::NT, LD = Cfg::LD;
   T* Es = reinterpret_cast<T*>(smem);
   T* Ts = Es + Cfg::TILE;
   T* stage0 = Ts + Cfg::TILE + Cfg::RS_ROWS * LD;
   const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
   const int64_t log2s = s.log2s;
 
   const int kx = p.n_steps > 0 ? p.step[p.n_steps - 1].rout_x : p.rx0;
@@ -589,13 +596,15 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
     const int nu = em.lead ? em.rb : em.ra;
     const bool fold = em.z_log2_out == nullptr && log2s != 0;
     int ebits = 0;
-    const int u0 = ty * TM, y0 = tx * TM;
+    constexpr int NS = Cfg::NS;
     for (int i = crank; i < em.I; i += C) {
-      T acc[TM][TM];
+      T acc[NS][4][4];
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+      for (int u = 0; u < NS; ++u)
 #pragma unroll
-        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[u][a][b] = T(0);
       for (int r0 = 0; r0 < kx; r0 += KC) {
         const int kc = min(KC, kx - r0);
         __syncthreads();
@@ -604,24 +613,33 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
-        if (u0 < nu && y0 < em.ry) outer_product<T, TM, LD>(acc, stage0, Ts + r0 * LD, kc, u0, y0);
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const Sub sb = sub_tile<NT>(u, nu, em.ry);
+          if (sb.on) outer_product<T, 4, LD>(acc[u], stage0, Ts + r0 * LD, kc, sb.m0, sb.n0);
+        }
       }
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
+      for (int u = 0; u < NS; ++u) {
+        const Sub sb = sub_tile<NT>(u, nu, em.ry);
+        if (!sb.on) continue;
 #pragma unroll
-        for (int b = 0; b < TM; ++b) {
-          const int u = u0 + a, y = y0 + b;
-          if (u < nu && y < em.ry) {
-            T v = acc[a][b];
-            if (fold) {
-              const T v0 = v;
-              v = scale_pow2_sat<T>(v, log2s);
-              if (isfinite(v0) && !isfinite(v)) ebits |= TT_STATUS_OVERFLOW;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int uu = sb.m0 + a, y = sb.n0 + b;
+            if (uu < nu && y < em.ry) {
+              T v = acc[u][a][b];
+              if (fold) {
+                const T v0 = v;
+                v = scale_pow2_sat<T>(v, log2s);
+                if (isfinite(v0) && !isfinite(v)) ebits |= TT_STATUS_OVERFLOW;
+              }
+              if (!isfinite(v)) ebits |= TT_STATUS_NONFINITE;
+              cout[(static_cast<int64_t>(uu) * em.I + i) * em.ry + y] = v;
             }
-            if (!isfinite(v)) ebits |= TT_STATUS_NONFINITE;
-            cout[(static_cast<int64_t>(u) * em.I + i) * em.ry + y] = v;
           }
-        }
+      }
     }
     if (ebits) set_status(o.status, ebits);
     if (crank == 0 && tid == 0 && em.z_log2_out != nullptr) *em.z_log2_out = log2s;
