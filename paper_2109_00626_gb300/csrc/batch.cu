@@ -18,8 +18,9 @@ struct tt_plan {
   std::vector<int32_t> order;
   std::vector<int32_t> tile;
   std::vector<double> cost;
-  size_t off_order = 0, off_tile = 0, packed_bytes = 0;
-  size_t ws_bytes = 256;  // device workspace the launch needs (the work-queue counter)
+  std::vector<ttc::CopyJob> jobs;
+  size_t off_order = 0, off_tile = 0, off_jobs = 0, packed_bytes = 0;
+  size_t ws_bytes = 256;  // device workspace the launch needs (the two work-queue counters)
 };
 
 namespace ttc {
@@ -111,9 +112,31 @@ int tt_batch_plan(const tt_batch* b, tt_plan** plan_out, size_t* packed_bytes, s
   std::iota(plan->order.begin(), plan->order.end(), 0);
   std::stable_sort(plan->order.begin(), plan->order.end(),
                    [&](int a, int c) { return plan->cost[a] > plan->cost[c]; });
+  // free-core copies as jobs of at least ~16K elements (whole slices)
+  for (int i = 0; i < n; ++i) {
+    const EmitParams& em = plan->table[plan->order[i]].emit;
+    if (!em.enabled) continue;
+    for (int t = 0; t < em.n_copies; ++t) {
+      const CopyTask& tk = em.copy[t];
+      const int per = std::max(1, 16384 / std::max(1, tk.r0 * tk.r1));
+      for (int i0 = 0; i0 < tk.I; i0 += per) {
+        CopyJob j;
+        j.src = tk.src;
+        j.dst = tk.dst;
+        j.r0 = tk.r0;
+        j.I = tk.I;
+        j.r1 = tk.r1;
+        j.swap = tk.swap;
+        j.i0 = i0;
+        j.i1 = std::min(tk.I, i0 + per);
+        plan->jobs.push_back(j);
+      }
+    }
+  }
   plan->off_order = align256(sizeof(SweepParams) * n);
   plan->off_tile = plan->off_order + align256(sizeof(int32_t) * n);
-  plan->packed_bytes = plan->off_tile + align256(sizeof(int32_t) * n);
+  plan->off_jobs = plan->off_tile + align256(sizeof(int32_t) * n);
+  plan->packed_bytes = plan->off_jobs + align256(sizeof(CopyJob) * std::max<size_t>(1, plan->jobs.size()));
   *packed_bytes = plan->packed_bytes;
   *ws_bytes = 256;  // work-queue counter
   *plan_out = plan;
@@ -127,6 +150,7 @@ int tt_batch_pack(const tt_plan* plan, void* packed_host, size_t packed_bytes) {
   memcpy(base, plan->table.data(), sizeof(SweepParams) * plan->n_pairs);
   memcpy(base + plan->off_order, plan->order.data(), sizeof(int32_t) * plan->n_pairs);
   memcpy(base + plan->off_tile, plan->tile.data(), sizeof(int32_t) * plan->n_pairs);
+  if (!plan->jobs.empty()) memcpy(base + plan->off_jobs, plan->jobs.data(), sizeof(CopyJob) * plan->jobs.size());
   return TT_OK;
 }
 
@@ -136,12 +160,13 @@ int tt_contract_batched(const tt_plan* plan, const void* packed_dev, double* out
   if (ws == nullptr || ws_bytes < 256) return TT_ERR_WS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const char* base = static_cast<const char*>(packed_dev);
-  if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, 2 * sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
   if (cudaMemsetAsync(out_dev, 0, sizeof(double) * plan->n_pairs, s) != cudaSuccess) return TT_ERR_CUDA;
   const cudaError_t err =
       launch_batched(base, reinterpret_cast<const int32_t*>(base + plan->off_order),
-                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs, static_cast<int*>(ws),
-                     out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
+                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs,
+                     reinterpret_cast<const CopyJob*>(base + plan->off_jobs), static_cast<int>(plan->jobs.size()),
+                     static_cast<int*>(ws), out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
   return err == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -223,11 +248,11 @@ int tt_autotune(int dtype, const char* cache_path) {
         cudaMemcpy(tb + sizeof(SweepParams) * npairs + 4 * npairs, tl.data(), 4 * npairs, cudaMemcpyHostToDevice);
         float ms_sum = 0.f;
         for (int rep = 0; rep < 4; ++rep) {
-          cudaMemsetAsync(counter, 0, 4, s);
+          cudaMemsetAsync(counter, 0, 8, s);
           cudaEventRecord(e0, s);
           launch_batched(tb, reinterpret_cast<int32_t*>(tb + sizeof(SweepParams) * npairs),
-                         reinterpret_cast<int32_t*>(tb + sizeof(SweepParams) * npairs + 4 * npairs), npairs, counter,
-                         out, nullptr, nullptr, dtype, 0, s);
+                         reinterpret_cast<int32_t*>(tb + sizeof(SweepParams) * npairs + 4 * npairs), npairs, nullptr,
+                         0, counter, out, nullptr, nullptr, dtype, 0, s);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
           float ms = 0.f;
@@ -311,11 +336,12 @@ extern "C" int tt_contract_batched_noalloc(const tt_plan* plan, const void* pack
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const char* base = static_cast<const char*>(packed_dev);
   // the counter must start at zero on every call; the array keeps the last call's contents
-  if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
   if (cudaMemsetAsync(out_dev, 0, sizeof(double) * plan->n_pairs, s) != cudaSuccess) return TT_ERR_CUDA;
   const cudaError_t err =
       launch_batched(base, reinterpret_cast<const int32_t*>(base + plan->off_order),
-                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs, static_cast<int*>(scratch),
-                     out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
+                     reinterpret_cast<const int32_t*>(base + plan->off_tile), plan->n_pairs,
+                     reinterpret_cast<const CopyJob*>(base + plan->off_jobs), static_cast<int>(plan->jobs.size()),
+                     static_cast<int*>(scratch), out_dev, out_log2_dev, status_dev, plan->dtype, 0, s);
   return err == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }

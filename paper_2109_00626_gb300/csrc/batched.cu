@@ -17,7 +17,9 @@ struct BatchKernelParams {
   const int32_t* order;      // [n] pair indices, longest first
   const int32_t* tile;       // [n] rank tile per pair: 0 -> 32, 1 -> 64, 2 -> 128
   int n;
-  int* counter;              // work queue head (zeroed before the launch)
+  const CopyJob* jobs;       // free-core copies of the partial pairs
+  int n_jobs;
+  int* counter;              // [0] pair queue head, [1] copy queue head (zeroed before the launch)
   double* out;               // [n]
   int64_t* out_log2;         // [n] or NULL
   int32_t* status;
@@ -50,7 +52,8 @@ __global__ void __launch_bounds__(512, 1) batched_kernel(const __grid_constant__
     if (idx >= bp.n) break;
     const int pair = bp.order[idx];
     const SweepParams& p = bp.table[pair];
-    const SweepOut o{bp.out + pair, bp.out_log2 != nullptr ? bp.out_log2 + pair : nullptr, bp.status};
+    SweepOut o{bp.out + pair, bp.out_log2 != nullptr ? bp.out_log2 + pair : nullptr, bp.status};
+    o.skip_copies = 1;
     const int tile = bp.tile[pair];
     if constexpr (sizeof(T) == 4) {
       if (tile == 0) run_pair<T, 32>(p, o, smem);
@@ -59,6 +62,60 @@ __global__ void __launch_bounds__(512, 1) batched_kernel(const __grid_constant__
     } else {
       if (tile == 0) run_pair<T, 32>(p, o, smem);
       else run_pair<T, 64>(p, o, smem);
+    }
+  }
+}
+
+// Free-core copies of the partial pairs (they depend on no sweep).  A grid of
+// many small CTAs per SM keeps enough loads in flight to run at memory speed;
+// jobs are dealt statically (job j to CTA j mod grid), so no scratch is used.
+template <typename T>
+__global__ void __launch_bounds__(256) copy_jobs_kernel(const CopyJob* __restrict__ jobs, int n_jobs) {
+  __shared__ T tile[32 * 33];
+  constexpr int U = 8;
+  for (int jb = blockIdx.x; jb < n_jobs; jb += gridDim.x) {
+    const CopyJob j = jobs[jb];
+    const T* __restrict__ src = static_cast<const T*>(j.src);
+    T* __restrict__ dst = static_cast<T*>(j.dst);
+    if (!j.swap) {
+      const int64_t run = static_cast<int64_t>(j.i1 - j.i0) * j.r1;
+      const int64_t total = static_cast<int64_t>(j.r0) * run;
+      for (int64_t e0 = threadIdx.x; e0 < total; e0 += static_cast<int64_t>(U) * blockDim.x) {
+        T v[U];
+        int64_t idx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t e = e0 + static_cast<int64_t>(u) * blockDim.x;
+          idx[u] = -1;
+          if (e < total) {
+            const int64_t c0 = e / run, off = e - c0 * run;
+            idx[u] = (c0 * j.I + j.i0) * j.r1 + off;
+            v[u] = ldg(src + idx[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (idx[u] >= 0) dst[idx[u]] = v[u];
+      }
+    } else {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int t0 = (j.r0 + 31) / 32, t1 = (j.r1 + 31) / 32;
+      for (int i = j.i0; i < j.i1; ++i)
+        for (int tt = 0; tt < t0 * t1; ++tt) {
+          const int b0 = (tt / t1) * 32, b1 = (tt % t1) * 32;
+          __syncthreads();
+#pragma unroll
+          for (int rr = warp; rr < 32; rr += 8) {
+            const int c0 = b0 + rr, c1 = b1 + lane;
+            if (c0 < j.r0 && c1 < j.r1) tile[rr * 33 + lane] = src[(static_cast<int64_t>(c0) * j.I + i) * j.r1 + c1];
+          }
+          __syncthreads();
+#pragma unroll
+          for (int rr = warp; rr < 32; rr += 8) {
+            const int c1 = b1 + rr, c0 = b0 + lane;
+            if (c0 < j.r0 && c1 < j.r1) dst[(static_cast<int64_t>(c1) * j.I + i) * j.r0 + c0] = tile[lane * 33 + rr];
+          }
+        }
     }
   }
 }
@@ -80,17 +137,27 @@ static cudaError_t launch_batched_impl(const BatchKernelParams& bp, int grid, cu
   grid = std::min(grid, std::max(bp.n, 1));
   count_launch();
   batched_kernel<T><<<grid, kBatchThreads, smem, s>>>(bp);
+  err = cudaGetLastError();
+  if (err != cudaSuccess || bp.n_jobs == 0) return err;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  count_launch();
+  copy_jobs_kernel<T><<<std::min(bp.n_jobs, sms * 8), 256, 0, s>>>(bp.jobs, bp.n_jobs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n, int* counter,
-                           double* out, int64_t* out_log2, int32_t* status, int dtype, int grid, cudaStream_t s) {
+cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n,
+                           const CopyJob* jobs, int n_jobs, int* counters, double* out, int64_t* out_log2,
+                           int32_t* status, int dtype, int grid, cudaStream_t s) {
   BatchKernelParams bp;
   bp.table = static_cast<const SweepParams*>(table);
   bp.order = order;
   bp.tile = tile;
   bp.n = n;
-  bp.counter = counter;
+  bp.jobs = jobs;
+  bp.n_jobs = n_jobs;
+  bp.counter = counters;
   bp.out = out;
   bp.out_log2 = out_log2;
   bp.status = status;

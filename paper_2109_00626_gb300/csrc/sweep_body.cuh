@@ -97,6 +97,8 @@ struct Vec16<double> {
 template <typename T, int LD, int NT>
 __device__ __forceinline__ void load_rows_async(T* __restrict__ dst, const T* __restrict__ core, int i, int I,
                                                 int rows, int cols, int transposed, int r0, int nr) {
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!transposed) {
     constexpr int V = 16 / sizeof(T);
     if ((cols % V) == 0 && (reinterpret_cast<uintptr_t>(core) & 15) == 0) {
@@ -106,15 +108,59 @@ __device__ __forceinline__ void load_rows_async(T* __restrict__ dst, const T* __
         cp_async16(dst + r * LD + c, core + (static_cast<int64_t>(r0 + r) * I + i) * cols + c);
       }
     } else {
-      for (int idx = threadIdx.x; idx < nr * cols; idx += NT) {
-        const int r = idx / cols, c = idx - r * cols;
-        cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(r0 + r) * I + i) * cols + c);
+      // one warp per row, lanes along the row: coalesced, no division
+      for (int r = warp; r < nr; r += NW) {
+        const T* src = core + (static_cast<int64_t>(r0 + r) * I + i) * cols;
+        for (int c = lane; c < cols; c += 32) cp_async_elem(dst + r * LD + c, src + c);
       }
     }
   } else {
-    for (int idx = threadIdx.x; idx < nr * cols; idx += NT) {
-      const int c = idx / nr, r = idx - c * nr;
-      cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(c) * I + i) * rows + r0 + r);
+    // one warp per source row (a column of dst), lanes along it
+    for (int c = warp; c < cols; c += NW) {
+      const T* src = core + (static_cast<int64_t>(c) * I + i) * rows + r0;
+      for (int r = lane; r < nr; r += 32) cp_async_elem(dst + r * LD + c, src + r);
+    }
+  }
+}
+
+// dst[e] = src[e] for e = g, g + gs, ... < n, four loads in flight per thread.
+template <typename T>
+__device__ __forceinline__ void copy_plain(T* __restrict__ dst, const T* __restrict__ src, int64_t n, int64_t g,
+                                           int64_t gs) {
+  int64_t e = g;
+  for (; e + 3 * gs < n; e += 4 * gs) {
+    const T a0 = ldg(src + e), a1 = ldg(src + e + gs), a2 = ldg(src + e + 2 * gs), a3 = ldg(src + e + 3 * gs);
+    dst[e] = a0;
+    dst[e + gs] = a1;
+    dst[e + 2 * gs] = a2;
+    dst[e + 3 * gs] = a3;
+  }
+  for (; e < n; e += gs) dst[e] = ldg(src + e);
+}
+
+// dst[c1][i][c0] = src[c0][i][c1] for one core ([r0][I][r1] -> [r1][I][r0]),
+// through 32 x 32 shared-memory tiles so both the reads and the writes are
+// coalesced.  Tiles are dealt to the CTAs of the cluster.
+template <typename T, int NT>
+__device__ void copy_swap_tiled(T* __restrict__ dst, const T* __restrict__ src, int r0, int I, int r1, T* tile,
+                                int C, int crank) {
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t0 = (r0 + 31) / 32, t1 = (r1 + 31) / 32;
+  const int ntiles = I * t0 * t1;
+  for (int job = crank; job < ntiles; job += C) {
+    const int i = job / (t0 * t1);
+    const int rem = job - i * t0 * t1;
+    const int b0 = (rem / t1) * 32, b1 = (rem % t1) * 32;
+    __syncthreads();
+    for (int rr = warp; rr < 32; rr += NW) {
+      const int c0 = b0 + rr, c1 = b1 + lane;
+      if (c0 < r0 && c1 < r1) tile[rr * 33 + lane] = src[(static_cast<int64_t>(c0) * I + i) * r1 + c1];
+    }
+    __syncthreads();
+    for (int rr = warp; rr < 32; rr += NW) {
+      const int c1 = b1 + rr, c0 = b0 + lane;
+      if (c0 < r0 && c1 < r1) dst[(static_cast<int64_t>(c1) * I + i) * r0 + c0] = tile[lane * 33 + rr];
     }
   }
 }
@@ -231,6 +277,7 @@ struct SweepOut {
   const void* e_in = nullptr;
   void* e_out = nullptr;
   int fold_e_out = 0;
+  int skip_copies = 0;  // the free-core copies are done elsewhere (batched launch)
 };
 
 // Result of a sweep that is not a full contraction: E (in Es, transposed) and
@@ -643,24 +690,17 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
     }
     if (ebits) set_status(o.status, ebits);
     if (crank == 0 && tid == 0 && em.z_log2_out != nullptr) *em.z_log2_out = log2s;
-    // free cores: plain or leg-swapped copies, grid-stride over the cluster
+    // free cores: plain copies grid-stride over the cluster, leg-swapped ones
+    // through shared-memory tiles
     const int64_t g = static_cast<int64_t>(crank) * NT + tid, gs = static_cast<int64_t>(C) * NT;
-    for (int t = 0; t < em.n_copies; ++t) {
+    for (int t = 0; t < (o.skip_copies ? 0 : em.n_copies); ++t) {
       const CopyTask& tk = em.copy[t];
       const T* __restrict__ src = static_cast<const T*>(tk.src);
       T* __restrict__ dst = static_cast<T*>(tk.dst);
-      const int64_t n = static_cast<int64_t>(tk.r0) * tk.I * tk.r1;
       if (!tk.swap) {
-        for (int64_t e = g; e < n; e += gs) dst[e] = ldg(src + e);
+        copy_plain<T>(dst, src, static_cast<int64_t>(tk.r0) * tk.I * tk.r1, g, gs);
       } else {
-        // dst is [r1][I][r0]; element e of dst = (c1, i, c0); 32-bit index math
-        const unsigned r0 = tk.r0, ii = tk.I, r1 = tk.r1;
-        for (int64_t e = g; e < n; e += gs) {
-          const unsigned ee = static_cast<unsigned>(e);
-          const unsigned c0 = ee % r0, rest = ee / r0;
-          const unsigned i2 = rest % ii, c1 = rest / ii;
-          dst[e] = ldg(src + (static_cast<int64_t>(c0) * ii + i2) * r1 + c1);
-        }
+        copy_swap_tiled<T, NT>(dst, src, tk.r0, tk.I, tk.r1, stage0, C, crank);
       }
     }
   }

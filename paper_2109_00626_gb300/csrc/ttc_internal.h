@@ -178,8 +178,19 @@ cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 
-cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n, int* counter,
-                           double* out, int64_t* out_log2, int32_t* status, int dtype, int grid, cudaStream_t s);
+// One slice range [i0, i1) of a free-core copy of a chain-layout output; the
+// batched launch works through these after its sweep queue.
+struct CopyJob {
+  const void* src;
+  void* dst;
+  int r0, I, r1;
+  int swap;
+  int i0, i1;
+};
+
+cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n,
+                           const CopyJob* jobs, int n_jobs, int* counters, double* out, int64_t* out_log2,
+                           int32_t* status, int dtype, int grid, cudaStream_t s);
 
 // Largest cluster size (<= want) the sweep kernel for this rank tile can run with.
 int sweep_cluster_size(int rmax, int elem_bytes, int want);
