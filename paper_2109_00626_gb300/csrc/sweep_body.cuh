@@ -33,6 +33,8 @@
 
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "ttc_device.cuh"
 #include "ttc_internal.h"
 
@@ -54,7 +56,7 @@ struct SweepCfg {
   static constexpr int IRED = 192;                 // ints of reduction scratch
   static constexpr int TM = RM / 16;               // thread tile of the chain emission (TM x TM)
   // sweep GEMMs: 4x4 sub-tiles dealt round-robin, at most NS per thread
-  static constexpr int NS = (RM / 4) * (RM / 4) / NT > 0 ? (RM / 4) * (RM / 4) / NT : 1;
+  static constexpr int NS = ((RM / 4) * (RM / 4) + NT - 1) / NT;
   static constexpr int V = 16 / sizeof(T);         // elements per 16-byte vector
   static constexpr int LD = RM + V;                // row stride (elements), 16-byte padded
   static constexpr int TILE = RM * LD;
@@ -350,12 +352,14 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   for (int s = 0; s < NST - 1; ++s) produce();
   __syncthreads();
 
-  constexpr int NS = Cfg::NS;
-  for (int j = 0; j < n_pipe; ++j) {
+  // One contracted mode; NSE = sub-tiles per thread this mode needs (the
+  // largest tile runs the one-sub-tile code whenever the ranks allow).
+  auto mode = [&](const int j, auto nse_tag) {
+    constexpr int NSE = decltype(nse_tag)::value;
     const SweepStep st = sst[j];
-    T acc[NS][4][4];
+    T acc[NSE][4][4];
 #pragma unroll
-    for (int u = 0; u < NS; ++u)
+    for (int u = 0; u < NSE; ++u)
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -363,9 +367,9 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 
     while (cons.valid && cons.j == j) {
       // ---- T = E B_i over chunks of q ----
-      T t[NS][4][4];
+      T t[NSE][4][4];
 #pragma unroll
-      for (int u = 0; u < NS; ++u)
+      for (int u = 0; u < NSE; ++u)
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -378,7 +382,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         ++Lc;
         const int q0 = cons.c * KC, kc = min(KC, st.rin_y - q0);
 #pragma unroll
-        for (int u = 0; u < NS; ++u) {
+        for (int u = 0; u < NSE; ++u) {
           const Sub sb = sub_tile<NT>(u, st.rin_x, st.rout_y);
           if (sb.on) outer_product<T, 4, LD>(t[u], Es + q0 * LD, Bs, kc, sb.m0, sb.n0);
         }
@@ -387,7 +391,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         if (last) break;
       }
 #pragma unroll
-      for (int u = 0; u < NS; ++u) {
+      for (int u = 0; u < NSE; ++u) {
         const Sub sb = sub_tile<NT>(u, st.rin_x, st.rout_y);
         if (sb.on) {
 #pragma unroll
@@ -407,7 +411,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         ++Lc;
         const int r0 = cons.c * KC, kc = min(KC, st.rin_x - r0);
 #pragma unroll
-        for (int u = 0; u < NS; ++u) {
+        for (int u = 0; u < NSE; ++u) {
           const Sub sb = sub_tile<NT>(u, st.rout_x, st.rout_y);
           if (sb.on) outer_product<T, 4, LD>(acc[u], As, Ts + r0 * LD, kc, sb.m0, sb.n0);
         }
@@ -422,7 +426,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
     if (!CL || C == 1) {
       int lexp = kNoExp, lbad = 0;
 #pragma unroll
-      for (int u = 0; u < NS; ++u) {
+      for (int u = 0; u < NSE; ++u) {
         const Sub sb = sub_tile<NT>(u, nu, nv);
         if (sb.on) {
 #pragma unroll
@@ -437,7 +441,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       const bool rescale = lexp != kNoExp && (lexp > p.renorm_bits || lexp < -p.renorm_bits);
       if (rescale) log2s += lexp;
 #pragma unroll
-      for (int u = 0; u < NS; ++u) {
+      for (int u = 0; u < NSE; ++u) {
         const Sub sb = sub_tile<NT>(u, nu, nv);
         if (sb.on) {
 #pragma unroll
@@ -448,14 +452,14 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         }
       }
       __syncthreads();
-      continue;
+      return;
     }
 
     if constexpr (CL) {
       cg::cluster_group cluster = cg::this_cluster();
       // ---- cluster reduction: E'[u][v] = sum over CTAs of P_c[u][v] ----
 #pragma unroll
-      for (int u = 0; u < NS; ++u) {
+      for (int u = 0; u < NSE; ++u) {
         const Sub sb = sub_tile<NT>(u, nu, nv);
         if (sb.on) {
 #pragma unroll
@@ -524,6 +528,14 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       }
       __syncthreads();
     }
+
+  };
+  for (int j = 0; j < n_pipe; ++j) {
+    const SweepStep& sj = sst[j];
+    const int need1 = ((sj.rin_x + 3) >> 2) * ((sj.rout_y + 3) >> 2);
+    const int need2 = ((sj.rout_x + 3) >> 2) * ((sj.rout_y + 3) >> 2);
+    if (Cfg::NS > 1 && need1 <= NT && need2 <= NT) mode(j, std::integral_constant<int, 1>{});
+    else mode(j, std::integral_constant<int, Cfg::NS>{});
   }
 
   // ---- last mode of a full contraction: float64 sum ----
