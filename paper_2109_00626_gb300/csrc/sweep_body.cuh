@@ -13,8 +13,12 @@
 // do not depend on E, so the next mode's chunks land while the cluster is
 // still reducing the current mode.  The cluster adds the partial P's through
 // distributed shared memory: CTA c sums its share of rows over all peers
-// (fixed order: deterministic), and every CTA pulls the reduced rows back into
-// its own copy of E'.
+// (fixed order: deterministic), and every CTA gets the reduced rows back into
+// its own copy of E'.  For float32 tiles up to rank 64 both exchanges are
+// pushes: bulk asynchronous copies from a CTA's shared memory into receive
+// buffers of its peers, completed on an mbarrier of the receiver (bounded
+// waits), so no cluster-wide barrier is taken per mode.  Other tiles pull
+// from the peers' shared memory between two cluster barriers.
 //
 // Scaling: after each mode the largest binary exponent of E' is compared with
 // +-s; outside that band E' is multiplied by an exact power of two and the
@@ -35,6 +39,7 @@
 
 #include <type_traits>
 
+#include "tc_common.cuh"
 #include "ttc_device.cuh"
 #include "ttc_internal.h"
 
@@ -63,8 +68,13 @@ struct SweepCfg {
   static constexpr int RS_ROWS = CL ? RM / 2 : 0;  // a CTA of a cluster (C >= 2) reduces <= RM/2 rows
   static constexpr int STAGE = KC * LD;
   static constexpr size_t kBudget = 232448 - 1024;
+  // Push exchange (float, ranks <= 64, cluster): partial rows go to their
+  // owner and reduced rows to every peer by bulk copies into receive buffers
+  static constexpr bool PUSH = CL && sizeof(T) == 4 && RM <= 64;
+  static constexpr int RB_ROWS = RM + 16;            // C slots of ceil(RM / C) rows
+  static constexpr size_t XB = PUSH ? ((RB_ROWS + RM) * LD * sizeof(T) + 16 * 16 + 16 + 16) : 0;
   static constexpr size_t FIXED = (2 * TILE + RS_ROWS * LD) * sizeof(T) + IRED * sizeof(int) +
-                                  kMaxOrder * sizeof(SweepStep);
+                                  kMaxOrder * sizeof(SweepStep) + XB;
   static constexpr int NST_FIT = static_cast<int>((kBudget - FIXED) / (STAGE * sizeof(T)));
   static constexpr int NST = NST_FIT >= 4 ? 4 : NST_FIT;
   static_assert(NST >= 2, "sweep tile does not fit in shared memory");
@@ -304,6 +314,13 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   T* stage0 = Rs + Cfg::RS_ROWS * LD;
   int* ired = reinterpret_cast<int*>(stage0 + NST * Cfg::STAGE);
   SweepStep* sst = reinterpret_cast<SweepStep*>(ired + Cfg::IRED);  // step table cached on chip
+  // push-exchange buffers (16-byte aligned: the step table is 40 * 64 bytes)
+  T* Rb = reinterpret_cast<T*>(sst + kMaxOrder);   // receive slots [C][chunk][LD]
+  T* Gb = Rb + Cfg::RB_ROWS * LD;                  // gathered E' [RM][LD]
+  int* grec = reinterpret_cast<int*>(Gb + RM * LD);  // 16 records of 16 bytes: (exponent, bad)
+  int* srec = grec + 64;                            // this CTA's record
+  uint64_t* xbar = reinterpret_cast<uint64_t*>(srec + 4);  // [0] partial rows in, [1] reduced rows in
+  int xph = 0;
 
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
@@ -327,6 +344,15 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   }
 
   for (int q = tid; q < p.n_steps; q += NT) sst[q] = p.step[q];
+  if constexpr (Cfg::PUSH) {
+    if (tid == 0) {
+      tc::mbar_init(&xbar[0], 1);
+      tc::mbar_init(&xbar[1], 1);
+      tc::mbar_init_fence();
+      ired[Cfg::IRED - 1] = 0;  // abort flag of the bounded waits
+    }
+    cg::this_cluster().sync();  // barriers exist before any peer pushes
+  }
   __syncthreads();
 
   // ---- chunk pipeline ----
@@ -469,6 +495,79 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
             for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
           }
         }
+      }
+      if constexpr (Cfg::PUSH) {
+        // ---- push exchange: owners receive partial rows, every CTA the reduced ones ----
+        const int chunk = (nu + C - 1) / C;
+        const uint32_t rowb = LD * sizeof(T);
+        const int my0 = min(nu, crank * chunk), my_rows = min(nu, my0 + chunk) - my0;
+        volatile int* abort = ired + Cfg::IRED - 1;
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::mbar_expect_tx(&xbar[0], static_cast<uint32_t>(C * my_rows) * rowb);
+          for (int o = 0; o < C; ++o) {
+            const int r0o = min(nu, o * chunk), ro = min(nu, r0o + chunk) - r0o;
+            if (ro > 0)
+              tc::bulk_s2c(tc::mapa(tc::su32(Rb + crank * chunk * LD), o), Ts + r0o * LD, ro * rowb,
+                           tc::mapa(tc::su32(&xbar[0]), o));
+          }
+        }
+        if (!tc::mbar_wait(&xbar[0], xph & 1, abort)) {
+          bad = 1;
+          set_status(o.status, TT_STATUS_TIMEOUT);
+        }
+        const int nvv = (nv + V - 1) / V;
+        int lexp = kNoExp, lbad = 0;
+        for (int idx = tid; idx < my_rows * nvv; idx += NT) {
+          const int u = idx / nvv, c = (idx % nvv) * V;
+          VT sum = Vec16<T>::zero();
+          for (int r = 0; r < C; ++r)
+            sum = Vec16<T>::add(sum, *reinterpret_cast<const VT*>(Rb + (r * chunk + u) * LD + c));
+          *reinterpret_cast<VT*>(Rs + u * LD + c) = sum;
+#pragma unroll
+          for (int q = 0; q < V; ++q)
+            if (c + q < nv) track(lexp, lbad, Vec16<T>::get(sum, q));
+        }
+        block_exp<NW>(lexp, lbad, ired);
+        if (tid == 0) {
+          srec[0] = lexp;
+          srec[1] = lbad;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::mbar_expect_tx(&xbar[1], static_cast<uint32_t>(nu) * rowb + 16u * C);
+          for (int o = 0; o < C; ++o) {
+            if (my_rows > 0)
+              tc::bulk_s2c(tc::mapa(tc::su32(Gb + my0 * LD), o), Rs, my_rows * rowb, tc::mapa(tc::su32(&xbar[1]), o));
+            tc::bulk_s2c(tc::mapa(tc::su32(grec + 4 * crank), o), srec, 16, tc::mapa(tc::su32(&xbar[1]), o));
+          }
+        }
+        if (!tc::mbar_wait(&xbar[1], xph & 1, abort)) {
+          bad = 1;
+          set_status(o.status, TT_STATUS_TIMEOUT);
+        }
+        ++xph;
+        int gexp = kNoExp, gbad = 0;
+        for (int r = 0; r < C; ++r) {
+          gexp = max(gexp, grec[4 * r]);
+          gbad |= grec[4 * r + 1];
+        }
+        if (gbad) bad = 1;
+        const bool rescale = gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits);
+        if (rescale) log2s += gexp;
+        for (int idx = tid; idx < nu * nvv; idx += NT) {
+          const int u = idx / nvv, c = (idx % nvv) * V;
+          const VT v = *reinterpret_cast<const VT*>(Gb + u * LD + c);
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const T e = Vec16<T>::get(v, q);
+            Es[(c + q) * LD + u] = rescale ? mul_pow2<T>(e, -gexp) : e;
+          }
+        }
+        __syncthreads();
+        return;
       }
       cluster.sync();
       const int nvv = (nv + V - 1) / V;
