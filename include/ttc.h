@@ -177,10 +177,15 @@ typedef struct {
   int32_t prec;                  /* TT_P_NATIVE                                     */
 } tt_batch;
 
-/* Validate every pair, order the work longest-first, choose a tile
- * configuration per pair and size the device tables.  Host only, synchronous,
- * allocates host memory (freed by tt_plan_free).  Returns the bytes of the
- * packed device table (*packed_bytes) and of the workspace (*ws_bytes). */
+/* Validate every pair, order the work longest-first, plan each pair's sweep
+ * and size the device tables.  The plan of a contracted mode is its
+ * evaluation order (E B_i first or A_i^T E first, whichever a cost model of
+ * the kernel rates faster) and how many mode slices one panel of the kernel's
+ * products takes; the panel budget is the tile configuration reported by
+ * tt_plan_info (0, 1, 2 = a quarter, half or all of the kernel's buffer),
+ * autotuned per (rank, mode size) bucket.  Host only, synchronous, allocates
+ * host memory (freed by tt_plan_free).  Returns the bytes of the packed
+ * device table (*packed_bytes) and of the workspace (*ws_bytes). */
 int tt_batch_plan(const tt_batch* batch, tt_plan** plan, size_t* packed_bytes, size_t* ws_bytes);
 
 /* Write the packed table into host memory `packed_host` (packed_bytes long);
@@ -222,13 +227,13 @@ int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile
 void tt_plan_free(tt_plan* plan);
 
 /* Tile autotuner for the batched launch.  For every (rank bucket <= 32, <= 64,
- * <= 128) x (mode-size bucket <= 8, <= 16, <= 32, > 32) it times each rank
- * tile that fits on a synthetic batch of order-6 pairs filling the GPU, and
- * writes the fastest as text lines "dtype rank_bucket mode_bucket tile" to
- * `cache_path`.  tt_batch_plan reads the file named by the environment
- * variable TTC_AUTOTUNE_CACHE (without it, the smallest tile that fits is
- * used).  Synchronous; unlike every other call it allocates (and frees)
- * device memory and must not be called during stream capture. */
+ * <= 128) x (mode-size bucket <= 8, <= 16, <= 32, > 32) it times each panel
+ * budget level (0, 1, 2) on a synthetic batch of order-6 pairs filling the
+ * GPU, and writes the fastest as text lines
+ * "dtype rank_bucket mode_bucket level" to `cache_path`.  tt_batch_plan reads
+ * the file named by the environment variable TTC_AUTOTUNE_CACHE (without it,
+ * level 2 is used).  Synchronous; unlike every other call it allocates (and
+ * frees) device memory and must not be called during stream capture. */
 int tt_autotune(int dtype, const char* cache_path);
 
 /* ---------------------------------------------------------------------------

@@ -25,7 +25,7 @@ struct tt_plan {
 
 namespace ttc {
 
-// Autotuned tile per (dtype, rank bucket, mode bucket); -1 = not tuned.
+// Autotuned panel-budget level per (dtype, rank bucket, mode bucket); -1 = not tuned.
 struct TuneTable {
   int tile[2][3][4];
   bool loaded = false;
@@ -55,13 +55,12 @@ static TuneTable& tune_table() {
   return t;
 }
 
-static int choose_tile(const SweepParams& p, int dtype) {
-  const int rmax = sweep_max_rank(p);
-  const int need = rank_bucket(rmax);
+// Panel-budget level of a pair's engine plan (see plan_engine_steps): the
+// autotuned value of its (rank, mode) bucket, else the full budget.
+static int choose_level(const SweepParams& p, int dtype) {
   const int d = dtype == TT_F64 ? 1 : 0;
-  const int tuned = tune_table().tile[d][need][mode_bucket(sweep_max_mode(p))];
-  const int maxt = dtype == TT_F64 ? 1 : 2;
-  return std::min(maxt, std::max(need, tuned));
+  const int tuned = tune_table().tile[d][rank_bucket(sweep_max_rank(p))][mode_bucket(sweep_max_mode(p))];
+  return tuned >= 0 ? tuned : 2;
 }
 
 }  // namespace ttc
@@ -104,7 +103,8 @@ int tt_batch_plan(const tt_batch* b, tt_plan** plan_out, size_t* packed_bytes, s
       delete plan;
       return rc;
     }
-    plan->tile[i] = choose_tile(plan->table[i], plan->dtype);
+    plan->tile[i] = choose_level(plan->table[i], plan->dtype);
+    plan_engine_steps(plan->table[i], plan->dtype, plan->tile[i]);
     plan->cost[i] = sweep_flops(plan->table[i]);
   }
   // longest processing time first
@@ -185,7 +185,7 @@ int tt_autotune(int dtype, const char* cache_path) {
   if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_DTYPE;
   const int d = dtype == TT_F64 ? 1 : 0;
   const int eb = dtype == TT_F64 ? 8 : 4;
-  const int ntiles = dtype == TT_F64 ? 2 : 3;
+  const int nlevels = 3;
   const int rank_of[3] = {32, 64, 128};
   const int mode_of[4] = {8, 16, 32, 48};
   int dev = 0, sms = 0;
@@ -208,7 +208,7 @@ int tt_autotune(int dtype, const char* cache_path) {
     return TT_ERR_CUDA;
   }
   for (int rb = 0; rb < 3 && rc == TT_OK; ++rb) {
-    if (rb >= ntiles) break;
+    if (dtype == TT_F64 && rb == 2) break;  // float64 ranks stop at 64
     for (int ib = 0; ib < 4 && rc == TT_OK; ++ib) {
       const int R = dtype == TT_F64 ? std::min(rank_of[rb], 64) : rank_of[rb];
       const int I = mode_of[ib];
@@ -232,6 +232,8 @@ int tt_autotune(int dtype, const char* cache_path) {
       build_full(&x, &x, nullptr, nullptr, nullptr, &p);
       std::vector<SweepParams> tab(npairs, p);
       std::vector<int32_t> ord(npairs), tl(npairs);
+      std::vector<SweepParams> lvl_tab(nlevels, p);
+      for (int t = 0; t < nlevels; ++t) plan_engine_steps(lvl_tab[t], dtype, t);
       std::iota(ord.begin(), ord.end(), 0);
       if (cudaMalloc(&dev_table, sizeof(SweepParams) * npairs + 8 * npairs + 256) != cudaSuccess ||
           cudaMalloc(&counter, 256) != cudaSuccess || cudaMalloc(&out, sizeof(double) * npairs) != cudaSuccess) {
@@ -239,11 +241,12 @@ int tt_autotune(int dtype, const char* cache_path) {
         break;
       }
       char* tb = static_cast<char*>(dev_table);
-      cudaMemcpy(tb, tab.data(), sizeof(SweepParams) * npairs, cudaMemcpyHostToDevice);
       cudaMemcpy(tb + sizeof(SweepParams) * npairs, ord.data(), 4 * npairs, cudaMemcpyHostToDevice);
       float best_ms = 1e30f;
-      int best = rb;
-      for (int t = rb; t < ntiles; ++t) {
+      int best = nlevels - 1;
+      for (int t = 0; t < nlevels; ++t) {
+        std::fill(tab.begin(), tab.end(), lvl_tab[t]);
+        cudaMemcpy(tb, tab.data(), sizeof(SweepParams) * npairs, cudaMemcpyHostToDevice);
         std::fill(tl.begin(), tl.end(), t);
         cudaMemcpy(tb + sizeof(SweepParams) * npairs + 4 * npairs, tl.data(), 4 * npairs, cudaMemcpyHostToDevice);
         float ms_sum = 0.f;

@@ -4,11 +4,12 @@
 // The grid holds as many CTAs as fit on the GPU at once.  Each CTA takes the
 // next pair from a global counter (pairs are pre-sorted longest-first, so the
 // queue is an LPT schedule) and runs the whole environment sweep of that pair
-// -- and, for a partial contraction, its chain emission -- with the shared
-// sweep body, using the rank tile the plan chose for the pair.  Nothing in
+// -- and, for a partial contraction, its chain emission -- with the per-CTA
+// engine of pair_engine.cuh, following the evaluation order and panels the plan chose
+// for each mode.  Nothing in
 // the launch depends on the host: the counter is reset by a memset node, so
 // the pair (memset, kernel) can be captured in a CUDA graph and replayed.
-#include "sweep_body.cuh"
+#include "pair_engine.cuh"
 
 namespace ttc {
 
@@ -25,23 +26,10 @@ struct BatchKernelParams {
   int32_t* status;
 };
 
-constexpr int kBatchThreads = SweepCfg<float, 128, false>::NT;
-static_assert(SweepCfg<double, 64, false>::NT == kBatchThreads, "one block size for every tile");
-
-template <typename T, int RM>
-__device__ __forceinline__ void run_pair(const SweepParams& p, const SweepOut& o, unsigned char* smem) {
-  SweepState<T, RM, false> st;
-  if (sweep_body<T, RM, false>(p, o, smem, 1, 0, st)) sweep_tail<T, RM, false>(p, o, smem, 1, 0, st);
-}
+constexpr int kBatchThreads = eng::NTOT;
 
 template <typename T>
-struct BatchSmem {
-  static constexpr size_t value =
-      sizeof(T) == 4 ? SweepCfg<float, 128, false>::SMEM : SweepCfg<double, 64, false>::SMEM;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(512, 1) batched_kernel(const __grid_constant__ BatchKernelParams bp) {
+__global__ void __launch_bounds__(eng::NTOT, 1) batched_kernel(const __grid_constant__ BatchKernelParams bp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   for (;;) {
@@ -51,18 +39,9 @@ __global__ void __launch_bounds__(512, 1) batched_kernel(const __grid_constant__
     const int idx = s_idx;
     if (idx >= bp.n) break;
     const int pair = bp.order[idx];
-    const SweepParams& p = bp.table[pair];
     SweepOut o{bp.out + pair, bp.out_log2 != nullptr ? bp.out_log2 + pair : nullptr, bp.status};
     o.skip_copies = 1;
-    const int tile = bp.tile[pair];
-    if constexpr (sizeof(T) == 4) {
-      if (tile == 0) run_pair<T, 32>(p, o, smem);
-      else if (tile == 1) run_pair<T, 64>(p, o, smem);
-      else run_pair<T, 128>(p, o, smem);
-    } else {
-      if (tile == 0) run_pair<T, 32>(p, o, smem);
-      else run_pair<T, 64>(p, o, smem);
-    }
+    eng::run_pair<T>(bp.table[pair], o, smem);
   }
 }
 
@@ -122,7 +101,7 @@ __global__ void __launch_bounds__(256) copy_jobs_kernel(const CopyJob* __restric
 
 template <typename T>
 static cudaError_t launch_batched_impl(const BatchKernelParams& bp, int grid, cudaStream_t s) {
-  const size_t smem = BatchSmem<T>::value;
+  const size_t smem = eng::smem_bytes<T>();
   cudaError_t err =
       cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;

@@ -419,6 +419,98 @@ inline int merged_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, 
   return TT_OK;
 }
 
+// ---- planning of the batched engine (pair_engine.cuh) ----
+//
+// For every contracted mode but the float64 last one, choose the evaluation
+// order (0: E B_i first, 1: A_i^T E first) and the slices per panel g that
+// minimise a model of the engine's time (eng_mode_cost).  `level` (0..2, the
+// autotuned knob) caps the T panel at 1/4, 1/2 or all of the engine's budget.
+inline int eng_r4(int v) { return (v + 3) & ~3; }
+inline int eng_pow2_floor(int v) { return v <= 1 ? 1 : pow2_floor(v); }
+
+struct EngGeom {
+  int v, tiles_cap, tbuf, stage, wmax;
+};
+inline EngGeom eng_geom(int dtype) {
+  if (dtype == TT_F64)
+    return {EngLimits<double>::V, EngLimits<double>::TILES, EngLimits<double>::TBUF, EngLimits<double>::STAGE,
+            EngLimits<double>::WMAX};
+  return {EngLimits<float>::V, EngLimits<float>::TILES, EngLimits<float>::TBUF, EngLimits<float>::STAGE,
+          EngLimits<float>::WMAX};
+}
+
+inline int eng_r8(int v) { return (v + 7) & ~7; }
+
+// Largest slices per panel the engine accepts for a mode (stage width and
+// T-panel budget r8(m) * r8(g n_pad) <= budget); mirrors pair_engine.cuh.
+inline int eng_gmax(const EngGeom& eg, int m, int n, int u, int I, int budget) {
+  const int n4 = eng_r4(n), u4 = eng_r4(u);
+  const int gw = std::max(1, eg.wmax / std::max(n4, u4));
+  const int gt = std::max(1, ((budget / eng_r8(m)) & ~7) / n4);
+  return std::max(1, std::min({I, gw, gt}));
+}
+
+// Model time (per-thread multiply-adds) of one mode of sizes m, k, n, u with
+// I slices in panels of g: one or two 4x4 tiles per thread (as the engine
+// picks), k (GEMM1) and m (GEMM2, per slice of a replica group) steps per
+// panel, plus a fixed cost per streamed chunk.
+inline double eng_mode_cost(const EngGeom& eg, bool f64, int m, int k, int n, int u, int I, int g) {
+  const int NT = kEngThreads;
+  constexpr double kChunk = 200.0;  // stage hand-off and pipeline bubble per streamed chunk
+  const int n_pad = eng_r4(n), u_pad = eng_r4(u), m_pad = eng_r4(m);
+  const int lwf = eng_r4(g * n_pad) + eg.v, lws = g * u_pad + eg.v;
+  const int kcf = eng_pow2_floor(std::min(32, eg.stage / lwf)), kcs = eng_pow2_floor(std::min(32, eg.stage / lws));
+  const int tiles1 = (m_pad / 4) * (eng_r4(g * n_pad) / 4);
+  const int tiles2 = (u_pad / 4) * (n_pad / 4);
+  int rep = std::min(g, NT / 32);
+  rep = std::min(rep, std::max(1, NT / tiles2));
+  rep = std::min(rep, std::max(1, eg.tbuf / (eng_r8(u) * eng_r8(n))));
+  rep = eng_pow2_floor(rep);
+  const int ntr = NT / rep;
+  const bool one = f64 || (tiles1 <= NT && tiles2 <= ntr);  // one 4x4 tile per thread, else two
+  const double fpk = one ? 16.0 : 32.0;                     // multiply-adds per thread per step
+  auto panel = [&](int gc) {
+    const double t1 = fpk * k + kChunk * ((k + kcf - 1) / kcf);
+    const double t2 = ((gc + rep - 1) / rep) * fpk * m + kChunk * ((m + kcs - 1) / kcs);
+    return t1 + t2;
+  };
+  const int full = I / g, rest = I - full * g;
+  double t = full * panel(g) + (rest > 0 ? panel(rest) : 0.0);
+  t += 4.0 * rep * ((u * (n_pad / 4) + NT - 1) / NT);  // reduction of the replica partials
+  return t;
+}
+
+inline void plan_engine_steps(SweepParams& p, int dtype, int level) {
+  const EngGeom eg = eng_geom(dtype);
+  const bool f64 = dtype == TT_F64;
+  const int budget = eg.tiles_cap >> (2 - std::max(0, std::min(2, level)));
+  const int n_modes = p.final_scalar ? p.n_steps - 1 : p.n_steps;
+  static const int cand[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128};
+  for (int j = 0; j < p.n_steps; ++j) {
+    SweepStep& st = p.step[j];
+    st.ord = 0;
+    st.g = 1;
+    if (j >= n_modes) continue;
+    double best = 1e300;
+    for (int ord = 0; ord < 2; ++ord) {
+      const int m = ord == 0 ? st.rin_x : st.rin_y, k = ord == 0 ? st.rin_y : st.rin_x;
+      const int n = ord == 0 ? st.rout_y : st.rout_x, u = ord == 0 ? st.rout_x : st.rout_y;
+      const int gmax = eng_gmax(eg, m, n, u, st.I, budget);
+      auto consider = [&](int g) {
+        const double c = eng_mode_cost(eg, f64, m, k, n, u, st.I, g);
+        if (c < best) {
+          best = c;
+          st.ord = ord;
+          st.g = g;
+        }
+      };
+      for (int g : cand)
+        if (g <= gmax) consider(g);
+      consider(gmax);
+    }
+  }
+}
+
 // Flops of one contracted mode, the cheaper of the two evaluation orders.
 inline double mode_flops(int rx, int rx2, int ry, int ry2, int I) {
   const double a = double(rx) * ry * I * ry2 + double(rx) * I * rx2 * ry2;

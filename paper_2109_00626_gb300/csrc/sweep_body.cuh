@@ -314,7 +314,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   T* stage0 = Rs + Cfg::RS_ROWS * LD;
   int* ired = reinterpret_cast<int*>(stage0 + NST * Cfg::STAGE);
   SweepStep* sst = reinterpret_cast<SweepStep*>(ired + Cfg::IRED);  // step table cached on chip
-  // push-exchange buffers (16-byte aligned: the step table is 40 * 64 bytes)
+  // push-exchange buffers (16-byte aligned: the step table is 48 * 64 bytes)
   T* Rb = reinterpret_cast<T*>(sst + kMaxOrder);   // receive slots [C][chunk][LD]
   T* Gb = Rb + Cfg::RB_ROWS * LD;                  // gathered E' [RM][LD]
   int* grec = reinterpret_cast<int*>(Gb + RM * LD);  // 16 records of 16 bytes: (exponent, bad)

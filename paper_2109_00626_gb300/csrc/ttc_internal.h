@@ -32,6 +32,36 @@ struct SweepStep {
   int I;
   int rin_x, rout_x;  // p range, u range
   int rin_y, rout_y;  // q range, v range
+  // Batched engine only (filled by plan_engine_steps): evaluation order
+  // (0: T_i = E B_i first, 1: U_i = A_i^T E first) and slices per panel.
+  int ord;
+  int g;
+};
+
+// Geometry limits of the per-CTA engine of the batched launch (pair_engine.cuh);
+// the host planner chooses each step's order and panel within them.
+constexpr int kEngThreads = 512;  // threads of a batched-engine CTA
+template <typename T>
+struct EngLimits;
+template <>
+struct EngLimits<float> {
+  static constexpr int RM = 128;          // largest rank
+  static constexpr int V = 4;             // elements per 16 bytes
+  static constexpr int LDE = RM + V;      // environment row stride
+  static constexpr int TBUF = RM * LDE;   // T panel / reduction scratch (elements)
+  static constexpr int STAGE = 32 * LDE;  // one pipeline stage (elements)
+  static constexpr int WMAX = 512;        // widest panel (columns)
+  static constexpr int TILES = 16384;     // r8(m) * r8(panel width) cap (two 4x4 tiles per thread)
+};
+template <>
+struct EngLimits<double> {
+  static constexpr int RM = 64;
+  static constexpr int V = 2;
+  static constexpr int LDE = RM + V;
+  static constexpr int TBUF = RM * LDE;
+  static constexpr int STAGE = 32 * LDE;
+  static constexpr int WMAX = 256;
+  static constexpr int TILES = 4096;      // one 4x4 tile per thread for both products
 };
 
 // Copy / leg-swap of one free core into the chain-layout output.

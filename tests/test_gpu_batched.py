@@ -127,6 +127,70 @@ def test_batched_matches_single_calls_and_graph_replay():
                 assert torch.equal(c, e)
 
 
+def _engine_pairs(dtype, rmax):
+    """Shapes that reach every branch of the batched kernel's planner: mode
+    sizes above one panel of the float64 last mode, ragged ranks up to the
+    cap, both evaluation orders (asymmetric ranks), right-to-left sweeps
+    (trailing blocks), an empty contracted set, order-1 pairs."""
+    r = lambda v: min(v, rmax)
+    shapes = [
+        ([70, 3, 45], [1, r(128), 5, 1], [1, 7, r(128), 1], None),
+        ([9, 33, 2, 17], [1, r(100), r(127), 3, 1], [1, 4, r(99), r(128), 1], [0, 0, 1, 1]),
+        ([5, 6, 7, 8, 9], [1, 3, r(90), 2, r(77), 1], [1, r(64), 1, r(80), 5, 1], [1, 1, 1, 0, 0]),
+        ([31, 2, 29], [1, r(65), r(66), 1], [1, r(67), r(68), 1], [0, 0, 0]),
+        ([37], [1, 1], [1, 1], None),
+        ([4, 130], [1, r(128), 1], [1, r(97), 1], None),
+        ([11, 12, 13], [1, 1, 1, 1], [1, r(128), r(128), 1], [1, 0, 0]),
+        ([16, 16, 16, 16], [1, r(120), 9, r(121), 1], [1, 2, r(122), 3, 1], [0, 1, 1, 1]),
+    ]
+    rng = np.random.default_rng(7)
+    out = []
+    for modes, rx, ry, mask in shapes:
+        x = G.random_tt(rng, modes, rx, dtype)
+        y = G.random_tt(rng, modes, ry, dtype)
+        out.append((x, y, mask))
+    return out
+
+
+@pytest.mark.parametrize("dtype,rmax,tol", [(np.float32, 128, 1e-5), (np.float64, 64, 1e-12)])
+def test_batched_engine_shapes(dtype, rmax, tol):
+    pairs = _engine_pairs(dtype, rmax)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, tol)
+
+
+def test_batched_rescaling_split_output():
+    """Cores scaled by 2^24 each: the float32 environment leaves the float
+    range after a few modes unless it is renormalised; the split output
+    (mantissa, exponent) must match the float64 oracle."""
+    rng = np.random.default_rng(11)
+    pairs = []
+    for n in (5, 7, 9):
+        modes = [int(v) for v in rng.integers(2, 20, size=n)]
+        rx = [1] + [int(v) for v in rng.integers(4, 100, size=n - 1)] + [1]
+        ry = [1] + [int(v) for v in rng.integers(4, 100, size=n - 1)] + [1]
+        x = [c * np.float32(2.0**24) for c in G.random_tt(rng, modes, rx, np.float32)]
+        y = [c * np.float32(2.0**24) for c in G.random_tt(rng, modes, ry, np.float32)]
+        pairs.append((x, y, None))
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev, split=True)
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    for p, (x, y, _) in enumerate(pairs):
+        n = len(x)
+        xs = [c.astype(np.float64) / 2.0**24 for c in x]
+        ys = [c.astype(np.float64) / 2.0**24 for c in y]
+        want = O.contract_full(xs, ys)  # z / 2^(48 n)
+        m, e = float(bat.out[p].item()), int(bat.log2[p].item())
+        got = np.ldexp(m, e - 48 * n)
+        assert abs(got - want) <= 1e-5 * norm_scale(xs, ys), (p, got, want)
+
+
 def test_batched_lpt_and_generator_shapes():
     """A slice of the 4096-pair workload itself (shapes from its generator)."""
     specs = G.batch4096_spec(64)
@@ -150,8 +214,8 @@ def test_autotune_cache(tmp_path, monkeypatch):
     lines = open(path).read().split("\n")
     rows = [list(map(int, ln.split())) for ln in lines if ln.strip()]
     assert len(rows) == 12
-    for d, rb, ib, tile in rows:
-        assert d == 0 and tile >= rb
+    for d, rb, ib, level in rows:
+        assert d == 0 and 0 <= level <= 2
     pairs = _uneven_pairs(8, 5)
     dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
     bat = T.BatchedContraction(dev)
