@@ -338,7 +338,7 @@ def run_ours(args):
             },
             "gflops": (f_full + f_part) / (ms / 1e3) / 1e9,
             "roofline": {
-                "kernel": "sweep_cluster_kernel<float,64> (full contraction)",
+                "kernel": "sweep_two_sided_kernel<float,64> (full contraction, two clusters from both ends)",
                 "bound": "alu",
                 "achieved": achieved,
                 "peak": peak,

@@ -110,6 +110,12 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
  * (Fig. 1b: contraction along every mode to a scalar; the all-mode
  * generalisation of Algorithm 2 step 4).  X and Y have the same order and mode
  * sizes; ranks are independent.
+ *   ws, ws_bytes device workspace.  For float32/float64 products with a
+ *                workspace of tt_workspace_bytes(TT_OP_FULL) bytes and order
+ *                >= 2, the environment is swept from both ends at once and
+ *                the halves meet in the middle (half the dependent steps);
+ *                with ws NULL or smaller the contraction runs as one sweep.
+ *                The tensor-core forms need their workspace (TT_ERR_WS).
  *   out_dev      device double.  If out_log2_dev is NULL it receives z;
  *                otherwise it receives a mantissa m and *out_log2_dev an int64 e
  *                with z = m * 2^e (use this form when |z| may leave the double

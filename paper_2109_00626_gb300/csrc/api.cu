@@ -137,6 +137,7 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
       *bytes = tc_full_ws(x, y, prec, &rc);
       return rc;
     }
+    if (x->order >= 2) *bytes = two_sided_layout(x, y).bytes;  // both-ends sweep
     return TT_OK;
   }
   if (op == TT_OP_PARTIAL) {
@@ -176,9 +177,24 @@ int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_d
     return tc_full_launch(x, y, prec, out_dev, out_log2_dev, status_dev, ws, ws_bytes,
                           reinterpret_cast<cudaStream_t>(stream));
   if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SweepParams p;
   build_full(x, y, out_dev, out_log2_dev, status_dev, &p);
-  return launch_sweep(p, x->dtype, reinterpret_cast<cudaStream_t>(stream));
+  const int rmax = sweep_max_rank(p);
+  if (rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
+  if (x->order >= 2 && ws != nullptr) {
+    // with a workspace, sweep from both ends on two clusters at once
+    const TwoSidedLayout L = two_sided_layout(x, y);
+    const int want = pow2_floor(std::min(16, sweep_max_mode(p)));
+    const int C = sweep_cluster_size(rmax, elem_bytes(x->dtype), want);
+    if (ws_bytes >= L.bytes && C >= 2) {
+      TwoSidedParams tp;  // copied by the launch
+      build_two_sided(x, y, L, ws, out_dev, out_log2_dev, status_dev, &tp);
+      if (cudaMemsetAsync(tp.counter, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+      return launch_two_sided(tp, x->dtype, rmax, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+    }
+  }
+  return launch_sweep(p, x->dtype, s);
 }
 
 int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int32_t* z_order,

@@ -286,6 +286,56 @@ inline void build_full(const tt_desc* x, const tt_desc* y, double* out_dev, int6
   p.status = status_dev;
 }
 
+// Workspace of a full contraction run from both ends (sweep.cu): the two
+// meeting environments, their scales and the arrival counter.
+struct TwoSidedLayout {
+  int h = 0;  // modes [0, h) sweep left to right, [h, N) right to left
+  int rx = 1, ry = 1;
+  size_t off_el = 0, off_er = 0, off_ll = 0, off_lr = 0, off_ctr = 0, bytes = 0;
+};
+
+inline TwoSidedLayout two_sided_layout(const tt_desc* x, const tt_desc* y) {
+  TwoSidedLayout L;
+  const int n = x->order;
+  L.h = n / 2;
+  L.rx = x->ranks[L.h];
+  L.ry = y->ranks[L.h];
+  const size_t env = align256(static_cast<size_t>(L.rx) * L.ry * elem_bytes(x->dtype));
+  L.off_el = 0;
+  L.off_er = env;
+  L.off_ll = 2 * env;
+  L.off_lr = L.off_ll + 256;
+  L.off_ctr = L.off_lr + 256;
+  L.bytes = L.off_ctr + 256;
+  return L;
+}
+
+// Parameters of the two half sweeps into a workspace laid out by L.
+inline void build_two_sided(const tt_desc* x, const tt_desc* y, const TwoSidedLayout& L, void* ws, double* out_dev,
+                            int64_t* out_log2_dev, int32_t* status_dev, TwoSidedParams* tp) {
+  char* w = static_cast<char*>(ws);
+  const int n = x->order;
+  for (int side = 0; side < 2; ++side) {
+    SweepParams& p = tp->half[side];
+    memset(&p, 0, sizeof(p));
+    if (side == 0) fill_left(p, x, y, 0, L.h);
+    else fill_right(p, x, y, L.h, n);
+    p.rx0 = 1;
+    p.ry0 = 1;
+    p.final_scalar = 0;
+    p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+    p.e_out = w + (side == 0 ? L.off_el : L.off_er);
+    p.e_out_log2 = reinterpret_cast<int64_t*>(w + (side == 0 ? L.off_ll : L.off_lr));
+    p.status = status_dev;
+  }
+  tp->rx = L.rx;
+  tp->ry = L.ry;
+  tp->z_out = out_dev;
+  tp->z_out_log2 = out_log2_dev;
+  tp->status = status_dev;
+  tp->counter = reinterpret_cast<int*>(w + L.off_ctr);
+}
+
 inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
   const int rc = check_desc(g);
   if (rc != TT_OK) return rc;

@@ -1,7 +1,8 @@
 // Single-contraction launches of the environment sweep (sweep_body.cuh): one
 // thread-block cluster of up to 16 CTAs splits every contracted mode over its
 // mode index; a cluster of one CTA runs the same body without the
-// distributed-shared-memory reduction.
+// distributed-shared-memory reduction; a full contraction with a workspace
+// runs as two clusters sweeping from both ends.
 #include "sweep_body.cuh"
 
 namespace ttc {
@@ -20,6 +21,73 @@ __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_cons
   }
 }
 
+// Full contraction from both ends: cluster 0 sweeps the leading modes left to
+// right, cluster 1 the trailing ones right to left, each on its own SMs, and
+// the two environments meet in the middle, z = sum_{a,b} E_L[a][b] F_R[a][b]
+// (float64).  Each cluster writes its environment (mantissa and power-of-two
+// scale) to the workspace; the one that finishes second (a counter in the
+// workspace, zeroed before the launch) forms z.  No cluster waits for the
+// other, so nothing depends on both being resident at once.
+template <typename T, int RM>
+__global__ void __launch_bounds__(256, 1) sweep_two_sided_kernel(const __grid_constant__ TwoSidedParams tp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_last;
+  __shared__ double s_red[8];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = static_cast<int>(cluster.num_blocks());
+  const int crank = static_cast<int>(cluster.block_rank());
+  const int side = static_cast<int>(blockIdx.x) / C;
+  const SweepParams& p = tp.half[side];
+  SweepState<T, RM, true> st;
+  const SweepOut o{nullptr, nullptr, tp.status};
+  if (sweep_body<T, RM, true>(p, o, smem, C, crank, st)) {
+    sweep_tail<T, RM, true>(p, o, smem, C, crank, st);
+    cluster.sync();  // peers may still be reading this CTA's reduced rows
+  }
+  if (crank != 0) return;
+  __threadfence();  // this cluster's environment and scale are visible before the count
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(tp.counter, 1);
+  __syncthreads();
+  if (s_last != 1) return;
+  __threadfence();
+  const T* el = static_cast<const T*>(tp.half[0].e_out);
+  const T* er = static_cast<const T*>(tp.half[1].e_out);
+  const int n = tp.rx * tp.ry;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    part = fma(static_cast<double>(__ldcg(el + i)), static_cast<double>(__ldcg(er + i)), part);
+  part = warp_sum(part);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double z = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) z += s_red[w];
+    const int64_t log2s = __ldcg(tp.half[0].e_out_log2) + __ldcg(tp.half[1].e_out_log2);
+    int st_bits = isfinite(z) ? 0 : TT_STATUS_NONFINITE;
+    if (tp.z_out_log2 != nullptr) {
+      *tp.z_out = z;
+      *tp.z_out_log2 = log2s;
+    } else {
+      double v = z;
+      if (z != 0.0 && isfinite(z)) {
+        const int64_t tot = static_cast<int64_t>(exp2_of(z)) + log2s;
+        if (tot > 1024) {
+          v = z > 0 ? INFINITY : -INFINITY;
+          st_bits |= TT_STATUS_OVERFLOW;
+        } else if (tot < -1074) {
+          v = 0.0;
+        } else {
+          v = ldexp(z, static_cast<int>(log2s));
+        }
+      }
+      *tp.z_out = v;
+    }
+    set_status(tp.status, st_bits);
+  }
+}
+
 template <typename T, int RM>
 __global__ void __launch_bounds__(512, 1) sweep_cta_kernel(const __grid_constant__ SweepParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -34,6 +102,11 @@ static cudaError_t prepare() {
                                          static_cast<int>(SweepCfg<T, RM, true>::SMEM));
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(sweep_cluster_kernel<T, RM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(sweep_two_sided_kernel<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(SweepCfg<T, RM, true>::SMEM));
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(sweep_two_sided_kernel<T, RM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err != cudaSuccess) return err;
   return cudaFuncSetAttribute(sweep_cta_kernel<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(SweepCfg<T, RM, false>::SMEM));
@@ -61,6 +134,26 @@ static cudaError_t launch_impl(const SweepParams& p, int C, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, sweep_cluster_kernel<T, RM>, p);
+}
+
+template <typename T, int RM>
+static cudaError_t launch_two_sided_impl(const TwoSidedParams& tp, int C, cudaStream_t s) {
+  cudaError_t err = prepare<T, RM>();
+  if (err != cudaSuccess) return err;
+  count_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * C, 1, 1);
+  cfg.blockDim = dim3(SweepCfg<T, RM, true>::NT, 1, 1);
+  cfg.dynamicSmemBytes = SweepCfg<T, RM, true>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_two_sided_kernel<T, RM>, tp);
 }
 
 template <typename T, int RM>
@@ -114,6 +207,19 @@ cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int C, cudaStream_t
   if (rmax <= 32) return launch_impl<float, 32>(p, C, s);
   if (rmax <= 64) return launch_impl<float, 64>(p, C, s);
   if (rmax <= 128) return launch_impl<float, 128>(p, C, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_two_sided(const TwoSidedParams& tp, int dtype, int rmax, int C, cudaStream_t s) {
+  if (C < 2) return cudaErrorInvalidValue;  // the kernel reduces across a cluster
+  if (dtype == TT_F64) {
+    if (rmax <= 32) return launch_two_sided_impl<double, 32>(tp, C, s);
+    if (rmax <= 64) return launch_two_sided_impl<double, 64>(tp, C, s);
+    return cudaErrorInvalidValue;
+  }
+  if (rmax <= 32) return launch_two_sided_impl<float, 32>(tp, C, s);
+  if (rmax <= 64) return launch_two_sided_impl<float, 64>(tp, C, s);
+  if (rmax <= 128) return launch_two_sided_impl<float, 128>(tp, C, s);
   return cudaErrorInvalidValue;
 }
 

@@ -106,6 +106,19 @@ struct SweepParams {
   EmitParams emit;        // fused chain emission after the sweep (partial contractions)
 };
 
+// Full contraction as two half sweeps meeting in the middle (sweep.cu):
+// half[0] covers the leading modes left to right, half[1] the trailing ones
+// right to left; both end with an environment of shape rx x ry in e_out (with
+// its scale in e_out_log2).
+struct TwoSidedParams {
+  SweepParams half[2];
+  int rx, ry;
+  double* z_out;
+  int64_t* z_out_log2;  // optional; if NULL the scale is folded into *z_out
+  int32_t* status;
+  int* counter;         // zeroed before the launch
+};
+
 // One mode of an adjoint block (left-to-right orientation): core k of X is
 // [rx][I][rx2], of Y [ry][I][ry2]; dgx / dgy receive the gradients.
 struct AdjStep {
@@ -207,6 +220,7 @@ cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStre
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
+cudaError_t launch_two_sided(const TwoSidedParams& tp, int dtype, int rmax, int cluster, cudaStream_t s);
 
 // One slice range [i0, i1) of a free-core copy of a chain-layout output; the
 // batched launch works through these after its sweep queue.

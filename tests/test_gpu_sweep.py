@@ -104,6 +104,34 @@ def test_full_renormalisation_split_scale():
     assert st == 0 and abs(np.ldexp(z, -480) - want) / norm_scale(x, y) <= 1e-5
 
 
+@pytest.mark.parametrize("dt,n", [(np.float32, 2), (np.float32, 3), (np.float32, 10), (np.float32, 11), (np.float64, 7)])
+def test_full_both_ends_matches_one_sweep(dt, n):
+    """With a workspace the full contraction runs from both ends (two
+    clusters meeting in the middle); without one, as a single sweep.  Both
+    must agree with the oracle."""
+    rng = np.random.default_rng(200 + n)
+    modes = [int(v) for v in rng.integers(1, 20, size=n)]
+    rmax = 64 if dt == np.float64 else 100
+    rx = [1] + [int(v) for v in rng.integers(1, rmax, size=n - 1)] + [1]
+    ry = [1] + [int(v) for v in rng.integers(1, rmax, size=n - 1)] + [1]
+    x = G.random_tt(rng, modes, rx, dt)
+    y = G.random_tt(rng, modes, ry, dt)
+    want = O.contract_full(x, y)
+    both = T.FullContraction(to_dev(x), to_dev(y))
+    one = T.FullContraction(to_dev(x), to_dev(y))
+    assert both.ws_bytes > 0
+    one.ws_bytes = 0  # no workspace: one sweep
+    n0 = T.launch_count()
+    both()
+    one()
+    torch.cuda.synchronize()
+    assert int(both.status.item()) == 0 and int(one.status.item()) == 0
+    for op in (both, one):
+        z = float(op.out.item())
+        assert abs(z - want) / norm_scale(x, y) <= TOL[dt], (z, want)
+    assert T.launch_count() - n0 == 2
+
+
 def test_full_overflow_status_without_split():
     x, y = G.pair(22, [4] * 4, G.tt_ranks(4, 4), G.tt_ranks(4, 4), np.float64)
     xs = [c * 2.0**300 for c in x]
