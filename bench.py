@@ -523,6 +523,31 @@ def bench_backward(T, dev, args):
     b.record(stream)
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(b) / K
+    # the same step captured once in a CUDA graph and replayed (how a training
+    # loop would run it: no Python between the kernels)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    stream.wait_stream(side)
+    for c in xd + yd:
+        c.grad = None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        zc = T.tt_partial(xd, yd, mask)
+        loss = T.tt_sum(zc)
+        loss.backward()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(K):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = a.elapsed_time(b) / K
+    del g
     modes, r = [16] * 12, G.tt_ranks(12, 64)
     fwd = W.partial_chain_flops(modes, r, r, mask)
     # adjoint: five products per contracted mode (U, dGx, W, dGy, next F), counted without recompute
@@ -532,6 +557,7 @@ def bench_backward(T, dev, args):
         "value": 1.0 / (ms / 1e3),
         "unit": "gradient evaluations/s",
         "ms_per_step": ms,
+        "ms_per_step_graph": graph_ms,
         "gflops": (fwd + bwd) / (ms / 1e3) / 1e9,
         "alg_flops": fwd + bwd,
         "roofline": {

@@ -421,55 +421,145 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
 //          dGx[a][i][u] = sum_y K[a][y] dC[u][i][y],  dK[a][y] = sum_{u,i} Gx[a][i][u] dC[u][i][y]
 //   trail: C[u][i][y] = sum_b Gx[u][i][b] K[b][y]
 //          dGx[u][i][b] = sum_y dC[u][i][y] K[b][y],  dK[b][y] = sum_{u,i} Gx[u][i][b] dC[u][i][y]
-// Blocks 0..I-1 compute the gradient slice i; block I computes dK; every
-// block then helps with the copies.
+// Both gradients are small products, run as shared-memory tiled GEMMs with
+// 4x4 register tiles (ranks <= 128): blocks 0..I-1 compute the gradient slice
+// i (K times the slice of dC), blocks I.. compute dK in 32-row tiles (a sum
+// over every (i, u) pair); every block then helps with the copies.  Operands
+// are staged in chunks of KCH rows of the summed index with coalesced loads.
 // ---------------------------------------------------------------------------
+namespace chainadj {
+constexpr int LDS = 132;  // staged row stride (elements): up to 128 columns
+constexpr int kRowsPerKBlock = 32;
+template <typename T>
+struct Ch {
+  static constexpr int KCH = sizeof(T) == 4 ? 32 : 16;  // 2 * KCH * 132 * sizeof(T) = 33.8 KB
+};
+
+// acc[a][b] += sum_{k<K} As[k][m0+a] * Bs[k][n0+b]
+template <typename T>
+__device__ __forceinline__ void tile44(T (&acc)[4][4], const T* As, const T* Bs, int K, int m0, int n0) {
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[k * LDS + m0 + a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bs[k * LDS + n0 + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+}
+}  // namespace chainadj
+
 template <typename T>
 __global__ void __launch_bounds__(256) chain_adjoint_kernel(const __grid_constant__ ChainAdjParams p) {
-  const int i = blockIdx.x;
+  using namespace chainadj;
+  constexpr int KCH = Ch<T>::KCH;
+  __shared__ __align__(16) T As[KCH * LDS];
+  __shared__ __align__(16) T Bs[KCH * LDS];
+  const int tid = threadIdx.x;
   const T* gx = static_cast<const T*>(p.gx);
   const T* k = static_cast<const T*>(p.k);
   const T* dc = static_cast<const T*>(p.dc);
-  const int64_t klg = p.k_log2 != nullptr ? *p.k_log2 : 0;
   const int ra = p.ra, rb = p.rb, I = p.I, ry = p.ry;
+  const int nk = p.lead ? ra : rb;  // rows of K
+  const int nkb = (nk + kRowsPerKBlock - 1) / kRowsPerKBlock;
   int bits = 0;
-  if (i < I) {
-    T* dg = static_cast<T*>(p.dgx);
-    if (p.lead) {
-      for (int idx = threadIdx.x; idx < ra * rb; idx += blockDim.x) {
-        const int a = idx / rb, u = idx - a * rb;
-        T s = T(0);
-        for (int y = 0; y < ry; ++y) s = fma(k[a * ry + y], dc[(static_cast<int64_t>(u) * I + i) * ry + y], s);
-        const T o = scale_pow2_sat<T>(s, klg);
-        if (!isfinite(o)) bits |= isfinite(s) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
-        dg[(static_cast<int64_t>(a) * I + i) * rb + u] = o;
+  if (static_cast<int>(blockIdx.x) < I) {
+    // ---- gradient slice i: out[m][n] = sum_y A[y][m] B[y][n] ----
+    //   lead : m = a < ra, n = u < rb, A[y][a] = K[a][y],         B[y][u] = dC[u][i][y]
+    //   trail: m = u < ra, n = b < rb, A[y][u] = dC[u][i][y],     B[y][b] = K[b][y]
+    const int i = blockIdx.x;
+    const int64_t klg = p.k_log2 != nullptr ? *p.k_log2 : 0;
+    const int M = ra, N = rb;
+    const int ncb = (N + 3) / 4, ntiles = ((M + 3) / 4) * ncb;
+    T acc[4][4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[t][a][b] = T(0);
+    for (int y0 = 0; y0 < ry; y0 += KCH) {
+      const int kc = min(KCH, ry - y0);
+      __syncthreads();
+      // stage: consecutive threads read consecutive y of one row
+      for (int e = tid; e < kc * M; e += blockDim.x) {
+        const int r = e / kc, yy = e - r * kc;
+        As[yy * LDS + r] = p.lead ? k[r * ry + y0 + yy] : dc[(static_cast<int64_t>(r) * I + i) * ry + y0 + yy];
       }
-    } else {
-      for (int idx = threadIdx.x; idx < ra * rb; idx += blockDim.x) {
-        const int u = idx / rb, b = idx - u * rb;
-        T s = T(0);
-        for (int y = 0; y < ry; ++y) s = fma(dc[(static_cast<int64_t>(u) * I + i) * ry + y], k[b * ry + y], s);
-        const T o = scale_pow2_sat<T>(s, klg);
-        if (!isfinite(o)) bits |= isfinite(s) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
-        dg[(static_cast<int64_t>(u) * I + i) * rb + b] = o;
+      for (int e = tid; e < kc * N; e += blockDim.x) {
+        const int c = e / kc, yy = e - c * kc;
+        Bs[yy * LDS + c] = p.lead ? dc[(static_cast<int64_t>(c) * I + i) * ry + y0 + yy] : k[c * ry + y0 + yy];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int tt = tid + t * 256;
+        if (tt < ntiles) tile44<T>(acc[t], As, Bs, kc, (tt / ncb) * 4, (tt % ncb) * 4);
       }
     }
-  } else if (i == I && p.dk != nullptr) {
-    T* dk = static_cast<T*>(p.dk);
-    const int nk = p.lead ? ra : rb;
-    for (int idx = threadIdx.x; idx < nk * ry; idx += blockDim.x) {
-      const int a = idx / ry, y = idx - a * ry;
-      T s = T(0);
-      for (int ii = 0; ii < I; ++ii) {
-        if (p.lead) {
-          for (int u = 0; u < rb; ++u)
-            s = fma(gx[(static_cast<int64_t>(a) * I + ii) * rb + u], dc[(static_cast<int64_t>(u) * I + ii) * ry + y], s);
-        } else {
-          for (int u = 0; u < ra; ++u)
-            s = fma(gx[(static_cast<int64_t>(u) * I + ii) * rb + a], dc[(static_cast<int64_t>(u) * I + ii) * ry + y], s);
+    T* dg = static_cast<T*>(p.dgx);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int tt = tid + t * 256;
+      if (tt >= ntiles) continue;
+      const int m0 = (tt / ncb) * 4, n0 = (tt % ncb) * 4;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int m = m0 + a, n = n0 + b;
+          if (m >= M || n >= N) continue;
+          const T sv = acc[t][a][b];
+          const T o = scale_pow2_sat<T>(sv, klg);
+          if (!isfinite(o)) bits |= isfinite(sv) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+          dg[(static_cast<int64_t>(m) * I + i) * rb + n] = o;
         }
+    }
+  } else if (static_cast<int>(blockIdx.x) < I + nkb && p.dk != nullptr) {
+    // ---- dK rows [r0, r0 + 32): dK[r][y] = sum_{i,u} A[(i,u)][r] dC[u][i][y] ----
+    //   lead : A = Gx[r][i][u] (u < rb);  trail: A = Gx[u][i][r] (u < ra)
+    const int r0 = (blockIdx.x - I) * kRowsPerKBlock;
+    const int M = min(kRowsPerKBlock, nk - r0), N = ry;
+    const int nu = p.lead ? rb : ra;
+    const int ncb = (N + 3) / 4, ntiles = ((M + 3) / 4) * ncb;  // <= 8 * 32 = 256
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    const bool on = tid < ntiles;
+    const int m0 = (tid / ncb) * 4, n0 = (tid % ncb) * 4;
+    for (int i = 0; i < I; ++i)
+      for (int u0 = 0; u0 < nu; u0 += KCH) {
+        const int kc = min(KCH, nu - u0);
+        __syncthreads();
+        for (int e = tid; e < kc * M; e += blockDim.x) {
+          if (p.lead) {
+            const int r = e / kc, uu = e - r * kc;  // contiguous in u
+            As[uu * LDS + r] = gx[(static_cast<int64_t>(r0 + r) * I + i) * rb + u0 + uu];
+          } else {
+            const int uu = e / M, r = e - uu * M;  // contiguous in r
+            As[uu * LDS + r] = gx[(static_cast<int64_t>(u0 + uu) * I + i) * rb + r0 + r];
+          }
+        }
+        for (int e = tid; e < kc * N; e += blockDim.x) {
+          const int uu = e / N, y = e - uu * N;  // contiguous in y
+          Bs[uu * LDS + y] = dc[(static_cast<int64_t>(u0 + uu) * I + i) * ry + y];
+        }
+        __syncthreads();
+        if (on) tile44<T>(acc, As, Bs, kc, m0, n0);
       }
-      dk[idx] = s;
+    if (on) {
+      T* dk = static_cast<T*>(p.dk);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (m0 + a < M && n0 + b < N) dk[(r0 + m0 + a) * ry + n0 + b] = acc[a][b];
     }
   }
   // copies: grid-stride over all blocks
@@ -551,9 +641,12 @@ cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStre
 }
 
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s) {
+  if (p.ra > 128 || p.rb > 128 || p.ry > 128) return cudaErrorInvalidValue;  // staged tiles hold 128 columns
+  const int nk = p.lead ? p.ra : p.rb;
+  const int grid = p.I + (nk + chainadj::kRowsPerKBlock - 1) / chainadj::kRowsPerKBlock;
   count_launch();
-  if (dtype == TT_F64) chain_adjoint_kernel<double><<<p.I + 1, 256, 0, s>>>(p);
-  else chain_adjoint_kernel<float><<<p.I + 1, 256, 0, s>>>(p);
+  if (dtype == TT_F64) chain_adjoint_kernel<double><<<grid, 256, 0, s>>>(p);
+  else chain_adjoint_kernel<float><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
