@@ -200,17 +200,21 @@ def to_bf16_f32(a: np.ndarray) -> np.ndarray:
     return out
 
 
-def batch4096_device(n_pairs: int = 4096, seed: int = 0, device="cuda", dtype=None):
+def batch4096_device(n_pairs: int = 4096, seed: int = 0, device="cuda", dtype=None, subset=None):
     """Cores of the uneven batch drawn on the device (the shapes are those of
     :func:`batch4096_spec`).  Core k of X (Y) of pair p is filled from a
     torch CUDA generator seeded with (seed, p, side, k), N(0, 1/(I_k R_k)).
     All cores of the batch live in one arena (16-byte aligned views), so the
     whole 15 GB batch is drawn in a few seconds.  Returns (specs, pairs) with
-    pairs[p] = (x_cores, y_cores, mask or None)."""
+    pairs[p] = (x_cores, y_cores, mask or None).  With ``subset`` (a list of
+    pair indices, e.g. one rank's shard) only those pairs are drawn, with the
+    same values as in the whole batch, and specs/pairs follow that list."""
     import torch
 
     dtype = dtype or torch.float32
-    specs = batch4096_spec(n_pairs, seed)
+    specs_all = batch4096_spec(n_pairs, seed)
+    ids = list(range(n_pairs)) if subset is None else [int(p) for p in subset]
+    specs = [specs_all[p] for p in ids]
     esize = torch.tensor([], dtype=dtype).element_size()
     align = max(1, 16 // esize)
     sizes = []
@@ -223,7 +227,7 @@ def batch4096_device(n_pairs: int = 4096, seed: int = 0, device="cuda", dtype=No
     gen = torch.Generator(device=device)
     off = 0
     pairs = []
-    for p, s in enumerate(specs):
+    for p, s in zip(ids, specs):
         sides = []
         for side, ranks in enumerate((s["ranks_x"], s["ranks_y"])):
             cores = []
