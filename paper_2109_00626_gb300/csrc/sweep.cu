@@ -7,14 +7,30 @@
 
 namespace ttc {
 
+// A chain-layout partial contraction launched with two clusters gives the
+// free-core copies (which depend on nothing) to the second one, so they run
+// while the first sweeps.
 template <typename T, int RM>
 __global__ void __launch_bounds__(256, 1) sweep_cluster_kernel(const __grid_constant__ SweepParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
+  if (blockIdx.x >= static_cast<unsigned>(C)) {
+    constexpr int NT = SweepCfg<T, RM, true>::NT;
+    const int64_t g = static_cast<int64_t>(crank) * NT + threadIdx.x, gs = static_cast<int64_t>(C) * NT;
+    for (int t = 0; t < p.emit.n_copies; ++t) {
+      const CopyTask& tk = p.emit.copy[t];
+      const T* __restrict__ src = static_cast<const T*>(tk.src);
+      T* __restrict__ dst = static_cast<T*>(tk.dst);
+      if (!tk.swap) copy_plain<T>(dst, src, static_cast<int64_t>(tk.r0) * tk.I * tk.r1, g, gs);
+      else copy_swap_tiled<T, NT>(dst, src, tk.r0, tk.I, tk.r1, reinterpret_cast<T*>(smem), C, crank);
+    }
+    return;
+  }
   SweepState<T, RM, true> st;
-  const SweepOut o{p.z_out, p.z_out_log2, p.status};
+  SweepOut o{p.z_out, p.z_out_log2, p.status};
+  o.skip_copies = gridDim.x > static_cast<unsigned>(C) ? 1 : 0;
   if (sweep_body<T, RM, true>(p, o, smem, C, crank, st)) {
     sweep_tail<T, RM, true>(p, o, smem, C, crank, st);
     cluster.sync();  // peers may still be reading this CTA's reduced rows
@@ -122,7 +138,8 @@ static cudaError_t launch_impl(const SweepParams& p, int C, cudaStream_t s) {
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C, 1, 1);
+  // a second cluster takes the free-core copies of a chain emission
+  cfg.gridDim = dim3(p.emit.enabled && p.emit.n_copies > 0 ? 2 * C : C, 1, 1);
   cfg.blockDim = dim3(SweepCfg<T, RM, true>::NT, 1, 1);
   cfg.dynamicSmemBytes = SweepCfg<T, RM, true>::SMEM;
   cfg.stream = s;
