@@ -344,8 +344,8 @@ def run_ours(args):
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": 4294656,
-                "note": "fp32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz (derived); single latency-bound contraction; traffic = ncu dram bytes read+write of one launch (profiles/two_sided_order10_r64.md)",
+                "traffic": None,
+                "note": "fp32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz (derived); single latency-bound contraction; traffic = ncu dram bytes read+write of one launch of this kernel",
             },
             "e2e": {
                 "value": 2 / (e2e_ms / 1e3) * world,

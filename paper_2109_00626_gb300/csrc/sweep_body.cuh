@@ -15,10 +15,11 @@
 // distributed shared memory: CTA c sums its share of rows over all peers
 // (fixed order: deterministic), and every CTA gets the reduced rows back into
 // its own copy of E'.  For float32 tiles up to rank 64 both exchanges are
-// pushes: bulk asynchronous copies from a CTA's shared memory into receive
-// buffers of its peers, completed on an mbarrier of the receiver (bounded
-// waits), so no cluster-wide barrier is taken per mode.  Other tiles pull
-// from the peers' shared memory between two cluster barriers.
+// pushes: bulk asynchronous copies from a CTA's shared memory into its peers'
+// (partial sums into receive slots, reduced rows straight into the peers'
+// transposed environments), completed on an mbarrier of the receiver
+// (bounded waits), so no cluster-wide barrier is taken per mode.  Other tiles
+// pull from the peers' shared memory between two cluster barriers.
 //
 // Scaling: after each mode the largest binary exponent of E' is compared with
 // +-s; outside that band E' is multiplied by an exact power of two and the
@@ -72,7 +73,7 @@ struct SweepCfg {
   // owner and reduced rows to every peer by bulk copies into receive buffers
   static constexpr bool PUSH = CL && sizeof(T) == 4 && RM <= 64;
   static constexpr int RB_ROWS = RM + 16;            // C slots of ceil(RM / C) rows
-  static constexpr size_t XB = PUSH ? ((RB_ROWS + RM) * LD * sizeof(T) + 16 * 16 + 16 + 16) : 0;
+  static constexpr size_t XB = PUSH ? (RB_ROWS * LD * sizeof(T) + 16 * 16 + 16 + 16) : 0;
   static constexpr size_t FIXED = (2 * TILE + RS_ROWS * LD) * sizeof(T) + IRED * sizeof(int) +
                                   kMaxOrder * sizeof(SweepStep) + XB;
   static constexpr int NST_FIT = static_cast<int>((kBudget - FIXED) / (STAGE * sizeof(T)));
@@ -316,8 +317,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   SweepStep* sst = reinterpret_cast<SweepStep*>(ired + Cfg::IRED);  // step table cached on chip
   // push-exchange buffers (16-byte aligned: the step table is 48 * 64 bytes)
   T* Rb = reinterpret_cast<T*>(sst + kMaxOrder);   // receive slots [C][chunk][LD]
-  T* Gb = Rb + Cfg::RB_ROWS * LD;                  // gathered E' [RM][LD]
-  int* grec = reinterpret_cast<int*>(Gb + RM * LD);  // 16 records of 16 bytes: (exponent, bad)
+  int* grec = reinterpret_cast<int*>(Rb + Cfg::RB_ROWS * LD);  // 16 records of 16 bytes: (exponent, bad)
   int* srec = grec + 64;                            // this CTA's record
   uint64_t* xbar = reinterpret_cast<uint64_t*>(srec + 4);  // [0] partial rows in, [1] reduced rows in
   int xph = 0;
@@ -484,65 +484,90 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
     if constexpr (CL) {
       cg::cluster_group cluster = cg::this_cluster();
       // ---- cluster reduction: E'[u][v] = sum over CTAs of P_c[u][v] ----
+      if constexpr (Cfg::PUSH) {
+        // Push exchange.  Partial sums are staged transposed (Ts[v][u]) and
+        // owned by blocks of v, so an owner's reduced block is whole rows of
+        // every CTA's transposed environment Es[v][u]: it is pushed straight
+        // into the peers' Es.  One lane per peer issues the bulk copies.
 #pragma unroll
-      for (int u = 0; u < NSE; ++u) {
-        const Sub sb = sub_tile<NT>(u, nu, nv);
-        if (sb.on) {
+        for (int u = 0; u < NSE; ++u) {
+          const Sub sb = sub_tile<NT>(u, nu, nv);
+          if (sb.on) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            T* row = Ts + (sb.m0 + a) * LD + sb.n0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
+            for (int b = 0; b < 4; ++b)
+              *reinterpret_cast<float4*>(Ts + (sb.n0 + b) * LD + sb.m0) =
+                  make_float4(acc[u][0][b], acc[u][1][b], acc[u][2][b], acc[u][3][b]);
           }
         }
-      }
-      if constexpr (Cfg::PUSH) {
-        // ---- push exchange: owners receive partial rows, every CTA the reduced ones ----
-        const int chunk = (nu + C - 1) / C;
+        const int chunk = (nv + C - 1) / C;
         const uint32_t rowb = LD * sizeof(T);
-        const int my0 = min(nu, crank * chunk), my_rows = min(nu, my0 + chunk) - my0;
+        const int my0 = min(nv, crank * chunk), my_rows = min(nv, my0 + chunk) - my0;
         volatile int* abort = ired + Cfg::IRED - 1;
         tc::fence_proxy_async();
         __syncthreads();
-        if (tid == 0) {
-          tc::mbar_expect_tx(&xbar[0], static_cast<uint32_t>(C * my_rows) * rowb);
-          for (int o = 0; o < C; ++o) {
-            const int r0o = min(nu, o * chunk), ro = min(nu, r0o + chunk) - r0o;
-            if (ro > 0)
-              tc::bulk_s2c(tc::mapa(tc::su32(Rb + crank * chunk * LD), o), Ts + r0o * LD, ro * rowb,
-                           tc::mapa(tc::su32(&xbar[0]), o));
-          }
+        if (tid == 0) tc::mbar_expect_tx(&xbar[0], static_cast<uint32_t>(C * my_rows) * rowb);
+        if (tid < C) {
+          const int o = tid;
+          const int r0o = min(nv, o * chunk), ro = min(nv, r0o + chunk) - r0o;
+          if (ro > 0)
+            tc::bulk_s2c(tc::mapa(tc::su32(Rb + crank * chunk * LD), o), Ts + r0o * LD, ro * rowb,
+                         tc::mapa(tc::su32(&xbar[0]), o));
         }
         if (!tc::mbar_wait(&xbar[0], xph & 1, abort)) {
           bad = 1;
           set_status(o.status, TT_STATUS_TIMEOUT);
         }
-        const int nvv = (nv + V - 1) / V;
-        int lexp = kNoExp, lbad = 0;
-        for (int idx = tid; idx < my_rows * nvv; idx += NT) {
-          const int u = idx / nvv, c = (idx % nvv) * V;
-          VT sum = Vec16<T>::zero();
-          for (int r = 0; r < C; ++r)
-            sum = Vec16<T>::add(sum, *reinterpret_cast<const VT*>(Rb + (r * chunk + u) * LD + c));
-          *reinterpret_cast<VT*>(Rs + u * LD + c) = sum;
+        // owner sum over the C peers: four threads per 4-column vector, C/4 peers each
+        const int nuv = (nu + 3) / 4;
+        float lmax = 0.f;
+        int lbad = 0;
+        const int sub = tid & 3;
+        const int nbase = my_rows * nuv, niter = (nbase + NT / 4 - 1) / (NT / 4);  // same for every thread
+        for (int it = 0; it < niter; ++it) {
+          const int base = (tid >> 2) + it * (NT / 4);
+          const bool act = base < nbase;
+          const int v = act ? base / nuv : 0, c = act ? (base - v * nuv) * 4 : 0;
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int r = sub; act && r < C; r += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(Rb + (r * chunk + v) * LD + c);
+            sum.x += x.x;
+            sum.y += x.y;
+            sum.z += x.z;
+            sum.w += x.w;
+          }
 #pragma unroll
-          for (int q = 0; q < V; ++q)
-            if (c + q < nv) track(lexp, lbad, Vec16<T>::get(sum, q));
+          for (int off = 1; off < 4; off <<= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+            sum.w += __shfl_xor_sync(0xffffffffu, sum.w, off);
+          }
+          if (act && sub == 0) {
+            *reinterpret_cast<float4*>(Rs + v * LD + c) = sum;
+            const float e4[4] = {sum.x, sum.y, sum.z, sum.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (c + q < nu) {
+                if (isfinite(e4[q])) lmax = fmaxf(lmax, fabsf(e4[q]));
+                else lbad = 1;
+              }
+          }
         }
+        // binary exponent e of the largest entry, 2^(e-1) <= max < 2^e (0 -> none)
+        int lexp = lmax > 0.f ? static_cast<int>((__float_as_uint(lmax) >> 23) & 0xff) - 126 : kNoExp;
         block_exp<NW>(lexp, lbad, ired);
         if (tid == 0) {
           srec[0] = lexp;
           srec[1] = lbad;
+          tc::mbar_expect_tx(&xbar[1], static_cast<uint32_t>(nv) * rowb + 16u * C);
         }
         tc::fence_proxy_async();
         __syncthreads();
-        if (tid == 0) {
-          tc::mbar_expect_tx(&xbar[1], static_cast<uint32_t>(nu) * rowb + 16u * C);
-          for (int o = 0; o < C; ++o) {
-            if (my_rows > 0)
-              tc::bulk_s2c(tc::mapa(tc::su32(Gb + my0 * LD), o), Rs, my_rows * rowb, tc::mapa(tc::su32(&xbar[1]), o));
-            tc::bulk_s2c(tc::mapa(tc::su32(grec + 4 * crank), o), srec, 16, tc::mapa(tc::su32(&xbar[1]), o));
-          }
+        if (tid < C) {
+          const int o = tid;
+          if (my_rows > 0)
+            tc::bulk_s2c(tc::mapa(tc::su32(Es + my0 * LD), o), Rs, my_rows * rowb, tc::mapa(tc::su32(&xbar[1]), o));
+          tc::bulk_s2c(tc::mapa(tc::su32(grec + 4 * crank), o), srec, 16, tc::mapa(tc::su32(&xbar[1]), o));
         }
         if (!tc::mbar_wait(&xbar[1], xph & 1, abort)) {
           bad = 1;
@@ -555,19 +580,27 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
           gbad |= grec[4 * r + 1];
         }
         if (gbad) bad = 1;
-        const bool rescale = gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits);
-        if (rescale) log2s += gexp;
-        for (int idx = tid; idx < nu * nvv; idx += NT) {
-          const int u = idx / nvv, c = (idx % nvv) * V;
-          const VT v = *reinterpret_cast<const VT*>(Gb + u * LD + c);
-#pragma unroll
-          for (int q = 0; q < V; ++q) {
-            const T e = Vec16<T>::get(v, q);
-            Es[(c + q) * LD + u] = rescale ? mul_pow2<T>(e, -gexp) : e;
+        if (gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits)) {
+          log2s += gexp;
+          for (int idx = tid; idx < nv * nu; idx += NT) {
+            const int v = idx / nu, u = idx - v * nu;
+            Es[v * LD + u] = mul_pow2<T>(Es[v * LD + u], -gexp);
           }
         }
         __syncthreads();
         return;
+      }
+#pragma unroll
+      for (int u = 0; u < NSE; ++u) {
+        const Sub sb = sub_tile<NT>(u, nu, nv);
+        if (sb.on) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            T* row = Ts + (sb.m0 + a) * LD + sb.n0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
+          }
+        }
       }
       cluster.sync();
       const int nvv = (nv + V - 1) / V;
