@@ -9,9 +9,10 @@
 // slices i = c, c + C, ...  Per slice a CTA computes T = E B_i and
 // P += A_i^T T out of shared memory with a register-blocked outer-product
 // loop.  Core slices stream in 32-row chunks through a ring of NST stages
-// filled by cp.async, NST-1 chunks ahead of the one being consumed; the loads
-// do not depend on E, so the next mode's chunks land while the cluster is
-// still reducing the current mode.  The cluster adds the partial P's through
+// filled by cp.async, NST-2 to NST-1 chunks ahead of the one being consumed
+// (a chunk's copies are issued after the products of the chunk before); the
+// loads do not depend on E, so the next mode's chunks land while the cluster
+// is still reducing the current mode.  The cluster adds the partial P's through
 // distributed shared memory: CTA c sums its share of rows over all peers
 // (fixed order: deterministic), and every CTA gets the reduced rows back into
 // its own copy of E'.  For float32 tiles up to rank 64 both exchanges are
@@ -49,7 +50,7 @@ namespace ttc {
 namespace cg = cooperative_groups;
 
 constexpr int kNoExp = -(1 << 30);  // exponent marker of an all-zero environment
-constexpr int KC = 32;               // rows per pipeline chunk
+constexpr int KC = 32;               // rows per pipeline chunk (ranks above 64)
 
 // Shared-memory plan of the sweep for element type T and rank tile RM.
 //   CL: cluster mode (a reduction buffer of RM/2 rows is needed)
@@ -67,6 +68,8 @@ struct SweepCfg {
   static constexpr int LD = RM + V;                // row stride (elements), 16-byte padded
   static constexpr int TILE = RM * LD;
   static constexpr int RS_ROWS = CL ? RM / 2 : 0;  // a CTA of a cluster (C >= 2) reduces <= RM/2 rows
+  // rows per pipeline chunk: a whole slice of a rank-64 core in one chunk
+  static constexpr int KC = RM <= 64 ? 64 : ttc::KC;
   static constexpr int STAGE = KC * LD;
   static constexpr size_t kBudget = 232448 - 1024;
   // Push exchange (float, ranks <= 64, cluster): partial rows go to their
@@ -248,34 +251,40 @@ struct ChunkIt {
   bool valid;
 };
 
-__device__ __forceinline__ int nchunks(int rows) { return (rows + KC - 1) / KC; }
+template <int KCV>
+__device__ __forceinline__ int nchunks(int rows) {
+  return (rows + KCV - 1) / KCV;
+}
 
+template <int KCV>
 __device__ __forceinline__ void it_settle(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank) {
   while (it.j < n_pipe && it.i >= steps[it.j].I) {
     ++it.j;
     it.i = crank;
   }
   it.valid = it.j < n_pipe;
-  if (it.valid) it.nch = nchunks(steps[it.j].rin_y);
+  if (it.valid) it.nch = nchunks<KCV>(steps[it.j].rin_y);
 }
+template <int KCV>
 __device__ __forceinline__ void it_first(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank) {
   it.j = 0;
   it.i = crank;
   it.which = 0;
   it.c = 0;
-  it_settle(it, steps, n_pipe, crank);
+  it_settle<KCV>(it, steps, n_pipe, crank);
 }
+template <int KCV>
 __device__ __forceinline__ void it_next(ChunkIt& it, const SweepStep* steps, int n_pipe, int crank, int C) {
   if (++it.c < it.nch) return;
   it.c = 0;
   if (it.which == 0) {
     it.which = 1;
-    it.nch = nchunks(steps[it.j].rin_x);
+    it.nch = nchunks<KCV>(steps[it.j].rin_x);
     return;
   }
   it.which = 0;
   it.i += C;
-  it_settle(it, steps, n_pipe, crank);
+  it_settle<KCV>(it, steps, n_pipe, crank);
 }
 
 // Where results and device status go (per call; the batched kernel points
@@ -357,8 +366,8 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 
   // ---- chunk pipeline ----
   ChunkIt prod, cons;
-  it_first(prod, sst, n_pipe, crank);
-  it_first(cons, sst, n_pipe, crank);
+  it_first<Cfg::KC>(prod, sst, n_pipe, crank);
+  it_first<Cfg::KC>(cons, sst, n_pipe, crank);
   int Lp = 0, Lc = 0;
   auto produce = [&]() {
     if (prod.valid) {
@@ -367,10 +376,10 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       const int rows = prod.which == 0 ? st.rin_y : st.rin_x;
       const int cols = prod.which == 0 ? st.rout_y : st.rout_x;
       const T* core = static_cast<const T*>(prod.which == 0 ? st.gy : st.gx);
-      const int r0 = prod.c * KC;
-      load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, p.transposed, r0, min(KC, rows - r0));
+      const int r0 = prod.c * Cfg::KC;
+      load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, p.transposed, r0, min(Cfg::KC, rows - r0));
       ++Lp;
-      it_next(prod, sst, n_pipe, crank, C);
+      it_next<Cfg::KC>(prod, sst, n_pipe, crank, C);
     }
     cp_async_commit();
   };
@@ -403,17 +412,17 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       while (true) {
         cp_async_wait<NST - 2>();
         __syncthreads();
-        produce();
         const T* Bs = stage0 + (Lc % NST) * Cfg::STAGE;
         ++Lc;
-        const int q0 = cons.c * KC, kc = min(KC, st.rin_y - q0);
+        const int q0 = cons.c * Cfg::KC, kc = min(Cfg::KC, st.rin_y - q0);
 #pragma unroll
         for (int u = 0; u < NSE; ++u) {
           const Sub sb = sub_tile<NT>(u, st.rin_x, st.rout_y);
           if (sb.on) outer_product<T, 4, LD>(t[u], Es + q0 * LD, Bs, kc, sb.m0, sb.n0);
         }
+        produce();  // refills the stage the barrier above freed, overlapping other warps' products
         const bool last = cons.c + 1 == cons.nch;
-        it_next(cons, sst, n_pipe, crank, C);
+        it_next<Cfg::KC>(cons, sst, n_pipe, crank, C);
         if (last) break;
       }
 #pragma unroll
@@ -423,8 +432,12 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             T* row = Ts + (sb.m0 + a) * LD + sb.n0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) row[b] = t[u][a][b];
+            if constexpr (sizeof(T) == 4) {
+              *reinterpret_cast<float4*>(row) = make_float4(t[u][a][0], t[u][a][1], t[u][a][2], t[u][a][3]);
+            } else {
+              *reinterpret_cast<double2*>(row) = make_double2(t[u][a][0], t[u][a][1]);
+              *reinterpret_cast<double2*>(row + 2) = make_double2(t[u][a][2], t[u][a][3]);
+            }
           }
         }
       }
@@ -432,17 +445,17 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       while (true) {
         cp_async_wait<NST - 2>();
         __syncthreads();
-        produce();
         const T* As = stage0 + (Lc % NST) * Cfg::STAGE;
         ++Lc;
-        const int r0 = cons.c * KC, kc = min(KC, st.rin_x - r0);
+        const int r0 = cons.c * Cfg::KC, kc = min(Cfg::KC, st.rin_x - r0);
 #pragma unroll
         for (int u = 0; u < NSE; ++u) {
           const Sub sb = sub_tile<NT>(u, st.rout_x, st.rout_y);
           if (sb.on) outer_product<T, 4, LD>(acc[u], As, Ts + r0 * LD, kc, sb.m0, sb.n0);
         }
+        produce();
         const bool last = cons.c + 1 == cons.nch;
-        it_next(cons, sst, n_pipe, crank, C);
+        it_next<Cfg::KC>(cons, sst, n_pipe, crank, C);
         if (last) break;
       }
     }
@@ -796,8 +809,8 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) acc[u][a][b] = T(0);
-      for (int r0 = 0; r0 < kx; r0 += KC) {
-        const int kc = min(KC, kx - r0);
+      for (int r0 = 0; r0 < kx; r0 += Cfg::KC) {
+        const int kc = min(Cfg::KC, kx - r0);
         __syncthreads();
         if (em.lead) load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.ra, em.rb, 0, r0, kc);
         else load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.rb, em.ra, 1, r0, kc);
