@@ -363,16 +363,25 @@ template <typename Tin>
 __global__ void __launch_bounds__(256) tc_last_parts_kernel(const float* __restrict__ e, const Tin* __restrict__ x,
                                                            const Tin* __restrict__ y, int I, int rx, int ry,
                                                            double* parts) {
+  // one block per i: the y column is staged once; each warp takes rows a
+  // with its lanes along the (contiguous) row of E, then reduces across lanes
+  extern __shared__ float ycol[];  // [ry]
   __shared__ double red[8];
   const int i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = threadIdx.x; b < ry; b += blockDim.x) ycol[b] = static_cast<float>(y[static_cast<size_t>(b) * I + i]);
+  __syncthreads();
   double part = 0.0;
-  for (int a = threadIdx.x; a < rx; a += blockDim.x) {
+  for (int a = warp; a < rx; a += blockDim.x / 32) {
+    const float* er = e + static_cast<size_t>(a) * ry;
     float t = 0.f;
-    for (int b = 0; b < ry; ++b) t = fmaf(e[static_cast<size_t>(a) * ry + b], static_cast<float>(y[b * I + i]), t);
-    part = fma(static_cast<double>(x[a * I + i]), static_cast<double>(t), part);
+    for (int b = lane; b < ry; b += 32) t = fmaf(er[b], ycol[b], t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) part = fma(static_cast<double>(x[static_cast<size_t>(a) * I + i]), static_cast<double>(t), part);
   }
   part = warp_sum(part);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  if (lane == 0) red[warp] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -447,12 +456,13 @@ cudaError_t tc_first(const void* x0, const void* y0, bool f32_in, int I, int rx2
 cudaError_t tc_last(const float* e, const void* x, const void* y, bool f32_in, int I, int rx, int ry, double* parts,
                     const int64_t* l_in, double* out, int64_t* out_log2, int32_t* status, cudaStream_t s) {
   count_launch(2);
+  const size_t ysm = static_cast<size_t>(ry) * sizeof(float);
   if (f32_in)
-    tc_last_parts_kernel<float><<<I, 256, 0, s>>>(e, static_cast<const float*>(x), static_cast<const float*>(y), I, rx,
-                                                  ry, parts);
+    tc_last_parts_kernel<float><<<I, 256, ysm, s>>>(e, static_cast<const float*>(x), static_cast<const float*>(y), I,
+                                                    rx, ry, parts);
   else
-    tc_last_parts_kernel<__nv_bfloat16><<<I, 256, 0, s>>>(e, static_cast<const __nv_bfloat16*>(x),
-                                                          static_cast<const __nv_bfloat16*>(y), I, rx, ry, parts);
+    tc_last_parts_kernel<__nv_bfloat16><<<I, 256, ysm, s>>>(e, static_cast<const __nv_bfloat16*>(x),
+                                                            static_cast<const __nv_bfloat16*>(y), I, rx, ry, parts);
   tc_last_sum_kernel<<<1, 1, 0, s>>>(parts, I, l_in, out, out_log2, status);
   return cudaGetLastError();
 }
