@@ -2,7 +2,8 @@
 // ranks that make each step a real GEMM (interior ranks multiples of 128 on X
 // and of 64 on Y, at most 256).
 //
-// Each interior mode k is one launch.  Its work, E' = sum_i Gx_i^T (E Gy_i),
+// Each interior mode k is one launch (programmatic dependent launch: the next
+// mode's CTAs set up while this one finishes).  Its work, E' = sum_i Gx_i^T (E Gy_i),
 // is split over 64-column blocks of E' (one thread-block cluster per block)
 // and, inside a cluster, over the mode index i (CTA c owns i = c, c + C, ...).
 // Per slice a CTA runs two chained tcgen05 GEMMs:
@@ -88,15 +89,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
     tc::mbar_init_fence();
   }
   if (tid == 64) {
-    int m = kNoExpT;
-    for (int q = 0; q < p.n_bmax_in; ++q) m = max(m, p.bmax_in[q]);
     sh_int[0] = 0;
-    sh_int[1] = m == kNoExpT ? 0 : m;
     sh_int[10] = 0;
   }
+  // Launched with programmatic stream serialisation: the next mode's grid may
+  // start its set-up (tensor memory, barriers) on idle SMs now; it waits below
+  // for this grid's results before touching global memory.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous mode's E, maxima and scale are complete
+  if (tid == 64) {
+    int m = kNoExpT;
+    for (int q = 0; q < p.n_bmax_in; ++q) m = max(m, p.bmax_in[q]);
+    sh_int[1] = m == kNoExpT ? 0 : m;
+  }
+  __syncthreads();
   const uint32_t tmem = *tmem_slot;
   const uint32_t tmem_T = tmem, tmem_P = tmem + 128;
   int bits = 0;
@@ -481,13 +490,15 @@ cudaError_t tc_mode(const TcModeParams& p, int cluster, cudaStream_t s) {
   cfg.blockDim = dim3(kTcThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // overlap with the previous mode's tail
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   count_launch();
   if (x3) return cudaLaunchKernelEx(&cfg, tc_mode_kernel<true>, p);
   return cudaLaunchKernelEx(&cfg, tc_mode_kernel<false>, p);
