@@ -141,19 +141,35 @@ __device__ __forceinline__ void store_tile(T* __restrict__ dst, int ld, const T 
     }
 }
 
-// Tile t of a rows x cols output covered row-major by SM x SN tiles.
+// Tile t of a rows x cols output covered by SM x SN tiles.  Tiles are taken
+// in strips 8 tiles wide (row by row inside a strip, the last strip narrower),
+// so the 32 tiles of a warp form a 4 x 8 block wherever the output allows: a
+// k-step then reads 4 distinct A vectors and 8 distinct B vectors (two
+// shared-memory wavefronts) instead of one row of 32 B vectors.  No tile is
+// padding.
 struct Sub {
   int r0, c0;
   bool on;
 };
 template <int SM, int SN>
 __device__ __forceinline__ Sub sub_at(int t, int rows, int cols) {
-  const int ncb = rpad<SN>(cols) / SN;
+  const int nrb = rpad<SM>(rows) / SM, ncb = rpad<SN>(cols) / SN;
+  const int nfull = ncb >> 3;              // strips of 8 tile columns
+  const int in_full = nfull * nrb * 8;     // tiles in full strips
   Sub s;
-  s.on = t < (rpad<SM>(rows) / SM) * ncb;
-  const int rb = udiv16(t, ncb);
+  s.on = t < nrb * ncb;
+  int rb, cb;
+  if (t < in_full) {
+    const int q = udiv16(t, nrb * 8), rem = t - q * nrb * 8;
+    rb = rem >> 3;
+    cb = q * 8 + (rem & 7);
+  } else {
+    const int wl = max(1, ncb - nfull * 8), rem = t - in_full;  // last, narrower strip
+    rb = udiv16(rem, wl);
+    cb = nfull * 8 + rem - rb * wl;
+  }
   s.r0 = rb * SM;
-  s.c0 = (t - rb * ncb) * SN;
+  s.c0 = cb * SN;
   return s;
 }
 
