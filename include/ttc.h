@@ -191,7 +191,9 @@ typedef struct {
  * tt_plan_info (0, 1, 2 = a quarter, half or all of the kernel's buffer),
  * autotuned per (rank, mode size) bucket.  Host only, synchronous, allocates
  * host memory (freed by tt_plan_free).  Returns the bytes of the packed
- * device table (*packed_bytes) and of the workspace (*ws_bytes). */
+ * device table (*packed_bytes) and of the workspace (*ws_bytes).
+ * TT_ERR_TOO_LARGE: a swept rank above 128 (F32) / 64 (F64), or a free core
+ * copied into a chain output with a right rank above 4096 (F32) / 2048 (F64). */
 int tt_batch_plan(const tt_batch* batch, tt_plan** plan, size_t* packed_bytes, size_t* ws_bytes);
 
 /* Write the packed table into host memory `packed_host` (packed_bytes long);

@@ -224,13 +224,19 @@ cudaError_t launch_two_sided(const TwoSidedParams& tp, int dtype, int rmax, int 
 
 // One slice range [i0, i1) of a free-core copy of a chain-layout output; the
 // batched launch works through these after its sweep queue.
+// One piece of a free-core copy: slices [i0, i1) and left-rank rows [a0, a1)
+// of a core [r0][I][r1]; swap = 1 writes it as [r1][I][r0].
 struct CopyJob {
   const void* src;
   void* dst;
   int r0, I, r1;
   int swap;
   int i0, i1;
+  int a0, a1;
 };
+
+// Bytes one copy job moves at most (a job is staged whole in shared memory).
+constexpr int kCopyJobBytes = 16384;
 
 cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n,
                            const CopyJob* jobs, int n_jobs, int* counters, double* out, int64_t* out_log2,

@@ -267,3 +267,27 @@ def test_batched_full_size_sampled():
                     np.testing.assert_array_equal(gq, wq)
     del bat, pairs
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype,scale", [(np.float32, 1.0), (np.float64, 0.5)])
+def test_batched_free_core_copies(dtype, scale):
+    """Partial pairs whose free cores are copied plainly and transposed: slices
+    of more than 4096 elements (a transposed copy cut by rows, ragged last
+    cut), right ranks that are and are not a multiple of the 16-byte width,
+    cores copied as one run and as runs per row.  Copies must be exact."""
+    r = lambda v: max(1, int(v * scale))  # noqa: E731
+    shapes = [
+        ([3, 70, 41, 9], [1, r(100), r(128), r(77), 1], [1, r(5), r(64), r(33), 1], [1, 0, 0, 0]),
+        ([9, 41, 70, 3], [1, r(77), r(128), r(100), 1], [1, r(33), r(64), r(5), 1], [0, 0, 0, 1]),
+        ([2, 5, 300, 7, 2], [1, r(4), r(8), r(12), r(3), 1], [1, r(127), r(1), r(13), r(6), 1], [1, 1, 0, 0, 0]),
+        ([6, 1, 33, 2], [1, r(128), r(128), r(128), 1], [1, r(128), r(128), r(128), 1], [0, 0, 1, 1]),
+    ]
+    rng = np.random.default_rng(11)
+    pairs = []
+    for modes, rx, ry, mask in shapes:
+        pairs.append((G.random_tt(rng, modes, rx, dtype), G.random_tt(rng, modes, ry, dtype), mask))
+    bat = T.BatchedContraction([(to_dev(x), to_dev(y), m) for x, y, m in pairs])
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
+    _check(pairs, bat, 1e-5 if dtype == np.float32 else 1e-12)
