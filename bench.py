@@ -35,6 +35,11 @@ import numpy as np  # noqa: E402
 from paper_2109_00626_gb300 import inputs as G  # noqa: E402
 from paper_2109_00626_gb300 import workload as W  # noqa: E402
 
+# DRAM bytes read + written by one launch of sweep_two_sided_kernel<float,64> on
+# this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2; see
+# profiles/two_sided_order10_r64.md).  Reset to None whenever that kernel changes.
+TWO_SIDED_TRAFFIC = 4287616
+
 METRIC = "TT contractions/s (order-10, I=16, R=64, fp32: full + partial over modes 1-6)"
 UNIT = "contractions/s"
 MASK = [1] * 6 + [0] * 4
@@ -344,8 +349,8 @@ def run_ours(args):
                 "peak": peak,
                 "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": None,
-                "note": "fp32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz (derived); single latency-bound contraction; traffic = ncu dram bytes read+write of one launch of this kernel",
+                "traffic": TWO_SIDED_TRAFFIC,
+                "note": "fp32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz (derived); single latency-bound contraction; traffic = ncu dram bytes read+write of one launch of this kernel (cold L2) against %d bytes of cores" % (b_full,),
             },
             "e2e": {
                 "value": 2 / (e2e_ms / 1e3) * world,

@@ -10,10 +10,11 @@
 // Per slice i this is evaluated as U = L Gy_i, dGx_i = U F^T, W = Gx_i F,
 // dGy_i = L^T W, and the next right environment gets W Gy_i^T.
 //
-// Memory: the left environments are not all kept.  A forward sweep stores L
-// every c modes (checkpoints) in the workspace; the backward walk then goes
-// segment by segment from the right, recomputing the c left environments of
-// the segment from its checkpoint before walking it backwards.  Workspace is
+// Memory: a forward sweep stores L every c modes (checkpoints) in the
+// workspace; the backward walk then goes segment by segment from the right,
+// recomputing the c left environments of the segment from its checkpoint
+// before walking it backwards.  With c = 1 (the default: environments are
+// small) every L is stored and nothing is recomputed; c > 1 needs
 // (ceil(n/c) + c) environments instead of n, for one extra forward sweep.
 //
 // Work split: like the forward sweep, the slices i of every mode are spread
@@ -21,6 +22,7 @@
 // distributed shared memory.
 #include <cooperative_groups.h>
 
+#include "copy_jobs.cuh"
 #include "ttc_device.cuh"
 #include "ttc_internal.h"
 
@@ -192,12 +194,14 @@ __device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, in
   return sh;
 }
 
-// Load an environment (row-major [nu][nv] in global memory) into Dn / Dt.
+// Load an environment (row-major [nu][nv] in global memory; the sum of
+// `parts` consecutive such matrices, added in order) into Dn / Dt.
 template <typename T, int LD, int NT>
-__device__ void load_env(const T* src, int nu, int nv, T* Dn, T* Dt) {
+__device__ void load_env(const T* src, int nu, int nv, T* Dn, T* Dt, int parts = 1) {
   for (int idx = threadIdx.x; idx < nu * nv; idx += NT) {
     const int u = idx / nv, v = idx - u * nv;
-    const T e = src[idx];
+    T e = src[idx];
+    for (int g = 1; g < parts; ++g) e += src[static_cast<int64_t>(g) * nu * nv + idx];
     Dn[u * LD + v] = e;
     Dt[v * LD + u] = e;
   }
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
   {
     const int rx0 = p.step[0].rx, ry0 = p.step[0].ry;
     if (p.l_seed != nullptr) {
-      load_env<T, LD, NT>(static_cast<const T*>(p.l_seed), rx0, ry0, Ls, LT);
+      load_env<T, LD, NT>(static_cast<const T*>(p.l_seed), rx0, ry0, Ls, LT, p.seed_parts);
       if (p.l_seed_log2 != nullptr) lg = *p.l_seed_log2;
     } else if (tid == 0) {
       Ls[0] = T(1);
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
   {
     const int rxn = p.step[n - 1].rx2, ryn = p.step[n - 1].ry2;
     if (p.f_seed != nullptr) {
-      load_env<T, LD, NT>(static_cast<const T*>(p.f_seed), rxn, ryn, Fs, FT);
+      load_env<T, LD, NT>(static_cast<const T*>(p.f_seed), rxn, ryn, Fs, FT, p.seed_parts);
       if (p.f_seed_log2 != nullptr) fl = *p.f_seed_log2;
     } else if (tid == 0) {
       Fs[0] = T(1);
@@ -422,17 +426,21 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
 //   trail: C[u][i][y] = sum_b Gx[u][i][b] K[b][y]
 //          dGx[u][i][b] = sum_y dC[u][i][y] K[b][y],  dK[b][y] = sum_{u,i} Gx[u][i][b] dC[u][i][y]
 // Both gradients are small products, run as shared-memory tiled GEMMs with
-// 4x4 register tiles (ranks <= 128): blocks 0..I-1 compute the gradient slice
-// i (K times the slice of dC), blocks I.. compute dK in 32-row tiles (a sum
-// over every (i, u) pair); every block then helps with the copies.  Operands
-// are staged in chunks of KCH rows of the summed index with coalesced loads.
+// register tiles (ranks <= 128): blocks 0..I-1 compute the gradient slice i
+// (K times the slice of dC), the next blocks compute dK in 32-row tiles (a
+// sum over every (i, u) pair, its operand chunks double-buffered with
+// cp.async), and the remaining blocks run the copies as jobs (copy_jobs.cuh).
 // ---------------------------------------------------------------------------
 namespace chainadj {
 constexpr int LDS = 132;  // staged row stride (elements): up to 128 columns
 constexpr int kRowsPerKBlock = 32;
 template <typename T>
 struct Ch {
-  static constexpr int KCH = sizeof(T) == 4 ? 32 : 16;  // 2 * KCH * 132 * sizeof(T) = 33.8 KB
+  static constexpr int KCH = sizeof(T) == 4 ? 32 : 16;  // one (As, Bs) set: 2 * KCH * 132 * sizeof(T) = 33.8 KB
+  static constexpr int SET = 2 * KCH * LDS;               // elements of one set
+  static constexpr int NSET = 4;                          // dK operand ring: three sets in flight
+  static constexpr size_t SMEM =
+      NSET * SET * sizeof(T) > copy_smem_bytes<T>() ? NSET * SET * sizeof(T) : copy_smem_bytes<T>();
 };
 
 // acc[a][b] += sum_{k<K} As[k][m0+a] * Bs[k][n0+b]
@@ -451,21 +459,109 @@ __device__ __forceinline__ void tile44(T (&acc)[4][4], const T* As, const T* Bs,
       for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
   }
 }
+// acc[a][b] += sum_{k<K} As[k][m0+a] * Bs[k][n0+b], a 4 x TW tile
+template <typename T, int TW>
+__device__ __forceinline__ void tile4w(T (&acc)[4][TW], const T* As, const T* Bs, int K, int m0, int n0) {
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    T av[4], bv[TW];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[k * LDS + m0 + a];
+#pragma unroll
+    for (int b = 0; b < TW; ++b) bv[b] = Bs[k * LDS + n0 + b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < TW; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+}
+
+// dK rows [r0, r0 + M), M <= 32, over slice group grp: partial sum
+//   dK_grp[r][y] = sum_{i in group, u} A[(i,u)][r] dC[u][i][y]
+//   lead : A = Gx[r][i][u] (u < rb);  trail: A = Gx[u][i][r] (u < ra)
+// (the adjoint adds the dk_parts partials as it loads its seed).
+// Thread tiles 4 x TW: with TW = 2 and ry <= 64, 8 x 32 tiles keep all 256
+// threads busy; the (i, u-chunk) operand pairs stream through a ring of NSET
+// cp.async sets, NSET - 1 of them in flight.
+template <typename T, int TW>
+__device__ void dk_block(const ChainAdjParams& p, int r0, int grp, T* sm) {
+  constexpr int KCH = Ch<T>::KCH, SET = Ch<T>::SET, NSET = Ch<T>::NSET;
+  const int tid = threadIdx.x;
+  const T* gx = static_cast<const T*>(p.gx);
+  const T* dc = static_cast<const T*>(p.dc);
+  const int I = p.I, rb = p.rb, ry = p.ry;
+  const int nk = p.lead ? p.ra : p.rb;
+  const int M = min(kRowsPerKBlock, nk - r0), N = ry;
+  const int nu = p.lead ? rb : p.ra;
+  const int i_lo = grp * I / p.dk_parts, i_hi = (grp + 1) * I / p.dk_parts;  // this group's slices
+  const int nuc = (nu + KCH - 1) / KCH, nit = (i_hi - i_lo) * nuc;
+  const int ncb = (N + TW - 1) / TW;  // <= 32
+  const bool on = tid < 8 * ncb;
+  const int m0 = (tid / ncb) * 4, n0 = (tid % ncb) * TW;
+  T acc[4][TW];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < TW; ++b) acc[a][b] = T(0);
+  auto issue = [&](int it) {  // one commit group per call, empty past the end
+    if (it >= nit) {
+      cp_async_commit();
+      return;
+    }
+    T* As = sm + (it % NSET) * SET;
+    T* Bs = As + KCH * LDS;
+    const int q = it / nuc, i = i_lo + q, u0 = (it - q * nuc) * KCH, kc = min(KCH, nu - u0);
+    for (int e = tid; e < kc * M; e += blockDim.x) {
+      if (p.lead) {
+        const int r = udiv16(e, kc), uu = e - r * kc;  // contiguous in u
+        cp_async_elem(As + uu * LDS + r, gx + (static_cast<int64_t>(r0 + r) * I + i) * rb + u0 + uu);
+      } else {
+        const int uu = udiv16(e, M), r = e - uu * M;  // contiguous in r
+        cp_async_elem(As + uu * LDS + r, gx + (static_cast<int64_t>(u0 + uu) * I + i) * rb + r0 + r);
+      }
+    }
+    for (int e = tid; e < kc * N; e += blockDim.x) {
+      const int uu = udiv16(e, N), y = e - uu * N;  // contiguous in y
+      cp_async_elem(Bs + uu * LDS + y, dc + (static_cast<int64_t>(u0 + uu) * I + i) * ry + y);
+    }
+    cp_async_commit();
+  };
+  for (int it = 0; it < NSET - 1; ++it) issue(it);
+  for (int it = 0; it < nit; ++it) {
+    // set (it + NSET - 1) % NSET was read in iteration it - 1, before its closing barrier
+    issue(it + NSET - 1);
+    cp_async_wait<NSET - 1>();  // the group of iteration it is complete
+    __syncthreads();
+    const int q = it / nuc, kc = min(KCH, nu - (it - q * nuc) * KCH);
+    const T* As = sm + (it % NSET) * SET;
+    if (on) tile4w<T, TW>(acc, As, As + KCH * LDS, kc, m0, n0);
+    __syncthreads();
+  }
+  if (on) {
+    T* dk = static_cast<T*>(p.dk) + static_cast<int64_t>(grp) * nk * ry;  // this group's partial sum
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < TW; ++b)
+        if (m0 + a < M && n0 + b < N) dk[(r0 + m0 + a) * ry + n0 + b] = acc[a][b];
+  }
+}
 }  // namespace chainadj
 
 template <typename T>
 __global__ void __launch_bounds__(256) chain_adjoint_kernel(const __grid_constant__ ChainAdjParams p) {
   using namespace chainadj;
   constexpr int KCH = Ch<T>::KCH;
-  __shared__ __align__(16) T As[KCH * LDS];
-  __shared__ __align__(16) T Bs[KCH * LDS];
+  extern __shared__ __align__(16) unsigned char chain_smem[];
+  T* const As = reinterpret_cast<T*>(chain_smem);
+  T* const Bs = As + KCH * LDS;
   const int tid = threadIdx.x;
   const T* gx = static_cast<const T*>(p.gx);
   const T* k = static_cast<const T*>(p.k);
   const T* dc = static_cast<const T*>(p.dc);
   const int ra = p.ra, rb = p.rb, I = p.I, ry = p.ry;
   const int nk = p.lead ? ra : rb;  // rows of K
-  const int nkb = (nk + kRowsPerKBlock - 1) / kRowsPerKBlock;
+  const int nkb = (nk + kRowsPerKBlock - 1) / kRowsPerKBlock * (p.dk != nullptr ? p.dk_parts : 1);
   int bits = 0;
   if (static_cast<int>(blockIdx.x) < I) {
     // ---- gradient slice i: out[m][n] = sum_y A[y][m] B[y][n] ----
@@ -519,66 +615,27 @@ __global__ void __launch_bounds__(256) chain_adjoint_kernel(const __grid_constan
           dg[(static_cast<int64_t>(m) * I + i) * rb + n] = o;
         }
     }
-  } else if (static_cast<int>(blockIdx.x) < I + nkb && p.dk != nullptr) {
-    // ---- dK rows [r0, r0 + 32): dK[r][y] = sum_{i,u} A[(i,u)][r] dC[u][i][y] ----
-    //   lead : A = Gx[r][i][u] (u < rb);  trail: A = Gx[u][i][r] (u < ra)
-    const int r0 = (blockIdx.x - I) * kRowsPerKBlock;
-    const int M = min(kRowsPerKBlock, nk - r0), N = ry;
-    const int nu = p.lead ? rb : ra;
-    const int ncb = (N + 3) / 4, ntiles = ((M + 3) / 4) * ncb;  // <= 8 * 32 = 256
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-    const bool on = tid < ntiles;
-    const int m0 = (tid / ncb) * 4, n0 = (tid % ncb) * 4;
-    for (int i = 0; i < I; ++i)
-      for (int u0 = 0; u0 < nu; u0 += KCH) {
-        const int kc = min(KCH, nu - u0);
-        __syncthreads();
-        for (int e = tid; e < kc * M; e += blockDim.x) {
-          if (p.lead) {
-            const int r = e / kc, uu = e - r * kc;  // contiguous in u
-            As[uu * LDS + r] = gx[(static_cast<int64_t>(r0 + r) * I + i) * rb + u0 + uu];
-          } else {
-            const int uu = e / M, r = e - uu * M;  // contiguous in r
-            As[uu * LDS + r] = gx[(static_cast<int64_t>(u0 + uu) * I + i) * rb + r0 + r];
-          }
-        }
-        for (int e = tid; e < kc * N; e += blockDim.x) {
-          const int uu = e / N, y = e - uu * N;  // contiguous in y
-          Bs[uu * LDS + y] = dc[(static_cast<int64_t>(u0 + uu) * I + i) * ry + y];
-        }
-        __syncthreads();
-        if (on) tile44<T>(acc, As, Bs, kc, m0, n0);
-      }
-    if (on) {
-      T* dk = static_cast<T*>(p.dk);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (m0 + a < M && n0 + b < N) dk[(r0 + m0 + a) * ry + n0 + b] = acc[a][b];
+  } else if (static_cast<int>(blockIdx.x) < I + nkb) {
+    if (p.dk != nullptr) {
+      const int nrb = (nk + kRowsPerKBlock - 1) / kRowsPerKBlock, b = blockIdx.x - I;
+      const int grp = b / nrb, r0 = (b - grp * nrb) * kRowsPerKBlock;
+      dk_block<T, 2>(p, r0, grp, As);  // ry <= 64 whenever there is a dK (checked at launch)
     }
-  }
-  // copies: grid-stride over all blocks
-  const int64_t g0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int t = 0; t < p.n_copies; ++t) {
-    const CopyTask& tk = p.copy[t];
-    const T* src = static_cast<const T*>(tk.src);
-    T* dst = static_cast<T*>(tk.dst);
-    const int64_t nn = static_cast<int64_t>(tk.r0) * tk.I * tk.r1;
-    if (!tk.swap) {
-      for (int64_t e = g0; e < nn; e += gs) dst[e] = src[e];
-    } else {
-      for (int64_t e = g0; e < nn; e += gs) {
-        const int64_t c0 = e % tk.r0, rest = e / tk.r0;
-        const int64_t ii = rest % tk.I, c1 = rest / tk.I;
-        dst[e] = src[(c0 * tk.I + ii) * tk.r1 + c1];
+  } else {
+    // the copies, as jobs of at most kCopyJobBytes dealt over the copy blocks
+    const int first = blockIdx.x - (I + nkb), step = gridDim.x - (I + nkb);
+    auto job_of = [&](int jb) {
+      int t = 0;
+      CopyCut cut = copy_cut(p.copy[0].r0, p.copy[0].I, p.copy[0].r1, static_cast<int>(sizeof(T)));
+      while (jb >= cut.n_i * cut.n_a && t + 1 < p.n_copies) {
+        jb -= cut.n_i * cut.n_a;
+        ++t;
+        cut = copy_cut(p.copy[t].r0, p.copy[t].I, p.copy[t].r1, static_cast<int>(sizeof(T)));
       }
-    }
+      return copy_job_at(p.copy[t], cut, jb);
+    };
+    T* const buf0 = reinterpret_cast<T*>(chain_smem);
+    copy_jobs_block<T>(job_of, first, p.n_copy_jobs, step, buf0, buf0 + copy_buf_elems<T>());
   }
   if (bits) set_status(p.status, bits);
 }
@@ -642,11 +699,36 @@ cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStre
 
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s) {
   if (p.ra > 128 || p.rb > 128 || p.ry > 128) return cudaErrorInvalidValue;  // staged tiles hold 128 columns
+  // a dK exists only for a non-empty contracted block, whose ranks are capped
+  // at 64 (F32) / 32 (F64) by the adjoint: the dK tiles cover ry <= 64
+  if (p.dk != nullptr && p.ry > 64) return cudaErrorInvalidValue;
   const int nk = p.lead ? p.ra : p.rb;
-  const int grid = p.I + (nk + chainadj::kRowsPerKBlock - 1) / chainadj::kRowsPerKBlock;
+  const int eb = dtype == TT_F64 ? 8 : 4;
+  ChainAdjParams q = p;
+  q.n_copy_jobs = 0;
+  for (int t = 0; t < p.n_copies; ++t) {
+    if (p.copy[t].r1 > kCopyJobBytes / eb) return cudaErrorInvalidValue;  // a copy slice row must fit a job
+    const CopyCut cut = copy_cut(p.copy[t].r0, p.copy[t].I, p.copy[t].r1, eb);
+    q.n_copy_jobs += cut.n_i * cut.n_a;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int copy_blocks = std::min(q.n_copy_jobs, 2 * std::max(sms, 1));
+  if (p.dk != nullptr && (p.dk_parts < 1 || p.dk_parts > std::min(p.I, kDkGroups))) return cudaErrorInvalidValue;
+  const int nkb = (nk + chainadj::kRowsPerKBlock - 1) / chainadj::kRowsPerKBlock * (p.dk != nullptr ? p.dk_parts : 1);
+  const int grid = p.I + nkb + copy_blocks;
+  const size_t smem = dtype == TT_F64 ? chainadj::Ch<double>::SMEM : chainadj::Ch<float>::SMEM;
+  cudaError_t err = dtype == TT_F64 ? cudaFuncSetAttribute(chain_adjoint_kernel<double>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           static_cast<int>(smem))
+                                    : cudaFuncSetAttribute(chain_adjoint_kernel<float>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
   count_launch();
-  if (dtype == TT_F64) chain_adjoint_kernel<double><<<grid, 256, 0, s>>>(p);
-  else chain_adjoint_kernel<float><<<grid, 256, 0, s>>>(p);
+  if (dtype == TT_F64) chain_adjoint_kernel<double><<<grid, 256, smem, s>>>(q);
+  else chain_adjoint_kernel<float><<<grid, 256, smem, s>>>(q);
   return cudaGetLastError();
 }
 

@@ -353,6 +353,7 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   cap.dc = dz->cores[m - 1];
   cap.dgx = gx->cores[kb];
   cap.dk = sS > 0 ? dkbuf : nullptr;
+  cap.dk_parts = std::max(1, std::min(cap.I, kDkGroups));
   cap.status = status_dev;
   auto add = [&](const void* src, void* dst, int r0, int I, int r1, int swap) {
     CopyTask& t = cap.copy[cap.n_copies++];
@@ -381,8 +382,10 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   }
   if (launch_chain_adjoint(cap, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
   (void)eb;
-  // 3. adjoint of the sweep over the contracted block, seeded with dK
+  // 3. adjoint of the sweep over the contracted block, seeded with dK (the
+  //    sum of the chain adjoint's partials)
   if (sS > 0) {
+    ap.seed_parts = cap.dk_parts;
     if (cp.side == 0) {
       fill_block(0, sS);
       ap.f_seed = dkbuf;

@@ -117,32 +117,15 @@ int tt_batch_plan(const tt_batch* b, tt_plan** plan_out, size_t* packed_bytes, s
   std::iota(plan->order.begin(), plan->order.end(), 0);
   std::stable_sort(plan->order.begin(), plan->order.end(),
                    [&](int a, int c) { return plan->cost[a] > plan->cost[c]; });
-  // free-core copies cut into jobs of whole slices of at most kCopyJobBytes
-  // (a core with larger slices is also cut by rows)
+  // free-core copies cut into jobs of at most kCopyJobBytes (copy_cut)
+  const int eb = elem_bytes(plan->dtype);
   for (int i = 0; i < n; ++i) {
     const EmitParams& em = plan->table[plan->order[i]].emit;
     if (!em.enabled) continue;
     for (int t = 0; t < em.n_copies; ++t) {
       const CopyTask& tk = em.copy[t];
-      const int cap = kCopyJobBytes / elem_bytes(plan->dtype);
-      const int slice = std::max(1, tk.r0 * tk.r1);
-      const int per = std::max(1, cap / slice);
-      const int rows = slice <= cap ? tk.r0 : std::max(1, cap / std::max(1, tk.r1));
-      for (int i0 = 0; i0 < tk.I; i0 += per)
-        for (int a0 = 0; a0 < tk.r0; a0 += rows) {
-          CopyJob j;
-          j.src = tk.src;
-          j.dst = tk.dst;
-          j.r0 = tk.r0;
-          j.I = tk.I;
-          j.r1 = tk.r1;
-          j.swap = tk.swap;
-          j.i0 = i0;
-          j.i1 = std::min(tk.I, i0 + per);
-          j.a0 = a0;
-          j.a1 = std::min(tk.r0, a0 + rows);
-          plan->jobs.push_back(j);
-        }
+      const CopyCut cut = copy_cut(tk.r0, tk.I, tk.r1, eb);
+      for (int j = 0; j < cut.n_i * cut.n_a; ++j) plan->jobs.push_back(copy_job_at(tk, cut, j));
     }
   }
   plan->off_order = align256(sizeof(SweepParams) * n);

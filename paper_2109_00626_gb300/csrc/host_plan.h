@@ -345,12 +345,6 @@ inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
   return TT_OK;
 }
 
-inline int isqrt_ceil(int n) {
-  int c = 1;
-  while (c * c < n) ++c;
-  return c;
-}
-
 // Workspace layout of tt_contract_backward.
 struct BackwardPlan {
   ChainPlan cp;
@@ -360,8 +354,12 @@ struct BackwardPlan {
   int64_t env_elems = 1;
   size_t off_k = 0, off_klog2 = 0, off_dk = 0, off_ckpt = 0, off_seg = 0, off_ckpt_log2 = 0, off_seg_log2 = 0;
   size_t ws_bytes = 0;
+  // Left environments stored every c modes.  By default every one is stored
+  // (an environment is at most 64 x 64 elements here, so N of them are a few
+  // hundred KB) and the backward walk recomputes nothing; a larger stride
+  // trades a recompute of each segment for ceil(N/c) + c environments.
   int stride_for(int nmodes) const {
-    int c = user_stride > 0 ? user_stride : isqrt_ceil(nmodes);
+    const int c = user_stride > 0 ? user_stride : 1;
     return std::max(1, std::min(c, nmodes));
   }
 };
@@ -400,7 +398,7 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     bp->off_klog2 = off;
     off += 256;
     bp->off_dk = off;
-    off += align256(static_cast<size_t>(bp->cp.kx) * bp->cp.ky * eb);
+    off += align256(static_cast<size_t>(kDkGroups) * bp->cp.kx * bp->cp.ky * eb);  // partial sums of dK
   }
   bp->off_ckpt = off;
   off += align256(static_cast<size_t>(nseg) * bp->env_elems * eb);

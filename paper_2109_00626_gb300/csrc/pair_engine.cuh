@@ -91,16 +91,6 @@ __device__ __forceinline__ int rpad(int v) {
 }
 __device__ __forceinline__ int pow2_floor_d(int v) { return v <= 1 ? 1 : (1 << (31 - __clz(v))); }
 
-// n / d for 0 <= n < 2^16, 1 <= d < 2^16 without the integer divide: the
-// float product n * rcp(d) is within n * 2^-23 of n / d, which is below the
-// 1 / d gap to the next integer whenever n / d is not one; an exact quotient
-// that rounds just below is fixed by the single correction step.
-__device__ __forceinline__ int udiv16(int n, int d) {
-  int q = __float2int_rz(__int2float_rn(n) * __frcp_rn(__int2float_rn(d)));
-  q += (q + 1) * d <= n ? 1 : 0;
-  return q;
-}
-
 // acc[a][b] += sum_{r<K} A[r*lda + a] * B[r*ldb + b]
 template <typename T, int SM, int SN>
 __device__ __forceinline__ void opk(T (&acc)[SM][SN], const T* __restrict__ A, int lda, const T* __restrict__ B,

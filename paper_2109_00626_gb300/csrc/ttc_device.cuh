@@ -70,6 +70,16 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
   else cp_async4(smem, gmem);
 }
 
+// n / d for 0 <= n < 2^16, 1 <= d < 2^16 without the integer divide: the
+// float product n * rcp(d) is within n * 2^-23 of n / d, which is below the
+// 1 / d gap to the next integer whenever n / d is not one; an exact quotient
+// that rounds just below is fixed by the single correction step.
+__device__ __forceinline__ int udiv16(int n, int d) {
+  int q = __float2int_rz(__int2float_rn(n) * __frcp_rn(__int2float_rn(d)));
+  q += (q + 1) * d <= n ? 1 : 0;
+  return q;
+}
+
 __device__ __forceinline__ void set_status(int32_t* status, int bits) {
   if (status != nullptr && bits != 0) atomicOr(status, bits);
 }

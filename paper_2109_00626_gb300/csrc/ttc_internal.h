@@ -140,6 +140,7 @@ struct AdjointParams {
   const int64_t* l_seed_log2;
   const void* f_seed;    // optional right seed [rx2(n-1)][ry2(n-1)] (NULL = [1])
   const int64_t* f_seed_log2;
+  int seed_parts;        // a seed is the sum of this many consecutive matrices (0 or 1 = one)
   const double* cot;     // optional scalar multiplier (device)
   void* ckpt;            // ceil(n/c) environments
   int64_t* ckpt_log2;
@@ -148,6 +149,10 @@ struct AdjointParams {
   int64_t env_elems;     // elements per stored environment
   int32_t* status;
 };
+
+// Most slice groups dK is split into (each group's partial sum is written
+// separately and the adjoint adds them as it loads its seed).
+constexpr int kDkGroups = 8;
 
 // Cotangents of a chain-layout output -> boundary-core gradient, dK and the
 // free-core gradients (see adjoint.cu).
@@ -160,9 +165,11 @@ struct ChainAdjParams {
   const int64_t* k_log2;
   const void* dc;
   void* dgx;
-  void* dk;  // NULL when the contracted block is empty
+  void* dk;  // NULL when the contracted block is empty; else dk_parts partial sums
+  int dk_parts;  // dK is summed over slice groups: partial g covers slices [g I / parts, (g + 1) I / parts)
   int n_copies;
   CopyTask copy[kMaxCopies];
+  int n_copy_jobs;  // jobs the copies are cut into (set by the launch)
   int32_t* status;
 };
 
@@ -222,8 +229,6 @@ cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaSt
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_two_sided(const TwoSidedParams& tp, int dtype, int rmax, int cluster, cudaStream_t s);
 
-// One slice range [i0, i1) of a free-core copy of a chain-layout output; the
-// batched launch works through these after its sweep queue.
 // One piece of a free-core copy: slices [i0, i1) and left-rank rows [a0, a1)
 // of a core [r0][I][r1]; swap = 1 writes it as [r1][I][r0].
 struct CopyJob {
@@ -237,6 +242,39 @@ struct CopyJob {
 
 // Bytes one copy job moves at most (a job is staged whole in shared memory).
 constexpr int kCopyJobBytes = 16384;
+
+// How a copy task is cut into jobs: per slices and rows left-rank rows a job,
+// n_i x n_a jobs.  Slices of at most kCopyJobBytes go whole, several to a job;
+// a larger slice is cut by rows (r1 <= kCopyJobBytes / elem_bytes).
+struct CopyCut {
+  int per, rows, n_i, n_a;
+};
+__host__ __device__ inline CopyCut copy_cut(int r0, int I, int r1, int elem_bytes) {
+  const int cap = kCopyJobBytes / elem_bytes;
+  const int slice = r0 * r1 > 1 ? r0 * r1 : 1;
+  CopyCut c;
+  c.per = cap / slice > 1 ? cap / slice : 1;
+  c.rows = slice <= cap ? r0 : (r1 > 0 && cap / r1 > 1 ? cap / r1 : 1);
+  c.n_i = (I + c.per - 1) / c.per;
+  c.n_a = (r0 + c.rows - 1) / c.rows;
+  return c;
+}
+// Job j (< n_i * n_a) of the task.
+__host__ __device__ inline CopyJob copy_job_at(const CopyTask& t, const CopyCut& c, int j) {
+  const int qi = j / c.n_a, qa = j - qi * c.n_a;
+  CopyJob job;
+  job.src = t.src;
+  job.dst = t.dst;
+  job.r0 = t.r0;
+  job.I = t.I;
+  job.r1 = t.r1;
+  job.swap = t.swap;
+  job.i0 = qi * c.per;
+  job.i1 = job.i0 + c.per < t.I ? job.i0 + c.per : t.I;
+  job.a0 = qa * c.rows;
+  job.a1 = job.a0 + c.rows < t.r0 ? job.a0 + c.rows : t.r0;
+  return job;
+}
 
 cudaError_t launch_batched(const void* table, const int32_t* order, const int32_t* tile, int n,
                            const CopyJob* jobs, int n_jobs, int* counters, double* out, int64_t* out_log2,
