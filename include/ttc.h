@@ -257,9 +257,9 @@ int tt_autotune(int dtype, const char* cache_path);
  *   gx, gy           caller-allocated gradient cores, shapes of x and y.
  *   ckpt_stride      left environments are stored every `ckpt_stride` modes
  *                    and recomputed inside each segment during the backward
- *                    sweep; 0 (default) or 1 = store all N and recompute
- *                    nothing, c > 1 = ceil(N/c) + c environments of workspace
- *                    for one extra forward sweep.
+ *                    sweep (0 = choose ceil(sqrt(N))): ceil(N/c) + c
+ *                    environments of workspace for one extra forward sweep;
+ *                    1 = store all N and recompute nothing.
  * For a full contraction, dz/dGx_k[:,i,:] = L_k Gy_k[:,i,:] F_{k+1}^T and
  * dz/dGy_k[:,i,:] = L_k^T Gx_k[:,i,:] F_{k+1}, where L_k / F_{k+1} are the left
  * / right environments; a chain-layout partial contraction reduces to this with

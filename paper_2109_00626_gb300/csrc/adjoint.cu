@@ -10,12 +10,12 @@
 // Per slice i this is evaluated as U = L Gy_i, dGx_i = U F^T, W = Gx_i F,
 // dGy_i = L^T W, and the next right environment gets W Gy_i^T.
 //
-// Memory: a forward sweep stores L every c modes (checkpoints) in the
-// workspace; the backward walk then goes segment by segment from the right,
-// recomputing the c left environments of the segment from its checkpoint
-// before walking it backwards.  With c = 1 (the default: environments are
-// small) every L is stored and nothing is recomputed; c > 1 needs
-// (ceil(n/c) + c) environments instead of n, for one extra forward sweep.
+// Memory: the left environments are not all kept.  A forward sweep stores L
+// every c modes (checkpoints, c = ceil(sqrt(n)) unless the caller picks one)
+// in the workspace; the backward walk then goes segment by segment from the
+// right, recomputing the c left environments of the segment from its
+// checkpoint before walking it backwards.  Workspace is (ceil(n/c) + c)
+// environments instead of n, for one extra forward sweep (c = 1 keeps all).
 //
 // Work split: like the forward sweep, the slices i of every mode are spread
 // over the CTAs of one cluster and the environment sums are reduced through
@@ -76,21 +76,45 @@ __device__ __forceinline__ void zero(T (&acc)[TM][TM]) {
 //   tr == 1: dst[r][c] = core[c][i][r]   (core [cols][I][rows])
 template <typename T, int LD, int NT>
 __device__ __forceinline__ void slice_async(T* dst, const T* core, int i, int I, int rows, int cols, int tr) {
-  for (int idx = threadIdx.x; idx < rows * cols; idx += NT) {
-    if (!tr) {
-      const int r = idx / cols, c = idx - r * cols;
-      cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(r) * I + i) * cols + c);
+  constexpr int V = 16 / static_cast<int>(sizeof(T));
+  if (!tr) {
+    // rows of `cols` contiguous elements, I * cols apart: 16-byte copies when aligned
+    const T* base = core + static_cast<int64_t>(i) * cols;
+    const int64_t rs = static_cast<int64_t>(I) * cols;
+    if (cols % V == 0 && rs % V == 0 && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+      const int cv = cols / V, tot = rows * cv;
+      for (int e = threadIdx.x; e < tot; e += NT) {
+        const int r = udiv16(e, cv), c = (e - r * cv) * V;
+        cp_async16(dst + r * LD + c, base + r * rs + c);
+      }
     } else {
-      const int c = idx / rows, r = idx - c * rows;
+      for (int e = threadIdx.x; e < rows * cols; e += NT) {
+        const int r = udiv16(e, cols), c = e - r * cols;
+        cp_async_elem(dst + r * LD + c, base + r * rs + c);
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * cols; e += NT) {
+      const int c = udiv16(e, rows), r = e - c * rows;
       cp_async_elem(dst + r * LD + c, core + (static_cast<int64_t>(c) * I + i) * rows + r);
     }
   }
 }
 
+// Binary exponent e of s (2^(e-1) <= |s| < 2^e; subnormals count as the
+// smallest normal exponent) read from its bits, folded into lexp; a non-finite
+// s sets lbad.
 template <typename T>
 __device__ __forceinline__ void track_e(int& lexp, int& lbad, T s) {
-  if (!isfinite(s)) lbad = 1;
-  else if (s != T(0)) lexp = max(lexp, exp2_of(static_cast<double>(s)));
+  if constexpr (sizeof(T) == 4) {
+    const int be = (__float_as_int(s) >> 23) & 0xff;
+    if (be == 0xff) lbad = 1;
+    else if (s != T(0)) lexp = max(lexp, max(be, 1) - 126);
+  } else {
+    const int be = static_cast<int>((__double_as_longlong(s) >> 52) & 0x7ff);
+    if (be == 0x7ff) lbad = 1;
+    else if (s != T(0)) lexp = max(lexp, max(be, 1) - 1022);
+  }
 }
 
 // Sum the thread tiles acc (tile at (u0, v0) of an nu x nv matrix) over the
@@ -136,6 +160,13 @@ __device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, in
     __syncthreads();
     return sh;
   }
+  // Two cluster barriers per reduction: (1) every partial is in its owner's
+  // reach, (2) every reduced chunk is.  The exponent is then taken by each CTA
+  // over the whole matrix it has pulled (the same data everywhere, so the same
+  // shift).  No third barrier is needed before Ps / Rs are written again: a
+  // CTA writes Ps only after barrier (2), which every peer passes after its
+  // last read of Ps, and writes Rs only after barrier (1) of the next
+  // reduction, which every peer passes after its last read of Rs.
   cg::cluster_group cluster = cg::this_cluster();
 #pragma unroll
   for (int a = 0; a < TM; ++a)
@@ -144,9 +175,8 @@ __device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, in
   cluster.sync();
   const int chunk = (nu + C - 1) / C;
   const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
-  int lexp = kNoExpA, lbad = 0;
   for (int idx = tid; idx < (ue - ub) * nv; idx += NT) {
-    const int u = ub + idx / nv, v = idx % nv;
+    const int q = udiv16(idx, nv), u = ub + q, v = idx - q * nv;
     T part[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r)
@@ -156,7 +186,51 @@ __device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, in
     for (int r = 0; r < 16; ++r)
       if (r < C) s += part[r];
     Rs[(u - ub) * LD + v] = s;
-    track_e(lexp, lbad, s);
+  }
+  cluster.sync();
+  // every CTA reads the reduced rows from their owners (16-byte remote loads,
+  // four per thread in flight) into Dn / Dt
+  int lexp = kNoExpA, lbad = 0;
+  constexpr int V = 16 / static_cast<int>(sizeof(T));
+  if (nv % V == 0) {
+    const int nvv = nv / V, tot = nu * nvv;
+    for (int b0 = tid; b0 < tot; b0 += 4 * NT) {
+      uint4 q[4];
+      int uu[4], vv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int idx = b0 + j * NT;
+        uu[j] = -1;
+        if (idx < tot) {
+          const int u = udiv16(idx, nvv), v = (idx - u * nvv) * V;
+          const int owner = udiv16(u, chunk);
+          q[j] = *reinterpret_cast<const uint4*>(cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + v, owner));
+          uu[j] = u;
+          vv[j] = v;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (uu[j] >= 0) {
+          T e[V];
+          memcpy(e, &q[j], sizeof(e));
+#pragma unroll
+          for (int t = 0; t < V; ++t) {
+            track_e(lexp, lbad, e[t]);
+            Dn[uu[j] * LD + vv[j] + t] = e[t];
+            Dt[(vv[j] + t) * LD + uu[j]] = e[t];
+          }
+        }
+    }
+  } else {
+    for (int idx = tid; idx < nu * nv; idx += NT) {
+      const int u = udiv16(idx, nv), v = idx - u * nv;
+      const int owner = udiv16(u, chunk);
+      const T e = *cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + v, owner);
+      track_e(lexp, lbad, e);
+      Dn[u * LD + v] = e;
+      Dt[v * LD + u] = e;
+    }
   }
   lexp = __reduce_max_sync(0xffffffffu, lexp);
   lbad = __reduce_or_sync(0xffffffffu, lbad);
@@ -165,32 +239,21 @@ __device__ int reduce_env(T (&acc)[RM / 16][RM / 16], int u0, int v0, int nu, in
     ired[16 + warp] = lbad;
   }
   __syncthreads();
-  if (tid < C) {
-    int m = kNoExpA, bb = 0;
-    for (int w = 0; w < NW; ++w) {
-      m = max(m, ired[w]);
-      bb |= ired[16 + w];
-    }
-    *cluster.map_shared_rank(ired + 32 + crank, tid) = m;
-    *cluster.map_shared_rank(ired + 64 + crank, tid) = bb;
-  }
-  cluster.sync();
   int g = kNoExpA, gb = 0;
-  for (int r = 0; r < C; ++r) {
-    g = max(g, ired[32 + r]);
-    gb |= ired[64 + r];
+  for (int w = 0; w < NW; ++w) {
+    g = max(g, ired[w]);
+    gb |= ired[16 + w];
   }
   if (gb) bad = 1;
   const int sh = (g != kNoExpA && (g > renorm_bits || g < -renorm_bits)) ? g : 0;
-  for (int idx = tid; idx < nu * nv; idx += NT) {
-    const int u = idx / nv, v = idx % nv;
-    const int owner = u / chunk;
-    T e = *cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + v, owner);
-    if (sh) e = mul_pow2<T>(e, -sh);
-    Dn[u * LD + v] = e;
-    Dt[v * LD + u] = e;
+  if (sh) {  // rare: rescale both copies in place
+    for (int idx = tid; idx < nu * nv; idx += NT) {
+      const int u = udiv16(idx, nv), v = idx - u * nv;
+      Dn[u * LD + v] = mul_pow2<T>(Dn[u * LD + v], -sh);
+      Dt[v * LD + u] = mul_pow2<T>(Dt[v * LD + u], -sh);
+    }
   }
-  cluster.sync();  // peers are done reading Rs / Ps before they are reused
+  __syncthreads();
   return sh;
 }
 
@@ -216,6 +279,22 @@ __device__ void store_env(T* dst, int nu, int nv, const T* Dn) {
 }
 
 }  // namespace
+
+// A gradient entry t times the scale fac = fm * 2^fe: in float64 for double
+// cores, in float (mantissa product, then an exact power of two, saturated)
+// for float cores.  Overflow of a finite value sets TT_STATUS_OVERFLOW, a
+// non-finite t TT_STATUS_NONFINITE.
+template <typename T>
+__device__ __forceinline__ T grad_out(T t, double fac, float fm, int fe, int& sbits) {
+  T o;
+  if constexpr (sizeof(T) == 4) {
+    o = scale_pow2_sat<float>(t * fm, fe);
+  } else {
+    o = t * fac;
+  }
+  if (!isfinite(o)) sbits |= isfinite(t) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
+  return o;
+}
 
 template <typename T, int RM>
 __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__ AdjointParams p) {
@@ -346,6 +425,12 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
       int64_t esum = lk + fl;
       esum = esum < -4000 ? -4000 : (esum > 4000 ? 4000 : esum);
       const double fac = ldexp(gbar, static_cast<int>(esum));
+      // float gradients are scaled in float: fac = fm * 2^fe with fm the
+      // float-rounded mantissa of gbar (the float64 pipe is a small fraction
+      // of the float32 one here)
+      int ge = 0;
+      const float fm = static_cast<float>(frexp(gbar, &ge));
+      const int fe = ge + static_cast<int>(esum);
       T facc[TM][TM];
       zero<T, TM>(facc);
       T* dgx = static_cast<T*>(st.dgx);
@@ -375,10 +460,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
 #pragma unroll
           for (int b = 0; b < TM; ++b)
             if (u0 + a < st.rx && v0 + b < st.rx2) {
-              const double v = static_cast<double>(t[a][b]) * fac;
-              const T o = static_cast<T>(v);
-              if (!isfinite(o)) sbits |= isfinite(v) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
-              dgx[(static_cast<int64_t>(u0 + a) * st.I + i) * st.rx2 + v0 + b] = o;
+              dgx[(static_cast<int64_t>(u0 + a) * st.I + i) * st.rx2 + v0 + b] = grad_out<T>(t[a][b], fac, fm, fe, sbits);
             }
         // W[a][b'] = Gx_i F : A = Gx^T[a'][a], B = F[a'][b']
         zero<T, TM>(t);
@@ -400,10 +482,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
 #pragma unroll
           for (int b = 0; b < TM; ++b)
             if (u0 + a < st.ry && v0 + b < st.ry2) {
-              const double v = static_cast<double>(t[a][b]) * fac;
-              const T o = static_cast<T>(v);
-              if (!isfinite(o)) sbits |= isfinite(v) ? TT_STATUS_OVERFLOW : TT_STATUS_NONFINITE;
-              dgy[(static_cast<int64_t>(u0 + a) * st.I + i) * st.ry2 + v0 + b] = o;
+              dgy[(static_cast<int64_t>(u0 + a) * st.I + i) * st.ry2 + v0 + b] = grad_out<T>(t[a][b], fac, fm, fe, sbits);
             }
         // F_k[a][b] += W Gy_i^T : A = W^T[b'][a], B = Gy^T[b'][b]
         if (u0 < st.rx && v0 < st.ry) op_acc<T, TM, LD>(facc, X1, GyT, st.ry2, u0, v0);

@@ -345,6 +345,12 @@ inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
   return TT_OK;
 }
 
+inline int isqrt_ceil(int n) {
+  int c = 1;
+  while (c * c < n) ++c;
+  return c;
+}
+
 // Workspace layout of tt_contract_backward.
 struct BackwardPlan {
   ChainPlan cp;
@@ -354,12 +360,12 @@ struct BackwardPlan {
   int64_t env_elems = 1;
   size_t off_k = 0, off_klog2 = 0, off_dk = 0, off_ckpt = 0, off_seg = 0, off_ckpt_log2 = 0, off_seg_log2 = 0;
   size_t ws_bytes = 0;
-  // Left environments stored every c modes.  By default every one is stored
-  // (an environment is at most 64 x 64 elements here, so N of them are a few
-  // hundred KB) and the backward walk recomputes nothing; a larger stride
-  // trades a recompute of each segment for ceil(N/c) + c environments.
+  // Left environments stored every c modes (default ceil(sqrt(N))): the
+  // backward walk recomputes each segment from its checkpoint, so the
+  // workspace holds ceil(N/c) + c environments instead of N.  c = 1 stores
+  // every one and recomputes nothing.
   int stride_for(int nmodes) const {
-    const int c = user_stride > 0 ? user_stride : 1;
+    const int c = user_stride > 0 ? user_stride : isqrt_ceil(nmodes);
     return std::max(1, std::min(c, nmodes));
   }
 };
