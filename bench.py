@@ -22,6 +22,7 @@ os.environ.setdefault("OMP_NUM_THREADS", "1")
 
 import argparse  # noqa: E402
 import json  # noqa: E402
+import math  # noqa: E402
 import statistics  # noqa: E402
 import subprocess  # noqa: E402
 import sys  # noqa: E402
@@ -610,6 +611,18 @@ def run_profile_case(case):
         for _ in range(2):
             op()
         status = op.status
+    elif case == "backward":
+        x, y = G.order12_r64(0)
+        xd = [torch.from_numpy(c).to(dev).requires_grad_(True) for c in x]
+        yd = [torch.from_numpy(c).to(dev).requires_grad_(True) for c in y]
+        mask = [1] * 8 + [0] * 4
+        for _ in range(2):
+            for c in xd + yd:
+                c.grad = None
+            loss = T.tt_sum(T.tt_partial(xd, yd, mask))
+            loss.backward()
+        torch.cuda.synchronize(dev)
+        status = torch.tensor([0 if math.isfinite(float(loss.detach())) else 1])
     elif case == "batched512":
         _, pairs = G.batch4096_device(512, 0, dev)
         op = T.BatchedContraction(pairs)
@@ -636,7 +649,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10"], default=None,
+    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "backward"], default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
