@@ -101,3 +101,19 @@ def test_partial_validation(L):
 def test_error_strings(L):
     for code in range(0, -9, -1):
         assert isinstance(T.error_string(code), str) and T.error_string(code)
+
+
+def test_partial_shape_degenerate_masks(L):
+    """Every mode contracted is a full contraction: the partial call refuses it
+    (TT_ERR_ARG); nothing contracted is the outer product, for any order
+    including 1 (the chain joins the two trains at rank 1)."""
+    x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
+    y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
+    with pytest.raises(B.TTError):
+        B.partial_shape(x, y, [1, 1, 1, 1], "chain")
+    modes, ranks, perm = B.partial_shape(x, y, [0, 0, 0, 0], "chain")
+    assert modes == [5, 4, 3, 2, 2, 3, 4, 5] and ranks[4] == 1 and sorted(perm) == list(range(8))
+    x1, y1 = FakeDesc([5], [1, 1]), FakeDesc([5], [1, 1])
+    assert B.partial_shape(x1, y1, [0], "chain") == ([5, 5], [1, 1, 1], [0, 1])
+    with pytest.raises(B.TTError):
+        B.partial_shape(x1, y1, [1], "chain")

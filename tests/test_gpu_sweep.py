@@ -214,3 +214,22 @@ def test_partial_split_scale_fp32():
     # undo: C carries 2^e and the input scaling of 4 X cores (K) and 1 X core (C) and 4 Y cores (K)
     c = got[1] * 2.0 ** (e - 30 * 9)
     assert np.abs(c - want[1]).max() <= 1e-5 * np.abs(want[1]).max() * 10
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("I", [1, 7])
+def test_order1_full_and_outer_product(dt, I):
+    """Order 1: the full contraction is the inner product of two vectors (the
+    last-mode float64 sum alone; no sweep from both ends), and the partial
+    contraction over no mode is their outer product as a two-core train."""
+    rng = np.random.default_rng(11 + I)
+    x = G.random_tt(rng, [I], [1, 1], dt)
+    y = G.random_tt(rng, [I], [1, 1], dt)
+    z, st = _full(x, y)
+    assert st == 0
+    want = float(np.dot(x[0].reshape(-1).astype(np.float64), y[0].reshape(-1).astype(np.float64)))
+    assert abs(z - want) <= TOL[dt] * norm_scale(x, y)
+    got, _ = _check_chain(x, y, [0], dt)
+    _, perm = O.partial_chain(x, y, [0])
+    dense = O.chain_to_dense(got, perm)
+    np.testing.assert_array_equal(dense, np.outer(x[0].reshape(-1).astype(np.float64), y[0].reshape(-1).astype(np.float64)))
