@@ -72,8 +72,8 @@ int tc_full_plan(const tt_desc* x, const tt_desc* y, int prec, TcPlan* tp) {
   }
   int imax = 1;
   for (int k = 0; k < n; ++k) imax = std::max(imax, x->modes[k]);
-  tp->off_parts = off;
-  off += a1k(sizeof(double) * imax);
+  tp->off_parts = off;  // one float64 partial per block of the last-mode kernel: 32 row blocks x ceil(I / 32)
+  off += a1k(sizeof(double) * 32 * ((imax + 31) / 32));
   tp->ws_bytes = off;
   return TT_OK;
 }

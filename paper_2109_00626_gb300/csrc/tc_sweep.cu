@@ -366,43 +366,54 @@ __global__ void __launch_bounds__(256) tc_first_kernel(const Tin* __restrict__ x
 
 // ---------------------------------------------------------------------------
 // Last mode (right rank 1), float64 sums:
-//   part_i = sum_a x[a][i] * (sum_b E[a][b] y[b][i]),  z = 2^L sum_i part_i
+//   t[a][i] = sum_b E[a][b] y[b][i],  z = 2^L sum_{a,i} x[a][i] t[a][i]
+// Blocks of kLastRB rows of E x kLastIB mode indices: the rows and the y slab
+// are staged in shared memory, each thread forms one t[a][i] (its warp shares
+// the row, so E is read as a broadcast) and the block sums x * t in float64
+// into one partial (partials summed in order by tc_last_sum_kernel).
 // ---------------------------------------------------------------------------
+constexpr int kLastRB = 8, kLastIB = 32;  // kLastRB * kLastIB = 256 threads
+
 template <typename Tin>
 __global__ void __launch_bounds__(256) tc_last_parts_kernel(const float* __restrict__ e, const Tin* __restrict__ x,
                                                            const Tin* __restrict__ y, int I, int rx, int ry,
                                                            double* parts) {
-  // one block per i: the y column is staged once; each warp takes rows a
-  // with its lanes along the (contiguous) row of E, then reduces across lanes
-  extern __shared__ float ycol[];  // [ry]
+  extern __shared__ float lsm[];  // es[kLastRB][ry], ys[ry][kLastIB]
   __shared__ double red[8];
-  const int i = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int b = threadIdx.x; b < ry; b += blockDim.x) ycol[b] = static_cast<float>(y[static_cast<size_t>(b) * I + i]);
+  float* es = lsm;
+  float* ys = lsm + kLastRB * ry;
+  const int a0 = blockIdx.x * kLastRB, i0 = blockIdx.y * kLastIB;
+  const int nr = min(kLastRB, rx - a0), ni = min(kLastIB, I - i0);
+  for (int t = threadIdx.x; t < nr * ry; t += blockDim.x) es[t] = e[static_cast<size_t>(a0) * ry + t];
+  for (int t = threadIdx.x; t < ry * kLastIB; t += blockDim.x) {
+    const int bq = t / kLastIB, j = t - bq * kLastIB;
+    ys[t] = j < ni ? static_cast<float>(y[static_cast<size_t>(bq) * I + i0 + j]) : 0.f;
+  }
   __syncthreads();
+  const int r = threadIdx.x / kLastIB, j = threadIdx.x - r * kLastIB;
   double part = 0.0;
-  for (int a = warp; a < rx; a += blockDim.x / 32) {
-    const float* er = e + static_cast<size_t>(a) * ry;
+  if (r < nr && j < ni) {
+    const float* er = es + r * ry;
     float t = 0.f;
-    for (int b = lane; b < ry; b += 32) t = fmaf(er[b], ycol[b], t);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) part = fma(static_cast<double>(x[static_cast<size_t>(a) * I + i]), static_cast<double>(t), part);
+#pragma unroll 8
+    for (int bq = 0; bq < ry; ++bq) t = fmaf(er[bq], ys[bq * kLastIB + j], t);
+    part = static_cast<double>(x[static_cast<size_t>(a0 + r) * I + i0 + j]) * static_cast<double>(t);
   }
   part = warp_sum(part);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[warp] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < blockDim.x / 32; ++w) s += red[w];
-    parts[i] = s;
+    double sum = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) sum += red[w];
+    parts[blockIdx.y * gridDim.x + blockIdx.x] = sum;
   }
 }
 
-__global__ void tc_last_sum_kernel(const double* parts, int I, const int64_t* l_in, double* out, int64_t* out_log2,
-                                   int32_t* status) {
+__global__ void tc_last_sum_kernel(const double* parts, int nparts, const int64_t* l_in, double* out,
+                                   int64_t* out_log2, int32_t* status) {
   double z = 0.0;
-  for (int i = 0; i < I; ++i) z += parts[i];
+  for (int q = 0; q < nparts; ++q) z += parts[q];
   const int64_t lg = *l_in;
   int bits = isfinite(z) ? 0 : TT_STATUS_NONFINITE;
   if (out_log2 != nullptr) {
@@ -465,14 +476,15 @@ cudaError_t tc_first(const void* x0, const void* y0, bool f32_in, int I, int rx2
 cudaError_t tc_last(const float* e, const void* x, const void* y, bool f32_in, int I, int rx, int ry, double* parts,
                     const int64_t* l_in, double* out, int64_t* out_log2, int32_t* status, cudaStream_t s) {
   count_launch(2);
-  const size_t ysm = static_cast<size_t>(ry) * sizeof(float);
+  const size_t lsm = static_cast<size_t>(kLastRB + kLastIB) * ry * sizeof(float);  // <= 40 KB (ry <= 256)
+  const dim3 grid((rx + kLastRB - 1) / kLastRB, (I + kLastIB - 1) / kLastIB);
   if (f32_in)
-    tc_last_parts_kernel<float><<<I, 256, ysm, s>>>(e, static_cast<const float*>(x), static_cast<const float*>(y), I,
-                                                    rx, ry, parts);
+    tc_last_parts_kernel<float><<<grid, kLastRB * kLastIB, lsm, s>>>(e, static_cast<const float*>(x),
+                                                                      static_cast<const float*>(y), I, rx, ry, parts);
   else
-    tc_last_parts_kernel<__nv_bfloat16><<<I, 256, ysm, s>>>(e, static_cast<const __nv_bfloat16*>(x),
-                                                            static_cast<const __nv_bfloat16*>(y), I, rx, ry, parts);
-  tc_last_sum_kernel<<<1, 1, 0, s>>>(parts, I, l_in, out, out_log2, status);
+    tc_last_parts_kernel<__nv_bfloat16><<<grid, kLastRB * kLastIB, lsm, s>>>(
+        e, static_cast<const __nv_bfloat16*>(x), static_cast<const __nv_bfloat16*>(y), I, rx, ry, parts);
+  tc_last_sum_kernel<<<1, 1, 0, s>>>(parts, static_cast<int>(grid.x * grid.y), l_in, out, out_log2, status);
   return cudaGetLastError();
 }
 
