@@ -101,20 +101,12 @@ __device__ __forceinline__ void slice_async(T* dst, const T* core, int i, int I,
   }
 }
 
-// Binary exponent e of s (2^(e-1) <= |s| < 2^e; subnormals count as the
-// smallest normal exponent) read from its bits, folded into lexp; a non-finite
-// s sets lbad.
+// Binary exponent of s folded into lexp (read from its bits); a non-finite s
+// sets lbad.
 template <typename T>
 __device__ __forceinline__ void track_e(int& lexp, int& lbad, T s) {
-  if constexpr (sizeof(T) == 4) {
-    const int be = (__float_as_int(s) >> 23) & 0xff;
-    if (be == 0xff) lbad = 1;
-    else if (s != T(0)) lexp = max(lexp, max(be, 1) - 126);
-  } else {
-    const int be = static_cast<int>((__double_as_longlong(s) >> 52) & 0x7ff);
-    if (be == 0x7ff) lbad = 1;
-    else if (s != T(0)) lexp = max(lexp, max(be, 1) - 1022);
-  }
+  if (!isfinite(s)) lbad = 1;
+  else if (s != T(0)) lexp = max(lexp, exp2_bits(s));
 }
 
 // Sum the thread tiles acc (tile at (u0, v0) of an nu x nv matrix) over the

@@ -569,7 +569,7 @@ __device__ void run_pair(const SweepParams& p, const SweepOut& o, unsigned char*
       }
     }
     // largest entry in [2^(e-1), 2^e): rescale when e leaves [-s, s]
-    int lexp = lmax > T(0) ? exp2_of(static_cast<double>(lmax)) : kNoExpE;
+    int lexp = lmax > T(0) ? exp2_bits(lmax) : kNoExpE;
     block_max_or(lexp, lbad, redi);
     if (lbad) bad = 1;
     if (lexp != kNoExpE && (lexp > p.renorm_bits || lexp < -p.renorm_bits)) {

@@ -220,7 +220,7 @@ __device__ __forceinline__ Sub sub_tile(int j, int M, int N) {
 template <typename T>
 __device__ __forceinline__ void track(int& lexp, int& lbad, T s) {
   if (!isfinite(s)) lbad = 1;
-  else if (s != T(0)) lexp = max(lexp, exp2_of(static_cast<double>(s)));
+  else if (s != T(0)) lexp = max(lexp, exp2_bits(s));
 }
 
 // Block-wide max exponent / or of bad flags; every thread gets the result.

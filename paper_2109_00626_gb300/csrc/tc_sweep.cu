@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (!isfinite(o[j])) lbad = 1;
-      else if (o[j] != 0.f) lexp = max(lexp, exp2_of(static_cast<double>(o[j])));
+      else if (o[j] != 0.f) lexp = max(lexp, exp2_bits(o[j]));
     }
     *reinterpret_cast<float4*>(p.eo_f32 + static_cast<size_t>(row) * p.ry2 + col0 + c) =
         make_float4(o[0], o[1], o[2], o[3]);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) tc_first_kernel(const Tin* __restrict__ x
     float s = 0.f;
     for (int i = 0; i < I; ++i) s = fmaf(static_cast<float>(x0[i * rx2 + a]), static_cast<float>(y0[i * ry2 + b]), s);
     if (!isfinite(s)) lbad = 1;
-    else if (s != 0.f) lexp = max(lexp, exp2_of(static_cast<double>(s)));
+    else if (s != 0.f) lexp = max(lexp, exp2_bits(s));
     eo_f32[static_cast<size_t>(a) * ry2 + b] = s;
     const __nv_bfloat16 h = __float2bfloat16_rn(s);
     const __nv_bfloat16 l = __float2bfloat16_rn(s - __bfloat162float(h));

@@ -122,6 +122,15 @@ __device__ __forceinline__ T scale_pow2_sat(T s, int64_t e) {
   return mul_pow2<T>(s, static_cast<int>(e));
 }
 
+// Binary exponent e with 2^(e-1) <= |v| < 2^e of a finite non-zero v, read
+// from its IEEE-754 bits (no float64 arithmetic, which runs at a small
+// fraction of the float32 rate here); subnormals are given the smallest
+// normal exponent, which only changes the power of two a rescale picks.
+__device__ __forceinline__ int exp2_bits(float v) { return max((__float_as_int(v) >> 23) & 0xff, 1) - 126; }
+__device__ __forceinline__ int exp2_bits(double v) {
+  return max(static_cast<int>((__double_as_longlong(v) >> 52) & 0x7ff), 1) - 1022;
+}
+
 // Binary exponent e with 2^(e-1) <= |v| < 2^e (v finite, non-zero).
 __device__ __forceinline__ int exp2_of(double v) {
   int e;
