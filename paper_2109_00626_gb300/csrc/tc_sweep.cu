@@ -13,6 +13,8 @@
 // copies) and core tiles (TMA, 128-byte swizzle) through an mbarrier ring; one
 // thread issues the MMAs; four warps drain T from tensor memory, round it to
 // bfloat16 and stage it as GEMM2's operand, and at the end drain P.  The
+// native variant keeps two T buffers and issues GEMM1 of the next slice before
+// GEMM2 of the current one, so a slice's T drain overlaps the next GEMM1.  The
 // cluster then sums the per-CTA P's through distributed shared memory and
 // writes E' both in float32 and as the bfloat16 K-major panels the next mode
 // streams in.
@@ -46,9 +48,15 @@ struct TcCfg {
   static constexpr uint32_t OFF_A_LO = 32768;
   static constexpr uint32_t OFF_B_HI = X3 ? 65536u : 32768u;  // Gy tile
   static constexpr uint32_t OFF_B_LO = OFF_B_HI + 8192u;
-  static constexpr uint32_t OFF_T = NST * STG;                // T hi (and lo)
+  // T buffers (tensor memory and the bf16 staging GEMM2 reads): with two, the
+  // next slice's GEMM1 runs while this slice's T is drained (no room for a
+  // second pair of hi / lo staging buffers in the split variant)
+  static constexpr int NTB = X3 ? 1 : 2;
+  static constexpr uint32_t OFF_T = NST * STG;                // T hi (and lo), per buffer
   static constexpr uint32_t T_BYTES = 32768;
-  static constexpr uint32_t OFF_BAR = OFF_T + (X3 ? 2 : 1) * T_BYTES;
+  static constexpr uint32_t T_STAGE = (X3 ? 2 : 1) * T_BYTES;
+  static constexpr uint32_t OFF_BAR = OFF_T + NTB * T_STAGE;
+  static constexpr uint32_t TMEM_COLS = NTB == 2 ? 512 : 256;  // T buffers of 128 columns, then P
   static constexpr size_t SMEM = OFF_BAR + 256 + 1024;        // barriers + alignment slack
 };
 
@@ -59,10 +67,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + Cfg::OFF_BAR);
   uint64_t* empty = full + Cfg::NST;
-  uint64_t* t_full = empty + Cfg::NST;
-  uint64_t* t_ready = t_full + 1;
-  uint64_t* t_free = t_ready + 1;
-  uint64_t* p_full = t_free + 1;
+  uint64_t* t_full = empty + Cfg::NST;   // [NTB]
+  uint64_t* t_ready = t_full + Cfg::NTB;  // [NTB]
+  uint64_t* t_free = t_ready + Cfg::NTB;  // [NTB]
+  uint64_t* p_full = t_free + Cfg::NTB;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(p_full + 1);
   int* sh_int = reinterpret_cast<int*>(tmem_slot + 1);  // [0] status bits, [1] M, [2..9] warp maxima, [10] abort
   volatile int* abort = sh_int + 10;
@@ -76,15 +84,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
   const int NPY = p.ry / 64, NPX = p.rx / 64;
   const int nslices = crank < p.I ? (p.I - 1 - crank) / C + 1 : 0;
 
-  if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   if (tid == 32) {
     for (int s = 0; s < Cfg::NST; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(t_full, 1);
-    tc::mbar_init(t_ready, 128);
-    tc::mbar_init(t_free, 1);
+    for (int b = 0; b < Cfg::NTB; ++b) {
+      tc::mbar_init(&t_full[b], 1);
+      tc::mbar_init(&t_ready[b], 128);
+      tc::mbar_init(&t_free[b], 1);
+    }
     tc::mbar_init(p_full, 1);
     tc::mbar_init_fence();
   }
@@ -107,38 +117,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
   }
   __syncthreads();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tmem_T = tmem, tmem_P = tmem + 128;
+  const uint32_t tmem_T = tmem, tmem_P = tmem + Cfg::NTB * 128;  // T buffer b at tmem_T + 128 b
+  // Slice order of the operand ring (producer and MMA issuer alike): step t
+  // takes GEMM1 of slice t and GEMM2 of slice t - LAG, so with two T buffers
+  // GEMM1 of the next slice overlaps the drain of this slice's T.
+  constexpr int LAG = Cfg::NTB - 1;
   int bits = 0;
 
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
       uint32_t it = 0;
-      for (int i = crank; i < p.I; i += C) {
-        for (int kp = 0; kp < NPY; ++kp, ++it) {
-          const int s = it % Cfg::NST;
-          const uint32_t round = it / Cfg::NST;
-          if (!tc::mbar_wait(&empty[s], (round & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-          unsigned char* st = sm + s * Cfg::STG;
-          const uint32_t eb = static_cast<uint32_t>(p.rx) * 128;
-          tc::mbar_expect_tx(&full[s], (X3 ? 2 : 1) * (eb + 8192));
-          tc::bulk_load(st + Cfg::OFF_A_HI, p.e_hi + static_cast<size_t>(kp) * p.rx * 64, eb, &full[s]);
-          tc::tma_load_3d(st + Cfg::OFF_B_HI, &p.gy_hi, 64 * vblk, i, 64 * kp, &full[s]);
-          if (X3) {
-            tc::bulk_load(st + Cfg::OFF_A_LO, p.e_lo + static_cast<size_t>(kp) * p.rx * 64, eb, &full[s]);
-            tc::tma_load_3d(st + Cfg::OFF_B_LO, &p.gy_lo, 64 * vblk, i, 64 * kp, &full[s]);
+      for (int t = 0; t < nslices + LAG; ++t) {
+        if (t < nslices) {
+          const int i = crank + t * C;
+          for (int kp = 0; kp < NPY; ++kp, ++it) {
+            const int s = it % Cfg::NST;
+            const uint32_t round = it / Cfg::NST;
+            if (!tc::mbar_wait(&empty[s], (round & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
+            unsigned char* st = sm + s * Cfg::STG;
+            const uint32_t eb = static_cast<uint32_t>(p.rx) * 128;
+            tc::mbar_expect_tx(&full[s], (X3 ? 2 : 1) * (eb + 8192));
+            tc::bulk_load(st + Cfg::OFF_A_HI, p.e_hi + static_cast<size_t>(kp) * p.rx * 64, eb, &full[s]);
+            tc::tma_load_3d(st + Cfg::OFF_B_HI, &p.gy_hi, 64 * vblk, i, 64 * kp, &full[s]);
+            if (X3) {
+              tc::bulk_load(st + Cfg::OFF_A_LO, p.e_lo + static_cast<size_t>(kp) * p.rx * 64, eb, &full[s]);
+              tc::tma_load_3d(st + Cfg::OFF_B_LO, &p.gy_lo, 64 * vblk, i, 64 * kp, &full[s]);
+            }
           }
         }
-        for (int kp = 0; kp < NPX; ++kp, ++it) {
-          const int s = it % Cfg::NST;
-          const uint32_t round = it / Cfg::NST;
-          if (!tc::mbar_wait(&empty[s], (round & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-          unsigned char* st = sm + s * Cfg::STG;
-          const int nmb = p.rx2 / 64;
-          tc::mbar_expect_tx(&full[s], (X3 ? 2 : 1) * nmb * 8192);
-          for (int mb = 0; mb < nmb; ++mb) {
-            tc::tma_load_3d(st + Cfg::OFF_A_HI + mb * 8192, &p.gx_hi, 64 * mb, i, 64 * kp, &full[s]);
-            if (X3) tc::tma_load_3d(st + Cfg::OFF_A_LO + mb * 8192, &p.gx_lo, 64 * mb, i, 64 * kp, &full[s]);
+        if (t >= LAG) {
+          const int i = crank + (t - LAG) * C;
+          for (int kp = 0; kp < NPX; ++kp, ++it) {
+            const int s = it % Cfg::NST;
+            const uint32_t round = it / Cfg::NST;
+            if (!tc::mbar_wait(&empty[s], (round & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
+            unsigned char* st = sm + s * Cfg::STG;
+            const int nmb = p.rx2 / 64;
+            tc::mbar_expect_tx(&full[s], (X3 ? 2 : 1) * nmb * 8192);
+            for (int mb = 0; mb < nmb; ++mb) {
+              tc::tma_load_3d(st + Cfg::OFF_A_HI + mb * 8192, &p.gx_hi, 64 * mb, i, 64 * kp, &full[s]);
+              if (X3) tc::tma_load_3d(st + Cfg::OFF_A_LO + mb * 8192, &p.gx_lo, 64 * mb, i, 64 * kp, &full[s]);
+            }
           }
         }
       }
@@ -149,72 +169,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
       constexpr uint32_t id1 = tc::idesc_bf16(128, 64, false, true);
       constexpr uint32_t id2 = tc::idesc_bf16(128, 64, true, true);
       uint32_t it = 0;
-      int sl = 0;
-      for (int i = crank; i < p.I; i += C, ++sl) {
-        for (int kp = 0; kp < NPY; ++kp, ++it) {
-          const int s = it % Cfg::NST;
-          if (!tc::mbar_wait(&full[s], (it / Cfg::NST) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
-          tc::fence_after_sync();
-          const uint32_t st = tc::su32(sm + s * Cfg::STG);
+      for (int t = 0; t < nslices + LAG; ++t) {
+        if (t < nslices) {
+          // GEMM1 of slice t into T buffer t % NTB (its previous contents were
+          // drained before GEMM2 of slice t - NTB, issued earlier)
+          const uint32_t tT = tmem_T + (t % Cfg::NTB) * 128;
+          for (int kp = 0; kp < NPY; ++kp, ++it) {
+            const int s = it % Cfg::NST;
+            if (!tc::mbar_wait(&full[s], (it / Cfg::NST) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
+            tc::fence_after_sync();
+            const uint32_t st = tc::su32(sm + s * Cfg::STG);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            for (int mt = 0; mt < MT1; ++mt) {
-              const uint32_t acc = (kp | ks) != 0;
-              const uint64_t a = tc::sdesc(st + Cfg::OFF_A_HI + mt * 128 * 128 + ks * 32, 16, 1024);
-              const uint64_t b = tc::sdesc(st + Cfg::OFF_B_HI + ks * 2048, 8192, 1024);
-              tc::mma_bf16(tmem_T + mt * 64, a, b, id1, acc);
-              if (X3) {
-                const uint64_t al = tc::sdesc(st + Cfg::OFF_A_LO + mt * 128 * 128 + ks * 32, 16, 1024);
-                const uint64_t bl = tc::sdesc(st + Cfg::OFF_B_LO + ks * 2048, 8192, 1024);
-                tc::mma_bf16(tmem_T + mt * 64, a, bl, id1, 1);
-                tc::mma_bf16(tmem_T + mt * 64, al, b, id1, 1);
+            for (int ks = 0; ks < 4; ++ks)
+              for (int mt = 0; mt < MT1; ++mt) {
+                const uint32_t acc = (kp | ks) != 0;
+                const uint64_t a = tc::sdesc(st + Cfg::OFF_A_HI + mt * 128 * 128 + ks * 32, 16, 1024);
+                const uint64_t b = tc::sdesc(st + Cfg::OFF_B_HI + ks * 2048, 8192, 1024);
+                tc::mma_bf16(tT + mt * 64, a, b, id1, acc);
+                if (X3) {
+                  const uint64_t al = tc::sdesc(st + Cfg::OFF_A_LO + mt * 128 * 128 + ks * 32, 16, 1024);
+                  const uint64_t bl = tc::sdesc(st + Cfg::OFF_B_LO + ks * 2048, 8192, 1024);
+                  tc::mma_bf16(tT + mt * 64, a, bl, id1, 1);
+                  tc::mma_bf16(tT + mt * 64, al, b, id1, 1);
+                }
               }
-            }
-          tc::mma_commit(&empty[s]);
+            tc::mma_commit(&empty[s]);
+          }
+          tc::mma_commit(&t_full[t % Cfg::NTB]);
         }
-        tc::mma_commit(t_full);
-        if (!tc::mbar_wait(t_ready, sl & 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        tc::fence_after_sync();
-        const uint32_t tb = tc::su32(sm + Cfg::OFF_T);
-        for (int kp = 0; kp < NPX; ++kp, ++it) {
-          const int s = it % Cfg::NST;
-          if (!tc::mbar_wait(&full[s], (it / Cfg::NST) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
+        const int u = t - LAG;
+        if (u >= 0) {
+          // GEMM2 of slice u from the bf16 staging of T buffer u % NTB
+          const int tbuf = u % Cfg::NTB;
+          if (!tc::mbar_wait(&t_ready[tbuf], (u / Cfg::NTB) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
           tc::fence_after_sync();
-          const uint32_t st = tc::su32(sm + s * Cfg::STG);
+          const uint32_t tb = tc::su32(sm + Cfg::OFF_T + tbuf * Cfg::T_STAGE);
+          for (int kp = 0; kp < NPX; ++kp, ++it) {
+            const int s = it % Cfg::NST;
+            if (!tc::mbar_wait(&full[s], (it / Cfg::NST) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
+            tc::fence_after_sync();
+            const uint32_t st = tc::su32(sm + s * Cfg::STG);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            for (int mt = 0; mt < MT2; ++mt) {
-              const uint32_t acc = (sl | kp | ks) != 0;
-              const uint64_t a = tc::sdesc(st + Cfg::OFF_A_HI + (2 * mt) * 8192 + ks * 2048, 8192, 1024);
-              const uint64_t b = tc::sdesc(tb + (64 * kp + 16 * ks) * 128, 8192, 1024);
-              tc::mma_bf16(tmem_P + mt * 64, a, b, id2, acc);
-              if (X3) {
-                const uint64_t al = tc::sdesc(st + Cfg::OFF_A_LO + (2 * mt) * 8192 + ks * 2048, 8192, 1024);
-                const uint64_t bl = tc::sdesc(tb + Cfg::T_BYTES + (64 * kp + 16 * ks) * 128, 8192, 1024);
-                tc::mma_bf16(tmem_P + mt * 64, a, bl, id2, 1);
-                tc::mma_bf16(tmem_P + mt * 64, al, b, id2, 1);
+            for (int ks = 0; ks < 4; ++ks)
+              for (int mt = 0; mt < MT2; ++mt) {
+                const uint32_t acc = (u | kp | ks) != 0;
+                const uint64_t a = tc::sdesc(st + Cfg::OFF_A_HI + (2 * mt) * 8192 + ks * 2048, 8192, 1024);
+                const uint64_t b = tc::sdesc(tb + (64 * kp + 16 * ks) * 128, 8192, 1024);
+                tc::mma_bf16(tmem_P + mt * 64, a, b, id2, acc);
+                if (X3) {
+                  const uint64_t al = tc::sdesc(st + Cfg::OFF_A_LO + (2 * mt) * 8192 + ks * 2048, 8192, 1024);
+                  const uint64_t bl = tc::sdesc(tb + Cfg::T_BYTES + (64 * kp + 16 * ks) * 128, 8192, 1024);
+                  tc::mma_bf16(tmem_P + mt * 64, a, bl, id2, 1);
+                  tc::mma_bf16(tmem_P + mt * 64, al, b, id2, 1);
+                }
               }
-            }
-          tc::mma_commit(&empty[s]);
+            tc::mma_commit(&empty[s]);
+          }
+          tc::mma_commit(&t_free[tbuf]);
         }
-        tc::mma_commit(t_free);
       }
       tc::mma_commit(p_full);
     }
   } else {
     // ---------------- epilogue: T -> bf16 operand of GEMM2 ----------------
     const int q = warp & 3;  // tensor-memory lane quadrant of this warp
-    unsigned char* tsm = sm + Cfg::OFF_T;
     for (int sl = 0; sl < nslices; ++sl) {
-      if (!tc::mbar_wait(t_full, sl & 1, abort)) bits |= TT_STATUS_TIMEOUT;
+      const int tbuf = sl % Cfg::NTB;
+      const uint32_t ph = (sl / Cfg::NTB) & 1;
+      unsigned char* tsm = sm + Cfg::OFF_T + tbuf * Cfg::T_STAGE;
+      const uint32_t tT = tmem_T + tbuf * 128;
+      if (!tc::mbar_wait(&t_full[tbuf], ph, abort)) bits |= TT_STATUS_TIMEOUT;
       tc::fence_after_sync();
-      if (sl > 0 && !tc::mbar_wait(t_free, (sl - 1) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
+      // this staging buffer was last read by GEMM2 of slice sl - NTB
+      if (sl >= Cfg::NTB && !tc::mbar_wait(&t_free[tbuf], ph ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
       for (int mt = 0; mt < MT1; ++mt) {
         const int row = mt * 128 + q * 32 + lane;
 #pragma unroll
         for (int c16 = 0; c16 < 4; ++c16) {
           float v[16];
-          tc::tmem_ld16(tmem_T + (static_cast<uint32_t>(q * 32) << 16) + mt * 64 + c16 * 16, v);
+          tc::tmem_ld16(tT + (static_cast<uint32_t>(q * 32) << 16) + mt * 64 + c16 * 16, v);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             uint4 hi, lo;
@@ -237,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
-      tc::mbar_arrive(t_ready);
+      tc::mbar_arrive(&t_ready[tbuf]);
     }
   }
 
@@ -324,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_mode_kernel(const __grid_con
   tc::fence_before_sync();
   __syncthreads();
   cluster.sync();  // peers are done reading this CTA's staging
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
