@@ -20,7 +20,7 @@ struct tt_plan {
   std::vector<double> cost;
   std::vector<ttc::CopyJob> jobs;
   size_t off_order = 0, off_tile = 0, off_jobs = 0, packed_bytes = 0;
-  size_t ws_bytes = 256;  // device workspace the launch needs (the two work-queue counters)
+  size_t ws_bytes = 256;  // device workspace the launch needs (the work-queue counter)
 };
 
 namespace ttc {

@@ -5,10 +5,12 @@
 // next pair from a global counter (pairs are pre-sorted longest-first, so the
 // queue is an LPT schedule) and runs the whole environment sweep of that pair
 // -- and, for a partial contraction, its chain emission -- with the per-CTA
-// engine of pair_engine.cuh, following the evaluation order and panels the plan chose
-// for each mode.  Nothing in
-// the launch depends on the host: the counter is reset by a memset node, so
-// the pair (memset, kernel) can be captured in a CUDA graph and replayed.
+// engine of pair_engine.cuh, following the evaluation order and panels the
+// plan chose for each mode.  The free-core copies of the partial pairs follow
+// in a second kernel (copy_jobs.cuh), launched as a programmatic dependent so
+// that it starts on the SMs the queue's tail leaves idle.  Nothing in the
+// launch depends on the host: the counter is reset by a memset node, so the
+// (memset, kernels) sequence can be captured in a CUDA graph and replayed.
 #include "copy_jobs.cuh"
 #include "pair_engine.cuh"
 
@@ -17,11 +19,11 @@ namespace ttc {
 struct BatchKernelParams {
   const SweepParams* table;  // [n] per-pair sweep parameters
   const int32_t* order;      // [n] pair indices, longest first
-  const int32_t* tile;       // [n] rank tile per pair: 0 -> 32, 1 -> 64, 2 -> 128
+  const int32_t* tile;       // [n] panel-budget level per pair (0, 1, 2: a quarter, half or all of the buffer)
   int n;
   const CopyJob* jobs;       // free-core copies of the partial pairs
   int n_jobs;
-  int* counter;              // [0] pair queue head, [1] copy queue head (zeroed before the launch)
+  int* counter;              // [0] pair queue head (zeroed before the launch)
   double* out;               // [n]
   int64_t* out_log2;         // [n] or NULL
   int32_t* status;
