@@ -29,6 +29,7 @@ EXPORTS = [
     "tt_contract_full",
     "tt_partial_shape",
     "tt_contract_partial",
+    "tt_contract_partial_k",
     "tt_batch_plan",
     "tt_batch_pack",
     "tt_contract_batched",
@@ -37,6 +38,7 @@ EXPORTS = [
     "tt_plan_free",
     "tt_autotune",
     "tt_contract_backward",
+    "tt_contract_backward_k",
     "tt_error_string",
     "tt_launch_count",
 ]
@@ -98,6 +100,10 @@ def lib():
     L.tt_plan_free.restype = None
     L.tt_contract_backward.argtypes = [
         D, D, U8, c_int, c_int, c_void_p, D, D, D, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
+    ]
+    L.tt_contract_partial_k.argtypes = [D, D, U8, c_int, D, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.tt_contract_backward_k.argtypes = [
+        D, D, U8, c_int, D, D, D, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
     ]
     L.tt_autotune.argtypes = [c_int, ctypes.c_char_p]
     L.tt_error_string.argtypes = [c_int]
@@ -433,10 +439,40 @@ def autotune(dtype="f32", cache_path=None):
     return path
 
 
-def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, layout="chain"):
+def k_shape(x, y, mask):
+    """Shape (kx, ky) of K, the environment over the contracted end block of a
+    chain-layout partial contraction (1 x 1 when no mode is contracted)."""
+    n, s = len(mask), sum(1 for v in mask if v)
+    if s == 0:
+        return 1, 1
+    k = s if mask[0] else n - s
+    return int(x[k].shape[0]) if k < n else 1, int(y[k].shape[0]) if k < n else 1
+
+
+def partial_k(x, y, mask, z, stream=None):
+    """Chain-layout partial contraction into the output cores ``z`` that also
+    returns K and its power-of-two scale (tt_contract_partial_k)."""
+    import torch
+
+    xd, yd, zd = Desc(x), Desc(y), Desc(z)
+    kx, ky = k_shape(x, y, mask)
+    dev = x[0].device
+    k = torch.empty((kx, ky), dtype=x[0].dtype, device=dev)
+    klog2 = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    rc = lib().tt_contract_partial_k(
+        xd.ref, yd.ref, _mask_arr(mask), TT_P_NATIVE, zd.ref, None, c_void_p(k.data_ptr()),
+        c_void_p(klog2.data_ptr()), c_void_p(status.data_ptr()), _stream_ptr(stream),
+    )
+    check(rc, "tt_contract_partial_k")
+    return k, klog2, status
+
+
+def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, layout="chain", k=None):
     """Gradients of a full (mask None; ``cot`` = float64 device scalar) or a
     chain-layout partial contraction (``dz`` = cotangents of the output cores)
-    with respect to every core of x and y.  Returns (gx, gy, status)."""
+    with respect to every core of x and y.  Returns (gx, gy, status).  ``k`` =
+    (K, K scale) kept by :func:`partial_k` skips the sweep that recomputes K."""
     import torch
 
     xd, yd = Desc(x), Desc(y)
@@ -453,6 +489,14 @@ def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, lay
     dzd = Desc(dz) if dz is not None else None
     if cot is not None:
         cot = cot.detach().to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    if k is not None:
+        rc = lib().tt_contract_backward_k(
+            xd.ref, yd.ref, m, TT_P_NATIVE, dzd.ref, gxd.ref, gyd.ref, c_void_p(k[0].data_ptr()),
+            c_void_p(k[1].data_ptr()), int(ckpt_stride), c_void_p(status.data_ptr()), c_void_p(ws.data_ptr()),
+            c_size_t(ws.numel()), _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_backward_k")
+        return gx, gy, status
     rc = lib().tt_contract_backward(
         xd.ref,
         yd.ref,
@@ -509,17 +553,20 @@ def _autograd():
         def forward(ctx, nx, mask, *cores):
             x = [c.contiguous() for c in cores[:nx]]
             y = [c.contiguous() for c in cores[nx:]]
-            op = PartialContraction(x, y, mask)
-            op()
+            modes, ranks, _ = partial_shape(Desc(x), Desc(y), mask, "chain")
+            z = [torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
+                 for t in range(len(modes))]
+            k, klog2, _ = partial_k(x, y, mask, z)  # K is kept for the backward pass
             ctx.nx = nx
             ctx.mask = list(mask)
-            ctx.save_for_backward(*x, *y)
-            return tuple(op.z)
+            ctx.save_for_backward(*x, *y, k, klog2)
+            return tuple(z)
 
         @staticmethod
         def backward(ctx, *gz):
             saved = ctx.saved_tensors
-            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx :])
+            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx : -2])
+            k, klog2 = saved[-2], saved[-1]
             xd, yd = Desc(x), Desc(y)
             modes, ranks, _ = partial_shape(xd, yd, ctx.mask, "chain")
             dz = []
@@ -527,7 +574,7 @@ def _autograd():
                 if g is None:
                     g = torch.zeros((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
                 dz.append(g.contiguous())
-            gx, gy, _ = backward(x, y, ctx.mask, dz=dz)
+            gx, gy, _ = backward(x, y, ctx.mask, dz=dz, k=(k, klog2))
             return (None, None, *gx, *gy)
 
     return TTFull, TTPartial

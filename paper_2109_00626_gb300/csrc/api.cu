@@ -237,33 +237,56 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
   return TT_ERR_ARG;
 }
 
-int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
-                        const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
-                        tt_stream stream) {
+// Chain-layout partial contraction; with k_dev set, K (and its scale) is also
+// written out, for a backward pass to reuse.
+static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* z,
+                          int64_t* z_log2_dev, void* k_dev, int64_t* k_log2_dev, int32_t* status_dev,
+                          tt_stream stream) {
   if (mask == nullptr) return TT_ERR_ARG;
   int rc = check_pair(x, y, mask);
   if (rc != TT_OK) return rc;
   if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
   if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
-  if (layout == TT_LAYOUT_MERGED) return contract_merged(x, y, mask, z, z_log2_dev, status_dev, ws, ws_bytes, stream);
-  if (layout != TT_LAYOUT_CHAIN) return TT_ERR_ARG;
   ChainPlan cp;
   rc = chain_plan(x, y, mask, &cp);
   if (rc != TT_OK) return rc;
   rc = check_chain_output(x, cp, z);
   if (rc != TT_OK) return rc;
-  (void)ws;
-  (void)ws_bytes;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SweepParams p;
   rc = build_partial(x, y, cp, z, z_log2_dev, status_dev, &p);
   if (rc != TT_OK) return rc;
+  p.e_out = k_dev;
+  p.e_out_log2 = k_dev != nullptr ? k_log2_dev : nullptr;
   return launch_sweep(p, x->dtype, s);
 }
 
-int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
+int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
+                        const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
+                        tt_stream stream) {
+  if (mask == nullptr) return TT_ERR_ARG;
+  if (layout == TT_LAYOUT_MERGED) {
+    const int rc = check_pair(x, y, mask);
+    if (rc != TT_OK) return rc;
+    if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+    if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
+    return contract_merged(x, y, mask, z, z_log2_dev, status_dev, ws, ws_bytes, stream);
+  }
+  if (layout != TT_LAYOUT_CHAIN) return TT_ERR_ARG;
+  return contract_chain(x, y, mask, prec, z, z_log2_dev, nullptr, nullptr, status_dev, stream);
+}
+
+int tt_contract_partial_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* z,
+                          int64_t* z_log2_dev, void* k_dev, int64_t* k_log2_dev, int32_t* status_dev,
+                          tt_stream stream) {
+  if (k_dev == nullptr || k_log2_dev == nullptr) return TT_ERR_ARG;
+  return contract_chain(x, y, mask, prec, z, z_log2_dev, k_dev, k_log2_dev, status_dev, stream);
+}
+
+static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
                          const double* cot_dev, const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
-                         int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+                         int32_t ckpt_stride, const void* k_given, const int64_t* k_log2_given, int32_t* status_dev,
+                         void* ws, size_t ws_bytes, tt_stream stream) {
   BackwardPlan bp;
   int rc = backward_plan(x, y, mask, layout, prec, ckpt_stride, &bp);
   if (rc != TT_OK) return rc;
@@ -317,12 +340,13 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   rc = check_chain_output(x, cp, dz);
   if (rc != TT_OK) return rc;
   const int m = cp.m, sS = cp.s;
-  void* kbuf = w + bp.off_k;
-  int64_t* klog2 = reinterpret_cast<int64_t*>(w + bp.off_klog2);
+  const void* kbuf = k_given != nullptr ? k_given : w + bp.off_k;
+  const int64_t* klog2 = k_given != nullptr ? k_log2_given : reinterpret_cast<int64_t*>(w + bp.off_klog2);
   void* dkbuf = w + bp.off_dk;
 
-  // 1. K again (the environment over the contracted block)
-  {
+  // 1. K again (the environment over the contracted block), unless the
+  //    forward pass kept it
+  if (k_given == nullptr) {
     SweepParams p;
     memset(&p, 0, sizeof(p));
     if (sS > 0) {
@@ -332,8 +356,8 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     p.rx0 = 1;
     p.ry0 = 1;
     p.renorm_bits = ap.renorm_bits;
-    p.e_out = kbuf;
-    p.e_out_log2 = klog2;
+    p.e_out = w + bp.off_k;
+    p.e_out_log2 = reinterpret_cast<int64_t*>(w + bp.off_klog2);
     p.status = status_dev;
     rc = launch_sweep(p, x->dtype, s);
     if (rc != TT_OK) return rc;
@@ -396,6 +420,21 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     if (launch_adjoint(ap, x->dtype, bp.rmax, s) != cudaSuccess) return TT_ERR_CUDA;
   }
   return TT_OK;
+}
+
+int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
+                         const double* cot_dev, const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
+                         int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+  return backward_impl(x, y, mask, layout, prec, cot_dev, dz, gx, gy, ckpt_stride, nullptr, nullptr, status_dev, ws,
+                       ws_bytes, stream);
+}
+
+int tt_contract_backward_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* dz,
+                           const tt_desc* gx, const tt_desc* gy, const void* k_dev, const int64_t* k_log2_dev,
+                           int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+  if (mask == nullptr || k_dev == nullptr || k_log2_dev == nullptr) return TT_ERR_ARG;
+  return backward_impl(x, y, mask, TT_LAYOUT_CHAIN, prec, nullptr, dz, gx, gy, ckpt_stride, k_dev, k_log2_dev,
+                       status_dev, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -117,3 +117,15 @@ def test_partial_shape_degenerate_masks(L):
     assert B.partial_shape(x1, y1, [0], "chain") == ([5, 5], [1, 1, 1], [0, 1])
     with pytest.raises(B.TTError):
         B.partial_shape(x1, y1, [1], "chain")
+
+
+def test_k_shape():
+    """K of a chain-layout partial contraction: R^x_s x R^y_s for a leading block
+    of s modes, R^x_m x R^y_m for a trailing block starting at mode m."""
+    import numpy as np
+
+    x = [np.zeros(s) for s in [(1, 2, 6), (6, 3, 7), (7, 4, 8), (8, 5, 1)]]
+    y = [np.zeros(s) for s in [(1, 2, 9), (9, 3, 10), (10, 4, 11), (11, 5, 1)]]
+    assert B.k_shape(x, y, [1, 1, 0, 0]) == (7, 10)
+    assert B.k_shape(x, y, [0, 0, 0, 1]) == (8, 11)
+    assert B.k_shape(x, y, [0, 0, 0, 0]) == (1, 1)
