@@ -129,3 +129,17 @@ def test_k_shape():
     assert B.k_shape(x, y, [1, 1, 0, 0]) == (7, 10)
     assert B.k_shape(x, y, [0, 0, 0, 1]) == (8, 11)
     assert B.k_shape(x, y, [0, 0, 0, 0]) == (1, 1)
+
+
+def test_k_entry_points_reject_missing_buffers(L):
+    """tt_contract_partial_k needs the K buffers and tt_contract_backward_k the
+    mask and the kept K: missing ones are argument errors, reported before
+    anything is enqueued."""
+    x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
+    y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
+    modes, ranks, _ = B.partial_shape(x, y, [1, 1, 0, 0], "chain")
+    z = FakeDesc(modes, ranks)
+    rc = L.tt_contract_partial_k(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, z.ref, None, None, None, None, None)
+    assert rc == -1
+    rc = L.tt_contract_backward_k(x.ref, y.ref, None, 0, z.ref, x.ref, y.ref, None, None, 0, None, None, 0, None)
+    assert rc == -1
