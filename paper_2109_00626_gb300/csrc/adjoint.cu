@@ -627,7 +627,6 @@ __global__ void __launch_bounds__(256) chain_adjoint_kernel(const __grid_constan
   T* const As = reinterpret_cast<T*>(chain_smem);
   T* const Bs = As + KCH * LDS;
   const int tid = threadIdx.x;
-  const T* gx = static_cast<const T*>(p.gx);
   const T* k = static_cast<const T*>(p.k);
   const T* dc = static_cast<const T*>(p.dc);
   const int ra = p.ra, rb = p.rb, I = p.I, ry = p.ry;

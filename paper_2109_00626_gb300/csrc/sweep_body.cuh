@@ -317,7 +317,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
                                            int crank, SweepState<T, RM, CL>& out) {
   using Cfg = SweepCfg<T, RM, CL>;
   using VT = typename Vec16<T>::type;
-  constexpr int NT = Cfg::NT, NW = Cfg::NW, TM = Cfg::TM, LD = Cfg::LD, V = Cfg::V, NST = Cfg::NST;
+  constexpr int NT = Cfg::NT, NW = Cfg::NW, LD = Cfg::LD, V = Cfg::V, NST = Cfg::NST;
   T* Es = reinterpret_cast<T*>(smem);  // E transposed: Es[q][p] = E[p][q]
   T* Ts = Es + Cfg::TILE;              // T = E B_i; the partial P at a mode's end
   T* Rs = Ts + Cfg::TILE;              // reduced rows of this CTA (cluster mode)
@@ -332,7 +332,6 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   int xph = 0;
 
   const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
   const int warp = tid >> 5, lane = tid & 31;
   const int n_pipe = p.final_scalar ? p.n_steps - 1 : p.n_steps;
 
@@ -602,76 +601,77 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
         }
         __syncthreads();
         return;
-      }
+      } else {
 #pragma unroll
-      for (int u = 0; u < NSE; ++u) {
-        const Sub sb = sub_tile<NT>(u, nu, nv);
-        if (sb.on) {
+        for (int u = 0; u < NSE; ++u) {
+          const Sub sb = sub_tile<NT>(u, nu, nv);
+          if (sb.on) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            T* row = Ts + (sb.m0 + a) * LD + sb.n0;
+            for (int a = 0; a < 4; ++a) {
+              T* row = Ts + (sb.m0 + a) * LD + sb.n0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
+              for (int b = 0; b < 4; ++b) row[b] = acc[u][a][b];
+            }
           }
         }
-      }
-      cluster.sync();
-      const int nvv = (nv + V - 1) / V;
-      const int chunk = (nu + C - 1) / C;
-      const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
-      int lexp = kNoExp, lbad = 0;
-      for (int idx = tid; idx < (ue - ub) * nvv; idx += NT) {
-        const int u = ub + idx / nvv, c = (idx % nvv) * V;
-        VT part[16];
+        cluster.sync();
+        const int nvv = (nv + V - 1) / V;
+        const int chunk = (nu + C - 1) / C;
+        const int ub = min(nu, crank * chunk), ue = min(nu, ub + chunk);
+        int lexp = kNoExp, lbad = 0;
+        for (int idx = tid; idx < (ue - ub) * nvv; idx += NT) {
+          const int u = ub + idx / nvv, c = (idx % nvv) * V;
+          VT part[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-          if (r < C) part[r] = *reinterpret_cast<const VT*>(cluster.map_shared_rank(Ts + u * LD + c, r));
-        VT s = Vec16<T>::zero();
+          for (int r = 0; r < 16; ++r)
+            if (r < C) part[r] = *reinterpret_cast<const VT*>(cluster.map_shared_rank(Ts + u * LD + c, r));
+          VT s = Vec16<T>::zero();
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-          if (r < C) s = Vec16<T>::add(s, part[r]);
-        *reinterpret_cast<VT*>(Rs + (u - ub) * LD + c) = s;
+          for (int r = 0; r < 16; ++r)
+            if (r < C) s = Vec16<T>::add(s, part[r]);
+          *reinterpret_cast<VT*>(Rs + (u - ub) * LD + c) = s;
 #pragma unroll
-        for (int q = 0; q < V; ++q)
-          if (c + q < nv) track(lexp, lbad, Vec16<T>::get(s, q));
-      }
-      lexp = __reduce_max_sync(0xffffffffu, lexp);
-      lbad = __reduce_or_sync(0xffffffffu, lbad);
-      if (lane == 0) {
-        ired[warp] = lexp;
-        ired[16 + warp] = lbad;
-      }
-      __syncthreads();
-      if (tid < C) {
-        int m = kNoExp, bb = 0;
-        for (int w = 0; w < NW; ++w) {
-          m = max(m, ired[w]);
-          bb |= ired[16 + w];
+          for (int q = 0; q < V; ++q)
+            if (c + q < nv) track(lexp, lbad, Vec16<T>::get(s, q));
         }
-        *cluster.map_shared_rank(ired + 32 + crank, tid) = m;
-        *cluster.map_shared_rank(ired + 64 + crank, tid) = bb;
-      }
-      cluster.sync();
-      int gexp = kNoExp, gbad = 0;
-      for (int r = 0; r < C; ++r) {
-        gexp = max(gexp, ired[32 + r]);
-        gbad |= ired[64 + r];
-      }
-      if (gbad) bad = 1;
-      const bool rescale = gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits);
-      if (rescale) log2s += gexp;
-      for (int idx = tid; idx < nu * nvv; idx += NT) {
-        const int u = idx / nvv, c = (idx % nvv) * V;
-        const int owner = u / chunk;
-        const VT v =
-            *reinterpret_cast<const VT*>(cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + c, owner));
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-          const T e = Vec16<T>::get(v, q);
-          Es[(c + q) * LD + u] = rescale ? mul_pow2<T>(e, -gexp) : e;
+        lexp = __reduce_max_sync(0xffffffffu, lexp);
+        lbad = __reduce_or_sync(0xffffffffu, lbad);
+        if (lane == 0) {
+          ired[warp] = lexp;
+          ired[16 + warp] = lbad;
         }
-      }
-      __syncthreads();
+        __syncthreads();
+        if (tid < C) {
+          int m = kNoExp, bb = 0;
+          for (int w = 0; w < NW; ++w) {
+            m = max(m, ired[w]);
+            bb |= ired[16 + w];
+          }
+          *cluster.map_shared_rank(ired + 32 + crank, tid) = m;
+          *cluster.map_shared_rank(ired + 64 + crank, tid) = bb;
+        }
+        cluster.sync();
+        int gexp = kNoExp, gbad = 0;
+        for (int r = 0; r < C; ++r) {
+          gexp = max(gexp, ired[32 + r]);
+          gbad |= ired[64 + r];
+        }
+        if (gbad) bad = 1;
+        const bool rescale = gexp != kNoExp && (gexp > p.renorm_bits || gexp < -p.renorm_bits);
+        if (rescale) log2s += gexp;
+        for (int idx = tid; idx < nu * nvv; idx += NT) {
+          const int u = idx / nvv, c = (idx % nvv) * V;
+          const int owner = u / chunk;
+          const VT v =
+              *reinterpret_cast<const VT*>(cluster.map_shared_rank(Rs + (u - owner * chunk) * LD + c, owner));
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const T e = Vec16<T>::get(v, q);
+            Es[(c + q) * LD + u] = rescale ? mul_pow2<T>(e, -gexp) : e;
+          }
+        }
+        __syncthreads();
+      }  // pull exchange
     }
 
   };
