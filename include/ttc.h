@@ -276,7 +276,10 @@ int tt_autotune(int dtype, const char* cache_path);
  * For a full contraction, dz/dGx_k[:,i,:] = L_k Gy_k[:,i,:] F_{k+1}^T and
  * dz/dGy_k[:,i,:] = L_k^T Gx_k[:,i,:] F_{k+1}, where L_k / F_{k+1} are the left
  * / right environments; a chain-layout partial contraction reduces to this with
- * the cotangent of its K as the boundary environment.
+ * the cotangent of its K as the boundary environment.  A full contraction whose
+ * y has every rank 1 (e.g. the sum of x's entries, y = all ones) takes a vector
+ * path: the environments are vectors, all of them kept (ckpt_stride unused),
+ * and x's ranks may go up to 1024.
  * Precision: TT_P_NATIVE (F64/F32). */
 int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
                          int prec, const double* cot_dev, const tt_desc* dz, const tt_desc* gx,

@@ -329,6 +329,33 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     ap.cluster = pow2_floor(std::min(16, mi));
   };
 
+  if (mask == nullptr && bp.r1) {
+    if (cot_dev == nullptr) return TT_ERR_ARG;
+    AdjR1Params rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.n = n;
+    for (int k = 0; k < n; ++k) {
+      AdjStep& st = rp.step[k];
+      st.gx = x->cores[k];
+      st.gy = y->cores[k];
+      st.dgx = gx->cores[k];
+      st.dgy = gy->cores[k];
+      st.I = x->modes[k];
+      st.rx = x->ranks[k];
+      st.rx2 = x->ranks[k + 1];
+      st.ry = 1;
+      st.ry2 = 1;
+    }
+    rp.lvec = w + bp.off_lvec;
+    rp.fvec = w + bp.off_fvec;
+    rp.llog = reinterpret_cast<int64_t*>(w + bp.off_llog);
+    rp.flog = reinterpret_cast<int64_t*>(w + bp.off_flog);
+    rp.vstride = bp.vstride;
+    rp.renorm_bits = ap.renorm_bits;
+    rp.cot = cot_dev;
+    rp.status = status_dev;
+    return launch_adjoint_r1(rp, x->dtype, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
   if (mask == nullptr) {
     if (cot_dev == nullptr) return TT_ERR_ARG;
     fill_block(0, n);

@@ -355,6 +355,9 @@ inline int isqrt_ceil(int n) {
 struct BackwardPlan {
   ChainPlan cp;
   int partial = 0;
+  int r1 = 0;  // full contraction with Y of rank 1 everywhere: vector adjoint (adjoint_r1.cu)
+  size_t off_lvec = 0, off_fvec = 0, off_llog = 0, off_flog = 0;
+  int64_t vstride = 1;
   int rmax = 1;
   int user_stride = 0;
   int64_t env_elems = 1;
@@ -391,6 +394,25 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   }
   const int rmax = std::max(max_rank(x), max_rank(y));
   bp->rmax = rmax;
+  if (mask == nullptr && max_rank(y) == 1) {
+    // environments are vectors: keep all of them, no checkpoints
+    if (max_rank(x) > kR1MaxRank) return TT_ERR_TOO_LARGE;
+    bp->r1 = 1;
+    const int eb1 = elem_bytes(x->dtype);
+    bp->vstride = max_rank(x);
+    const size_t vbytes = align256(static_cast<size_t>(n + 1) * bp->vstride * eb1);
+    size_t off1 = 0;
+    bp->off_lvec = off1;
+    off1 += vbytes;
+    bp->off_fvec = off1;
+    off1 += vbytes;
+    bp->off_llog = off1;
+    off1 += align256(sizeof(int64_t) * (n + 1));
+    bp->off_flog = off1;
+    off1 += align256(sizeof(int64_t) * (n + 1));
+    bp->ws_bytes = off1;
+    return TT_OK;
+  }
   if (rmax > adjoint_rank_cap(x->dtype) && (mask == nullptr || bp->cp.s > 0)) return TT_ERR_TOO_LARGE;
   if (mask != nullptr && rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
   const int eb = elem_bytes(x->dtype);

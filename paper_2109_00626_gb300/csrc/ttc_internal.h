@@ -150,6 +150,23 @@ struct AdjointParams {
   int32_t* status;
 };
 
+// Adjoint of a full contraction whose Y has every rank 1 (adjoint_r1.cu): the
+// environments are vectors, kept for every mode.
+constexpr int kR1MaxRank = 1024;  // ranks of X on this path
+struct AdjR1Params {
+  int n;
+  AdjStep step[kMaxOrder];   // gx, gy, dgx, dgy, I, rx, rx2 (ry = ry2 = 1)
+  void* lvec;                // [n + 1][vstride] L_0 .. L_n
+  void* fvec;                // [n + 1][vstride] F_0 .. F_n
+  int64_t* llog;             // [n + 1] power-of-two scales of L_k
+  int64_t* flog;             // [n + 1] power-of-two scales of F_k
+  int64_t vstride;
+  int renorm_bits;
+  const double* cot;         // scalar multiplier (device; NULL = 1)
+  int32_t* status;
+};
+cudaError_t launch_adjoint_r1(const AdjR1Params& p, int dtype, cudaStream_t s);
+
 // Most slice groups dK is split into (each group's partial sum is written
 // separately and the adjoint adds them as it loads its seed).
 constexpr int kDkGroups = 8;

@@ -210,3 +210,33 @@ def test_partial_k_kept_for_backward(dt, lead):
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         assert _rel(to_host(gx) + to_host(gy), wx + wy) <= (2e-5 if dt == np.float32 else 1e-12)
+
+
+@pytest.mark.parametrize(
+    "dt,rx,scale",
+    [
+        (np.float32, [1, 33, 61, 56, 34, 1], 0),
+        (np.float32, [1, 530, 40, 600, 7, 1], 0),
+        (np.float64, [1, 23, 30, 1, 28, 1], 0),
+        (np.float32, [1, 24, 24, 27, 41, 1], 20),
+    ],
+)
+def test_full_grad_rank1_y(dt, rx, scale):
+    """Full contraction with every rank of Y equal to 1 (the sum of a TT's
+    entries is the case y = ones): the vector adjoint against the oracle's
+    gradients, for ranks of X above the matrix path's cap (the environment
+    columns then run in chunks), a mode of size 1, a cotangent, and cores
+    scaled by 2^20 each (the vectors are renormalised on the way)."""
+    rng = np.random.default_rng(sum(rx) + scale)
+    modes = [3, 16, 1, 7, 5]
+    x = G.random_tt(rng, modes, rx, dt)
+    if scale:
+        x = [c * dt(2.0**scale) for c in x]
+    y = G.random_tt(rng, modes, [1] * 6, dt)
+    cot = torch.tensor([-1.5], dtype=torch.float64, device="cuda")
+    gx, gy, st = T.backward(to_dev(x), to_dev(y), None, cot=cot)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    wx, wy = O.grad_full(x, y, cot=-1.5)
+    assert _rel(to_host(gx), wx) <= (2e-5 if dt == np.float32 else 1e-12)
+    assert _rel(to_host(gy), wy) <= (2e-5 if dt == np.float32 else 1e-12)
