@@ -167,18 +167,19 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
                         int prec, const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev,
                         void* ws, size_t ws_bytes, tt_stream stream);
 
-/* The chain-layout partial contraction that also keeps K, the environment over
- * the contracted block (Algorithm 2 step 4), for a later tt_contract_backward_k
- * (the backward pass then does not sweep the block again).
- *   k_dev       device buffer of the dtype of x, [kx][ky] row-major, with
- *               kx = R^x_s, ky = R^y_s for a leading block of s modes and
- *               kx = R^x_m, ky = R^y_m for a trailing block starting at mode m
- *               (1 x 1 when no mode is contracted).
- *   k_log2_dev  device int64: K's power-of-two scale (true K = K * 2^k_log2).
- * Everything else as tt_contract_partial with TT_LAYOUT_CHAIN; no workspace. */
+/* The chain-layout partial contraction that also leaves, in `ws`, what its
+ * backward pass (tt_contract_backward_k with the same ws) would otherwise
+ * recompute: K, the environment over the contracted block (Algorithm 2 step
+ * 4), with its scale, and for a leading block the adjoint's checkpoints of the
+ * left environments (every ceil(sqrt(s)) modes; the backward still re-sweeps
+ * each segment from them).
+ *   ws, ws_bytes  device workspace of at least tt_workspace_bytes(TT_OP_BACKWARD,
+ *                 x, y, mask, TT_LAYOUT_CHAIN, prec) bytes, owned by the caller,
+ *                 kept unchanged until the backward call (TT_ERR_WS if short).
+ * Everything else as tt_contract_partial with TT_LAYOUT_CHAIN. */
 int tt_contract_partial_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec,
-                          const tt_desc* z, int64_t* z_log2_dev, void* k_dev, int64_t* k_log2_dev,
-                          int32_t* status_dev, tt_stream stream);
+                          const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev, void* ws,
+                          size_t ws_bytes, tt_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Batched contraction of many independent pairs in one persistent launch.
@@ -286,14 +287,13 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
                          const tt_desc* gy, int32_t ckpt_stride, int32_t* status_dev, void* ws,
                          size_t ws_bytes, tt_stream stream);
 
-/* tt_contract_backward of a chain-layout partial contraction whose K (and
- * scale) the forward pass kept with tt_contract_partial_k: the sweep over the
- * contracted block is not run again.  k_dev / k_log2_dev must hold what that
- * call wrote for the same x, y and mask (read only).  Workspace as
- * tt_contract_backward (TT_OP_BACKWARD with the same mask). */
+/* tt_contract_backward of a chain-layout partial contraction run with
+ * tt_contract_partial_k: `ws` is the workspace that call filled (same x, y,
+ * mask), so K is not swept again and, for a leading block, the adjoint starts
+ * from the stored checkpoints (default checkpoint stride).  Arguments as
+ * tt_contract_backward (mask required, TT_LAYOUT_CHAIN). */
 int tt_contract_backward_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec,
                            const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
-                           const void* k_dev, const int64_t* k_log2_dev, int32_t ckpt_stride,
                            int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream);
 
 /* ---------------------------------------------------------------------------

@@ -26,7 +26,6 @@ from ._binding import (  # noqa: F401
     error_string,
     launch_count,
     lib,
-    k_shape,
     partial_k,
     partial_shape,
     workspace_bytes,

@@ -101,10 +101,8 @@ def lib():
     L.tt_contract_backward.argtypes = [
         D, D, U8, c_int, c_int, c_void_p, D, D, D, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
     ]
-    L.tt_contract_partial_k.argtypes = [D, D, U8, c_int, D, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
-    L.tt_contract_backward_k.argtypes = [
-        D, D, U8, c_int, D, D, D, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p
-    ]
+    L.tt_contract_partial_k.argtypes = [D, D, U8, c_int, D, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.tt_contract_backward_k.argtypes = [D, D, U8, c_int, D, D, D, c_void_p, c_void_p, c_size_t, c_void_p]
     L.tt_autotune.argtypes = [c_int, ctypes.c_char_p]
     L.tt_error_string.argtypes = [c_int]
     L.tt_error_string.restype = ctypes.c_char_p
@@ -439,40 +437,32 @@ def autotune(dtype="f32", cache_path=None):
     return path
 
 
-def k_shape(x, y, mask):
-    """Shape (kx, ky) of K, the environment over the contracted end block of a
-    chain-layout partial contraction (1 x 1 when no mode is contracted)."""
-    n, s = len(mask), sum(1 for v in mask if v)
-    if s == 0:
-        return 1, 1
-    k = s if mask[0] else n - s
-    return int(x[k].shape[0]) if k < n else 1, int(y[k].shape[0]) if k < n else 1
-
-
 def partial_k(x, y, mask, z, stream=None):
     """Chain-layout partial contraction into the output cores ``z`` that also
-    returns K and its power-of-two scale (tt_contract_partial_k)."""
+    fills a backward workspace (K and, for a leading block, the adjoint's
+    checkpoints; tt_contract_partial_k).  Returns (ws, status); pass ``ws`` to
+    :func:`backward` as ``fwd_ws``."""
     import torch
 
     xd, yd, zd = Desc(x), Desc(y), Desc(z)
-    kx, ky = k_shape(x, y, mask)
     dev = x[0].device
-    k = torch.empty((kx, ky), dtype=x[0].dtype, device=dev)
-    klog2 = torch.zeros(1, dtype=torch.int64, device=dev)
+    nb = workspace_bytes(TT_OP_BACKWARD, xd, yd, mask, "chain")
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     rc = lib().tt_contract_partial_k(
-        xd.ref, yd.ref, _mask_arr(mask), TT_P_NATIVE, zd.ref, None, c_void_p(k.data_ptr()),
-        c_void_p(klog2.data_ptr()), c_void_p(status.data_ptr()), _stream_ptr(stream),
+        xd.ref, yd.ref, _mask_arr(mask), TT_P_NATIVE, zd.ref, None, c_void_p(status.data_ptr()),
+        c_void_p(ws.data_ptr()), c_size_t(ws.numel()), _stream_ptr(stream),
     )
     check(rc, "tt_contract_partial_k")
-    return k, klog2, status
+    return ws, status
 
 
-def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, layout="chain", k=None):
+def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, layout="chain", fwd_ws=None):
     """Gradients of a full (mask None; ``cot`` = float64 device scalar) or a
     chain-layout partial contraction (``dz`` = cotangents of the output cores)
-    with respect to every core of x and y.  Returns (gx, gy, status).  ``k`` =
-    (K, K scale) kept by :func:`partial_k` skips the sweep that recomputes K."""
+    with respect to every core of x and y.  Returns (gx, gy, status).
+    ``fwd_ws``: the workspace :func:`partial_k` filled in the forward pass
+    (tt_contract_backward_k: K and the checkpoints are not computed again)."""
     import torch
 
     xd, yd = Desc(x), Desc(y)
@@ -489,11 +479,10 @@ def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, lay
     dzd = Desc(dz) if dz is not None else None
     if cot is not None:
         cot = cot.detach().to(device=dev, dtype=torch.float64).reshape(1).contiguous()
-    if k is not None:
+    if fwd_ws is not None:
         rc = lib().tt_contract_backward_k(
-            xd.ref, yd.ref, m, TT_P_NATIVE, dzd.ref, gxd.ref, gyd.ref, c_void_p(k[0].data_ptr()),
-            c_void_p(k[1].data_ptr()), int(ckpt_stride), c_void_p(status.data_ptr()), c_void_p(ws.data_ptr()),
-            c_size_t(ws.numel()), _stream_ptr(stream),
+            xd.ref, yd.ref, m, TT_P_NATIVE, dzd.ref, gxd.ref, gyd.ref, c_void_p(status.data_ptr()),
+            c_void_p(fwd_ws.data_ptr()), c_size_t(fwd_ws.numel()), _stream_ptr(stream),
         )
         check(rc, "tt_contract_backward_k")
         return gx, gy, status
@@ -556,17 +545,17 @@ def _autograd():
             modes, ranks, _ = partial_shape(Desc(x), Desc(y), mask, "chain")
             z = [torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
                  for t in range(len(modes))]
-            k, klog2, _ = partial_k(x, y, mask, z)  # K is kept for the backward pass
+            fws, _ = partial_k(x, y, mask, z)  # K and checkpoints kept for the backward pass
             ctx.nx = nx
             ctx.mask = list(mask)
-            ctx.save_for_backward(*x, *y, k, klog2)
+            ctx.save_for_backward(*x, *y, fws)
             return tuple(z)
 
         @staticmethod
         def backward(ctx, *gz):
             saved = ctx.saved_tensors
-            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx : -2])
-            k, klog2 = saved[-2], saved[-1]
+            x, y = list(saved[: ctx.nx]), list(saved[ctx.nx : -1])
+            fws = saved[-1]
             xd, yd = Desc(x), Desc(y)
             modes, ranks, _ = partial_shape(xd, yd, ctx.mask, "chain")
             dz = []
@@ -574,7 +563,7 @@ def _autograd():
                 if g is None:
                     g = torch.zeros((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
                 dz.append(g.contiguous())
-            gx, gy, _ = backward(x, y, ctx.mask, dz=dz, k=(k, klog2))
+            gx, gy, _ = backward(x, y, ctx.mask, dz=dz, fwd_ws=fws)
             return (None, None, *gx, *gy)
 
     return TTFull, TTPartial

@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const __grid_constant__
   }
   const int nseg = (n + c - 1) / c;
   const int last_ck = (nseg - 1) * c;
-  for (int k = 0; k <= last_ck; ++k) {
+  // (skipped when the forward sweep of the contraction already stored them)
+  for (int k = 0; k <= last_ck && !p.ckpt_given; ++k) {
     if (k % c == 0 && crank == 0) {
       store_env<T, LD, NT>(ckpt + (k / c) * env_elems, p.step[k].rx, p.step[k].ry, Ls);
       if (tid == 0) p.ckpt_log2[k / c] = lg;

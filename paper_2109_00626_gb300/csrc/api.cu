@@ -237,10 +237,11 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
   return TT_ERR_ARG;
 }
 
-// Chain-layout partial contraction; with k_dev set, K (and its scale) is also
-// written out, for a backward pass to reuse.
+// Chain-layout partial contraction; with bws set (a backward workspace laid
+// out by bp), K and its scale -- and, for a leading block, the left-environment
+// checkpoints of the adjoint -- are also written into it.
 static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* z,
-                          int64_t* z_log2_dev, void* k_dev, int64_t* k_log2_dev, int32_t* status_dev,
+                          int64_t* z_log2_dev, char* bws, const BackwardPlan* bp, int32_t* status_dev,
                           tt_stream stream) {
   if (mask == nullptr) return TT_ERR_ARG;
   int rc = check_pair(x, y, mask);
@@ -256,8 +257,18 @@ static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mas
   SweepParams p;
   rc = build_partial(x, y, cp, z, z_log2_dev, status_dev, &p);
   if (rc != TT_OK) return rc;
-  p.e_out = k_dev;
-  p.e_out_log2 = k_dev != nullptr ? k_log2_dev : nullptr;
+  if (bws != nullptr) {
+    p.e_out = bws + bp->off_k;
+    p.e_out_log2 = reinterpret_cast<int64_t*>(bws + bp->off_klog2);
+    if (cp.side == 0 && cp.s > 0) {
+      const int c = bp->stride_for(cp.s);
+      p.ckpt = bws + bp->off_ckpt;
+      p.ckpt_log2 = reinterpret_cast<int64_t*>(bws + bp->off_ckpt_log2);
+      p.ckpt_stride = c;
+      p.ckpt_n = (cp.s + c - 1) / c;
+      p.ckpt_elems = bp->env_elems;
+    }
+  }
   return launch_sweep(p, x->dtype, s);
 }
 
@@ -277,16 +288,17 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
 }
 
 int tt_contract_partial_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* z,
-                          int64_t* z_log2_dev, void* k_dev, int64_t* k_log2_dev, int32_t* status_dev,
-                          tt_stream stream) {
-  if (k_dev == nullptr || k_log2_dev == nullptr) return TT_ERR_ARG;
-  return contract_chain(x, y, mask, prec, z, z_log2_dev, k_dev, k_log2_dev, status_dev, stream);
+                          int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
+  BackwardPlan bp;
+  const int rc = backward_plan(x, y, mask, TT_LAYOUT_CHAIN, prec, 0, &bp);
+  if (rc != TT_OK) return rc;
+  if (ws == nullptr || ws_bytes < bp.ws_bytes) return TT_ERR_WS;
+  return contract_chain(x, y, mask, prec, z, z_log2_dev, static_cast<char*>(ws), &bp, status_dev, stream);
 }
-
 static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
                          const double* cot_dev, const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
-                         int32_t ckpt_stride, const void* k_given, const int64_t* k_log2_given, int32_t* status_dev,
-                         void* ws, size_t ws_bytes, tt_stream stream) {
+                         int32_t ckpt_stride, int from_forward, int32_t* status_dev, void* ws, size_t ws_bytes,
+                         tt_stream stream) {
   BackwardPlan bp;
   int rc = backward_plan(x, y, mask, layout, prec, ckpt_stride, &bp);
   if (rc != TT_OK) return rc;
@@ -367,13 +379,13 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   rc = check_chain_output(x, cp, dz);
   if (rc != TT_OK) return rc;
   const int m = cp.m, sS = cp.s;
-  const void* kbuf = k_given != nullptr ? k_given : w + bp.off_k;
-  const int64_t* klog2 = k_given != nullptr ? k_log2_given : reinterpret_cast<int64_t*>(w + bp.off_klog2);
+  const void* kbuf = w + bp.off_k;
+  const int64_t* klog2 = reinterpret_cast<int64_t*>(w + bp.off_klog2);
   void* dkbuf = w + bp.off_dk;
 
   // 1. K again (the environment over the contracted block), unless the
-  //    forward pass kept it
-  if (k_given == nullptr) {
+  //    forward pass left it in the workspace
+  if (!from_forward) {
     SweepParams p;
     memset(&p, 0, sizeof(p));
     if (sS > 0) {
@@ -440,6 +452,7 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     if (cp.side == 0) {
       fill_block(0, sS);
       ap.f_seed = dkbuf;
+      ap.ckpt_given = from_forward;  // the forward sweep stored the left checkpoints
     } else {
       fill_block(m, n);
       ap.l_seed = dkbuf;
@@ -452,16 +465,16 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
 int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout, int prec,
                          const double* cot_dev, const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,
                          int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
-  return backward_impl(x, y, mask, layout, prec, cot_dev, dz, gx, gy, ckpt_stride, nullptr, nullptr, status_dev, ws,
-                       ws_bytes, stream);
+  return backward_impl(x, y, mask, layout, prec, cot_dev, dz, gx, gy, ckpt_stride, 0, status_dev, ws, ws_bytes,
+                       stream);
 }
 
 int tt_contract_backward_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec, const tt_desc* dz,
-                           const tt_desc* gx, const tt_desc* gy, const void* k_dev, const int64_t* k_log2_dev,
-                           int32_t ckpt_stride, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
-  if (mask == nullptr || k_dev == nullptr || k_log2_dev == nullptr) return TT_ERR_ARG;
-  return backward_impl(x, y, mask, TT_LAYOUT_CHAIN, prec, nullptr, dz, gx, gy, ckpt_stride, k_dev, k_log2_dev,
-                       status_dev, ws, ws_bytes, stream);
+                           const tt_desc* gx, const tt_desc* gy, int32_t* status_dev, void* ws, size_t ws_bytes,
+                           tt_stream stream) {
+  if (mask == nullptr) return TT_ERR_ARG;
+  return backward_impl(x, y, mask, TT_LAYOUT_CHAIN, prec, nullptr, dz, gx, gy, 0, 1, status_dev, ws, ws_bytes,
+                       stream);
 }
 
 }  // extern "C"

@@ -676,6 +676,18 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 
   };
   for (int j = 0; j < n_pipe; ++j) {
+    if (p.ckpt != nullptr && crank == 0 && j % p.ckpt_stride == 0 && j / p.ckpt_stride < p.ckpt_n) {
+      // checkpoint: the environment before mode j (read before this mode's
+      // products; nothing writes Es until its exchange)
+      const int g = j / p.ckpt_stride;
+      const int rxk = j == 0 ? p.rx0 : sst[j - 1].rout_x, ryk = j == 0 ? p.ry0 : sst[j - 1].rout_y;
+      T* dst = static_cast<T*>(p.ckpt) + g * p.ckpt_elems;
+      for (int idx = tid; idx < rxk * ryk; idx += NT) {
+        const int u = idx / ryk, v = idx - u * ryk;
+        dst[idx] = Es[v * LD + u];
+      }
+      if (tid == 0) p.ckpt_log2[g] = log2s;
+    }
     const SweepStep& sj = sst[j];
     const int need1 = ((sj.rin_x + 3) >> 2) * ((sj.rout_y + 3) >> 2);
     const int need2 = ((sj.rout_x + 3) >> 2) * ((sj.rout_y + 3) >> 2);

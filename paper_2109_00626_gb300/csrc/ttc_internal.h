@@ -104,6 +104,13 @@ struct SweepParams {
   int64_t* z_out_log2;    // optional; if NULL the scale is folded into *z_out
   int32_t* status;
   EmitParams emit;        // fused chain emission after the sweep (partial contractions)
+  // optional checkpoints of a left-to-right sweep for a later adjoint: the
+  // environment before modes 0, c, 2c, ... (ckpt_n of them, c = ckpt_stride),
+  // each row-major at ckpt + g * ckpt_elems, its scale in ckpt_log2[g]
+  void* ckpt;
+  int64_t* ckpt_log2;
+  int ckpt_stride, ckpt_n;
+  int64_t ckpt_elems;
 };
 
 // Full contraction as two half sweeps meeting in the middle (sweep.cu):
@@ -138,6 +145,7 @@ struct AdjointParams {
   AdjStep step[kMaxOrder];
   const void* l_seed;    // optional left seed [rx(0)][ry(0)] (NULL = [1])
   const int64_t* l_seed_log2;
+  int ckpt_given;        // 1: the checkpoints are already in ckpt / ckpt_log2 (written by the forward sweep)
   const void* f_seed;    // optional right seed [rx2(n-1)][ry2(n-1)] (NULL = [1])
   const int64_t* f_seed_log2;
   int seed_parts;        // a seed is the sum of this many consecutive matrices (0 or 1 = one)

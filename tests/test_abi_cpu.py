@@ -119,27 +119,15 @@ def test_partial_shape_degenerate_masks(L):
         B.partial_shape(x1, y1, [1], "chain")
 
 
-def test_k_shape():
-    """K of a chain-layout partial contraction: R^x_s x R^y_s for a leading block
-    of s modes, R^x_m x R^y_m for a trailing block starting at mode m."""
-    import numpy as np
-
-    x = [np.zeros(s) for s in [(1, 2, 6), (6, 3, 7), (7, 4, 8), (8, 5, 1)]]
-    y = [np.zeros(s) for s in [(1, 2, 9), (9, 3, 10), (10, 4, 11), (11, 5, 1)]]
-    assert B.k_shape(x, y, [1, 1, 0, 0]) == (7, 10)
-    assert B.k_shape(x, y, [0, 0, 0, 1]) == (8, 11)
-    assert B.k_shape(x, y, [0, 0, 0, 0]) == (1, 1)
-
-
 def test_k_entry_points_reject_missing_buffers(L):
-    """tt_contract_partial_k needs the K buffers and tt_contract_backward_k the
-    mask and the kept K: missing ones are argument errors, reported before
-    anything is enqueued."""
+    """tt_contract_partial_k needs the backward workspace it fills, and
+    tt_contract_backward_k the mask: missing ones are reported before anything
+    is enqueued."""
     x = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1])
     y = FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
     modes, ranks, _ = B.partial_shape(x, y, [1, 1, 0, 0], "chain")
     z = FakeDesc(modes, ranks)
-    rc = L.tt_contract_partial_k(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, z.ref, None, None, None, None, None)
-    assert rc == -1
-    rc = L.tt_contract_backward_k(x.ref, y.ref, None, 0, z.ref, x.ref, y.ref, None, None, 0, None, None, 0, None)
-    assert rc == -1
+    rc = L.tt_contract_partial_k(x.ref, y.ref, _mask([1, 1, 0, 0]), 0, z.ref, None, None, None, 0, None)
+    assert rc == -6  # TT_ERR_WS
+    rc = L.tt_contract_backward_k(x.ref, y.ref, None, 0, z.ref, x.ref, y.ref, None, None, 0, None)
+    assert rc == -1  # TT_ERR_ARG

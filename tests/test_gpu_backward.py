@@ -176,37 +176,34 @@ def test_partial_grad_uneven_ranks_fp32(lead):
 @pytest.mark.parametrize("dt,lead", [(np.float32, True), (np.float32, False), (np.float64, True), (np.float64, False)])
 def test_partial_k_kept_for_backward(dt, lead):
     """tt_contract_partial_k writes the same output cores as the plain partial
-    contraction plus K (the environment over the contracted block, against the
-    oracle's L_s / F_m with the Cauchy-Schwarz scale), and the backward pass
-    that takes this K gives the oracle's gradients like the one that sweeps
-    the block again."""
+    contraction and fills a backward workspace (K; for a leading block also
+    the adjoint's checkpoints, stored by the forward sweep); the backward pass
+    that starts from it gives the oracle's gradients, like the one that
+    recomputes everything."""
     rng = np.random.default_rng(51 if lead else 53)
-    modes = [5, 7, 3, 9, 4, 6]
+    modes = [5, 7, 3, 9, 4, 6, 3, 2, 4]
     r = 64 if dt == np.float32 else 32
-    x = G.random_tt(rng, modes, [1, 16, r - 1, 20, r, 8, 1], dt)
-    y = G.random_tt(rng, modes, [1, 12, r, 17, r - 3, 9, 1], dt)
-    mask = [1, 1, 1, 0, 0, 0] if lead else [0, 0, 0, 1, 1, 1]
-    side, s = O.end_block(mask)
+    rx = [1, 16, r - 1, 20, r, 8, r, 5, 9, 1]
+    ry = [1, 12, r, 17, r - 3, 9, 11, r, 3, 1]
+    x = G.random_tt(rng, modes, rx, dt)
+    y = G.random_tt(rng, modes, ry, dt)
+    mask = [1] * 7 + [0] * 2 if lead else [0] * 2 + [1] * 7  # seven modes: three checkpoint segments
     xd, yd = to_dev(x), to_dev(y)
     ref = T.PartialContraction(xd, yd, mask)
     ref()
     z = [torch.empty_like(c) for c in ref.z]
-    k, klog2, st = T.partial_k(xd, yd, mask, z)
+    fws, st = T.partial_k(xd, yd, mask, z)
     torch.cuda.synchronize()
     assert int(st.item()) == 0 and int(ref.status.item()) == 0
     tol = 1e-5 if dt == np.float32 else 1e-12
     for a, b in zip(to_host(z), to_host(ref.z)):
         assert np.abs(a - b).max() <= tol * max(1.0, float(np.abs(b).max()))
-    kw = O.left_envs(x[:s], y[:s])[-1] if lead else O.right_envs(x[len(x) - s :], y[len(y) - s :])[0]
-    kg = k.detach().cpu().double().numpy() * 2.0 ** int(klog2.item())
-    assert kg.shape == kw.shape == T.k_shape(xd, yd, mask)
-    assert np.abs(kg - kw).max() <= tol * cs_bound(x, y, side, s).max()
     zo, _ = O.partial_chain(x, y, mask)
     dz = [rng.standard_normal(c.shape).astype(dt) for c in zo]
     dzd = to_dev(dz)
     wx, wy = O.grad_partial_chain(x, y, mask, [d.astype(np.float64) for d in dz])
-    for kept in (None, (k, klog2)):
-        gx, gy, st = T.backward(xd, yd, mask, dz=dzd, k=kept)
+    for kept in (None, fws):
+        gx, gy, st = T.backward(xd, yd, mask, dz=dzd, fwd_ws=kept)
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         assert _rel(to_host(gx) + to_host(gy), wx + wy) <= (2e-5 if dt == np.float32 else 1e-12)
