@@ -237,3 +237,20 @@ def test_full_grad_rank1_y(dt, rx, scale):
     wx, wy = O.grad_full(x, y, cot=-1.5)
     assert _rel(to_host(gx), wx) <= (2e-5 if dt == np.float32 else 1e-12)
     assert _rel(to_host(gy), wy) <= (2e-5 if dt == np.float32 else 1e-12)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("modes,rx", [([5], [1, 1]), ([4, 6], [1, 9, 1]), ([1, 1], [1, 3, 1])])
+def test_full_grad_rank1_y_short_trains(dt, modes, rx):
+    """The vector adjoint on trains of order 1 and 2 (the left or right vector
+    is the unit start for every core) and on modes of size 1."""
+    rng = np.random.default_rng(len(modes) * 10 + rx[1])
+    x = G.random_tt(rng, modes, rx, dt)
+    y = G.random_tt(rng, modes, [1] * (len(modes) + 1), dt)
+    cot = torch.tensor([0.75], dtype=torch.float64, device="cuda")
+    gx, gy, st = T.backward(to_dev(x), to_dev(y), None, cot=cot)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    wx, wy = O.grad_full(x, y, cot=0.75)
+    tol = 2e-5 if dt == np.float32 else 1e-12
+    assert _rel(to_host(gx), wx) <= tol and _rel(to_host(gy), wy) <= tol
