@@ -28,11 +28,12 @@ constexpr int kR1Warps = kR1Threads / 32;
 constexpr int kNoExpR1 = -(1 << 30);
 
 // Block-wide max of an exponent and OR of a flag (every thread gets both).
+// One barrier: callers alternate `red` between two buffers, so the previous
+// reduction's readers are past a later barrier before it is written again.
 __device__ __forceinline__ void block_max_or_r1(int& e, int& bad, int* red) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   e = __reduce_max_sync(0xffffffffu, e);
   bad = __reduce_or_sync(0xffffffffu, bad);
-  __syncthreads();  // earlier readers of red are done
   if (lane == 0) {
     red[warp] = e;
     red[kR1Warps + warp] = bad;
@@ -44,24 +45,6 @@ __device__ __forceinline__ void block_max_or_r1(int& e, int& bad, int* red) {
     e = max(e, red[w]);
     bad |= red[kR1Warps + w];
   }
-}
-
-// Rescale v[0..n) by an exact power of two when its largest exponent leaves
-// [-s, s]; returns the exponent folded out (0 when none).
-template <typename T>
-__device__ int renorm_vec(T* v, int n, int s, int* red, int& bad) {
-  int e = kNoExpR1, lbad = 0;
-  for (int a = threadIdx.x; a < n; a += kR1Threads) {
-    if (!isfinite(v[a])) lbad = 1;
-    else if (v[a] != T(0)) e = max(e, exp2_bits(v[a]));
-  }
-  block_max_or_r1(e, lbad, red);
-  if (lbad) bad = 1;
-  const int sh = (e != kNoExpR1 && (e > s || e < -s)) ? e : 0;
-  if (sh)
-    for (int a = threadIdx.x; a < n; a += kR1Threads) v[a] = mul_pow2<T>(v[a], -sh);
-  __syncthreads();
-  return sh;
 }
 
 // Cluster of kR1Cluster CTAs per direction (blocks [0, C): L, [C, 2C): F).
@@ -80,7 +63,7 @@ __global__ void __launch_bounds__(kR1Threads) r1_sweep_kernel(const __grid_const
   T* nxt = cur + kR1MaxRank;                // [kR1MaxRank] the next vector
   T* parts = nxt + kR1MaxRank;              // [2][kR1MaxRank] this CTA's part, by mode parity
   T* tmp = parts + 2 * kR1MaxRank;          // [16 / sizeof(T)][kR1Threads] per-thread partial columns
-  __shared__ int red[2 * kR1Warps];
+  __shared__ int red[2][2 * kR1Warps];  // block reductions, alternating by mode parity
   cg::cluster_group cluster = cg::this_cluster();
   const int C = static_cast<int>(cluster.num_blocks());
   const int crank = static_cast<int>(cluster.block_rank());
@@ -115,6 +98,7 @@ __global__ void __launch_bounds__(kR1Threads) r1_sweep_kernel(const __grid_const
       const bool vec = R2 % VW == 0 && (reinterpret_cast<uintptr_t>(gx) & 15) == 0;
       const int w = vec ? VW : 1;
       for (int c0 = 0; c0 < R2; c0 += kR1Threads * w) {
+        if (c0 > 0) __syncthreads();  // the previous pass has read tmp
         const int nc = min(kR1Threads, (R2 - c0 + w - 1) / w);  // column units of this pass
         const int G = max(1, kR1Threads / nc);                   // row groups
         const int col = tid % nc, grp = tid / nc;
@@ -154,7 +138,6 @@ __global__ void __launch_bounds__(kR1Threads) r1_sweep_kernel(const __grid_const
             part[c0 + cu * w + q] = sum;
           }
         }
-        __syncthreads();
       }
     } else {
       // F_k[a] = sum_{i,a'} Gx_k[a][i][a'] y_k[i] F_{k+1}[a'] for rows a in [a0, a1)
@@ -173,32 +156,42 @@ __global__ void __launch_bounds__(kR1Threads) r1_sweep_kernel(const __grid_const
         if (lane == 0) part[a] = acc;
       }
     }
-    cluster.sync();  // every CTA's part of this mode is visible
+    cluster.sync();  // every CTA's part of this mode is visible (and this CTA's threads are in step)
+    // gather the whole vector (each thread keeps its own entries in nxt) and
+    // its largest binary exponent
+    int e = kNoExpR1, lbad = 0;
     if (left) {
       for (int c = tid; c < nout; c += kR1Threads) {
-        T s = T(0);
-        for (int r = 0; r < C; ++r) s += *cluster.map_shared_rank(part + c, r);
-        nxt[c] = s;
+        T sum = T(0);
+        for (int r = 0; r < C; ++r) sum += *cluster.map_shared_rank(part + c, r);
+        nxt[c] = sum;
+        if (!isfinite(sum)) lbad = 1;
+        else if (sum != T(0)) e = max(e, exp2_bits(sum));
       }
     } else {
       for (int a = tid; a < nout; a += kR1Threads) {
-        const int owner = min(C - 1, static_cast<int>((static_cast<int64_t>(a) * C + C - 1) / R));
         // rows [R r / C, R (r + 1) / C) belong to rank r
-        int o = owner;
+        int o = min(C - 1, static_cast<int>((static_cast<int64_t>(a) * C + C - 1) / R));
         while (o > 0 && a < R * o / C) --o;
         while (o + 1 < C && a >= R * (o + 1) / C) ++o;
-        nxt[a] = *cluster.map_shared_rank(part + a, o);
+        const T v = *cluster.map_shared_rank(part + a, o);
+        nxt[a] = v;
+        if (!isfinite(v)) lbad = 1;
+        else if (v != T(0)) e = max(e, exp2_bits(v));
       }
     }
-    __syncthreads();
-    lg += renorm_vec<T>(nxt, nout, p.renorm_bits, red, bad);
+    block_max_or_r1(e, lbad, red[step & 1]);
+    if (lbad) bad = 1;
+    const int sh = (e != kNoExpR1 && (e > p.renorm_bits || e < -p.renorm_bits)) ? e : 0;
+    lg += sh;
     const int64_t vk = left ? k + 1 : k;
-    for (int a = tid; a < nout; a += kR1Threads) {
-      cur[a] = nxt[a];
-      if (crank == 0) vecs[vk * p.vstride + a] = nxt[a];
+    for (int a = tid; a < nout; a += kR1Threads) {  // the same entries this thread gathered
+      const T v = sh ? mul_pow2<T>(nxt[a], -sh) : nxt[a];
+      cur[a] = v;
+      if (crank == 0) vecs[vk * p.vstride + a] = v;
     }
     if (crank == 0 && tid == 0) scl[vk] = lg;
-    __syncthreads();
+    __syncthreads();  // cur is complete before the next mode reads it
   }
   if (bad && tid == 0 && crank == 0) set_status(p.status, TT_STATUS_NONFINITE);
   cluster.sync();  // peers' parts stay readable until everyone is done
