@@ -181,17 +181,53 @@ def _stream_ptr(stream):
     return c_void_p(s.cuda_stream)
 
 
+_ws_cache = {}
+
+
+def _shape_key(d):
+    """(order, modes, ranks, dtype) of a descriptor, read from its C struct."""
+    t = d.desc
+    n = int(t.order)
+    return (n, tuple(t.modes[k] for k in range(n)), tuple(t.ranks[k] for k in range(n + 1)), int(t.dtype))
+
+
 def workspace_bytes(op, xd, yd, mask=None, layout="chain", prec="native"):
+    """tt_workspace_bytes; the answer depends on shapes, dtype, mask, layout and
+    precision only, so it is remembered per such key (the autograd functions
+    ask on every call)."""
+    key = (op, _shape_key(xd), _shape_key(yd), None if mask is None else tuple(int(bool(v)) for v in mask),
+           layout, prec)
+    hit = _ws_cache.get(key)
+    if hit is not None:
+        return hit
     nb = c_size_t(0)
     m = _mask_arr(mask) if mask is not None else None
     check(
         lib().tt_workspace_bytes(op, xd.ref, yd.ref, m, LAYOUT[layout], PREC[prec], ctypes.byref(nb)),
         "tt_workspace_bytes",
     )
+    if len(_ws_cache) < 4096:
+        _ws_cache[key] = int(nb.value)
     return int(nb.value)
 
 
+_shape_cache = {}
+
+
 def partial_shape(xd, yd, mask, layout="chain"):
+    """tt_partial_shape: (modes, ranks, perm) of the result; remembered per
+    (shapes, dtype, mask, layout) like the workspace sizes."""
+    key = (_shape_key(xd), _shape_key(yd), tuple(int(bool(v)) for v in mask), layout)
+    hit = _shape_cache.get(key)
+    if hit is not None:
+        return list(hit[0]), list(hit[1]), list(hit[2])
+    res = _partial_shape(xd, yd, mask, layout)
+    if len(_shape_cache) < 4096:
+        _shape_cache[key] = res
+    return list(res[0]), list(res[1]), list(res[2])
+
+
+def _partial_shape(xd, yd, mask, layout):
     n = xd.desc.order
     order = c_int32(0)
     modes = (c_int32 * (2 * n))()
@@ -220,7 +256,7 @@ class FullContraction:
 
         self.xd, self.yd = Desc(x), Desc(y)
         dev = x[0].device
-        self.out = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.out = torch.empty(1, dtype=torch.float64, device=dev)  # every path writes it
         self.log2 = torch.zeros(1, dtype=torch.int64, device=dev) if split else None
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.prec = PREC[prec]
@@ -588,9 +624,18 @@ def tt_partial(x, y, mask):
     return list(_fns[1].apply(len(x), list(mask), *x, *y))
 
 
+_ones_cache = {}
+
+
 def tt_sum(cores):
-    """Sum of all entries of a TT (= <Z, all-ones rank-1 TT>), differentiable."""
+    """Sum of all entries of a TT (= <Z, all-ones rank-1 TT>), differentiable.
+    The all-ones TT is a constant, built once per (mode sizes, dtype, device)."""
     import torch
 
-    ones = [torch.ones((1, int(c.shape[1]), 1), dtype=c.dtype, device=c.device) for c in cores]
-    return tt_full(list(cores), ones)
+    key = (tuple(int(c.shape[1]) for c in cores), cores[0].dtype, cores[0].device)
+    ones = _ones_cache.get(key)
+    if ones is None:
+        ones = [torch.ones((1, int(c.shape[1]), 1), dtype=c.dtype, device=c.device) for c in cores]
+        if len(_ones_cache) < 256:
+            _ones_cache[key] = ones
+    return tt_full(list(cores), list(ones))
