@@ -60,6 +60,40 @@ def fp32_simt_peak_tflops():
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def measure_peaks():
+    """Reference peaks the driver does not measure: cuBLAS SGEMM with TF32 off
+    (the float32 FMA pipe) and DGEMM, square n x n, timed with CUDA events
+    after warm-up; one JSON line.  Context for the float32 roofline, whose
+    denominator stays the derived FMA peak."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {"derived_fp32_fma_tflops": fp32_simt_peak_tflops()}
+    for name, dt, n, reps in (("sgemm", torch.float32, 8192, 20), ("dgemm", torch.float64, 4096, 5)):
+        a = torch.randn(n, n, dtype=dt, device=dev)
+        b = torch.randn(n, n, dtype=dt, device=dev)
+        c = torch.empty(n, n, dtype=dt, device=dev)
+        for _ in range(3):
+            torch.mm(a, b, out=c)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(0)
+        sampler.start()
+        e0.record()
+        for _ in range(reps):
+            torch.mm(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1) / reps
+        out[name + "_tflops"] = 2.0 * n**3 / (ms / 1e3) / 1e12
+        out[name + "_n"] = n
+        out[name + "_clocks"] = clocks
+    print(json.dumps(out))
+    return 0
+
+
 def work_per_step():
     modes = [16] * 10
     r = G.tt_ranks(10, 64)
@@ -719,6 +753,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "backward"], default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="time cuBLAS SGEMM (TF32 off) and DGEMM as reference peaks and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -726,6 +762,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return run_profile_case(args.profile_case)
+    if args.measure_peaks:
+        return measure_peaks()
     return run_ours(args)
 
 
