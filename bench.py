@@ -415,6 +415,7 @@ def run_ours(args):
         forms["bf16"] = bench_bf16(T, dev, args, "native")
         forms["bf16x3"] = bench_bf16(T, dev, args, "bf16x3")
         forms["backward"] = bench_backward(T, dev, args)
+        forms["merged"] = bench_merged(T, dev, args)
 
     if rank == 0:
         line = {
@@ -555,6 +556,81 @@ def bench_batched(T, dev, args):
 def _bf16_peak():
     pk = _peaks()
     return pk.get("bf16_tflops", 1933.5), pk.get("bf16_tflops_sustained", 1747.6)
+
+
+def merged_masks(draws=8, order=6, size=3):
+    """Seeded random contracted sets S, |S| = size of order modes."""
+    out = []
+    for d in range(draws):
+        mask = [0] * order
+        for k in np.random.default_rng([2109, d]).choice(order, size, replace=False):
+            mask[int(k)] = 1
+        out.append(mask)
+    return out
+
+
+def merged_bytes(x, y, zs, ebytes):
+    """Cores read once plus the merged output cores written once."""
+    return ebytes * (sum(c.size for c in x) + sum(c.size for c in y) + sum(int(np.prod(s)) for s in zs))
+
+
+def bench_merged(T, dev, args):
+    """Partial contraction over a random set of three of six modes, merged
+    (TT-matrix) layout: modes 8, ranks 16, float32; eight seeded draws of S,
+    timed in turn with an L2 flush before each contraction."""
+    import torch
+
+    x, y = G.pair(13, [8] * 6, G.tt_ranks(6, 16), G.tt_ranks(6, 16), np.float32)
+    xd = [torch.from_numpy(c).to(dev) for c in x]
+    yd = [torch.from_numpy(c).to(dev) for c in y]
+    masks = merged_masks()
+    ops = [T.PartialContraction(xd, yd, m, layout="merged") for m in masks]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        for op in ops:
+            op(stream)
+    torch.cuda.synchronize(dev)
+    R = max(3, args.steps // 40)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R * len(ops))]
+    for r in range(R):
+        for k, op in enumerate(ops):
+            flush.fill_(float(r))  # L2 flush between timed contractions (untimed)
+            a, b = ev[r * len(ops) + k]
+            a.record(stream)
+            op(stream)
+            b.record(stream)
+    torch.cuda.synchronize(dev)
+    per = [statistics.mean(ev[r * len(ops) + k][0].elapsed_time(ev[r * len(ops) + k][1]) for r in range(R))
+           for k in range(len(ops))]
+    ms = statistics.mean(per)
+    nbytes = statistics.mean(merged_bytes(x, y, [tuple(c.shape) for c in op.z], 4) for op in ops)
+    hbm = _peaks().get("hbm_gbs", 6683.2)
+    status = 0
+    for op in ops:
+        status |= int(op.status.item())
+    return {
+        "workload": "order-6 TT pair, modes 8, ranks 16, float32; partial contraction over a random S, |S| = 3, "
+                    "merged layout; eight seeded draws of S timed in turn",
+        "sets": ["".join(str(v) for v in m) for m in masks],
+        "value": 1.0 / (ms / 1e3),
+        "unit": "contractions/s",
+        "ms_per_contraction": ms,
+        "ms_per_set": per,
+        "alg_bytes": nbytes,
+        "roofline": {
+            "kernel": "whole contraction (zrows_kernel writes the merged cores)",
+            "bound": "hbm",
+            "achieved": nbytes / (ms / 1e3) / 1e9,
+            "peak": hbm,
+            "unit": "GB/s",
+            "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+            "note": "bytes = cores read once + merged cores written once, mean over the draws; "
+                    "peak = measured HBM copy bandwidth",
+        },
+        "device_status": status,
+        "l2": "flushed before each contraction",
+    }
 
 
 def bench_bf16(T, dev, args, prec):
@@ -725,6 +801,14 @@ def run_profile_case(case):
             loss.backward()
         torch.cuda.synchronize(dev)
         status = torch.tensor([0 if math.isfinite(float(loss.detach())) else 1])
+    elif case == "merged":
+        x, y = G.pair(13, [8] * 6, G.tt_ranks(6, 16), G.tt_ranks(6, 16), np.float32)
+        xd, yd = [torch.from_numpy(c).to(dev) for c in x], [torch.from_numpy(c).to(dev) for c in y]
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        for m in merged_masks():
+            op = T.PartialContraction(xd, yd, m, layout="merged")
+            op()
+            status |= op.status
     elif case == "batched512":
         _, pairs = G.batch4096_device(512, 0, dev)
         op = T.BatchedContraction(pairs)
@@ -751,7 +835,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "backward"], default=None,
+    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "backward", "merged"],
+                    default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")
     ap.add_argument("--measure-peaks", action="store_true",
                     help="time cuBLAS SGEMM (TF32 off) and DGEMM as reference peaks and exit")

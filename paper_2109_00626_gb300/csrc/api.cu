@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "host_plan.h"
@@ -23,6 +24,170 @@ int tc_full_launch(const tt_desc* x, const tt_desc* y, int prec, double* out, in
                    void* ws, size_t ws_bytes, cudaStream_t s);
 size_t tc_full_ws(const tt_desc* x, const tt_desc* y, int prec, int* rc);
 
+// Auxiliary streams of one device for the independent per-core chains of a
+// merged-layout contraction: forked from the caller's stream by an event and
+// joined back into it by one event per auxiliary stream, so the contraction
+// stays ordered on the caller's stream (and captures into a graph as such).
+struct ForkStreams {
+  static constexpr int kAux = 3;
+  cudaStream_t aux[kAux];
+  cudaEvent_t fork, done[kAux];
+  bool ok = false;
+};
+static std::mutex g_fork_mu;  // guards g_fork and the use of its events
+static ForkStreams g_fork[64];
+
+static ForkStreams* fork_streams() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  ForkStreams& f = g_fork[dev];
+  if (!f.ok) {
+    for (int i = 0; i < ForkStreams::kAux; ++i)
+      if (cudaStreamCreateWithFlags(&f.aux[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&f.done[i], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    if (cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    f.ok = true;
+  }
+  return &f;
+}
+
+// Output core t of a merged-layout contraction on stream s (see merged.cu).
+static int merged_core(const tt_desc* x, const tt_desc* y, const tt_desc* z, const MergedPlan& mp, int t, char* w,
+                       int32_t* status_dev, cudaStream_t s) {
+  const int n = x->order;
+  const int f0 = mp.free_pos[0];
+  const int f = mp.free_pos[t];
+  const int k0 = f + 1, k1 = mp.run_k1[t];
+  const bool run = k1 > k0;
+  const bool trail = run && k1 == n;
+  const int rx = x->ranks[f], ry = y->ranks[f], I = x->modes[f], J = y->modes[f];
+  const int rx2 = x->ranks[f + 1], ry2 = y->ranks[f + 1];
+  const int C = x->ranks[k1] * y->ranks[k1];
+  int64_t* slots = reinterpret_cast<int64_t*>(w + mp.off_slots);
+  int64_t* emax = slots + 1 + kMergedSlotsPerCore * t;  // M; then P, W_0, V
+  void* mbuf = w + mp.off_m[t];
+  // the run's map M on the right leg: E_R of a right-to-left sweep for a
+  // trailing run (one scale), the transfer matrix otherwise (a scale per row)
+  const int64_t* mexp = emax;
+  if (trail) {
+    SweepParams p;
+    memset(&p, 0, sizeof(p));
+    fill_right(p, x, y, k0, n);
+    p.rx0 = 1;
+    p.ry0 = 1;
+    p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+    p.e_out = mbuf;
+    p.e_out_log2 = emax;
+    p.status = status_dev;
+    const int rc = launch_sweep(p, x->dtype, s);
+    if (rc != TT_OK) return rc;
+  } else if (run) {
+    if (cudaMemsetAsync(emax, 0xC0, sizeof(int64_t), s) != cudaSuccess) return TT_ERR_CUDA;
+    TransferParams tp;
+    memset(&tp, 0, sizeof(tp));
+    SweepParams sp;
+    memset(&sp, 0, sizeof(sp));
+    fill_left(sp, x, y, k0, k1);
+    tp.n_steps = sp.n_steps;
+    memcpy(tp.step, sp.step, sizeof(tp.step));
+    tp.m = mbuf;
+    tp.mexp = reinterpret_cast<int64_t*>(w + mp.off_mexp[t]);
+    tp.emax = emax;
+    tp.status = status_dev;
+    if (launch_transfer(tp, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    mexp = tp.mexp;
+  }
+  if (t == 0) {
+    // the left core, E_L folded in (E_L from the caller's stream, before the fork)
+    KronParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.gx = x->cores[f];
+    kp.gy = y->cores[f];
+    kp.rx = rx;
+    kp.ry = ry;
+    kp.I = I;
+    kp.J = J;
+    kp.rx2 = rx2;
+    kp.ry2 = ry2;
+    kp.out = run ? static_cast<void*>(w + mp.off_w0) : z->cores[0];
+    kp.el = f0 > 0 ? w + mp.off_el : nullptr;
+    kp.el_log2 = f0 > 0 ? slots : nullptr;
+    kp.tmp = w + mp.off_v;
+    kp.vexp = emax + 3;
+    kp.wexp = emax + 2;
+    kp.scale_out = run ? 0 : 1;  // with a run the scale is applied after M
+    kp.status = status_dev;
+    if (cudaMemsetAsync(kp.vexp, 0xC0, sizeof(int64_t), s) != cudaSuccess) return TT_ERR_CUDA;
+    if (launch_kron0(kp, 1, x->dtype, s) != cudaSuccess || launch_kron0(kp, 2, x->dtype, s) != cudaSuccess)
+      return TT_ERR_CUDA;
+    if (run) {
+      ScaledGemmParams g;
+      memset(&g, 0, sizeof(g));
+      g.a = w + mp.off_w0;
+      g.lda = static_cast<int64_t>(rx2) * ry2;
+      g.b = mbuf;
+      g.ldb = C;
+      g.out = z->cores[0];
+      g.ldo = C;
+      g.rows = I * J;
+      g.K = rx2 * ry2;
+      g.C = C;
+      g.nz = 1;
+      g.mexp = mexp;
+      g.es = trail ? 0 : 1;
+      g.emax = emax;
+      g.out_log2 = kp.wexp;
+      g.status = status_dev;
+      if (launch_scaled_gemm(g, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    }
+    return TT_OK;
+  }
+  ZRowsParams zp;
+  memset(&zp, 0, sizeof(zp));
+  zp.gx = x->cores[f];
+  zp.gy = y->cores[f];
+  zp.out = z->cores[t];
+  zp.rx = rx;
+  zp.ry = ry;
+  zp.I = I;
+  zp.J = J;
+  zp.rx2 = rx2;
+  zp.ry2 = ry2;
+  zp.C = C;
+  zp.status = status_dev;
+  if (run) {
+    // P[a][i][b'][col] = sum_a' Gx[a][i][a'] M[(a', b')][col]
+    ScaledGemmParams g;
+    memset(&g, 0, sizeof(g));
+    g.a = x->cores[f];
+    g.lda = rx2;
+    g.b = mbuf;
+    g.ldb = static_cast<int64_t>(ry2) * C;
+    g.bz = C;
+    g.out = w + mp.off_p[t];
+    g.ldo = static_cast<int64_t>(ry2) * C;
+    g.oz = C;
+    g.rows = rx * I;
+    g.K = rx2;
+    g.C = C;
+    g.nz = ry2;
+    g.mexp = mexp;
+    g.es = trail ? 0 : ry2;
+    g.ez = trail ? 0 : 1;
+    g.emax = emax;
+    g.oexp = emax + 1;
+    g.status = status_dev;
+    if (cudaMemsetAsync(g.oexp, 0xC0, sizeof(int64_t), s) != cudaSuccess) return TT_ERR_CUDA;
+    if (launch_scaled_gemm(g, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    zp.p = w + mp.off_p[t];
+    zp.e = emax;
+    zp.ep = emax + 1;
+  }
+  if (launch_zrows(zp, run, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+  return TT_OK;
+}
+
 static int contract_merged(const tt_desc* x, const tt_desc* y, const uint8_t* mask, const tt_desc* z,
                            int64_t* z_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream) {
   MergedPlan mp;
@@ -41,66 +206,39 @@ static int contract_merged(const tt_desc* x, const tt_desc* y, const uint8_t* ma
   if (ws_bytes < mp.ws_bytes || ws == nullptr) return TT_ERR_WS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
-  const int eb = elem_bytes(x->dtype);
   const int f0 = mp.free_pos[0];
-  // 1. left environment of the contracted modes before f_0 (E_L = [1] when none)
-  {
+  // 1. left environment of the contracted modes before f_0 (none when f_0 = 0)
+  if (f0 > 0) {
     SweepParams p;
     memset(&p, 0, sizeof(p));
-    if (f0 > 0) fill_left(p, x, y, 0, f0);
+    fill_left(p, x, y, 0, f0);
     p.rx0 = 1;
     p.ry0 = 1;
     p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
     p.e_out = w + mp.off_el;
-    p.e_out_log2 = reinterpret_cast<int64_t*>(w + mp.off_ellog2);
+    p.e_out_log2 = reinterpret_cast<int64_t*>(w + mp.off_slots);
     p.status = status_dev;
     rc = launch_sweep(p, x->dtype, s);
     if (rc != TT_OK) return rc;
   }
-  for (int t = 0; t < mp.m; ++t) {
-    const int f = mp.free_pos[t];
-    const bool run = mp.run_k1[t] > mp.run_k0[t];
-    void* dest = run ? static_cast<void*>(w + mp.off_pre) : z->cores[t];
-    KronParams kp;
-    memset(&kp, 0, sizeof(kp));
-    kp.gx = x->cores[f];
-    kp.gy = y->cores[f];
-    kp.rx = x->ranks[f];
-    kp.ry = y->ranks[f];
-    kp.I = x->modes[f];
-    kp.J = y->modes[f];
-    kp.rx2 = x->ranks[f + 1];
-    kp.ry2 = y->ranks[f + 1];
-    kp.out = dest;
-    kp.status = status_dev;
-    if (t == 0) {
-      kp.el = w + mp.off_el;
-      kp.el_log2 = reinterpret_cast<int64_t*>(w + mp.off_ellog2);
-      kp.tmp = w + mp.off_v;
-      if (launch_kron(kp, 1, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
-      if (launch_kron(kp, 2, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
-    } else {
-      if (launch_kron(kp, 0, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
-    }
-    if (run) {
-      SweepParams p;
-      memset(&p, 0, sizeof(p));
-      fill_left(p, x, y, mp.run_k0[t], mp.run_k1[t]);
-      p.rx0 = x->ranks[f + 1];
-      p.ry0 = y->ranks[f + 1];
-      p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
-      p.status = status_dev;
-      const int nxt = mp.run_k1[t];
-      const int64_t r_next = t + 1 < mp.m ? static_cast<int64_t>(x->ranks[nxt]) * y->ranks[nxt] : 1;
-      RowIO io;
-      io.in = dest;
-      io.in_stride_bytes = mp.pre_cols[t] * eb;
-      io.out = z->cores[t];
-      io.out_stride_bytes = r_next * eb;
-      io.n_rows = mp.rows[t];
-      if (launch_rows_sweep(p, io, x->dtype, mp.rmax, s) != cudaSuccess) return TT_ERR_CUDA;
-    }
+  // 2. the output cores: independent chains, core 0 on the caller's stream and
+  //    the others on the auxiliary streams
+  std::lock_guard<std::mutex> lock(g_fork_mu);
+  ForkStreams* fs = mp.m > 1 ? fork_streams() : nullptr;
+  if (mp.m > 1 && fs == nullptr) return TT_ERR_CUDA;
+  const int n_aux = fs != nullptr ? std::min(ForkStreams::kAux, mp.m - 1) : 0;
+  if (n_aux > 0) {
+    if (cudaEventRecord(fs->fork, s) != cudaSuccess) return TT_ERR_CUDA;
+    for (int i = 0; i < n_aux; ++i)
+      if (cudaStreamWaitEvent(fs->aux[i], fs->fork, 0) != cudaSuccess) return TT_ERR_CUDA;
   }
+  for (int t = 0; t < mp.m && rc == TT_OK; ++t)
+    rc = merged_core(x, y, z, mp, t, w, status_dev, t == 0 ? s : fs->aux[(t - 1) % n_aux]);
+  // join even after an error, so that no work is left unordered behind the caller's stream
+  for (int i = 0; i < n_aux; ++i)
+    if (cudaEventRecord(fs->done[i], fs->aux[i]) != cudaSuccess || cudaStreamWaitEvent(s, fs->done[i], 0) != cudaSuccess)
+      rc = rc == TT_OK ? TT_ERR_CUDA : rc;
+  if (rc != TT_OK) return rc;
   if (z_log2_dev != nullptr && cudaMemsetAsync(z_log2_dev, 0, sizeof(int64_t), s) != cudaSuccess) return TT_ERR_CUDA;
   return TT_OK;
 }

@@ -440,18 +440,22 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   return TT_OK;
 }
 
-// Plan of a merged-layout partial contraction (see merged.cu).
+// Plan of a merged-layout partial contraction (see merged.cu).  Every output
+// core has workspace of its own (its run's map M, M's row scales, P and four
+// scale slots), so that the cores can be built concurrently.
 struct MergedPlan {
   int m = 0;
   int free_pos[kMaxOrder];
-  int64_t pre_cols[kMaxOrder];   // R^x_{f+1} R^y_{f+1}: row length before the run
-  int64_t rows[kMaxOrder];       // r_t I J
-  int run_k0[kMaxOrder], run_k1[kMaxOrder];
+  int run_k1[kMaxOrder];  // the run after free position f is [f + 1, run_k1)
   int rmax = 1;
-  size_t off_el = 0, off_ellog2 = 0, off_v = 0, off_pre = 0, ws_bytes = 0;
+  size_t off_m[kMaxOrder], off_mexp[kMaxOrder], off_p[kMaxOrder];
+  size_t off_el = 0, off_v = 0, off_w0 = 0, off_slots = 0, ws_bytes = 0;
 };
 
-constexpr int64_t kMergedCoreCap = int64_t(1) << 30;  // elements per merged core
+// int64 scale slots: 0 = E_L, then per core t at 1 + 4 t: M, P, W_0, V
+constexpr int kMergedSlotsPerCore = 4;
+
+constexpr int64_t kMergedCoreCap = int64_t(1) << 30;  // elements per merged core (and per intermediate)
 
 inline int merged_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, MergedPlan* mp) {
   const int n = x->order;
@@ -464,33 +468,46 @@ inline int merged_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, 
   int rmax = 1;
   const int f0 = mp->free_pos[0];
   for (int k = 0; k <= f0; ++k) rmax = std::max({rmax, x->ranks[k], y->ranks[k]});
-  int64_t max_pre = 0;
-  int64_t r_t = 1;
+  int64_t mt[kMaxOrder], qt[kMaxOrder], pt[kMaxOrder], w0 = 0;
   for (int t = 0; t < m; ++t) {
     const int f = mp->free_pos[t];
     const int nxt = t + 1 < m ? mp->free_pos[t + 1] : n;
-    mp->run_k0[t] = f + 1;
     mp->run_k1[t] = nxt;
-    mp->pre_cols[t] = static_cast<int64_t>(x->ranks[f + 1]) * y->ranks[f + 1];
-    mp->rows[t] = r_t * x->modes[f] * y->modes[f];
-    const int64_t r_next = t + 1 < m ? static_cast<int64_t>(x->ranks[nxt]) * y->ranks[nxt] : 1;
-    if (mp->rows[t] * mp->pre_cols[t] > kMergedCoreCap || mp->rows[t] * r_next > kMergedCoreCap) return TT_ERR_TOO_LARGE;
-    if (nxt > f + 1) max_pre = std::max(max_pre, mp->rows[t] * mp->pre_cols[t]);
+    const int64_t rows = static_cast<int64_t>(t == 0 ? 1 : x->ranks[f] * y->ranks[f]) * x->modes[f] * y->modes[f];
+    const int64_t q = static_cast<int64_t>(x->ranks[f + 1]) * y->ranks[f + 1];  // rows of M
+    const int64_t C = static_cast<int64_t>(x->ranks[nxt]) * y->ranks[nxt];      // 1 at the end
+    if (rows * C > kMergedCoreCap) return TT_ERR_TOO_LARGE;
+    mt[t] = qt[t] = pt[t] = 0;
+    if (nxt > f + 1) {
+      const int64_t pe = static_cast<int64_t>(x->ranks[f]) * x->modes[f] * y->ranks[f + 1] * C;
+      if (q * C > kMergedCoreCap || pe > kMergedCoreCap) return TT_ERR_TOO_LARGE;
+      mt[t] = q * C;
+      qt[t] = q;
+      if (t > 0) pt[t] = pe;
+      if (t == 0) w0 = static_cast<int64_t>(x->modes[f]) * y->modes[f] * q;
+    }
     for (int k = f + 1; k <= nxt && k <= n; ++k) rmax = std::max({rmax, x->ranks[k], y->ranks[k]});
-    r_t = r_next;
   }
   mp->rmax = rmax;
   if (rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
   const int kx = x->ranks[f0], ky = y->ranks[f0];
   size_t off = 0;
+  mp->off_slots = off;
+  off += align256(static_cast<size_t>(1 + kMergedSlotsPerCore * m) * sizeof(int64_t));
   mp->off_el = off;
   off += align256(static_cast<size_t>(kx) * ky * eb);
-  mp->off_ellog2 = off;
-  off += 256;
   mp->off_v = off;
   off += align256(static_cast<size_t>(kx) * y->modes[f0] * y->ranks[f0 + 1] * eb);
-  mp->off_pre = off;
-  off += align256(static_cast<size_t>(max_pre) * eb);
+  mp->off_w0 = off;
+  off += align256(static_cast<size_t>(w0) * eb);
+  for (int t = 0; t < m; ++t) {
+    mp->off_m[t] = off;
+    off += align256(static_cast<size_t>(mt[t]) * eb);
+    mp->off_mexp[t] = off;
+    off += align256(static_cast<size_t>(qt[t]) * sizeof(int64_t));
+    mp->off_p[t] = off;
+    off += align256(static_cast<size_t>(pt[t]) * eb);
+  }
   mp->ws_bytes = off;
   return TT_OK;
 }

@@ -198,7 +198,12 @@ struct ChainAdjParams {
   int32_t* status;
 };
 
-// Kronecker expansion of one free core pair (merged layout, see merged.cu).
+// Left core of the merged layout with the left environment folded in (see
+// merged.cu): V = E_L Gy, whose largest binary exponent ev is folded into
+// *vexp (atomic max; the slot is filled with the byte 0xC0 first), then
+// W_0 = sum_a Gx[a] 2^-ev V[a], of scale 2^(*el_log2 + ev): applied with
+// saturation when scale_out is set, else written to *wexp.  el == NULL (with
+// el_log2 == NULL) stands for E_L = [1] (the first mode is free).
 struct KronParams {
   const void* gx;
   const void* gy;
@@ -207,16 +212,61 @@ struct KronParams {
   const void* el;           // left environment folded into the first core
   const int64_t* el_log2;
   void* tmp;                // V = E_L Gy
+  int64_t* vexp;
+  int64_t* wexp;
+  int scale_out;
   int32_t* status;
 };
 
-// Rows of a merged core swept through a contracted run.
-struct RowIO {
-  const void* in;
-  int64_t in_stride_bytes;
+// Transfer matrix of an interior contracted run (merged layout):
+//   M[(a, b)][(c, d)] = the run swept from the basis environment e_a e_b^T,
+// row (a, b) = a * R^y_in + b, column (c, d) = c * R^y_out + d; each row is
+// kept with its own power-of-two scale mexp[row] (kMergedZeroExp for a zero
+// row), and the largest of them is folded into *emax (atomic max; the slot is
+// filled with the byte 0xC0 first, i.e. kMergedNoExp).
+struct TransferParams {
+  int n_steps;
+  SweepStep step[kMaxOrder];
+  void* m;
+  int64_t* mexp;
+  int64_t* emax;
+  int32_t* status;
+};
+constexpr int64_t kMergedZeroExp = INT64_MIN / 4;
+constexpr int64_t kMergedNoExp = static_cast<int64_t>(0xC0C0C0C0C0C0C0C0ull);  // < kMergedZeroExp
+
+// out[r][z][c] = sum_k A[r][k] 2^(mexp[k es + z ez] - *emax) B[k][z][c]
+// (row strides lda, ldb, ldo; slice offsets bz, oz), scaled by
+// 2^(*out_log2 + *emax) with saturation when out_log2 is set; when oexp is
+// set, the largest binary exponent of the output is folded into *oexp
+// (atomic max; the slot is filled with the byte 0xC0 first).
+struct ScaledGemmParams {
+  const void* a;
+  const void* b;
   void* out;
-  int64_t out_stride_bytes;
-  int64_t n_rows;
+  int64_t lda, ldb, bz, ldo, oz;
+  int rows, K, C, nz;
+  const int64_t* mexp;
+  int64_t es, ez;
+  const int64_t* emax;
+  const int64_t* out_log2;
+  int64_t* oexp;
+  int32_t* status;
+};
+
+// Rows of a merged core W_t[(a, b)][i][j][col] (row ((a ry + b) I + i) J + j):
+//   kron: col = c ry2 + d, W = Gx[a][i][c] Gy[b][j][d];
+//   prod: W = 2^(*e + *ep) sum_b' Gy[b][j][b'] 2^(-*ep) P[a I + i][b'][col]
+//         (b' < ry2; *ep is the largest binary exponent of P).
+struct ZRowsParams {
+  const void* gx;
+  const void* gy;
+  const void* p;
+  const int64_t* e;
+  const int64_t* ep;
+  void* out;
+  int rx, ry, I, J, rx2, ry2, C;
+  int32_t* status;
 };
 
 // One interior mode of the tensor-core full contraction (see tc_sweep.cu).
@@ -246,8 +296,10 @@ cudaError_t tc_mode(const TcModeParams& p, int cluster, cudaStream_t s);
 int tc_cluster_size(bool x3, int want);
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_kron(const KronParams& p, int which, int dtype, cudaStream_t s);
-cudaError_t launch_rows_sweep(const SweepParams& p, const RowIO& io, int dtype, int rmax, cudaStream_t s);
+cudaError_t launch_kron0(const KronParams& p, int which, int dtype, cudaStream_t s);
+cudaError_t launch_transfer(const TransferParams& p, int dtype, cudaStream_t s);
+cudaError_t launch_scaled_gemm(const ScaledGemmParams& p, int dtype, cudaStream_t s);
+cudaError_t launch_zrows(const ZRowsParams& p, bool prod, int dtype, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStream_t s);
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);

@@ -70,3 +70,99 @@ def test_merged_secondary_fp32():
     for g, w in zip(got, want):
         w = w.reshape(g.shape)
         assert np.abs(g - w).max() <= 1e-5 * max(np.abs(w).max(), 1e-30) * 10
+
+
+def _rel_err(got, want):
+    return max(np.abs(g - w.reshape(g.shape)).max() / max(np.abs(w).max(), 1e-300) for g, w in zip(got, want))
+
+
+@pytest.mark.parametrize("mask", [[int(b) for b in format(v, "06b")] for v in range(64) if bin(v).count("1") == 3])
+def test_merged_all_three_of_six_fp32(mask):
+    """Every contracted set of three of six modes (modes 8, ranks 16, float32):
+    Kronecker cores, interior runs through the transfer matrix, trailing runs
+    through the right environment, the left environment folded into core 0."""
+    x, y = G.pair(13, [8] * 6, G.tt_ranks(6, 16), G.tt_ranks(6, 16), np.float32)
+    op, got = _run(x, y, mask)
+    assert int(op.status.item()) == 0
+    want, perm = O.partial_merged(x, y, mask)
+    assert op.perm == perm
+    assert _rel_err(got, want) <= 2e-5
+
+
+@pytest.mark.parametrize("mask", [[0, 1, 1, 1, 0, 1, 0], [0, 0, 1, 1, 1, 1, 0], [1, 0, 1, 1, 0, 1, 1], [0, 1, 1, 1, 1, 1, 1]])
+def test_merged_long_runs_fp64(mask):
+    """Interior runs of up to four modes, ragged ranks (columns not a multiple
+    of the vector width), float64."""
+    rng = np.random.default_rng(31 + sum(m << k for k, m in enumerate(mask)))
+    modes = [3, 2, 3, 2, 3, 2, 3]
+    x = G.random_tt(rng, modes, [1, 3, 5, 2, 6, 3, 5, 1], np.float64)
+    y = G.random_tt(rng, modes, [1, 2, 3, 7, 2, 5, 3, 1], np.float64)
+    op, got = _run(x, y, mask)
+    assert int(op.status.item()) == 0
+    want, perm = O.partial_merged(x, y, mask)
+    dense = O.merged_to_dense([g.reshape(w.shape) for g, w in zip(got, want)], perm)
+    ref = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [k for k in range(7) if mask[k]])
+    assert np.abs(dense - ref).max() <= 1e-12 * norm_scale(x, y)
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float32, 2e-5), (np.float64, 1e-12)])
+def test_merged_rank24_interior_run(dtype, tol):
+    """Ranks 24 (the transfer matrix has 576 rows of 576), a two-mode interior
+    run after an interior free core, and a free core after it."""
+    rng = np.random.default_rng(77)
+    modes = [3, 3, 3, 3, 3]
+    x = G.random_tt(rng, modes, [1, 24, 24, 24, 24, 1], dtype)
+    y = G.random_tt(rng, modes, [1, 24, 24, 24, 24, 1], dtype)
+    mask = [1, 0, 1, 1, 0]
+    op, got = _run(x, y, mask)
+    assert int(op.status.item()) == 0
+    want, _ = O.partial_merged(x, y, mask)
+    assert _rel_err(got, want) <= tol
+
+
+@pytest.mark.parametrize("mask", [[1, 0, 1, 1, 1, 1, 0], [0, 0, 1, 1, 1, 1, 0]])
+def test_merged_run_scales_beyond_float32(mask):
+    """An interior run whose transfer matrix is of order 2^240 (past the float32
+    range) between free cores of order 2^-100 each: the power-of-two scales of
+    the transfer matrix and of P carry the result (of order 2^36), where
+    Gy P taken at the scale of the inputs would underflow.  The first set puts
+    the small cores in the left core (E_L folded in), the second in an
+    interior one (P, then the rows)."""
+    rng = np.random.default_rng(5)
+    modes = [4] * 7
+    r = [1, 6, 6, 6, 6, 6, 6, 1]
+    x = G.random_tt(rng, modes, r, np.float64)
+    y = G.random_tt(rng, modes, r, np.float64)
+    for k in (2, 3, 4, 5):
+        x[k] = x[k] * 2.0**30
+        y[k] = y[k] * 2.0**30
+    x[1] = x[1] * 2.0**-100
+    y[1] = y[1] * 2.0**-100
+    x32 = [c.astype(np.float32) for c in x]
+    y32 = [c.astype(np.float32) for c in y]
+    op, got = _run(x32, y32, mask)
+    assert int(op.status.item()) == 0
+    want, _ = O.partial_merged([c.astype(np.float64) for c in x32], [c.astype(np.float64) for c in y32], mask)
+    assert all(np.isfinite(g).all() for g in got)
+    assert _rel_err(got, want) <= 2e-5
+
+
+def test_merged_zero_rows_of_transfer():
+    """Rows of the transfer matrix that vanish (a zero row of the first run
+    core) and a run core that vanishes outright."""
+    rng = np.random.default_rng(9)
+    modes = [3] * 6
+    r = [1, 4, 4, 4, 4, 4, 1]
+    x = G.random_tt(rng, modes, r, np.float64)
+    y = G.random_tt(rng, modes, r, np.float64)
+    x[2][1] = 0.0
+    y[2][3] = 0.0
+    op, got = _run(x, y, [0, 0, 1, 1, 0, 0])
+    assert int(op.status.item()) == 0
+    want, _ = O.partial_merged(x, y, [0, 0, 1, 1, 0, 0])
+    assert _rel_err(got, want) <= 1e-12
+    x[3] = np.zeros_like(x[3])
+    op, got = _run(x, y, [0, 0, 1, 1, 0, 0])
+    assert int(op.status.item()) == 0
+    want, _ = O.partial_merged(x, y, [0, 0, 1, 1, 0, 0])
+    assert all(np.abs(g - w.reshape(g.shape)).max() == 0.0 for g, w in zip(got, want))
