@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kMT) kron0_v_kernel(const __grid_constant__ Kr
     if (el == nullptr)  // no contracted mode before the first free one: E_L = [1]
       s = gy[static_cast<int64_t>(j) * p.ry2 + b2];
     else
+#pragma unroll 4
       for (int b = 0; b < p.ry; ++b) s = fma(el[a * p.ry + b], gy[(static_cast<int64_t>(b) * p.J + j) * p.ry2 + b2], s);
     v[e] = s;
     if (isfinite(s) && s != T(0)) vmax = max(vmax, exp2_bits(s));
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kMT) kron0_w_kernel(const __grid_constant__ Kr
     const int j = static_cast<int>(r % p.J), i = static_cast<int>(r / p.J);
     const int a2 = static_cast<int>(c / p.ry2), b2 = static_cast<int>(c % p.ry2);
     T s = T(0);
+#pragma unroll 4
     for (int a = 0; a < p.rx; ++a)
       s = fma(gx[(static_cast<int64_t>(a) * p.I + i) * p.rx2 + a2], vsc(v[(static_cast<int64_t>(a) * p.J + j) * p.ry2 + b2]), s);
     if (p.scale_out) {
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kMT) transfer_kernel(const __grid_constant__ T
       for (int k = tid; k < n; k += kMT) {
         const int c = udiv16(k, s0.rout_y), d = k - c * s0.rout_y;
         T acc = T(0);
+#pragma unroll 8
         for (int i = 0; i < s0.I; ++i) acc = fma(gx[i * s0.rout_x + c], gy[i * s0.rout_y + d], acc);
         e[k] = acc;
       }
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(kMT) transfer_kernel(const __grid_constant__ T
           const T* gcol = gy + static_cast<int64_t>(i0) * ry2 + rem;
           const int64_t gs = static_cast<int64_t>(I) * ry2;
           T acc = T(0);
+#pragma unroll 8
           for (int d = 0; d < ry; ++d) acc = fma(er[d], gcol[d * gs], acc);
           tb[k] = acc;
         }
@@ -368,14 +372,7 @@ __global__ void __launch_bounds__(kMT) zrows_kernel(const __grid_constant__ ZRow
           cp_async_elem(ps + bp * ct + c, P + static_cast<int64_t>(bp) * C + c);
       }
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const Pow2Sat<T> psc(-ep);
-    for (int e = tid; e < ry2 * ct; e += kMT) {
-      const int c = e - (e / ct) * ct;
-      ps[e] = c < ncol ? psc(ps[e]) : T(0);
-    }
+    cp_async_commit();  // completes with the first chunk's Gy rows
   }
   T gxv = T(0);
   int d0 = 0;
@@ -388,12 +385,24 @@ __global__ void __launch_bounds__(kMT) zrows_kernel(const __grid_constant__ ZRow
   const int64_t IJ = static_cast<int64_t>(p.I) * p.J;
   T* const out = static_cast<T*>(p.out) + (static_cast<int64_t>(a) * p.ry * IJ + static_cast<int64_t>(i) * p.J) * C + col;
   int bits = 0;
+  bool first = true;
   for (int yb = blockIdx.y; static_cast<int64_t>(yb) * rb < nrho; yb += gridDim.y) {
     const int rho0 = yb * rb, nr = min(rb, nrho - rho0);
     __syncthreads();  // the previous chunk's rows are consumed
     const T* gy = static_cast<const T*>(p.gy) + static_cast<int64_t>(rho0) * ry2;
-    for (int e = tid; e < nr * ry2; e += kMT) gys[e] = gy[e];
+    for (int e = tid; e < nr * ry2; e += kMT) cp_async_elem(gys + e, gy + e);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
+    if (PROD && first) {  // P's tile to scale 2^-ep, in place
+      const Pow2Sat<T> psc(-ep);
+      for (int e = tid; e < ry2 * ct; e += kMT) {
+        const int c = e - (e / ct) * ct;
+        ps[e] = c < ncol ? psc(ps[e]) : T(0);
+      }
+      __syncthreads();
+    }
+    first = false;
     if (!active) continue;
     for (int rl = lane; rl < nr; rl += NL * kZRR) {
       Pack<T, VW> res[kZRR];
