@@ -161,7 +161,21 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
  * copied for it.
  *   z_log2_dev  optional device int64: if non-NULL the power-of-two scale of
  *               the environment is stored there and left out of C (Z = Z_stored
- *               * 2^e); if NULL it is folded into C.
+ *               * 2^e); if NULL it is folded into C.  The merged layout always
+ *               folds its scales into the cores and stores e = 0.
+ * Merged layout: the contracted run after a free core acts on that core's
+ * right rank leg; an interior run as its transfer matrix (the run swept from
+ * every basis environment, R^x R^y sweeps, each with its own power-of-two
+ * scale; a row more than 2^250 (F32) / 2^2000 (F64) below the largest
+ * contributes zero), a trailing run as its right environment.  The m output
+ * cores are built concurrently: the call forks from `stream` onto up to three
+ * library-owned streams of the current device (created on first use, never
+ * destroyed) and joins back into `stream` with events, so the result is
+ * ordered on `stream` like any other call (and a captured stream captures the
+ * whole fork and join).  Calls are serialised by a host mutex while they
+ * enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
+ * the intermediate P (R^x I R^y' x the next pair rank) exceeds 2^30 entries,
+ * or a rank exceeds 128 (F32) / 64 (F64).
  * Precision: TT_P_NATIVE (F64/F32). */
 int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
                         int prec, const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev,

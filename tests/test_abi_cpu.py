@@ -131,3 +131,32 @@ def test_k_entry_points_reject_missing_buffers(L):
     assert rc == -6  # TT_ERR_WS
     rc = L.tt_contract_backward_k(x.ref, y.ref, None, 0, z.ref, x.ref, y.ref, None, None, 0, None)
     assert rc == -1  # TT_ERR_ARG
+
+
+def _merged_ws(L, x, y, mask):
+    nb = ctypes.c_size_t(0)
+    rc = L.tt_workspace_bytes(B.TT_OP_PARTIAL, x.ref, y.ref, _mask(mask), B.LAYOUT["merged"], B.PREC["native"],
+                              ctypes.byref(nb))
+    return rc, nb.value
+
+
+def test_merged_workspace_and_caps(L):
+    # order 3, S = {1}: the first core has an interior run after it.  Slots
+    # (1 + 4 per core), E_L, V, W_0 (I J R^x'R^y' = 24), then for core 0 its
+    # transfer matrix (6 x 6) and 6 row scales; core 1 needs nothing: six
+    # 256-byte blocks.
+    x = FakeDesc([2, 2, 2], [1, 2, 3, 1])
+    y = FakeDesc([2, 2, 2], [1, 3, 2, 1])
+    assert _merged_ws(L, x, y, [0, 1, 0]) == (0, 6 * 256)
+    # no contracted run after any free core: slots, E_L, V only
+    assert _merged_ws(L, x, y, [1, 0, 0]) == (0, 3 * 256)
+    # an interior run after a later core needs P (R^x I R^y' x the next pair rank)
+    x4 = FakeDesc([8] * 6, [1] + [16] * 5 + [1])
+    rc, nb = _merged_ws(L, x4, x4, [0, 0, 1, 0, 0, 0])
+    assert rc == 0 and nb >= 4 * (16 * 8 * 16 * 256 + 256 * 256) + 8 * 256
+    # caps: a merged core over 2^30 entries; a rank above the float64 cap
+    big = FakeDesc([3, 3, 3, 3], [1, 128, 128, 128, 1])  # core 1: 128^2 * 9 rows x 128^2 > 2^30
+    assert _merged_ws(L, big, big, [0, 1, 0, 0])[0] == -5
+    assert _merged_ws(L, big, big, [1, 1, 0, 1])[0] == 0
+    d65 = FakeDesc([2, 2, 2], [1, 65, 65, 1], dtype=B.TT_F64)
+    assert _merged_ws(L, d65, d65, [0, 1, 0])[0] == -5
