@@ -172,8 +172,9 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
  * library-owned streams of the current device (created on first use, never
  * destroyed) and joins back into `stream` with events, so the result is
  * ordered on `stream` like any other call (and a captured stream captures the
- * whole fork and join).  Calls are serialised by a host mutex while they
- * enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
+ * whole fork and join; until that capture ends the auxiliary streams belong
+ * to it, so no other merged-layout call on the device may run meanwhile).
+ * Calls are serialised by a host mutex while they enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
  * the intermediate P (R^x I R^y' x the next pair rank) exceeds 2^30 entries,
  * or a rank exceeds 128 (F32) / 64 (F64).
  * Precision: TT_P_NATIVE (F64/F32). */
