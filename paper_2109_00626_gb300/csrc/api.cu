@@ -99,7 +99,21 @@ static int merged_core(const tt_desc* x, const tt_desc* y, const tt_desc* z, con
     mexp = tp.mexp;
   }
   if (t == 0) {
-    // the left core, E_L folded in (E_L from the caller's stream, before the fork)
+    // the left core with E_L, the left environment of the contracted modes
+    // before f_0 (none when f_0 = 0), folded in
+    if (f0 > 0) {
+      SweepParams p;
+      memset(&p, 0, sizeof(p));
+      fill_left(p, x, y, 0, f0);
+      p.rx0 = 1;
+      p.ry0 = 1;
+      p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+      p.e_out = w + mp.off_el;
+      p.e_out_log2 = slots;
+      p.status = status_dev;
+      const int rc = launch_sweep(p, x->dtype, s);
+      if (rc != TT_OK) return rc;
+    }
     KronParams kp;
     memset(&kp, 0, sizeof(kp));
     kp.gx = x->cores[f];
@@ -206,23 +220,8 @@ static int contract_merged(const tt_desc* x, const tt_desc* y, const uint8_t* ma
   if (ws_bytes < mp.ws_bytes || ws == nullptr) return TT_ERR_WS;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
-  const int f0 = mp.free_pos[0];
-  // 1. left environment of the contracted modes before f_0 (none when f_0 = 0)
-  if (f0 > 0) {
-    SweepParams p;
-    memset(&p, 0, sizeof(p));
-    fill_left(p, x, y, 0, f0);
-    p.rx0 = 1;
-    p.ry0 = 1;
-    p.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
-    p.e_out = w + mp.off_el;
-    p.e_out_log2 = reinterpret_cast<int64_t*>(w + mp.off_slots);
-    p.status = status_dev;
-    rc = launch_sweep(p, x->dtype, s);
-    if (rc != TT_OK) return rc;
-  }
-  // 2. the output cores: independent chains, core 0 on the caller's stream and
-  //    the others on the auxiliary streams
+  // the output cores: independent chains, core 0 on the caller's stream and
+  // the others on the auxiliary streams
   std::lock_guard<std::mutex> lock(g_fork_mu);
   ForkStreams* fs = mp.m > 1 ? fork_streams() : nullptr;
   if (mp.m > 1 && fs == nullptr) return TT_ERR_CUDA;
