@@ -166,3 +166,21 @@ def test_merged_zero_rows_of_transfer():
     assert int(op.status.item()) == 0
     want, _ = O.partial_merged(x, y, [0, 0, 1, 1, 0, 0])
     assert all(np.abs(g - w.reshape(g.shape)).max() == 0.0 for g, w in zip(got, want))
+
+
+@pytest.mark.parametrize("mask", [[0, 1, 0, 1, 0], [1, 0, 1, 0, 1], [0, 1, 1, 0, 0], [0, 0, 1, 1, 0], [1, 1, 0, 0, 0]])
+def test_merged_unequal_free_modes_fp64(mask):
+    """Free modes of X and Y of different sizes (I != J on the free positions;
+    equal on S), float64, against the dense Eq. 8."""
+    rng = np.random.default_rng(8 + sum(m << k for k, m in enumerate(mask)))
+    mx = [3, 2, 4, 2, 3]
+    my = [m if mask[k] else m + 2 for k, m in enumerate(mx)]
+    x = G.random_tt(rng, mx, [1, 2, 5, 3, 2, 1], np.float64)
+    y = G.random_tt(rng, my, [1, 3, 1, 4, 2, 1], np.float64)
+    op, got = _run(x, y, mask)
+    assert int(op.status.item()) == 0
+    want, perm = O.partial_merged(x, y, mask)
+    assert [g.shape for g in got] == [(w.shape[0], w.shape[1] * w.shape[2], w.shape[3]) for w in want]
+    dense = O.merged_to_dense([g.reshape(w.shape) for g, w in zip(got, want)], perm)
+    ref = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [k for k in range(5) if mask[k]])
+    assert np.abs(dense - ref).max() <= 1e-12 * norm_scale(x, y)
