@@ -160,3 +160,26 @@ def test_merged_workspace_and_caps(L):
     assert _merged_ws(L, big, big, [1, 1, 0, 1])[0] == 0
     d65 = FakeDesc([2, 2, 2], [1, 65, 65, 1], dtype=B.TT_F64)
     assert _merged_ws(L, d65, d65, [0, 1, 0])[0] == -5
+
+
+def test_merged_rejects_before_enqueue(L):
+    """The merged layout checks its output cores and workspace before it touches
+    a stream: wrong core count, wrong core shape or dtype, short workspace."""
+    x = FakeDesc([3, 2, 4, 2], [1, 2, 5, 3, 1])
+    y = FakeDesc([3, 2, 4, 2], [1, 3, 1, 4, 1])
+    mask = [0, 1, 0, 1]
+    modes, ranks, _ = B.partial_shape(x, y, mask, "merged")
+    rc, nb = _merged_ws(L, x, y, mask)
+    assert rc == 0 and nb > 0
+    ws = ctypes.c_void_p(0x100000)
+    z = FakeDesc(modes, ranks)
+    assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z.ref, None, None, ws, nb - 1, None) == -6
+    assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z.ref, None, None, None, nb, None) == -6
+    z_short = FakeDesc(modes[:1], ranks[:1] + [1])
+    assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z_short.ref, None, None, ws, nb, None) == -2
+    bad = list(ranks)
+    bad[1] += 1
+    z_bad = FakeDesc(modes, bad)
+    assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z_bad.ref, None, None, ws, nb, None) == -2
+    z64 = FakeDesc(modes, ranks, dtype=B.TT_F64)
+    assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z64.ref, None, None, ws, nb, None) == -2
