@@ -1,4 +1,5 @@
-// Partial contraction over any contracted set, merged (TT-matrix) layout.
+// Partial contraction over any contracted set (Eq. 8 over every mode pair in
+// S), merged (TT-matrix) layout.
 //
 // With free positions f_0 < ... < f_{m-1}, output core t is built from the
 // Kronecker pair
@@ -22,7 +23,9 @@
 //    are both kept renormalised (their scales are powers of two applied once,
 //    with saturation, to the finished entries), so a run far outside the
 //    float range between free cores far inside it still gives finite cores.
-// Writing the merged cores dominates: zrows_kernel is bound by HBM writes.
+// zrows_kernel, which writes the merged cores, is bound by HBM writes; at small
+// ranks the short dependent launches before it set the time, and the host
+// builds the output cores, which are independent, on forked streams.
 #include <limits.h>
 
 #include <algorithm>
@@ -72,11 +75,12 @@ __global__ void __launch_bounds__(kMT) kron0_v_kernel(const __grid_constant__ Kr
     const int64_t r = e / p.ry2;
     const int j = static_cast<int>(r % p.J), a = static_cast<int>(r / p.J);
     T s = T(0);
-    if (el == nullptr)  // no contracted mode before the first free one: E_L = [1]
+    if (el == nullptr) {  // no contracted mode before the first free one: E_L = [1]
       s = gy[static_cast<int64_t>(j) * p.ry2 + b2];
-    else
+    } else {
 #pragma unroll 4
       for (int b = 0; b < p.ry; ++b) s = fma(el[a * p.ry + b], gy[(static_cast<int64_t>(b) * p.J + j) * p.ry2 + b2], s);
+    }
     v[e] = s;
     if (isfinite(s) && s != T(0)) vmax = max(vmax, exp2_bits(s));
   }
