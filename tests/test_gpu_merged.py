@@ -184,3 +184,20 @@ def test_merged_unequal_free_modes_fp64(mask):
     dense = O.merged_to_dense([g.reshape(w.shape) for g, w in zip(got, want)], perm)
     ref = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [k for k in range(5) if mask[k]])
     assert np.abs(dense - ref).max() <= 1e-12 * norm_scale(x, y)
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float32, 2e-5), (np.float64, 1e-12)])
+def test_merged_transfer_slice_chunks(dtype, tol):
+    """A run mode of ranks 64 -> 64 with 16 slices: the transfer kernel's slice
+    products do not fit shared memory at once and go in chunks (8 slices in
+    float32, 4 in float64)."""
+    rng = np.random.default_rng(64)
+    modes = [3, 3, 16, 3, 3, 3]
+    r = [1, 2, 64, 64, 2, 2, 1]
+    x = G.random_tt(rng, modes, r, dtype)
+    y = G.random_tt(rng, modes, r, dtype)
+    mask = [0, 1, 1, 1, 0, 0]
+    op, got = _run(x, y, mask)
+    assert int(op.status.item()) == 0
+    want, _ = O.partial_merged(x, y, mask)
+    assert _rel_err(got, want) <= tol
