@@ -169,8 +169,10 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
  * scale; a row more than 2^250 (F32) / 2^2000 (F64) below the largest
  * contributes zero), a trailing run as its right environment.  The m output
  * cores are built concurrently: the call forks from `stream` onto up to three
- * library-owned streams of the current device (created on first use, never
- * destroyed) and joins back into `stream` with events, so the result is
+ * library-owned streams of the current device (created, with four events, by
+ * the first merged-layout call on the device, which should therefore be made
+ * outside any stream capture; never destroyed) and joins back into `stream`
+ * with events, so the result is
  * ordered on `stream` like any other call (and a captured stream captures the
  * whole fork and join; until that capture ends the auxiliary streams belong
  * to it, so no other merged-layout call on the device may run meanwhile).
