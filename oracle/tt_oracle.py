@@ -34,6 +34,9 @@ absorb_left            one contracted mode folded into the left environment
                        (Example 1's K = A_x^T A_y generalised, Algorithm 2 step 4)
 absorb_right           the mirror image, right environment
 contract_full          all modes contracted -> scalar (Fig. 1b's full contraction)
+two_sum / two_product / dot2_dd / absorb_left_dd / contract_full_dd
+                       the same sweep with compensated (double-double)
+                       accumulation, for reference values under cancellation
 partial_chain          end-block S -> chain TT (Algorithm 2 steps 4-6)
 partial_merged         any S -> TT-matrix of merged cores
 chain_to_dense / merged_to_dense   dense reconstruction + un-permutation
@@ -61,6 +64,11 @@ __all__ = [
     "left_envs",
     "right_envs",
     "contract_full",
+    "two_sum",
+    "two_product",
+    "dot2_dd",
+    "absorb_left_dd",
+    "contract_full_dd",
     "end_block",
     "partial_chain",
     "partial_merged",
@@ -182,6 +190,90 @@ def contract_full(xc, yc):
     """<X, Y>: every position contracted (Fig. 1b's all-mode contraction to a scalar)."""
     assert len(xc) == len(yc)
     return float(left_envs(xc, yc)[-1][0, 0])
+
+
+# --------------------------------------------------------------------------
+# Compensated accumulation for reference values (Ogita, Rump and Oishi,
+# "Accurate Sum and Dot Product", SIAM J. Sci. Comput. 26(6), 2005): the
+# error-free transformations of a sum (Knuth's TwoSum) and of a product
+# (Dekker's TwoProduct with Veltkamp's splitting), and their Dot2, a dot
+# product as accurate as one computed in twice the working precision.  The
+# arithmetic is elementwise numpy float64, which rounds every operation to
+# nearest and never fuses a multiply with an add (the transformations rely on
+# both).  The sweep below carries each environment as an unevaluated pair
+# hi + lo, so that no intermediate rounding is left uncompensated.
+# --------------------------------------------------------------------------
+_VELTKAMP = 134217729.0  # 2^27 + 1
+
+
+def two_sum(a, b):
+    """(s, e) with s = fl(a + b) and s + e = a + b exactly (Knuth)."""
+    s = a + b
+    z = s - a
+    e = (a - (s - z)) + (b - z)
+    return s, e
+
+
+def _split(a):
+    """(hi, lo) with a = hi + lo exactly, each of at most 26 significant bits (Veltkamp)."""
+    c = _VELTKAMP * a
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def two_product(a, b):
+    """(p, e) with p = fl(a * b) and p + e = a * b exactly (Dekker)."""
+    p = a * b
+    a1, a2 = _split(a)
+    b1, b2 = _split(b)
+    e = a2 * b2 - (((p - a1 * b1) - a2 * b1) - a1 * b2)
+    return p, e
+
+
+def dot2_dd(x, y):
+    """Dot2 over the last axis (vectorised over the leading ones), returned
+    unrounded as a pair (hi, lo): the running sum p is kept with the exact
+    errors of every product and every addition, those errors are summed in a
+    second accumulator s, and hi + lo = p + s exactly.  The error of hi + lo
+    against the exact dot product is at most gamma_n^2 sum |x_k y_k| (plus the
+    rounding of s), gamma_n = n u / (1 - n u)."""
+    x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+    p, s = two_product(x[..., 0], y[..., 0])
+    for k in range(1, x.shape[-1]):
+        h, r = two_product(x[..., k], y[..., k])
+        p, q = two_sum(p, h)
+        s = s + (q + r)
+    return two_sum(p, s)
+
+
+def absorb_left_dd(ehi, elo, gx, gy):
+    """absorb_left on an environment held as E = ehi + elo, in two Dot2 stages
+    that keep their results as pairs:
+        T[a][i][b'] = sum_b E[a,b] Gy[b,i,b']         (2 R^y terms: hi and lo)
+        E'[a',b']   = sum_{a,i} Gx[a,i,a'] T[a,i,b']  (2 R^x I terms)
+    Returns (E'hi, E'lo)."""
+    gx = np.asarray(gx, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    assert gx.shape[1] == gy.shape[1]
+    rx, i_dim, rx2 = gx.shape
+    ry2 = gy.shape[2]
+    e2 = np.concatenate([ehi, elo], axis=1)                      # [a][b | b]
+    gyy = np.concatenate([gy, gy], axis=0).transpose(1, 2, 0)    # [i][b'][b | b]
+    thi, tlo = dot2_dd(e2[:, None, None, :], gyy[None, :, :, :])  # [a][i][b']
+    t2 = np.concatenate([thi.reshape(rx * i_dim, ry2), tlo.reshape(rx * i_dim, ry2)], axis=0)  # [(a,i) | (a,i)][b']
+    gxx = np.concatenate([gx.reshape(rx * i_dim, rx2)] * 2, axis=0)                           # [(a,i) | (a,i)][a']
+    return dot2_dd(gxx.T[:, None, :], t2.T[None, :, :])           # [a'][b']
+
+
+def contract_full_dd(xc, yc):
+    """<X, Y> by the left-to-right sweep with double-double environments
+    (absorb_left_dd); returns the float64 nearest to the final pair."""
+    assert len(xc) == len(yc)
+    xc, yc = _f64(xc), _f64(yc)
+    ehi, elo = np.ones((1, 1)), np.zeros((1, 1))
+    for gx, gy in zip(xc, yc):
+        ehi, elo = absorb_left_dd(ehi, elo, gx, gy)
+    return float(ehi[0, 0] + elo[0, 0])
 
 
 # --------------------------------------------------------------------------

@@ -101,3 +101,49 @@ def test_grad_pin_catches_shifted_env(monkeypatch):
     gx, _ = T.grad_full(x, y)
     # Euler's identity <G_k, dz/dG_k> = z fails for at least one core
     assert max(abs(np.sum(g * c) - z) for g, c in zip(gx, x)) > 1e-6
+
+
+# ---- compensated accumulation ----
+
+def _dot2_no_error_sum(x, y):
+    x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+    p = x[..., 0] * y[..., 0]
+    for k in range(1, x.shape[-1]):
+        p = p + x[..., k] * y[..., k]
+    return p, np.zeros_like(p)
+
+
+def _absorb_dd_drop_lo(ehi, elo, gx, gy):
+    return _ORIG_ABSORB_DD(ehi, np.zeros_like(elo), gx, gy)
+
+
+def _two_product_no_error(a, b):
+    return a * b, np.zeros_like(a * b)
+
+
+_ORIG_ABSORB_DD = T.absorb_left_dd
+
+
+def _cancelling_pair():
+    rng = np.random.default_rng(21)
+    x = G.random_tt(rng, [3, 2, 3], [1, 2, 3, 1], np.float64)
+    w = [c.copy() for c in x]
+    w[0] = w[0] * -(1 + 2.0**-30)
+    # Y = X + X'' as a TT sum: first cores side by side, interior block-diagonal, last stacked
+    y = [np.concatenate([x[0], w[0]], axis=2)]
+    g = np.zeros((4, 2, 6))
+    g[:2, :, :3] = x[1]
+    g[2:, :, 3:] = w[1]
+    y.append(g)
+    y.append(np.concatenate([x[2], w[2]], axis=0))
+    return x, y
+
+
+@pytest.mark.parametrize("name,mutant", [("dot2_dd", _dot2_no_error_sum), ("absorb_left_dd", _absorb_dd_drop_lo),
+                                         ("two_product", _two_product_no_error)])
+def test_cancellation_pin_catches_compensation_mutants(name, mutant, monkeypatch):
+    x, y = _cancelling_pair()
+    # reference from the unmutated compensated sweep; its own pin (exact rationals) is in test_oracle_pins
+    ref = O.contract_full_dd(x, y)
+    monkeypatch.setattr(T, name, mutant)
+    assert abs(T.contract_full_dd(x, y) - ref) > 1e3 * 2.0**-53 * abs(ref)

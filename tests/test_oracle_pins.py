@@ -8,6 +8,7 @@ dropped term, a transposed operand, a wrong leg order) fails at least one of
 them; ``test_oracle_mutants.py`` plants such slips and checks that.
 """
 import itertools
+from fractions import Fraction
 import json
 import math
 import os
@@ -386,3 +387,97 @@ def test_generator_norm_expectation():
         x = G.random_tt(np.random.default_rng(s), [4, 4, 4], [1, 3, 3, 1])
         vals.append(O.contract_full(x, x))
     assert abs(np.mean(vals) - 1.0) < 0.1
+
+
+# ---- compensated accumulation (reference values under cancellation) ----
+
+U64 = 2.0**-53
+
+
+def _fr(v):
+    return Fraction(float(v))
+
+
+def _exact_full(x, y):
+    """<X, Y> in exact rational arithmetic from the TT entries (Eq. 9)."""
+    shape = tuple(g.shape[1] for g in x)
+    total = Fraction(0)
+    for idx in itertools.product(*[range(s) for s in shape]):
+        vx = [[Fraction(1)]]
+        vy = [[Fraction(1)]]
+        for gx, gy, i in zip(x, y, idx):
+            sx = [[_fr(gx[a, i, b]) for b in range(gx.shape[2])] for a in range(gx.shape[0])]
+            sy = [[_fr(gy[a, i, b]) for b in range(gy.shape[2])] for a in range(gy.shape[0])]
+            vx = [[sum(vx[0][a] * sx[a][b] for a in range(len(sx))) for b in range(len(sx[0]))]]
+            vy = [[sum(vy[0][a] * sy[a][b] for a in range(len(sy))) for b in range(len(sy[0]))]]
+        total += vx[0][0] * vy[0][0]
+    return total
+
+
+def _tt_sum(a, b):
+    """The TT of the entrywise sum A + B (ranks added: first cores side by side,
+    interior cores block-diagonal, last cores stacked)."""
+    n = len(a)
+    out = []
+    for k, (ga, gb) in enumerate(zip(a, b)):
+        ra0, i_dim, ra1 = ga.shape
+        rb0, _, rb1 = gb.shape
+        r0 = 1 if k == 0 else ra0 + rb0
+        r1 = 1 if k == n - 1 else ra1 + rb1
+        g = np.zeros((r0, i_dim, r1))
+        oa0, ob0 = 0, (0 if k == 0 else ra0)
+        oa1, ob1 = 0, (0 if k == n - 1 else ra1)
+        g[oa0:oa0 + ra0, :, oa1:oa1 + ra1] = ga
+        g[ob0:ob0 + rb0, :, ob1:ob1 + rb1] = gb
+        out.append(g)
+    return out
+
+
+def test_error_free_transformations_are_exact(rng):
+    a = rng.standard_normal(300) * 2.0 ** rng.integers(-60, 61, 300)
+    b = rng.standard_normal(300) * 2.0 ** rng.integers(-60, 61, 300)
+    s, e = O.two_sum(a, b)
+    p, f = O.two_product(a, b)
+    for k in range(300):
+        assert _fr(s[k]) + _fr(e[k]) == _fr(a[k]) + _fr(b[k])
+        assert _fr(p[k]) + _fr(f[k]) == _fr(a[k]) * _fr(b[k])
+        assert s[k] == a[k] + b[k] and p[k] == a[k] * b[k]
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64])
+def test_dot2_within_its_bound(n, rng):
+    """|hi + lo - x.y| <= 2 gamma_n^2 sum |x_k y_k| against exact rationals, on
+    plain vectors and on vectors whose products cancel to a small remainder
+    (where a plain float64 dot product errs by about u sum |x_k y_k|)."""
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(n)
+    cases = [(x, y), (np.concatenate([x, x, [1e-3]]), np.concatenate([y, -y, [1.0]]))]
+    for u, v in cases:
+        m = len(u)
+        exact = sum((_fr(a) * _fr(b) for a, b in zip(u, v)), Fraction(0))
+        hi, lo = O.dot2_dd(u, v)
+        gamma = m * U64 / (1 - m * U64)
+        bound = 2 * gamma**2 * float(np.sum(np.abs(u * v)))
+        assert abs(float(_fr(hi) + _fr(lo) - exact)) <= bound
+        assert hi == float(hi + lo)  # a normalised pair
+
+
+def test_contract_full_dd_exact_to_rounding(rng):
+    for modes, rx, ry in [([3, 2, 3], [1, 2, 3, 1], [1, 3, 2, 1]), ([2, 2, 2, 2], [1, 2, 2, 2, 1], [1, 2, 3, 2, 1])]:
+        x = _rand_tt(rng, modes, rx)
+        y = _rand_tt(rng, modes, ry)
+        exact = _exact_full(x, y)
+        assert abs(O.contract_full_dd(x, y) - float(exact)) <= U64 * abs(float(exact))
+
+
+def test_contract_full_dd_under_cancellation(rng):
+    """Y = X + X'' where X'' is X with its first core scaled by -(1 + 2^-30): Y's
+    entries cancel to about 2^-30 of its parts, and the plain sweep loses about
+    30 bits; the compensated sweep stays within one rounding of the exact value."""
+    x = _rand_tt(rng, [3, 2, 3], [1, 2, 3, 1])
+    w = [c.copy() for c in x]
+    w[0] = w[0] * -(1 + 2.0**-30)
+    y = _tt_sum(x, w)
+    exact = float(_exact_full(x, y))
+    assert abs(O.contract_full_dd(x, y) - exact) <= 2 * U64 * abs(exact)
+    assert abs(O.contract_full(x, y) - exact) > 1e3 * U64 * abs(exact)  # the case does need compensation
