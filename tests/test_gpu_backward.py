@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import cs_bound, to_dev, to_host
+from helpers import to_dev, to_host
 from paper_2109_00626_gb300 import inputs as G
 
 pytestmark = pytest.mark.gpu
