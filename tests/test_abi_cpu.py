@@ -183,3 +183,94 @@ def test_merged_rejects_before_enqueue(L):
     assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z_bad.ref, None, None, ws, nb, None) == -2
     z64 = FakeDesc(modes, ranks, dtype=B.TT_F64)
     assert L.tt_contract_partial(x.ref, y.ref, _mask(mask), 1, 0, z64.ref, None, None, ws, nb, None) == -2
+
+
+def _batch(xs, ys, masks, zs, prec=0):
+    """A tt_batch over FakeDescs; returns it with the arrays it points into."""
+    n = len(xs)
+    xarr = (B.TTDesc * n)(*[d.desc for d in xs])
+    yarr = (B.TTDesc * n)(*[d.desc for d in ys])
+    bufs = [(_mask(m) if m is not None else None) for m in masks]
+    mp = (ctypes.POINTER(ctypes.c_uint8) * n)(
+        *[(ctypes.cast(b, ctypes.POINTER(ctypes.c_uint8)) if b is not None else ctypes.POINTER(ctypes.c_uint8)())
+          for b in bufs])
+    zarr = None
+    if zs is not None:
+        zarr = (B.TTDesc * n)(*[(z.desc if z is not None else xs[0].desc) for z in zs])
+    batch = B.TTBatch(n, xarr, yarr, mp, zarr, prec)
+    return batch, (xarr, yarr, mp, zarr, bufs)
+
+
+def _plan(L, batch):
+    plan = ctypes.c_void_p()
+    pb = ctypes.c_size_t(0)
+    wb = ctypes.c_size_t(0)
+    rc = L.tt_batch_plan(ctypes.byref(batch), ctypes.byref(plan), ctypes.byref(pb), ctypes.byref(wb))
+    return rc, plan, pb.value, wb.value
+
+
+def test_batch_plan_on_the_host(L):
+    """tt_batch_plan / tt_batch_pack / tt_plan_info are host-only: a mix of full
+    and partial pairs plans, packs into exactly packed_bytes, reports a tile
+    configuration per pair; bad pairs are rejected with their codes."""
+    specs = [([4, 3, 5], [1, 4, 6, 1], [1, 5, 3, 1], None),
+             ([2, 3, 4, 5], [1, 6, 7, 8, 1], [1, 9, 10, 11, 1], [1, 1, 0, 0]),
+             ([3, 3, 3, 3, 3], [1, 16, 16, 16, 16, 1], [1, 16, 16, 16, 16, 1], None),
+             ([2, 3, 4, 5], [1, 6, 7, 8, 1], [1, 9, 10, 11, 1], [0, 0, 1, 1])]
+    xs, ys, masks, zs = [], [], [], []
+    for modes, rx, ry, mask in specs:
+        x, y = FakeDesc(modes, rx), FakeDesc(modes, ry)
+        xs.append(x)
+        ys.append(y)
+        masks.append(mask)
+        if mask is None:
+            zs.append(None)
+        else:
+            zm, zr, _ = B.partial_shape(x, y, mask, "chain")
+            zs.append(FakeDesc(zm, zr))
+    batch, keep = _batch(xs, ys, masks, zs)
+    rc, plan, pb, wb = _plan(L, batch)
+    assert rc == 0 and pb > 0 and wb == 256
+    try:
+        n = ctypes.c_int32(0)
+        t = ctypes.c_int32(-1)
+        for p in range(len(specs)):
+            assert L.tt_plan_info(plan, p, ctypes.byref(n), ctypes.byref(t)) == 0
+            assert n.value == len(specs) and t.value in (0, 1, 2)
+        assert L.tt_plan_info(plan, len(specs), None, ctypes.byref(t)) == -1
+        buf = (ctypes.c_uint8 * pb)()
+        assert L.tt_batch_pack(plan, buf, pb) == 0
+        assert L.tt_batch_pack(plan, buf, pb - 1) == -1
+    finally:
+        L.tt_plan_free(plan)
+    # the partial pairs' free-core copies are packed as jobs: more partial pairs, more bytes
+    batch1, keep1 = _batch(xs[:1], ys[:1], masks[:1], zs[:1])
+    batch2, keep2 = _batch(xs[:2], ys[:2], masks[:2], zs[:2])
+    rc1, p1, pb1, _ = _plan(L, batch1)
+    rc2, p2, pb2, _ = _plan(L, batch2)
+    assert rc1 == 0 and rc2 == 0 and pb2 > pb1
+    L.tt_plan_free(p1)
+    L.tt_plan_free(p2)
+
+    def rejects(code, xs_, ys_, masks_, zs_, prec=0):
+        b, k = _batch(xs_, ys_, masks_, zs_, prec)
+        rc, plan, _, _ = _plan(L, b)
+        assert rc == code, (rc, code)
+        assert not plan.value  # nothing to free on an error
+
+    x4, y4 = FakeDesc([2, 3, 4, 5], [1, 6, 7, 8, 1]), FakeDesc([2, 3, 4, 5], [1, 9, 10, 11, 1])
+    rejects(-4, [x4], [y4], [[0, 1, 1, 0]], [x4])                       # not an end block
+    rejects(-1, [x4], [y4], [[1, 1, 0, 0]], None)                       # partial pair, no outputs
+    zm, zr, _ = B.partial_shape(x4, y4, [1, 1, 0, 0], "chain")
+    zr_bad = list(zr)
+    zr_bad[1] += 1
+    rejects(-2, [x4], [y4], [[1, 1, 0, 0]], [FakeDesc(zm, zr_bad)])     # output of the wrong shape
+    x8 = FakeDesc([4, 3, 5], [1, 4, 6, 1], dtype=B.TT_F64)
+    y8 = FakeDesc([4, 3, 5], [1, 5, 3, 1], dtype=B.TT_F64)
+    rejects(-3, [xs[0], x8], [ys[0], y8], [None, None], [None, None])   # mixed dtypes
+    xb = FakeDesc([4, 3, 5], [1, 4, 6, 1], dtype=B.TT_BF16)
+    yb = FakeDesc([4, 3, 5], [1, 5, 3, 1], dtype=B.TT_BF16)
+    rejects(-8, [xb], [yb], [None], [None])                              # bfloat16 pairs
+    rejects(-8, [xs[0]], [ys[0]], [None], [None], prec=B.PREC["bf16"])  # reduced-precision products
+    big = FakeDesc([2, 2, 2], [1, 129, 129, 1])
+    rejects(-5, [big], [big], [None], [None])                            # rank above the float32 cap
