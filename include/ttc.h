@@ -122,7 +122,10 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
  *                range).
  *   status_dev   device int32, see TT_STATUS_*.
  * Precision: TT_P_NATIVE for F64/F32/BF16 storage; TT_P_BF16 and TT_P_BF16X3
- * for F32 storage.  The final sum of the last mode is accumulated in float64. */
+ * for F32 storage.  The final sum of the last mode is accumulated in float64.
+ * The bfloat16 forms run on the tensor cores and need order >= 3, every
+ * interior rank of X equal to 128 or 256 and every interior rank of Y a
+ * multiple of 64 up to 256 (TT_ERR_UNSUPPORTED otherwise). */
 int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_dev,
                      int64_t* out_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
                      tt_stream stream);
@@ -169,14 +172,14 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
  * scale; a row more than 2^250 (F32) / 2^2000 (F64) below the largest
  * contributes zero), a trailing run as its right environment.  The m output
  * cores are built concurrently: the call forks from `stream` onto up to three
- * library-owned streams of the current device (created, with four events, by
- * the first merged-layout call on the device, which should therefore be made
- * outside any stream capture; never destroyed) and joins back into `stream`
- * with events, so the result is
- * ordered on `stream` like any other call (and a captured stream captures the
- * whole fork and join; until that capture ends the auxiliary streams belong
- * to it, so no other merged-layout call on the device may run meanwhile).
- * Calls are serialised by a host mutex while they enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
+ * library-owned streams of the current device and joins back into `stream`
+ * with events, so the result is ordered on `stream` like any other call.  The
+ * first merged-layout call on a device creates those streams and four events
+ * (never destroyed), so it should be made outside any stream capture.  A
+ * captured stream captures the whole fork and join; until that capture ends
+ * the auxiliary streams belong to it, so no other merged-layout call on the
+ * device may run meanwhile.  Calls are serialised by a host mutex while they
+ * enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
  * the intermediate P (R^x I R^y' x the next pair rank) exceeds 2^30 entries,
  * or a rank exceeds 128 (F32) / 64 (F64).
  * Precision: TT_P_NATIVE (F64/F32). */

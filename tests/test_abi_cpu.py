@@ -274,3 +274,48 @@ def test_batch_plan_on_the_host(L):
     rejects(-8, [xs[0]], [ys[0]], [None], [None], prec=B.PREC["bf16"])  # reduced-precision products
     big = FakeDesc([2, 2, 2], [1, 129, 129, 1])
     rejects(-5, [big], [big], [None], [None])                            # rank above the float32 cap
+
+
+def _ws(L, op, x, y, mask=None, layout="chain", prec="native"):
+    nb = ctypes.c_size_t(0)
+    m = _mask(mask) if mask is not None else None
+    rc = L.tt_workspace_bytes(op, x.ref, y.ref, m, B.LAYOUT[layout], B.PREC[prec], ctypes.byref(nb))
+    return rc, nb.value
+
+
+def test_workspace_queries_and_their_limits(L):
+    """tt_workspace_bytes per operation, and the conditions the header states
+    for each path (host only)."""
+    x = FakeDesc([16] * 10, [1] + [64] * 9 + [1])
+    rc, nb = _ws(L, B.TT_OP_FULL, x, x)
+    assert rc == 0 and nb > 0                        # the two-sided sweep's meeting environments
+    one = FakeDesc([5], [1, 1])
+    assert _ws(L, B.TT_OP_FULL, one, one) == (0, 0)  # order 1: one sweep, nothing to meet
+    assert _ws(L, B.TT_OP_PARTIAL, x, x, [1] * 6 + [0] * 4) == (0, 0)  # chain: K stays on chip
+    # tensor-core forms: bfloat16 storage, or float32 storage with bf16 / bf16x3 products
+    xb = FakeDesc([32] * 4, [1, 256, 128, 256, 1], dtype=B.TT_BF16)
+    yb = FakeDesc([32] * 4, [1, 64, 192, 256, 1], dtype=B.TT_BF16)
+    rc, nb = _ws(L, B.TT_OP_FULL, xb, yb)
+    assert rc == 0 and nb > 0
+    x32 = FakeDesc([32] * 4, [1, 128, 128, 128, 1])
+    y32 = FakeDesc([32] * 4, [1, 128, 64, 128, 1])
+    r3, n3 = _ws(L, B.TT_OP_FULL, x32, y32, prec="bf16x3")
+    r1, n1 = _ws(L, B.TT_OP_FULL, x32, y32, prec="bf16")
+    assert r3 == 0 and r1 == 0 and n3 > n1 > 0      # the split form keeps hi and lo copies
+    assert _ws(L, B.TT_OP_FULL, FakeDesc([32] * 4, [1, 64, 64, 64, 1], dtype=B.TT_BF16), yb)[0] == -8
+    assert _ws(L, B.TT_OP_FULL, xb, FakeDesc([32] * 4, [1, 96, 64, 64, 1], dtype=B.TT_BF16))[0] == -8
+    assert _ws(L, B.TT_OP_FULL, FakeDesc([32] * 2, [1, 128, 1], dtype=B.TT_BF16),
+               FakeDesc([32] * 2, [1, 128, 1], dtype=B.TT_BF16))[0] == -8
+    x64 = FakeDesc([32] * 4, [1, 128, 128, 128, 1], dtype=B.TT_F64)
+    assert _ws(L, B.TT_OP_FULL, x64, x64, prec="bf16")[0] == -3  # bf16 products need float32 storage
+    # backward: the adjoint's rank cap, lifted when Y has rank 1 everywhere (the vector adjoint)
+    xs = FakeDesc([4] * 5, [1, 3, 3, 3, 3, 1])
+    rc, nb = _ws(L, B.TT_OP_BACKWARD, xs, xs)
+    assert rc == 0 and nb > 0
+    rc, nb = _ws(L, B.TT_OP_BACKWARD, xs, xs, [1, 1, 0, 0, 0])
+    assert rc == 0 and nb > 0
+    wide = FakeDesc([4] * 3, [1, 33, 33, 1], dtype=B.TT_F64)
+    ones = FakeDesc([4] * 3, [1, 1, 1, 1], dtype=B.TT_F64)
+    assert _ws(L, B.TT_OP_BACKWARD, wide, wide)[0] == -5
+    rc, nb = _ws(L, B.TT_OP_BACKWARD, wide, ones)
+    assert rc == 0 and nb > 0
