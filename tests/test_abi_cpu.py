@@ -319,3 +319,12 @@ def test_workspace_queries_and_their_limits(L):
     assert _ws(L, B.TT_OP_BACKWARD, wide, wide)[0] == -5
     rc, nb = _ws(L, B.TT_OP_BACKWARD, wide, ones)
     assert rc == 0 and nb > 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """With no built library the binding raises; there is no other code path
+    to fall back to."""
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "libttc.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        B.lib()
