@@ -201,6 +201,40 @@ def cpu_baseline(seconds=10.0):
     }
 
 
+def accuracy(x32, y32, z_gpu, zc_gpu):
+    """Part of the CPU-baseline leg: errors of the headline step's GPU results
+    against the float64 oracle on the same float32 cores.  Full contraction:
+    eps = |z - z*| / (||X|| ||Y||) (norms from the oracle's <X,X>, <Y,Y>), the
+    plain relative error and kappa = ||X|| ||Y|| / |z*|.  Partial contraction:
+    the joined core C's largest error relative to its largest entry, and
+    whether the copied cores are bit-exact."""
+    import oracle as O
+
+    x = [np.asarray(c, dtype=np.float64) for c in x32]
+    y = [np.asarray(c, dtype=np.float64) for c in y32]
+    z_star = O.contract_full(x, y)
+    nrm = math.sqrt(O.contract_full(x, x) * O.contract_full(y, y))
+    want, _ = O.partial_chain(x, y, MASK)
+    _, s = O.end_block(MASK)
+    c_at = len(x) - s - 1  # position of the joined core C in the chain (leading block)
+    got = [np.asarray(g, dtype=np.float64).reshape(w.shape) for g, w in zip(zc_gpu, want)]
+    c_err = float(np.abs(got[c_at] - want[c_at]).max() / np.abs(want[c_at]).max())
+    copies_exact = all(np.array_equal(g, w) for p, (g, w) in enumerate(zip(got, want)) if p != c_at)
+
+    def fin(v):
+        return float(v) if math.isfinite(v) else None
+
+    return {
+        "reference": "float64 oracle on the same float32 cores",
+        "full_eps": fin(abs(z_gpu - z_star) / nrm),
+        "full_rel": fin(abs(z_gpu - z_star) / abs(z_star)),
+        "kappa": fin(nrm / abs(z_star)),
+        "partial_c_rel": fin(c_err),
+        "partial_copies_exact": bool(copies_exact),
+        "bound_eps": 1e-5,
+    }
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -467,6 +501,10 @@ def run_ours(args):
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            try:
+                line["accuracy"] = accuracy(x, y, float(full.out.item()), [c.detach().cpu().numpy() for c in part.z])
+            except Exception as e:  # a report, never a reason to lose the measurement line
+                line["accuracy"] = {"error": repr(e)[:200]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -24,3 +24,37 @@ def test_reference_arm_json_line():
     assert line["steps"] == 3 and line["warmup"] == 3 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_accuracy_report_of_the_headline_step():
+    """bench.accuracy on results with known errors: the oracle's own values give
+    zero error and bit-exact copies; a relative slip of 1e-6 in z shows as
+    full_rel = 1e-6 and full_eps = 1e-6 / kappa; a slip in C shows in
+    partial_c_rel; a non-finite z is reported as null (the line stays JSON)."""
+    import sys
+
+    import numpy as np
+
+    import oracle as O
+    from paper_2109_00626_gb300 import inputs as G
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    x, y = G.order10_r64(0, np.float32)
+    x64 = [c.astype(np.float64) for c in x]
+    y64 = [c.astype(np.float64) for c in y]
+    z = O.contract_full(x64, y64)
+    zc, _ = O.partial_chain(x64, y64, bench.MASK)
+    a = bench.accuracy(x, y, z, zc)
+    assert a["full_eps"] == 0.0 and a["partial_c_rel"] == 0.0 and a["partial_copies_exact"]
+    b = bench.accuracy(x, y, z * (1 + 1e-6), zc)
+    assert abs(b["full_rel"] - 1e-6) < 1e-12 and abs(b["full_eps"] * b["kappa"] - 1e-6) < 1e-12
+    zc2 = [c.copy() for c in zc]
+    zc2[3] = zc2[3] * (1 + 1e-4)
+    c = bench.accuracy(x, y, z, zc2)
+    assert 0.5e-4 < c["partial_c_rel"] <= 1e-4 * (1 + 1e-9)
+    zc2[0] = zc2[0] + 1.0
+    assert not bench.accuracy(x, y, z, zc2)["partial_copies_exact"]
+    d = bench.accuracy(x, y, float("nan"), zc)
+    assert d["full_eps"] is None and d["full_rel"] is None
