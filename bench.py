@@ -235,6 +235,43 @@ def accuracy(x32, y32, z_gpu, zc_gpu):
     }
 
 
+def tc_accuracy(results):
+    """Part of the CPU-baseline leg: each tensor-core form's z (mantissa,
+    exponent) against the float64 oracle on the order-16 rank-256 pair, as
+    eps = |z - z*| / (||X|| ||Y||) on the float32 cores (end to end) and, for
+    the bfloat16 form, on the bfloat16-rounded cores it reads (arithmetic
+    error); with kappa and the bound the tests hold each form to."""
+    import oracle as O
+    import torch
+
+    x, y = G.order16_r256(0)
+    x64 = [c.astype(np.float64) for c in x]
+    y64 = [c.astype(np.float64) for c in y]
+    z32 = O.contract_full(x64, y64)
+    nrm = math.sqrt(O.contract_full(x64, x64) * O.contract_full(y64, y64))
+    n = len(x)
+
+    def fin(v):
+        return float(v) if math.isfinite(v) else None
+
+    out = {}
+    for prec, (m, e) in results.items():
+        z = math.ldexp(m, e)
+        rep = {
+            "reference": "float64 oracle",
+            "eps_vs_fp32_cores": fin(abs(z - z32) / nrm),
+            "rel_vs_fp32_cores": fin(abs(z - z32) / abs(z32)),
+            "kappa": fin(nrm / abs(z32)),
+            "bound_eps": 2 * n * 2.0 ** (-8 if prec == "native" else -15),
+        }
+        if prec == "native":
+            xb = [torch.from_numpy(c).bfloat16().double().numpy() for c in x]
+            yb = [torch.from_numpy(c).bfloat16().double().numpy() for c in y]
+            rep["eps_vs_bf16_cores"] = fin(abs(z - O.contract_full(xb, yb)) / nrm)
+        out[prec] = rep
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -505,6 +542,12 @@ def run_ours(args):
                 line["accuracy"] = accuracy(x, y, float(full.out.item()), [c.detach().cpu().numpy() for c in part.z])
             except Exception as e:  # a report, never a reason to lose the measurement line
                 line["accuracy"] = {"error": repr(e)[:200]}
+            if _TC_RESULTS:
+                try:
+                    for prec, rep in tc_accuracy(_TC_RESULTS).items():
+                        forms["bf16" if prec == "native" else prec]["accuracy"] = rep
+                except Exception as e:
+                    forms["bf16"]["accuracy"] = {"error": repr(e)[:200]}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -673,6 +716,9 @@ def bench_merged(T, dev, args):
     }
 
 
+_TC_RESULTS = {}  # precision form -> (mantissa, exponent) of its last z, for the accuracy report
+
+
 def bench_bf16(T, dev, args, prec):
     """Order 16, modes 32, ranks 256, log-normal core scales; full contraction
     on the tensor cores: bfloat16 cores with float32 sums ("native"), or the
@@ -703,6 +749,7 @@ def bench_bf16(T, dev, args, prec):
         b.record(stream)
     torch.cuda.synchronize(dev)
     ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    _TC_RESULTS[prec] = (float(op.out.item()), int(op.log2.item()))
     modes, r = [32] * 16, G.tt_ranks(16, 256)
     flops = W.full_flops(modes, r, r)
     nprod = 3 if prec == "bf16x3" else 1

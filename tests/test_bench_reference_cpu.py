@@ -58,3 +58,28 @@ def test_accuracy_report_of_the_headline_step():
     assert not bench.accuracy(x, y, z, zc2)["partial_copies_exact"]
     d = bench.accuracy(x, y, float("nan"), zc)
     assert d["full_eps"] is None and d["full_rel"] is None
+
+
+def test_tensor_core_accuracy_report():
+    """bench.tc_accuracy: the oracle's own z gives zero end-to-end error and, for
+    the bf16 form, the (small) effect of rounding the cores; a relative slip of
+    1e-6 shows as rel = 1e-6; the stated bounds are 2N 2^-8 and 2N 2^-15."""
+    import math
+    import sys
+
+    import numpy as np
+
+    import oracle as O
+    from paper_2109_00626_gb300 import inputs as G
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    x, y = G.order16_r256(0)
+    z = O.contract_full([c.astype(np.float64) for c in x], [c.astype(np.float64) for c in y])
+    m, e = math.frexp(z)
+    rep = bench.tc_accuracy({"native": (m, e), "bf16x3": (m * (1 + 1e-6), e)})
+    assert rep["native"]["eps_vs_fp32_cores"] == 0.0
+    assert 0.0 < rep["native"]["eps_vs_bf16_cores"] < 1e-10
+    assert abs(rep["bf16x3"]["rel_vs_fp32_cores"] - 1e-6) < 1e-12
+    assert rep["native"]["bound_eps"] == 32 * 2.0**-8 and rep["bf16x3"]["bound_eps"] == 32 * 2.0**-15
