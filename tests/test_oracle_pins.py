@@ -221,6 +221,18 @@ def test_partial_merged_vs_dense(mask, rng):
     np.testing.assert_allclose(O.merged_to_dense(cores, perm), want, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("mask", [[0, 1, 0, 1, 0], [1, 0, 1, 0, 1], [0, 0, 1, 1, 0], [1, 1, 0, 0, 0]])
+def test_partial_merged_unequal_free_modes_vs_dense(mask, rng):
+    """Free modes of X and Y of different sizes (equal on S)."""
+    mx = [3, 2, 4, 2, 3]
+    my = [m if mask[k] else m + 2 for k, m in enumerate(mx)]
+    x = _rand_tt(rng, mx, [1, 2, 5, 3, 2, 1])
+    y = _rand_tt(rng, my, [1, 3, 1, 4, 2, 1])
+    cores, perm = O.partial_merged(x, y, mask)
+    want = O.tcp(_dense_by_entries(x), _dense_by_entries(y), [k for k in range(5) if mask[k]])
+    np.testing.assert_allclose(O.merged_to_dense(cores, perm), want, rtol=1e-12, atol=1e-14)
+
+
 def test_chain_rejects_interior_and_all():
     x, y = G.small_fp64(0)
     with pytest.raises(ValueError):
