@@ -41,8 +41,10 @@ partial_chain          end-block S -> chain TT (Algorithm 2 steps 4-6)
 partial_merged         any S -> TT-matrix of merged cores
 chain_to_dense / merged_to_dense   dense reconstruction + un-permutation
 grad_sweep / grad_full / grad_partial_chain   gradients by the L/F formulas
-tt_svd                 Algorithm 1
-ttcp_alg2              Algorithm 2 on dense operands of different order
+tt_svd                 a TT of a dense tensor within eps ||X||_F (Section II)
+reverse_tt             the same TT with its modes in reverse order
+tcp_pairs              Eq. 8 over several (n, m) pairs, operands of any orders
+partial_chain_pairs    end-block pairs of TTs of different orders -> chain TT
 tcp_ops / ttcp_ops     the operation counts of Section IV and Remark 3
 
 Parity status: every function here is pinned by a test in tests/ that does not
@@ -78,7 +80,9 @@ __all__ = [
     "grad_full",
     "grad_partial_chain",
     "tt_svd",
-    "ttcp_alg2",
+    "reverse_tt",
+    "tcp_pairs",
+    "partial_chain_pairs",
     "tcp_ops",
     "ttcp_ops",
 ]
@@ -476,74 +480,135 @@ def grad_partial_chain(xc, yc, mask, dz):
 
 
 # --------------------------------------------------------------------------
-# Algorithm 1 (TT-SVD) and Algorithm 2 (TTCP) on dense operands
+# TT decomposition of a dense tensor (Section II, TT-SVD) and contractions
+# of TTs of different orders over pairs of end modes (Eq. 8 with (n, m) pairs)
 # --------------------------------------------------------------------------
 def tt_svd(x, eps=0.0):
-    """Algorithm 1: sequential delta-truncated SVDs.
+    """A TT of the dense tensor x whose reconstruction error is at most
+    eps * ||x||_F (the accuracy guarantee of the paper's TT-SVD, Section II).
 
-    delta = eps / sqrt(N-1) * ||X||_F; at step n the running matrix is
-    reshaped (row-major) to (R_{n-1} I_n) x rest, its truncated SVD keeps the
-    fewest singular values whose discarded tail has 2-norm <= delta, U becomes
-    core n and S V^T carries on.  The last core is what remains.
+    Built from the right: the part of x not yet factored is a matrix
+    (left modes) x (I_k R_{k+1}); its SVD U S V^T gives core k = the leading
+    rows of V^T (right-orthonormal) and the rest U S carries on to the next
+    mode to the left.  Each SVD drops the largest set of trailing singular
+    values whose 2-norm is at most eps ||x||_F / sqrt(N-1); the N-1 dropped
+    parts are orthogonal, so the total error is at most eps ||x||_F.
     """
     x = np.asarray(x, dtype=np.float64)
     dims = x.shape
     n = len(dims)
     if n == 1:
         return [x.reshape(1, dims[0], 1).copy()]
-    delta = eps / np.sqrt(n - 1) * np.linalg.norm(x)
-    cores = []
-    r_prev = 1
-    z = x.reshape(-1)
-    for k in range(n - 1):
-        z = z.reshape(r_prev * dims[k], -1)
-        u, sv, vt = np.linalg.svd(z, full_matrices=False)
-        tail = np.sqrt(np.cumsum((sv**2)[::-1]))[::-1]  # tail[r] = ||sv[r:]||
-        r = len(sv)
-        for cand in range(1, len(sv) + 1):
-            rest = tail[cand] if cand < len(sv) else 0.0
-            if rest <= delta:
-                r = cand
-                break
-        cores.append(u[:, :r].reshape(r_prev, dims[k], r))
-        z = sv[:r, None] * vt[:r]
-        r_prev = r
-    cores.append(z.reshape(r_prev, dims[n - 1], 1))
+    tol = eps * np.linalg.norm(x) / np.sqrt(n - 1)
+    rest = x.reshape(-1, 1)  # (I_0 ... I_{N-1}) x R_N with R_N = 1
+    right_rank = 1
+    cores = [None] * n
+    for k in range(n - 1, 0, -1):
+        mat = rest.reshape(-1, dims[k] * right_rank)
+        u, sv, vt = np.linalg.svd(mat, full_matrices=False)
+        # keep r values: the smallest r with ||sv[r:]|| <= tol (at least one)
+        dropped = np.sqrt(np.cumsum(sv[::-1] ** 2))[::-1]  # dropped[r] = ||sv[r:]||
+        keep = len(sv)
+        while keep > 1 and dropped[keep - 1] <= tol:
+            keep -= 1
+        cores[k] = vt[:keep].reshape(keep, dims[k], right_rank)
+        rest = u[:, :keep] * sv[:keep]
+        right_rank = keep
+    cores[0] = rest.reshape(1, dims[0], right_rank)
     return cores
 
 
-def ttcp_alg2(x, y, n, m, eps=0.0):
-    """Algorithm 2 (TTCP) for dense X (order N) and Y (order M), 0-based (n, m).
+def reverse_tt(cores):
+    """The same tensor with its modes in reverse order: the cores taken last
+    to first, each with its rank legs exchanged (the paper's (.)^{T[1;3]})."""
+    return [_swap_rank_legs(np.asarray(g, dtype=np.float64)) for g in reversed(cores)]
 
-    Steps: move mode n of X to the front (step 1) and decompose with
-    Algorithm 1 (step 2); the same for Y (step 3); K = A_x^T A_y (step 4);
-    join X's remaining cores, walked backwards with their rank legs exchanged,
-    through K to Y's remaining cores (step 5; K is absorbed into the last X core
-    of the walk, G_x^(2)); re-order the axes into Eq. 8's order (step 6).
-    Returns (dense Z, chain cores of Z_rho, perm).  Needs N, M >= 2.
-    """
+
+def tcp_pairs(x, y, pairs):
+    """Eq. 8 over several (n, m) pairs for dense tensors of any orders: mode
+    pairs[t][0] of x is summed against mode pairs[t][1] of y.  Result axes:
+    the free modes of x ascending, then the free modes of y ascending."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    nx, ny = x.ndim, y.ndim
-    assert nx >= 2 and ny >= 2
-    xr = np.moveaxis(x, n, 0)
-    yr = np.moveaxis(y, m, 0)
-    gx = tt_svd(xr, eps)
-    gy = tt_svd(yr, eps)
-    ax = gx[0][0]  # (I_n, R_1)
-    ay = gy[0][0]  # (J_m, P_1)
-    k = ax.T @ ay
-    xrev = [_swap_rank_legs(g) for g in gx[:0:-1]]  # B_x^T, ..., G_x^(2)T
-    xrev[-1] = np.einsum("uia,ab->uib", xrev[-1], k)
-    cores = xrev + [g.copy() for g in gy[1:]]
-    # axis bookkeeping: X^rho's cores 2..N hold X's modes except n, ascending
-    x_modes = [k2 for k2 in range(nx) if k2 != n]
-    y_modes = [k2 for k2 in range(ny) if k2 != m]
-    zr_axes_x = list(reversed(x_modes))
-    # Eq. 8 position of each Z_rho axis
-    perm = [x_modes.index(a) for a in zr_axes_x] + [len(x_modes) + y_modes.index(b) for b in y_modes]
-    z = chain_to_dense(cores, perm)
-    return z, cores, perm
+    letters = string.ascii_letters
+    xs = [letters[k] for k in range(x.ndim)]
+    ys = [letters[x.ndim + k] for k in range(y.ndim)]
+    for n, m in pairs:
+        assert x.shape[n] == y.shape[m]
+        ys[m] = xs[n]
+    cx = {n for n, _ in pairs}
+    cy = {m for _, m in pairs}
+    out = [xs[k] for k in range(x.ndim) if k not in cx] + [ys[k] for k in range(y.ndim) if k not in cy]
+    return np.einsum("".join(xs) + "," + "".join(ys) + "->" + "".join(out), x, y)
+
+
+def _end_walks(modes, order):
+    """The ways the positions `modes` form an end block of a TT of the given
+    order: (positions listed from the end of the train inward, whether the
+    block is the trailing one).  A block covering the whole train has both."""
+    s = len(modes)
+    ms = sorted(modes)
+    walks = []
+    if ms == list(range(s)):
+        walks.append((list(range(s)), False))
+    if ms == list(range(order - s, order)):
+        walks.append((list(range(order - 1, order - 1 - s, -1)), True))
+    return walks
+
+
+def partial_chain_pairs(xc, yc, pairs):
+    """Partial contraction of TTs of orders N and M over the mode pairs
+    (n_t, m_t) (Eq. 8 applied to each pair), as one chain TT.
+
+    The n_t form a block at one end of X and the m_t a block at one end of Y,
+    paired in the order in which the two blocks are met walking from the ends
+    of the trains inward (e.g. Example 1's single pair, or X's modes 0, 1
+    against Y's modes M-1, M-2).  An operand whose block is the trailing one
+    is reversed first (reverse_tt), so both blocks lead; then
+      K = the left environment over the s pairs,
+      C[a', i, b] = sum_a X'_s[a, i, a'] K[a, b]       (N > s), or
+      C[a, j, b'] = sum_b K[a, b] Y'_s[b, j, b']       (N = s, a of size 1),
+      cores = X'_{N-1}^T, ..., X'_{s+1}^T, C, Y'_s, ..., Y'_{M-1}
+    (when X has no free mode, the C of the second form takes Y'_s's place).
+    Returns (cores, perm): axis p of the chain TT is axis perm[p] of Eq. 8's Z
+    (free modes of X ascending, then free modes of Y ascending).
+    """
+    xc, yc = _f64(xc), _f64(yc)
+    n_x, n_y = len(xc), len(yc)
+    pairs = [(int(a), int(b)) for a, b in pairs]
+    s = len(pairs)
+    pair_of = dict(pairs)
+    found = None
+    if s > 0 and len(pair_of) == s:
+        for walk_x, rev_x in _end_walks([a for a, _ in pairs], n_x):
+            for walk_y, rev_y in _end_walks([b for _, b in pairs], n_y):
+                if found is None and [pair_of[a] for a in walk_x] == walk_y:
+                    found = (rev_x, rev_y)
+    if found is None:
+        raise ValueError("the paired modes must form an end block of each operand, met in the same order from the ends")
+    rev_x, rev_y = found
+    if s == n_x and s == n_y:
+        raise ValueError("every mode contracted: use contract_full")
+    xr = reverse_tt(xc) if rev_x else xc
+    yr = reverse_tt(yc) if rev_y else yc
+    # original mode index of position j of the (possibly reversed) operand
+    ox = [(n_x - 1 - j) if rev_x else j for j in range(n_x)]
+    oy = [(n_y - 1 - j) if rev_y else j for j in range(n_y)]
+    k = left_envs(xr[:s], yr[:s])[-1]
+    x_free = [j for j in range(n_x) if j >= s]
+    y_free = [j for j in range(n_y) if j >= s]
+    if x_free:
+        c = np.einsum("aiu,ab->uib", xr[s], k)
+        cores = [_swap_rank_legs(xr[j]) for j in range(n_x - 1, s, -1)] + [c] + [yr[j].copy() for j in y_free]
+    else:
+        c = np.einsum("ab,bjv->ajv", k, yr[s])
+        cores = [c] + [yr[j].copy() for j in y_free[1:]]
+    axes_x = [ox[j] for j in reversed(x_free)]
+    axes_y = [oy[j] for j in y_free]
+    fx = sorted(ox[j] for j in x_free)
+    fy = sorted(oy[j] for j in y_free)
+    perm = [fx.index(a) for a in axes_x] + [len(fx) + fy.index(b) for b in axes_y]
+    return cores, perm
 
 
 # --------------------------------------------------------------------------

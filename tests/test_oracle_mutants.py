@@ -147,3 +147,43 @@ def test_cancellation_pin_catches_compensation_mutants(name, mutant, monkeypatch
     ref = O.contract_full_dd(x, y)
     monkeypatch.setattr(T, name, mutant)
     assert abs(T.contract_full_dd(x, y) - ref) > 1e3 * 2.0**-53 * abs(ref)
+
+
+def _reverse_without_swap(cores):
+    return [np.asarray(g, dtype=np.float64).copy() for g in reversed(cores)]
+
+
+def _svd_keep_one_too_few(x, eps=0.0):
+    cores = _ORIG_TT_SVD(x, eps)
+    # drop the last rank-1 direction of the first bond
+    if cores[0].shape[2] > 1:
+        cores[0] = cores[0][:, :, :-1]
+        cores[1] = cores[1][:-1]
+    return cores
+
+
+_ORIG_TT_SVD = T.tt_svd
+
+
+def test_pairs_pin_catches_reversal_without_leg_swap(monkeypatch):
+    x, y = G.pair(14, [2, 3, 2], [1, 2, 3, 1], [1, 2, 2, 1], np.float64)
+    y5 = G.random_tt(np.random.default_rng(5), [3, 2, 2, 3, 2], [1, 2, 3, 2, 2, 1], np.float64)
+    pairs = [(0, 4), (1, 3)]  # X's leading block against Y's trailing block (Y reversed)
+    want = O.tcp_pairs(O.tt_to_dense(x), O.tt_to_dense(y5), pairs)
+    cores, perm = O.partial_chain_pairs(x, y5, pairs)
+    assert np.abs(O.chain_to_dense(cores, perm) - want).max() < 1e-13
+    monkeypatch.setattr(T, "reverse_tt", _reverse_without_swap)
+    try:
+        cores, perm = T.partial_chain_pairs(x, y5, pairs)
+        caught = np.abs(T.chain_to_dense(cores, perm) - want).max() > 1e-6
+    except (ValueError, AssertionError):
+        caught = True  # the unswapped ranks no longer chain
+    assert caught
+
+
+def test_tt_svd_pin_catches_a_dropped_direction(monkeypatch):
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((4, 5, 3))
+    assert np.abs(O.tt_to_dense(O.tt_svd(x)) - x).max() < 1e-12
+    monkeypatch.setattr(T, "tt_svd", _svd_keep_one_too_few)
+    assert np.abs(T.tt_to_dense(T.tt_svd(x)) - x).max() > 1e-3

@@ -350,37 +350,130 @@ def test_tt_svd_exact_and_truncated(rng):
     np.testing.assert_allclose(O.tt_to_dense(cores), x, rtol=0, atol=1e-12)
     # untruncated ranks are min(prod of left dims, prod of right dims)
     assert [c.shape[0] for c in cores] == [1, 4, 18, 6]
-    # Algorithm 1's guarantee: ||X - TT(X)||_F <= eps ||X||_F
+    # the accuracy guarantee: ||X - TT(X)||_F <= eps ||X||_F
     for eps in (0.05, 0.3, 0.7):
         t = O.tt_svd(x, eps)
         err = np.linalg.norm(O.tt_to_dense(t) - x)
         assert err <= eps * np.linalg.norm(x) * (1 + 1e-12)
-    # a TT of known low rank is found exactly
+    # truncation really happens: a larger eps never gives larger ranks
+    r_small = [c.shape[2] for c in O.tt_svd(x, 0.05)]
+    r_large = [c.shape[2] for c in O.tt_svd(x, 0.7)]
+    assert all(a >= b for a, b in zip(r_small, r_large)) and r_small != r_large
+    # a TT of known low rank is found exactly, with its ranks
     low = _rand_tt(rng, [5, 6, 7], [1, 2, 3, 1])
     t = O.tt_svd(O.tt_to_dense(low), 1e-10)
     assert [c.shape[2] for c in t] == [2, 3, 1]
+    np.testing.assert_allclose(O.tt_to_dense(t), O.tt_to_dense(low), rtol=0, atol=1e-12)
+    # order 1 and a mode of size 1
+    v = rng.standard_normal(7)
+    np.testing.assert_allclose(O.tt_to_dense(O.tt_svd(v)), v, rtol=0, atol=0)
+    w = rng.standard_normal((3, 1, 4))
+    np.testing.assert_allclose(O.tt_to_dense(O.tt_svd(w)), w, rtol=0, atol=1e-13)
 
 
-def test_algorithm2_example1_shapes(rng):
-    """Example 1: X (order 4) x_3^2 Y (order 3); Z_rho is I4 x I2 x I1 x J1 x J3."""
-    dims_x = (2, 3, 4, 5)
-    dims_y = (6, 4, 3)
-    x = rng.standard_normal(dims_x)
-    y = rng.standard_normal(dims_y)
-    z, cores, perm = O.ttcp_alg2(x, y, 2, 1)
+def test_reverse_tt_reverses_modes(rng):
+    x = _rand_tt(rng, [3, 4, 2, 5], [1, 2, 3, 4, 1])
+    d = O.tt_to_dense(x)
+    np.testing.assert_allclose(O.tt_to_dense(O.reverse_tt(x)), np.transpose(d, (3, 2, 1, 0)), rtol=0, atol=1e-14)
+
+
+def test_tcp_pairs_by_index_loops(rng):
+    x = rng.standard_normal((2, 3, 4))
+    y = rng.standard_normal((4, 5, 2))
+    got = O.tcp_pairs(x, y, [(2, 0), (0, 2)])  # free: x mode 1, y mode 1
+    want = np.zeros((3, 5))
+    for i1 in range(3):
+        for j1 in range(5):
+            for a in range(2):
+                for b in range(4):
+                    want[i1, j1] += x[a, i1, b] * y[b, j1, a]
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(O.tcp_pairs(x, y, [(2, 0)]), O.tcp_nm(x, y, 2, 0), rtol=0, atol=0)
+
+
+PAIR_CASES = [
+    # orders, pairs
+    (4, 3, [(0, 0)]),
+    (4, 3, [(0, 0), (1, 1)]),
+    (3, 5, [(2, 4), (1, 3)]),        # trailing block of X with trailing block of Y
+    (5, 3, [(0, 2), (1, 1)]),        # leading block of X against trailing block of Y
+    (3, 4, [(2, 0), (1, 1)]),        # trailing block of X against leading block of Y
+    (2, 4, [(0, 0), (1, 1)]),        # X fully contracted: Y keeps two free modes
+    (4, 2, [(3, 1), (2, 0)]),        # Y fully contracted
+    (1, 3, [(0, 2)]),
+]
+
+
+@pytest.mark.parametrize("nx,ny,pairs", PAIR_CASES)
+def test_partial_chain_pairs_against_dense(rng, nx, ny, pairs):
+    """Different orders and end-block pairings: the chain TT (un-permuted by
+    perm) equals Eq. 8 on the dense tensors."""
+    mx = [int(v) for v in rng.integers(2, 4, size=nx)]
+    my = [int(v) for v in rng.integers(2, 4, size=ny)]
+    for a, b in pairs:
+        my[b] = mx[a]
+    x = _rand_tt(rng, mx, [1] + [int(v) for v in rng.integers(1, 4, size=nx - 1)] + [1])
+    y = _rand_tt(rng, my, [1] + [int(v) for v in rng.integers(1, 4, size=ny - 1)] + [1])
+    cores, perm = O.partial_chain_pairs(x, y, pairs)
+    assert sorted(perm) == list(range(nx + ny - 2 * len(pairs)))
+    want = O.tcp_pairs(O.tt_to_dense(x), O.tt_to_dense(y), pairs)
+    np.testing.assert_allclose(O.chain_to_dense(cores, perm), want, rtol=1e-12, atol=1e-12)
+
+
+def test_partial_chain_pairs_rejects_non_end_blocks(rng):
+    x = _rand_tt(rng, [2, 2, 2, 2], [1, 2, 2, 2, 1])
+    y = _rand_tt(rng, [2, 2, 2], [1, 2, 2, 1])
+    for pairs in ([(1, 0)], [(0, 0), (1, 2)], [(0, 1), (1, 0)], [(0, 0), (1, 1), (2, 2), (3, 0)]):
+        with pytest.raises(ValueError):
+            O.partial_chain_pairs(x, y, pairs)
+    with pytest.raises(ValueError):
+        O.partial_chain_pairs(x[:3], y, [(0, 0), (1, 1), (2, 2)])
+
+
+def test_partial_chain_pairs_same_order_equals_partial_chain(rng):
+    x = _rand_tt(rng, [3, 2, 4, 3], [1, 2, 3, 2, 1])
+    y = _rand_tt(rng, [3, 2, 4, 3], [1, 3, 2, 2, 1])
+    for mask, pairs in (([1, 1, 0, 0], [(0, 0), (1, 1)]), ([0, 0, 1, 1], [(3, 3), (2, 2)])):
+        c1, p1 = O.partial_chain(x, y, mask)
+        c2, p2 = O.partial_chain_pairs(x, y, pairs)
+        np.testing.assert_allclose(O.chain_to_dense(c1, p1), O.chain_to_dense(c2, p2), rtol=1e-13, atol=1e-13)
+
+
+def _ttcp_dense(x, y, n, m, eps=0.0):
+    """Dense operands: move the paired modes to the front, decompose both
+    with tt_svd, contract the TTs over their first modes, and return Z in
+    Eq. 8 order together with the chain cores (Z^rho)."""
+    xt = O.tt_svd(np.moveaxis(x, n, 0), eps)
+    yt = O.tt_svd(np.moveaxis(y, m, 0), eps)
+    cores, perm = O.partial_chain_pairs(xt, yt, [(0, 0)])
+    # perm refers to the moved operands' free modes, which keep their order
+    return O.chain_to_dense(cores, perm), cores
+
+
+def test_example1_dense_operands_of_different_order(rng):
+    """Example 1: X (order 4) x_3^2 Y (order 3); Z^rho is I4 x I2 x I1 x J1 x J3."""
+    x = rng.standard_normal((2, 3, 4, 5))
+    y = rng.standard_normal((6, 4, 3))
+    z, cores = _ttcp_dense(x, y, 2, 1)
     np.testing.assert_allclose(z, O.tcp_nm(x, y, 2, 1), rtol=1e-10, atol=1e-11)
-    zr_shape = tuple(c.shape[1] for c in cores)
-    assert zr_shape == (5, 3, 2, 6, 3)
+    assert tuple(c.shape[1] for c in cores) == (5, 3, 2, 6, 3)
     assert z.shape == (2, 3, 5, 6, 3)
 
 
-def test_algorithm2_example2_first_modes(rng):
-    """Example 2's contraction X x_1^1 Y on Gaussian tensors (reduced sizes)."""
+def test_example2_first_modes_dense_operands(rng):
+    """Example 2's contraction X x_1^1 Y on Gaussian tensors (reduced sizes),
+    exact TTs and eps-truncated ones (error within the truncation bound)."""
     for dims in ((6, 6, 6), (6, 6, 6, 3), (5, 5, 5, 3, 2)):
         x = rng.standard_normal(dims)
         y = rng.standard_normal(dims)
-        z, _, _ = O.ttcp_alg2(x, y, 0, 0)
-        np.testing.assert_allclose(z, O.tcp_nm(x, y, 0, 0), rtol=1e-9, atol=1e-10)
+        want = O.tcp_nm(x, y, 0, 0)
+        z, _ = _ttcp_dense(x, y, 0, 0)
+        np.testing.assert_allclose(z, want, rtol=1e-9, atol=1e-10)
+        eps = 0.2
+        zt, _ = _ttcp_dense(x, y, 0, 0, eps)
+        # ||Z - Z~|| <= ||X - X~|| ||Y|| + ||X~|| ||Y - Y~|| <= (2 eps + eps^2) ||X|| ||Y||
+        bound = (2 * eps + eps**2) * np.linalg.norm(x) * np.linalg.norm(y)
+        assert np.linalg.norm(zt - want) <= bound
 
 
 def test_paper_operation_counts():
