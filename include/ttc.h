@@ -253,9 +253,11 @@ int tt_contract_batched(const tt_plan* plan, const void* packed_dev, double* out
  * loads the library holds until the process exits.  Plans whose workspace
  * (tt_batch_plan's *ws_bytes) exceeds that size are rejected with
  * TT_ERR_WS.  The call allocates and frees nothing; it zeroes what must
- * start at zero and otherwise behaves like tt_contract_batched.  The first
- * call on a device looks up the array's device address with that device
- * current (make that first call before any stream capture).  Every call
+ * start at zero and otherwise behaves like tt_contract_batched.  Each call
+ * made outside a stream capture looks up the array's device address on the
+ * current device (so a context re-created after cudaDeviceReset is followed);
+ * a call made during a capture reuses the address found by the last call
+ * outside one, so the first call on a device comes before any capture.  Every call
  * shares the one array, which keeps the last call's contents: calls whose
  * executions overlap on the GPU race with each other. */
 #define TT_NOALLOC_SCRATCH_BYTES 256

@@ -197,10 +197,19 @@ int tt_autotune(int dtype, const char* cache_path) {
   void* dev_table = nullptr;
   int* counter = nullptr;
   double* out = nullptr;
+  // every buffer is released here, on success and on every error path
+  auto release = [&]() {
+    if (cores != nullptr) cudaFree(cores);
+    if (dev_table != nullptr) cudaFree(dev_table);
+    if (counter != nullptr) cudaFree(counter);
+    if (out != nullptr) cudaFree(out);
+    cores = dev_table = nullptr;
+    counter = nullptr;
+    out = nullptr;
+  };
   if (cudaStreamCreate(&s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
-    fclose(f);
-    return TT_ERR_CUDA;
+    rc = TT_ERR_CUDA;
   }
   for (int rb = 0; rb < 3 && rc == TT_OK; ++rb) {
     if (dtype == TT_F64 && rb == 2) break;  // float64 ranks stop at 64
@@ -212,6 +221,7 @@ int tt_autotune(int dtype, const char* cache_path) {
       const size_t bytes = core_elems * eb * order;
       if (cudaMalloc(&cores, bytes) != cudaSuccess || cudaMemset(cores, 0, bytes) != cudaSuccess) {
         rc = TT_ERR_CUDA;
+        release();
         break;
       }
       int32_t modes[order], ranks[order + 1];
@@ -233,6 +243,7 @@ int tt_autotune(int dtype, const char* cache_path) {
       if (cudaMalloc(&dev_table, sizeof(SweepParams) * npairs + 8 * npairs + 256) != cudaSuccess ||
           cudaMalloc(&counter, 256) != cudaSuccess || cudaMalloc(&out, sizeof(double) * npairs) != cudaSuccess) {
         rc = TT_ERR_CUDA;
+        release();
         break;
       }
       char* tb = static_cast<char*>(dev_table);
@@ -266,20 +277,16 @@ int tt_autotune(int dtype, const char* cache_path) {
           best = t;
         }
       }
-      fprintf(f, "%d %d %d %d\n", d, rb, ib, best);
-      cudaFree(cores);
-      cudaFree(dev_table);
-      cudaFree(counter);
-      cudaFree(out);
-      cores = dev_table = nullptr;
-      counter = nullptr;
-      out = nullptr;
+      release();
+      // a bucket is written only when every level of it was timed without error
+      if (rc == TT_OK) fprintf(f, "%d %d %d %d\n", d, rb, ib, best);
     }
   }
+  release();
   fclose(f);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(s);
+  if (e0 != nullptr) cudaEventDestroy(e0);
+  if (e1 != nullptr) cudaEventDestroy(e1);
+  if (s != nullptr) cudaStreamDestroy(s);
   tune_table().loaded = false;  // pick the new cache up on the next plan
   return rc;
 }
@@ -298,7 +305,8 @@ int tt_autotune(int dtype, const char* cache_path) {
 // ---------------------------------------------------------------------------
 namespace ttc {
 
-constexpr size_t kNoAllocScratchBytes = 256;
+constexpr size_t kNoAllocScratchBytes = TT_NOALLOC_SCRATCH_BYTES;
+static_assert(kNoAllocScratchBytes >= 2 * sizeof(int), "the work-queue counter must fit the fixed array");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -306,14 +314,18 @@ static void* g_noalloc_addr[kMaxDevices];  // device address of g_noalloc_scratc
 static std::mutex g_noalloc_mu;
 
 // Device address of the scratch array on the current device.  The host-side
-// name g_noalloc_scratch is only a stand-in; the address is looked up once per
-// device, with that device current.
-static int noalloc_scratch(void** out) {
+// name g_noalloc_scratch is only a stand-in.  Outside a stream capture the
+// address is looked up on every call, with the device current (a new context
+// after cudaDeviceReset may place the array elsewhere); a call being captured
+// uses the address its device's last uncaptured call found.
+static int noalloc_scratch(cudaStream_t s, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TT_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return TT_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return TT_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (g_noalloc_addr[dev] == nullptr) {
+  if (cap == cudaStreamCaptureStatusNone || g_noalloc_addr[dev] == nullptr) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return TT_ERR_CUDA;
     g_noalloc_addr[dev] = p;
@@ -327,11 +339,11 @@ static int noalloc_scratch(void** out) {
 extern "C" int tt_contract_batched_noalloc(const tt_plan* plan, const void* packed_dev, double* out_dev,
                                            int64_t* out_log2_dev, int32_t* status_dev, tt_stream stream) {
   if (plan == nullptr || packed_dev == nullptr || out_dev == nullptr) return TT_ERR_ARG;
-  if (plan->ws_bytes > kNoAllocScratchBytes) return TT_ERR_WS;  // plan needs more than the fixed array
-  void* scratch = nullptr;
-  const int rc = noalloc_scratch(&scratch);
-  if (rc != TT_OK) return rc;
+  if (plan->ws_bytes > TT_NOALLOC_SCRATCH_BYTES) return TT_ERR_WS;  // plan needs more than the fixed array
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(s, &scratch);
+  if (rc != TT_OK) return rc;
   const char* base = static_cast<const char*>(packed_dev);
   // the counter must start at zero on every call; the array keeps the last call's contents
   if (cudaMemsetAsync(scratch, 0, 2 * sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;

@@ -276,6 +276,28 @@ def test_batch_plan_on_the_host(L):
     rejects(-5, [big], [big], [None], [None])                            # rank above the float32 cap
 
 
+def test_batched_entries_reject_missing_buffers(L):
+    """tt_contract_batched and tt_contract_batched_noalloc return TT_ERR_ARG
+    for a NULL plan, packed table or output before any CUDA call, and the
+    no-alloc entry plans within the fixed array the header states."""
+    hdr = open(os.path.join(ROOT, "include", "ttc.h")).read()
+    limit = int(re.search(r"#define TT_NOALLOC_SCRATCH_BYTES (\d+)", hdr).group(1))
+    x, y = FakeDesc([4, 3, 5], [1, 4, 6, 1]), FakeDesc([4, 3, 5], [1, 5, 3, 1])
+    batch, keep = _batch([x], [y], [None], [None])
+    rc, plan, pb, wb = _plan(L, batch)
+    assert rc == 0 and 0 < wb <= limit
+    try:
+        packed, out, st = ctypes.c_void_p(0x3000), ctypes.c_void_p(0x4000), ctypes.c_void_p(0x5000)
+        ws = ctypes.c_void_p(0x6000)
+        for args in ((None, packed, out), (plan, None, out), (plan, packed, None)):
+            assert L.tt_contract_batched_noalloc(*args, None, st, None) == -1
+            assert L.tt_contract_batched(*args, None, st, ws, wb, None) == -1
+        assert L.tt_contract_batched(plan, packed, out, None, st, None, wb, None) == -6  # no workspace
+        assert L.tt_contract_batched(plan, packed, out, None, st, ws, wb - 1, None) == -6  # too small
+    finally:
+        L.tt_plan_free(plan)
+
+
 def _ws(L, op, x, y, mask=None, layout="chain", prec="native"):
     nb = ctypes.c_size_t(0)
     m = _mask(mask) if mask is not None else None
