@@ -178,6 +178,56 @@ class ClockSampler:
         }
 
 
+def _oracle_pair_seconds(p):
+    """Worker of the batched CPU baseline: host time of the float64 oracle on
+    pair p of the uneven batch (its cores drawn on the host from the pair's
+    seed; drawing is not timed)."""
+    import oracle as O
+
+    spec, x, y = G.batch_pair(p, 0, np.float64)
+    t0 = time.perf_counter()
+    if spec["kind"] == "full":
+        O.contract_full(x, y)
+    else:
+        O.partial_chain(x, y, spec["mask"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_batched(stride=2, n_pairs=4096):
+    """The float64 oracle over every `stride`-th pair of the 4096-pair batch,
+    the pairs spread over every host core by a process pool (spawned: the
+    calling process already holds a CUDA context).  The rate for the whole
+    batch is the sample's wall time scaled by the batch's flops over the
+    sample's (the flop model of the benchmark)."""
+    import multiprocessing as mp
+
+    specs = G.batch4096_spec(n_pairs, 0)
+
+    def flops_of(sp):
+        if sp["kind"] == "full":
+            return W.full_flops(sp["modes"], sp["ranks_x"], sp["ranks_y"])
+        return W.partial_chain_flops(sp["modes"], sp["ranks_x"], sp["ranks_y"], sp["mask"])
+
+    sample = list(range(0, n_pairs, stride))
+    f_all = sum(flops_of(sp) for sp in specs)
+    f_sample = sum(flops_of(specs[p]) for p in sample)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_pair_seconds, sample[: 2 * cores])  # workers started and warm
+        t0 = time.perf_counter()
+        per_pair = pool.map(_oracle_pair_seconds, sample, chunksize=1)
+        wall = time.perf_counter() - t0
+    batch_s = wall * f_all / f_sample
+    return {
+        "value": n_pairs / batch_s,
+        "unit": "contractions/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"every {stride}th pair ({len(sample)} of {n_pairs}, {f_sample / f_all:.1%} of the batch's flops) in {wall:.1f} s wall on {cores} host processes (one thread each); {sum(per_pair):.1f} s of oracle time; rate scaled to the whole batch by flops",
+    }
+
+
 def cpu_baseline(seconds=10.0):
     """The float64 oracle, as it stands, on the same pair (one host thread)."""
     import oracle as O
@@ -279,6 +329,16 @@ def dist_env():
     return rank, world, local
 
 
+def step_config(world):
+    """The `config` of both arms' JSON lines (same keys and values)."""
+    return {
+        "workload": WORKLOAD,
+        "seed": 0,
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "replicas" if world > 1 else "none",
+    }
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -289,11 +349,16 @@ def run_reference(args):
     for _ in range(args.warmup):
         O.contract_full(x, y)
         O.partial_chain(x, y, MASK)
-    t0 = time.perf_counter()
+    # the host caches are flushed between timed steps too (a 256 MiB write),
+    # outside the timed region
+    flush = np.empty(256 << 20, dtype=np.uint8)
+    dt = 0.0
     for _ in range(args.steps):
+        flush.fill(1)
+        t0 = time.perf_counter()
         O.contract_full(x, y)
         O.partial_chain(x, y, MASK)
-    dt = time.perf_counter() - t0
+        dt += time.perf_counter() - t0
     val = 2 * args.steps / dt
     line = {
         "impl": "reference",
@@ -309,13 +374,13 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "seed": 0},
+        "config": step_config(world),
         "cpu_baseline": {
             "value": val,
             "unit": UNIT,
             "cores": 1,
             "kind": "oracle",
-            "sample": f"{args.steps} steps of the full workload, numpy float64 oracle, one host thread",
+            "sample": f"{args.steps} steps of the full workload, numpy float64 oracle, one host thread on rank 0 (host caches flushed between steps)",
         },
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -504,12 +569,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {
-                "workload": WORKLOAD,
-                "seed": 0,
-                "l2": "flushed between timed steps (256 MiB write)",
-                "parallelism": "replicas" if world > 1 else "single GPU",
-            },
+            "config": step_config(world),
             "gflops": (f_full + f_part) / (ms / 1e3) / 1e9,
             "roofline": {
                 "kernel": "sweep_two_sided_kernel<float,64> (full contraction, two clusters from both ends)",
@@ -633,6 +693,8 @@ def bench_batched(T, dev, args):
     }
     del g, bat, pairs
     torch.cuda.empty_cache()
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batched()
     return out
 
 

@@ -456,22 +456,10 @@ __device__ void run_pair(const SweepParams& p, const SweepOut& o, unsigned char*
   }
   __syncthreads();  // the phase table is complete
 
-  // ---- start environment, in the layout of the first phase ----
+  // ---- start environment: [1] (either layout) ----
   int64_t log2s = 0;
   int bad = 0;
-  {
-    const int lay = ng > 0 ? layout_of(geo[0]) : 1;
-    if (p.e_in == nullptr) {
-      if (tid == 0) Ein[0] = T(1);
-    } else {
-      const T* e = static_cast<const T*>(p.e_in);
-      for (int idx = tid; idx < p.rx0 * p.ry0; idx += NT) {
-        const int a = idx / p.ry0, b = idx - a * p.ry0;
-        Ein[lay == 0 ? b * LDE + a : a * LDE + b] = e[idx];
-      }
-      if (p.e_in_log2 != nullptr) log2s = *p.e_in_log2;
-    }
-  }
+  if (tid == 0) Ein[0] = T(1);
 
   Pipe<T> pipe;
   pipe.st0 = st0;

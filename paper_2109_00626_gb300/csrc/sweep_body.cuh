@@ -293,12 +293,6 @@ struct SweepOut {
   double* z_out;
   int64_t* z_out_log2;
   int32_t* status;
-  // Optional per-call start / final environment (override p.e_in / p.e_out);
-  // with fold_e_out the final environment is written with its power-of-two
-  // scale multiplied back in.
-  const void* e_in = nullptr;
-  void* e_out = nullptr;
-  int fold_e_out = 0;
   int skip_copies = 0;  // the free-core copies are done elsewhere (batched launch)
 };
 
@@ -338,18 +332,8 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   int64_t log2s = 0;
   int bad = 0;
 
-  // ---- start environment ----
-  const void* e_in = o.e_in != nullptr ? o.e_in : p.e_in;
-  if (e_in == nullptr) {
-    if (tid == 0) Es[0] = T(1);
-  } else {
-    const T* e = static_cast<const T*>(e_in);
-    for (int idx = tid; idx < p.rx0 * p.ry0; idx += NT) {
-      const int a = idx / p.ry0, b = idx - a * p.ry0;
-      Es[b * LD + a] = e[idx];
-    }
-    if (p.e_in_log2 != nullptr) log2s = *p.e_in_log2;
-  }
+  // ---- start environment: [1] (the trains start and end with rank 1) ----
+  if (tid == 0) Es[0] = T(1);
 
   for (int q = tid; q < p.n_steps; q += NT) sst[q] = p.step[q];
   if constexpr (Cfg::PUSH) {
@@ -782,22 +766,13 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
 
   const int kx = p.n_steps > 0 ? p.step[p.n_steps - 1].rout_x : p.rx0;
   const int ky = p.n_steps > 0 ? p.step[p.n_steps - 1].rout_y : p.ry0;
-  void* e_out = o.e_out != nullptr ? o.e_out : p.e_out;
-  if (crank == 0 && e_out != nullptr) {
-    T* e = static_cast<T*>(e_out);
-    int fbits = 0;
+  if (crank == 0 && p.e_out != nullptr) {
+    T* e = static_cast<T*>(p.e_out);
     for (int idx = tid; idx < kx * ky; idx += NT) {
       const int u = idx / ky, v = idx - u * ky;
-      T val = Es[v * LD + u];
-      if (o.fold_e_out && log2s != 0) {
-        const T v0 = val;
-        val = scale_pow2_sat<T>(val, log2s);
-        if (isfinite(v0) && !isfinite(val)) fbits |= TT_STATUS_OVERFLOW;
-      }
-      e[idx] = val;
+      e[idx] = Es[v * LD + u];
     }
-    if (fbits) set_status(o.status, fbits);
-    if (tid == 0 && p.e_out_log2 != nullptr && o.e_out == nullptr) *p.e_out_log2 = log2s;
+    if (tid == 0 && p.e_out_log2 != nullptr) *p.e_out_log2 = log2s;
   }
 
   if (p.emit.enabled) {

@@ -95,9 +95,7 @@ struct SweepParams {
   int final_scalar;       // 1 = the last step ends at a 1x1 environment summed in float64
   int renorm_bits;
   SweepStep step[kMaxOrder];
-  const void* e_in;       // optional start environment [rx0][ry0], row-major
-  const int64_t* e_in_log2;
-  int rx0, ry0;           // shape of the start environment (1x1 when e_in is NULL)
+  int rx0, ry0;           // shape of the start environment [1] (both 1)
   void* e_out;            // optional final environment [rx][ry], row-major
   int64_t* e_out_log2;    // scale of e_out (written when e_out is set)
   double* z_out;          // final scalar (final_scalar == 1)

@@ -24,6 +24,11 @@ def test_reference_arm_json_line():
     assert line["steps"] == 3 and line["warmup"] == 3 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    # the same config keys and values as the GPU arm's line at the same N
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert line["config"] == bench.step_config(1)
 
 
 def test_accuracy_report_of_the_headline_step():
