@@ -290,16 +290,18 @@ def tc_accuracy(results):
     exponent) against the float64 oracle on the order-16 rank-256 pair, as
     eps = |z - z*| / (||X|| ||Y||) on the float32 cores (end to end) and, for
     the bfloat16 form, on the bfloat16-rounded cores it reads (arithmetic
-    error); with kappa and the bound the tests hold each form to."""
+    error); with kappa and the bound the tests hold each form to (the
+    rounding-error model's 8 sigma plus twice its coherent bias, relative to
+    |z*| of the cores the form reads)."""
     import oracle as O
     import torch
+    from oracle import error_model as M
 
     x, y = G.order16_r256(0)
     x64 = [c.astype(np.float64) for c in x]
     y64 = [c.astype(np.float64) for c in y]
     z32 = O.contract_full(x64, y64)
     nrm = math.sqrt(O.contract_full(x64, x64) * O.contract_full(y64, y64))
-    n = len(x)
 
     def fin(v):
         return float(v) if math.isfinite(v) else None
@@ -312,12 +314,16 @@ def tc_accuracy(results):
             "eps_vs_fp32_cores": fin(abs(z - z32) / nrm),
             "rel_vs_fp32_cores": fin(abs(z - z32) / abs(z32)),
             "kappa": fin(nrm / abs(z32)),
-            "bound_eps": 2 * n * 2.0 ** (-8 if prec == "native" else -15),
         }
         if prec == "native":
             xb = [torch.from_numpy(c).bfloat16().double().numpy() for c in x]
             yb = [torch.from_numpy(c).bfloat16().double().numpy() for c in y]
-            rep["eps_vs_bf16_cores"] = fin(abs(z - O.contract_full(xb, yb)) / nrm)
+            z16 = O.contract_full(xb, yb)
+            rep["eps_vs_bf16_cores"] = fin(abs(z - z16) / nrm)
+            rep["rel_vs_bf16_cores"] = fin(abs(z - z16) / abs(z16))
+            rep["bound_rel"] = fin(M.tc_bound(xb, yb, "bf16", z16) / abs(z16))
+        else:
+            rep["bound_rel"] = fin(M.tc_bound(x64, y64, "bf16x3", z32) / abs(z32))
         out[prec] = rep
     return out
 

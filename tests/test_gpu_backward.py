@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import to_dev, to_host
+from helpers import grad_cs_eps, grad_cs_scale, to_dev, to_host
 from paper_2109_00626_gb300 import inputs as G
 
 pytestmark = pytest.mark.gpu
@@ -22,6 +22,12 @@ def _rel(got, want):
     num = max(float(np.abs(g - w).max()) for g, w in zip(got, want))
     den = max(float(np.abs(w).max()) for w in want)
     return num / den
+
+
+# float32 gradients: within 1e-5 of the largest oracle gradient (every core of
+# both operands); the full-contraction gradients also within 1e-5 of their
+# per-entry Cauchy-Schwarz scale.  float64: 1e-12.
+F32_TOL = 1e-5
 
 
 def test_full_grad_fd_fp64():
@@ -80,7 +86,10 @@ def test_full_grad_order10_fp32_checkpoint_strides(stride):
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     wx, wy = O.grad_full(x, y)
-    assert _rel(to_host(gx) + to_host(gy), wx + wy) <= 2e-5
+    got = to_host(gx) + to_host(gy)
+    rel, cs = _rel(got, wx + wy), grad_cs_eps(got, wx + wy, grad_cs_scale(x, y))
+    print(f"order10 grads stride {stride}: rel={rel:.2e} cs_eps={cs:.2e}")
+    assert rel <= F32_TOL and cs <= F32_TOL
 
 
 def _sum_cotangents(zc):
@@ -116,7 +125,9 @@ def test_partial_grad_order12_sum_fp32():
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     wx, wy = O.grad_partial_chain(x, y, mask, dz)
-    assert _rel(to_host(gx) + to_host(gy), wx + wy) <= 2e-5
+    rel = _rel(to_host(gx) + to_host(gy), wx + wy)
+    print(f"order12 partial grads: rel={rel:.2e}")
+    assert rel <= F32_TOL
 
 
 def test_autograd_sum_of_partial_fp32():
@@ -135,7 +146,9 @@ def test_autograd_sum_of_partial_fp32():
     dz = _sum_cotangents(zo)
     wx, wy = O.grad_partial_chain(x, y, mask, dz)
     got = [c.grad.detach().cpu().double().numpy() for c in xd + yd]
-    assert _rel(got, wx + wy) <= 2e-5
+    rel = _rel(got, wx + wy)
+    print(f"autograd order12: rel={rel:.2e}")
+    assert rel <= F32_TOL
 
 
 def test_autograd_gradcheck_full_fp64():
@@ -163,7 +176,9 @@ def test_partial_grad_uneven_ranks_fp32(lead):
     assert int(st.item()) == 0
     wx, wy = O.grad_partial_chain(x, y, mask, [d.astype(np.float64) for d in dz])
     gxh, gyh = to_host(gx), to_host(gy)
-    assert _rel(gxh + gyh, wx + wy) <= 2e-5
+    rel = _rel(gxh + gyh, wx + wy)
+    print(f"chain grads: rel={rel:.2e}")
+    assert rel <= F32_TOL
     n, s = len(modes), 3
     free_x = range(s + 1, n) if lead else range(0, n - s - 1)  # the boundary core is X's s (lead) / n-s-1 (trail)
     free_y = range(s, n) if lead else range(0, n - s)
@@ -206,7 +221,9 @@ def test_partial_k_kept_for_backward(dt, lead):
         gx, gy, st = T.backward(xd, yd, mask, dz=dzd, fwd_ws=kept)
         torch.cuda.synchronize()
         assert int(st.item()) == 0
-        assert _rel(to_host(gx) + to_host(gy), wx + wy) <= (2e-5 if dt == np.float32 else 1e-12)
+        rel = _rel(to_host(gx) + to_host(gy), wx + wy)
+        print(f"{dt.__name__} grads: rel={rel:.2e}")
+        assert rel <= (F32_TOL if dt == np.float32 else 1e-12)
 
 
 @pytest.mark.parametrize(
@@ -235,8 +252,10 @@ def test_full_grad_rank1_y(dt, rx, scale):
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     wx, wy = O.grad_full(x, y, cot=-1.5)
-    assert _rel(to_host(gx), wx) <= (2e-5 if dt == np.float32 else 1e-12)
-    assert _rel(to_host(gy), wy) <= (2e-5 if dt == np.float32 else 1e-12)
+    rx_, ry_ = _rel(to_host(gx), wx), _rel(to_host(gy), wy)
+    print(f"{dt.__name__} grads: rel x {rx_:.2e} y {ry_:.2e}")
+    assert rx_ <= (F32_TOL if dt == np.float32 else 1e-12)
+    assert ry_ <= (F32_TOL if dt == np.float32 else 1e-12)
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
@@ -252,5 +271,7 @@ def test_full_grad_rank1_y_short_trains(dt, modes, rx):
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     wx, wy = O.grad_full(x, y, cot=0.75)
-    tol = 2e-5 if dt == np.float32 else 1e-12
-    assert _rel(to_host(gx), wx) <= tol and _rel(to_host(gy), wy) <= tol
+    tol = F32_TOL if dt == np.float32 else 1e-12
+    rx_, ry_ = _rel(to_host(gx), wx), _rel(to_host(gy), wy)
+    print(f"{dt.__name__} grads: rel x {rx_:.2e} y {ry_:.2e}")
+    assert rx_ <= tol and ry_ <= tol

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from helpers import norm_scale, to_dev, to_host
+from helpers import dense_cs_eps, norm_scale, to_dev, to_host
 from paper_2109_00626_gb300 import inputs as G
 
 pytestmark = pytest.mark.gpu
@@ -66,14 +66,29 @@ def test_merged_secondary_fp32():
         mask[int(k)] = 1
     op, got = _run(x, y, mask)
     assert int(op.status.item()) == 0
-    want, _ = O.partial_merged(x, y, mask)
-    for g, w in zip(got, want):
-        w = w.reshape(g.shape)
-        assert np.abs(g - w).max() <= 1e-5 * max(np.abs(w).max(), 1e-30) * 10
+    want, perm = O.partial_merged(x, y, mask)
+    _f32_check(x, y, mask, got, want, perm)
 
 
 def _rel_err(got, want):
     return max(np.abs(g - w.reshape(g.shape)).max() / max(np.abs(w).max(), 1e-300) for g, w in zip(got, want))
+
+
+def _f32_check(x, y, mask, got, want, perm):
+    """float32 merged cores: the represented tensor within 1e-5 of the
+    per-entry Cauchy-Schwarz scale of Eq. 8's Z (the float64 oracle's dense
+    result on the same float32 cores), and every core within 1e-5 of its
+    largest entry (the library and the oracle fold the environments into the
+    same cores)."""
+    x64 = [np.asarray(c, dtype=np.float64) for c in x]
+    y64 = [np.asarray(c, dtype=np.float64) for c in y]
+    contracted = [k for k in range(len(x)) if mask[k]]
+    dense = O.merged_to_dense([g.reshape(w.shape) for g, w in zip(got, want)], perm)
+    ref = O.tcp(O.tt_to_dense(x64), O.tt_to_dense(y64), contracted)
+    eps = dense_cs_eps(dense, ref, x64, y64, contracted)
+    rel = _rel_err(got, want)
+    print(f"merged {''.join(map(str, mask))}: cs_eps={eps:.2e} core_rel={rel:.2e}")
+    assert eps <= 1e-5 and rel <= 1e-5
 
 
 @pytest.mark.parametrize("mask", [[int(b) for b in format(v, "06b")] for v in range(64) if bin(v).count("1") == 3])
@@ -86,7 +101,7 @@ def test_merged_all_three_of_six_fp32(mask):
     assert int(op.status.item()) == 0
     want, perm = O.partial_merged(x, y, mask)
     assert op.perm == perm
-    assert _rel_err(got, want) <= 2e-5
+    _f32_check(x, y, mask, got, want, perm)
 
 
 @pytest.mark.parametrize("mask", [[0, 1, 1, 1, 0, 1, 0], [0, 0, 1, 1, 1, 1, 0], [1, 0, 1, 1, 0, 1, 1], [0, 1, 1, 1, 1, 1, 1]])
@@ -105,7 +120,7 @@ def test_merged_long_runs_fp64(mask):
     assert np.abs(dense - ref).max() <= 1e-12 * norm_scale(x, y)
 
 
-@pytest.mark.parametrize("dtype,tol", [(np.float32, 2e-5), (np.float64, 1e-12)])
+@pytest.mark.parametrize("dtype,tol", [(np.float32, None), (np.float64, 1e-12)])
 def test_merged_rank24_interior_run(dtype, tol):
     """Ranks 24 (the transfer matrix has 576 rows of 576), a two-mode interior
     run after an interior free core, and a free core after it."""
@@ -116,8 +131,11 @@ def test_merged_rank24_interior_run(dtype, tol):
     mask = [1, 0, 1, 1, 0]
     op, got = _run(x, y, mask)
     assert int(op.status.item()) == 0
-    want, _ = O.partial_merged(x, y, mask)
-    assert _rel_err(got, want) <= tol
+    want, perm = O.partial_merged(x, y, mask)
+    if tol is None:
+        _f32_check(x, y, mask, got, want, perm)
+    else:
+        assert _rel_err(got, want) <= tol
 
 
 @pytest.mark.parametrize("mask", [[1, 0, 1, 1, 1, 1, 0], [0, 0, 1, 1, 1, 1, 0]])
@@ -142,9 +160,9 @@ def test_merged_run_scales_beyond_float32(mask):
     y32 = [c.astype(np.float32) for c in y]
     op, got = _run(x32, y32, mask)
     assert int(op.status.item()) == 0
-    want, _ = O.partial_merged([c.astype(np.float64) for c in x32], [c.astype(np.float64) for c in y32], mask)
+    want, perm = O.partial_merged([c.astype(np.float64) for c in x32], [c.astype(np.float64) for c in y32], mask)
     assert all(np.isfinite(g).all() for g in got)
-    assert _rel_err(got, want) <= 2e-5
+    _f32_check(x32, y32, mask, got, want, perm)
 
 
 def test_merged_zero_rows_of_transfer():
@@ -186,7 +204,7 @@ def test_merged_unequal_free_modes_fp64(mask):
     assert np.abs(dense - ref).max() <= 1e-12 * norm_scale(x, y)
 
 
-@pytest.mark.parametrize("dtype,tol", [(np.float32, 2e-5), (np.float64, 1e-12)])
+@pytest.mark.parametrize("dtype,tol", [(np.float32, None), (np.float64, 1e-12)])
 def test_merged_transfer_slice_chunks(dtype, tol):
     """A run mode of ranks 64 -> 64 with 16 slices: the transfer kernel's slice
     products do not fit shared memory at once and go in chunks (8 slices in
@@ -199,5 +217,8 @@ def test_merged_transfer_slice_chunks(dtype, tol):
     mask = [0, 1, 1, 1, 0, 0]
     op, got = _run(x, y, mask)
     assert int(op.status.item()) == 0
-    want, _ = O.partial_merged(x, y, mask)
-    assert _rel_err(got, want) <= tol
+    want, perm = O.partial_merged(x, y, mask)
+    if tol is None:
+        _f32_check(x, y, mask, got, want, perm)
+    else:
+        assert _rel_err(got, want) <= tol
