@@ -555,6 +555,8 @@ def run_ours(args):
     status = int(full.status.item()) | int(part.status.item()) | int(full2.status.item()) | int(part2.status.item())
     forms = {}
     if not args.no_forms:
+        forms["tf32x3"] = bench_step_prec(T, dev, args, "tf32x3")
+        forms["tf32"] = bench_step_prec(T, dev, args, "tf32")
         forms["batched"] = bench_batched(T, dev, args)
         forms["bf16"] = bench_bf16(T, dev, args, "native")
         forms["bf16x3"] = bench_bf16(T, dev, args, "bf16x3")
@@ -618,6 +620,130 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def tf32_peak_tflops():
+    """Dense tf32 tensor peak: the measured bf16 burst peak times the nominal
+    tf32 / bf16 ratio of the part (1.1 / 2.25 PFLOP/s dense)."""
+    return _bf16_peak()[0] * 1.1 / 2.25
+
+
+def tf32_issued_flops(x, y, mask=None):
+    """Tensor-core flops the tf32x3 sweep issues for a full contraction (mask
+    None: every mode but the last) or a chain partial one (the contracted
+    modes and the boundary core): per slice, GEMM 1 and GEMM 2 of 128 x 64 x
+    (8 ceil(K / 8)) in two passes."""
+    n = len(x)
+    if mask is None:
+        modes = list(range(n - 1))
+        extra = []
+    else:
+        side, s = W.end_block(mask)
+        modes = list(range(s)) if side == "lead" else list(range(n - s, n))
+        extra = [s if side == "lead" else n - s - 1]
+    tot = 0
+    for k in modes:
+        i_dim = x[k].shape[1]
+        k1 = -(-y[k].shape[0] // 8)
+        k2 = -(-x[k].shape[0] // 8)
+        tot += i_dim * 2 * 2 * 128 * 64 * 8 * (k1 + k2)
+    for k in extra:
+        tot += x[k].shape[1] * 2 * 2 * 128 * 64 * 8 * -(-x[k].shape[0] // 8)
+    return tot
+
+
+def bench_step_prec(T, dev, args, prec):
+    """The headline step (full and partial contraction of the order-10 pair,
+    side by side on two streams, L2 flushed between steps) with the products
+    of `prec` on the tensor cores; CUDA events on the launching streams; the
+    full contraction's launch timed alone for its roofline; accuracy against
+    the float64 oracle on the same float32 cores."""
+    import torch
+
+    import oracle as O
+
+    x, y = G.order10_r64(0, np.float32)
+    xd = [torch.from_numpy(c).to(dev) for c in x]
+    yd = [torch.from_numpy(c).to(dev) for c in y]
+    full = T.FullContraction(xd, yd, prec=prec)
+    part = T.PartialContraction(xd, yd, MASK, prec=prec)
+    stream = torch.cuda.current_stream(dev)
+    side = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(evs=None):
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        side.wait_event(fork)
+        if evs is not None:
+            evs[0].record(side)
+        full(side)
+        if evs is not None:
+            evs[1].record(side)
+        part(stream)
+        join = torch.cuda.Event()
+        join.record(side)
+        stream.wait_event(join)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for k in range(K):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step(ev[k][2:4])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
+    full_ms = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(K))
+    f_full, f_part, _, _ = work_per_step()
+    issued = tf32_issued_flops(x, y)
+    peak = tf32_peak_tflops()
+    out = {
+        "workload": WORKLOAD + "; products on the tensor cores (" + prec + ")",
+        "value": 2 / (ms / 1e3),
+        "unit": UNIT,
+        "ms_per_step": ms,
+        "ms_full": full_ms,
+        "gflops": (f_full + f_part) / (ms / 1e3) / 1e9,
+        "roofline": {
+            "kernel": "tf_two_sided_kernel<%s> (full contraction, two clusters from both ends)"
+                      % ("true" if prec == "tf32x3" else "false"),
+            "bound": "tensor",
+            "achieved": issued / (full_ms / 1e3) / 1e12,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": issued / (full_ms / 1e3) / 1e12 / peak,
+            "note": "tensor flops issued (128 x 64 tiles, hi and lo stacked, two passes) per launch over its CUDA-event "
+                    "time; peak = measured bf16 burst x 1.1 / 2.25 (nominal dense tf32 / bf16); latency-bound single "
+                    "contraction",
+        },
+        "device_status": int(full.status.item()) | int(part.status.item()),
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+    if not args.no_cpu_baseline:
+        try:
+            x64 = [c.astype(np.float64) for c in x]
+            y64 = [c.astype(np.float64) for c in y]
+            z = float(full.out.item())
+            zs = O.contract_full(x64, y64)
+            nrm = math.sqrt(O.contract_full(x64, x64) * O.contract_full(y64, y64))
+            zc, _ = O.partial_chain(x64, y64, MASK)
+            got = [c.detach().cpu().double().numpy() for c in part.z]
+            c_rel = max(float(np.abs(g - w).max() / np.abs(w).max()) for g, w in zip(got, zc))
+            out["accuracy"] = {
+                "reference": "float64 oracle on the same float32 cores",
+                "full_eps": abs(z - zs) / nrm,
+                "full_rel": abs(z - zs) / abs(zs),
+                "kappa": nrm / abs(zs),
+                "partial_core_rel": c_rel,
+                "bound_eps": 1e-5,
+            }
+        except Exception as e:  # a report, never a reason to lose the measurement line
+            out["accuracy"] = {"error": repr(e)[:200]}
+    return out
 
 
 def bench_batched(T, dev, args):
@@ -964,6 +1090,15 @@ def run_profile_case(case):
             op = T.PartialContraction(xd, yd, m, layout="merged")
             op()
             status |= op.status
+    elif case == "order10_tf32x3":
+        x, y = G.order10_r64(0, np.float32)
+        xd, yd = [torch.from_numpy(c).to(dev) for c in x], [torch.from_numpy(c).to(dev) for c in y]
+        full = T.FullContraction(xd, yd, prec="tf32x3")
+        part = T.PartialContraction(xd, yd, MASK, prec="tf32x3")
+        for _ in range(2):
+            full()
+            part()
+        status = full.status | part.status
     elif case == "batched512":
         _, pairs = G.batch4096_device(512, 0, dev)
         op = T.BatchedContraction(pairs)
@@ -990,7 +1125,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "backward", "merged"],
+    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "order10_tf32x3", "backward", "merged"],
                     default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")
     ap.add_argument("--measure-peaks", action="store_true",

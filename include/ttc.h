@@ -56,8 +56,11 @@ typedef enum { TT_F64 = 0, TT_F32 = 1, TT_BF16 = 2 } tt_dtype;
  *   TT_P_BF16X3  float32 operands split as hi + lo bfloat16 pairs; the
  *                products hi*hi + hi*lo + lo*hi are summed in float32 (tensor
  *                cores), the lo*lo term is dropped.
- *   TT_P_TF32X3  the same split with tf32 pieces. */
-typedef enum { TT_P_NATIVE = 0, TT_P_TF32X3 = 1, TT_P_BF16 = 2, TT_P_BF16X3 = 3 } tt_prec;
+ *   TT_P_TF32X3  float32 operands split as hi = tf32(x) (rounded to nearest)
+ *                and lo = x - hi; all four products hi*hi + hi*lo + lo*hi +
+ *                lo*lo summed in float32 (tensor cores, kind::tf32).
+ *   TT_P_TF32    float32 operands rounded to tf32, float32 sums (tensor cores). */
+typedef enum { TT_P_NATIVE = 0, TT_P_TF32X3 = 1, TT_P_BF16 = 2, TT_P_BF16X3 = 3, TT_P_TF32 = 4 } tt_prec;
 
 /* Layout of a partial contraction's result (see tt_partial_shape). */
 typedef enum { TT_LAYOUT_CHAIN = 0, TT_LAYOUT_MERGED = 1 } tt_layout;
@@ -121,11 +124,13 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
  *                with z = m * 2^e (use this form when |z| may leave the double
  *                range).
  *   status_dev   device int32, see TT_STATUS_*.
- * Precision: TT_P_NATIVE for F64/F32/BF16 storage; TT_P_BF16 and TT_P_BF16X3
- * for F32 storage.  The final sum of the last mode is accumulated in float64.
- * The bfloat16 forms run on the tensor cores and need order >= 3, every
- * interior rank of X equal to 128 or 256 and every interior rank of Y a
- * multiple of 64 up to 256 (TT_ERR_UNSUPPORTED otherwise). */
+ * Precision: TT_P_NATIVE for F64/F32/BF16 storage; TT_P_BF16, TT_P_BF16X3,
+ * TT_P_TF32 and TT_P_TF32X3 for F32 storage.  The final sum of the last mode
+ * is accumulated in float64.  The bfloat16 forms run on the tensor cores and
+ * need order >= 3, every interior rank of X equal to 128 or 256 and every
+ * interior rank of Y a multiple of 64 up to 256; the tf32 forms run the whole
+ * sweep (from both ends with the workspace) on the tensor cores and need every
+ * rank of both operands <= 64 (TT_ERR_UNSUPPORTED otherwise). */
 int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_dev,
                      int64_t* out_log2_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
                      tt_stream stream);
@@ -182,7 +187,9 @@ int tt_partial_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, in
  * enqueue.  TT_ERR_TOO_LARGE when a merged core, its run's transfer matrix or
  * the intermediate P (R^x I R^y' x the next pair rank) exceeds 2^30 entries,
  * or a rank exceeds 128 (F32) / 64 (F64).
- * Precision: TT_P_NATIVE (F64/F32). */
+ * Precision: TT_P_NATIVE (F64/F32); for the chain layout also TT_P_TF32 and
+ * TT_P_TF32X3 on F32 storage with every rank <= 64 (the sweep and the
+ * boundary core C on the tensor cores). */
 int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int layout,
                         int prec, const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev,
                         void* ws, size_t ws_bytes, tt_stream stream);

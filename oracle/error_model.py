@@ -180,3 +180,57 @@ def tc_bound(xc, yc, prec, z_ref, k_sigma=8.0):
     k_sigma predicted standard deviations of the random part, plus twice the
     predicted coherent bias (|z*| times tc_bias)."""
     return k_sigma * tc_error_sigma(xc, yc, prec) + 2.0 * abs(tc_bias(xc, yc, prec)) * abs(z_ref)
+
+
+U_TF32 = 2.0**-11  # unit roundoff of tf32 (11 significant bits)
+
+
+def tf32_rounds(prec):
+    """Roundings of the tf32 tensor-core sweep (every mode but the float64
+    last one of a one-sided full contraction runs on the tensor cores):
+      "tf32":   E, each T_i and every core entry rounded to tf32 (nearest);
+      "tf32x3": each of them held as hi = tf32(x) (nearest) and lo = x - hi,
+                lo read by the tensor core with its low 13 bits dropped (a
+                rounding toward zero to tf32's 11 bits: twice the standard
+                deviation of one to nearest, on a value whose size relative to
+                x has standard deviation rn_std(2^-11)); all four products
+                hi*hi + hi*lo + lo*hi + lo*lo formed.
+    Sums in float32 in both."""
+    if prec == "tf32":
+        s = rn_std(U_TF32)
+        return {"e": s, "t": s, "core": s, "acc": rn_std(U_F32)}
+    if prec == "tf32x3":
+        s = 2.0 * rn_std(U_TF32) ** 2
+        return {"e": s, "t": s, "core": s, "acc": rn_std(U_F32)}
+    raise ValueError(prec)
+
+
+def tf32_modes(n, two_sided):
+    """Modes of an order-n full contraction that run on the tensor cores."""
+    return list(range(n)) if two_sided else list(range(n - 1))
+
+
+def tf32_bias(xc, yc, prec, two_sided, cluster=16):
+    """Predicted coherent relative bias (negative) of the tf32 sweep: every
+    tensor-core mode accumulates T over passes x ceil(R^y_k / 8) steps and P
+    over passes x ceil(R^x_k / 8) steps per slice, ceil(I_k / cluster) slices
+    per CTA; passes = 2 for the split form (the other operand's hi, then lo),
+    1 for tf32."""
+    m = {"tf32": 1, "tf32x3": 2}[prec]
+    rel = 0.0
+    for k in tf32_modes(len(xc), two_sided):
+        rx, i_dim, _ = np.shape(xc[k])
+        ry = np.shape(yc[k])[0]
+        rel += acc_bias_rel(m * -(-ry // 8)) + acc_bias_rel(m * -(-rx // 8) * -(-i_dim // cluster))
+    return -rel
+
+
+def tf32_bound(xc, yc, prec, z_ref, two_sided, cluster=16, k_sigma=8.0):
+    """The tests' bound on |z - z*| for the tf32 forms: k_sigma standard
+    deviations of the random part plus twice the coherent bias."""
+    modes = tf32_modes(len(xc), two_sided)
+    sig = sweep_error_sigma(xc, yc, tf32_rounds(prec), modes)
+    rest = [k for k in range(len(xc)) if k not in modes]
+    if rest:
+        sig = float(np.hypot(sig, sweep_error_sigma(xc, yc, {"acc": rn_std(U_F32)}, rest)))
+    return k_sigma * sig + 2.0 * abs(tf32_bias(xc, yc, prec, two_sided, cluster)) * abs(z_ref)

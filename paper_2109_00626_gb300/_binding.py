@@ -14,13 +14,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libttc.so")
 
 TT_F64, TT_F32, TT_BF16 = 0, 1, 2
-TT_P_NATIVE, TT_P_TF32X3, TT_P_BF16, TT_P_BF16X3 = 0, 1, 2, 3
+TT_P_NATIVE, TT_P_TF32X3, TT_P_BF16, TT_P_BF16X3, TT_P_TF32 = 0, 1, 2, 3, 4
 TT_LAYOUT_CHAIN, TT_LAYOUT_MERGED = 0, 1
 TT_OP_FULL, TT_OP_PARTIAL, TT_OP_BACKWARD = 0, 1, 2
 TT_STATUS_NONFINITE, TT_STATUS_OVERFLOW, TT_STATUS_TIMEOUT = 1, 2, 4
 TT_MAX_ORDER = 64
 
-PREC = {"native": TT_P_NATIVE, "tf32x3": TT_P_TF32X3, "bf16": TT_P_BF16, "bf16x3": TT_P_BF16X3}
+PREC = {"native": TT_P_NATIVE, "tf32x3": TT_P_TF32X3, "bf16": TT_P_BF16, "bf16x3": TT_P_BF16X3, "tf32": TT_P_TF32}
 LAYOUT = {"chain": TT_LAYOUT_CHAIN, "merged": TT_LAYOUT_MERGED}
 
 # Every symbol include/ttc.h declares (checked by the CPU test-suite).

@@ -274,6 +274,7 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
       *bytes = tc_full_ws(x, y, prec, &rc);
       return rc;
     }
+    if (prec != TT_P_NATIVE && prec != TT_P_TF32X3 && prec != TT_P_TF32) return TT_ERR_UNSUPPORTED;
     if (x->order >= 2) *bytes = two_sided_layout(x, y).bytes;  // both-ends sweep
     return TT_OK;
   }
@@ -313,11 +314,30 @@ int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_d
   if (x->dtype == TT_BF16 || prec == TT_P_BF16 || prec == TT_P_BF16X3)
     return tc_full_launch(x, y, prec, out_dev, out_log2_dev, status_dev, ws, ws_bytes,
                           reinterpret_cast<cudaStream_t>(stream));
-  if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+  const bool tf32 = prec == TT_P_TF32X3 || prec == TT_P_TF32;
+  if (prec != TT_P_NATIVE && !tf32) return TT_ERR_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SweepParams p;
   build_full(x, y, out_dev, out_log2_dev, status_dev, &p);
   const int rmax = sweep_max_rank(p);
+  if (tf32) {
+    if (x->dtype != TT_F32) return TT_ERR_DTYPE;
+    if (rmax > kTf32MaxRank) return TT_ERR_UNSUPPORTED;
+    const bool x3 = prec == TT_P_TF32X3;
+    const int want = pow2_floor(std::min(16, sweep_max_mode(p)));
+    const int C = tf32_cluster_size(want);
+    if (C < 1) return TT_ERR_CUDA;
+    if (x->order >= 2 && ws != nullptr && C >= 1) {
+      const TwoSidedLayout L = two_sided_layout(x, y);
+      if (ws_bytes >= L.bytes) {
+        TwoSidedParams tp;
+        build_two_sided(x, y, L, ws, out_dev, out_log2_dev, status_dev, &tp);
+        if (cudaMemsetAsync(tp.counter, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+        return launch_tf32_two_sided(tp, x3, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+      }
+    }
+    return launch_tf32_sweep(p, x3, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
   if (rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
   if (x->order >= 2 && ws != nullptr) {
     // with a workspace, sweep from both ends on two clusters at once
@@ -383,8 +403,10 @@ static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mas
   if (mask == nullptr) return TT_ERR_ARG;
   int rc = check_pair(x, y, mask);
   if (rc != TT_OK) return rc;
-  if (prec != TT_P_NATIVE) return TT_ERR_UNSUPPORTED;
+  const bool tf32 = prec == TT_P_TF32X3 || prec == TT_P_TF32;
+  if (prec != TT_P_NATIVE && !(tf32 && bws == nullptr)) return TT_ERR_UNSUPPORTED;
   if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
+  if (tf32 && x->dtype != TT_F32) return TT_ERR_DTYPE;
   ChainPlan cp;
   rc = chain_plan(x, y, mask, &cp);
   if (rc != TT_OK) return rc;
@@ -405,6 +427,12 @@ static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mas
       p.ckpt_n = (cp.s + c - 1) / c;
       p.ckpt_elems = bp->env_elems;
     }
+  }
+  if (tf32) {
+    if (sweep_max_rank(p) > kTf32MaxRank) return TT_ERR_UNSUPPORTED;
+    const int C = tf32_cluster_size(pow2_floor(std::min(16, sweep_max_mode(p))));
+    if (C < 1) return TT_ERR_CUDA;
+    return launch_tf32_sweep(p, prec == TT_P_TF32X3, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   return launch_sweep(p, x->dtype, s);
 }

@@ -303,6 +303,11 @@ cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_two_sided(const TwoSidedParams& tp, int dtype, int rmax, int cluster, cudaStream_t s);
+// Tensor-core (tf32) sweeps for float32 cores with ranks <= 64 (tf32_sweep.cu).
+constexpr int kTf32MaxRank = 64;
+cudaError_t launch_tf32_sweep(const SweepParams& p, bool x3, int cluster, cudaStream_t s);
+cudaError_t launch_tf32_two_sided(const TwoSidedParams& tp, bool x3, int cluster, cudaStream_t s);
+int tf32_cluster_size(int want);
 
 // One piece of a free-core copy: slices [i0, i1) and left-rank rows [a0, a1)
 // of a core [r0][I][r1]; swap = 1 writes it as [r1][I][r0].

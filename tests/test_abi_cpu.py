@@ -298,6 +298,29 @@ def test_batched_entries_reject_missing_buffers(L):
         L.tt_plan_free(plan)
 
 
+def test_tf32_forms_rejections(L):
+    """The tf32 forms take float32 cores with every rank <= 64; the checks
+    come back before anything is enqueued."""
+    out = ctypes.c_void_p(0x2000)
+    st = ctypes.c_void_p(0x3000)
+    ok = FakeDesc([4, 4, 4], [1, 64, 8, 1])
+    big = FakeDesc([4, 4, 4], [1, 65, 8, 1])
+    f64 = FakeDesc([4, 4, 4], [1, 8, 8, 1], dtype=B.TT_F64)
+    for prec in ("tf32", "tf32x3"):
+        pr = B.PREC[prec]
+        assert L.tt_contract_full(big.ref, ok.ref, pr, out, None, st, None, 0, None) == -8
+        assert L.tt_contract_full(f64.ref, f64.ref, pr, out, None, st, None, 0, None) == -3
+        zm, zr, _ = B.partial_shape(big, ok, [1, 0, 0], "chain")
+        z = FakeDesc(zm, zr)
+        assert L.tt_contract_partial(big.ref, ok.ref, _mask([1, 0, 0]), 0, pr, z.ref, None, st, None, 0, None) == -8
+        # the merged layout has no tf32 form
+        assert L.tt_contract_partial(ok.ref, ok.ref, _mask([0, 1, 0]), 1, pr, z.ref, None, st, None, 0, None) == -8
+        # workspace query of a full contraction in a tf32 form: the two meeting environments
+        rc, nb = _ws(L, B.TT_OP_FULL, ok, ok, prec=prec)
+        assert rc == 0 and nb > 0
+    assert L.tt_contract_full(ok.ref, ok.ref, 7, out, None, st, None, 0, None) == -8  # unknown form
+
+
 def _ws(L, op, x, y, mask=None, layout="chain", prec="native"):
     nb = ctypes.c_size_t(0)
     m = _mask(mask) if mask is not None else None

@@ -179,6 +179,56 @@ def test_tc_bias_counts_roundings():
     assert M.tc_bias(x, y, "bf16x3") == -1.5 * n_r * M.U_F32
 
 
+def _trunc_bits(x, bits):
+    """Round toward zero to `bits` significant bits."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.trunc(m * 2.0**bits) / 2.0**bits, e)
+
+
+def _tf32_repr(x, x3):
+    """The value the tf32 sweep multiplies: tf32(x), or hi + (lo with its low
+    bits dropped) for the split form."""
+    hi = _round_bits(x, 11)
+    return hi + _trunc_bits(x - hi, 11) if x3 else hi
+
+
+def _sim_sweep_tf32(xc, yc, x3, modes):
+    """<X, Y> with E, each T_i and the core slices of `modes` replaced by their
+    tf32 representation (float64 arithmetic otherwise)."""
+    e = np.ones((1, 1))
+    for k, (gx, gy) in enumerate(zip(xc, yc)):
+        out = np.zeros((gx.shape[2], gy.shape[2]))
+        if k in modes:
+            er = _tf32_repr(e, x3)
+            for i in range(gx.shape[1]):
+                t = _tf32_repr(er @ _tf32_repr(gy[:, i, :], x3), x3)
+                out += _tf32_repr(gx[:, i, :], x3).T @ t
+        else:
+            for i in range(gx.shape[1]):
+                out += gx[:, i, :].T @ e @ gy[:, i, :]
+        e = out
+    return float(e[0, 0])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3"])
+def test_model_predicts_tf32_forms(prec):
+    """The tf32 forms' random part (tf32_rounds without accumulation) against
+    a literal simulation of their representations, over 120 seeds."""
+    r = []
+    rounds = dict(M.tf32_rounds(prec))
+    rounds.pop("acc")
+    for s in range(120):
+        rng = np.random.default_rng(2000 + s)
+        x = G.random_tt(rng, [4, 3, 5, 4, 3], [1, 12, 16, 16, 12, 1], np.float64)
+        y = G.random_tt(rng, [4, 3, 5, 4, 3], [1, 16, 12, 16, 16, 1], np.float64)
+        z = O.contract_full(x, y)
+        sig = M.sweep_error_sigma(x, y, rounds, modes=[0, 1, 2, 3])
+        r.append((_sim_sweep_tf32(x, y, prec == "tf32x3", [0, 1, 2, 3]) - z) / sig)
+    rms = float(np.sqrt(np.mean(np.square(r))))
+    assert 0.5 <= rms <= 1.5, rms
+    assert np.abs(r).max() <= 5.0
+
+
 def _absorb_drop_slice(e, gx, gy, drop=5):
     out = np.zeros((gx.shape[2], gy.shape[2]))
     for i in range(gx.shape[1]):
