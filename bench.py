@@ -555,13 +555,18 @@ def run_ours(args):
     status = int(full.status.item()) | int(part.status.item()) | int(full2.status.item()) | int(part2.status.item())
     forms = {}
     if not args.no_forms:
-        forms["tf32x3"] = bench_step_prec(T, dev, args, "tf32x3")
-        forms["tf32"] = bench_step_prec(T, dev, args, "tf32")
-        forms["batched"] = bench_batched(T, dev, args)
-        forms["bf16"] = bench_bf16(T, dev, args, "native")
-        forms["bf16x3"] = bench_bf16(T, dev, args, "bf16x3")
-        forms["backward"] = bench_backward(T, dev, args)
-        forms["merged"] = bench_merged(T, dev, args)
+        runners = {
+            "tf32x3": lambda: bench_step_prec(T, dev, args, "tf32x3"),
+            "tf32": lambda: bench_step_prec(T, dev, args, "tf32"),
+            "batched": lambda: bench_batched(T, dev, args),
+            "bf16": lambda: bench_bf16(T, dev, args, "native"),
+            "bf16x3": lambda: bench_bf16(T, dev, args, "bf16x3"),
+            "backward": lambda: bench_backward(T, dev, args),
+            "merged": lambda: bench_merged(T, dev, args),
+        }
+        wanted = list(runners) if args.forms == "all" else [f for f in args.forms.split(",") if f]
+        for name in wanted:
+            forms[name] = runners[name]()
 
     if rank == 0:
         line = {
@@ -1125,6 +1130,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--forms", default="all", help="comma-separated subset of the secondary forms to run (default all)")
     ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "order10_tf32x3", "backward", "merged"],
                     default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")

@@ -332,7 +332,7 @@ int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_d
       if (ws_bytes >= L.bytes) {
         TwoSidedParams tp;
         build_two_sided(x, y, L, ws, out_dev, out_log2_dev, status_dev, &tp);
-        if (cudaMemsetAsync(tp.counter, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+        if (cudaMemsetAsync(tp.counter, 0, 128, s) != cudaSuccess) return TT_ERR_CUDA;  // join counters
         return launch_tf32_two_sided(tp, x3, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
       }
     }
@@ -347,7 +347,7 @@ int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_d
     if (ws_bytes >= L.bytes && C >= 2) {
       TwoSidedParams tp;  // copied by the launch
       build_two_sided(x, y, L, ws, out_dev, out_log2_dev, status_dev, &tp);
-      if (cudaMemsetAsync(tp.counter, 0, sizeof(int), s) != cudaSuccess) return TT_ERR_CUDA;
+      if (cudaMemsetAsync(tp.counter, 0, 128, s) != cudaSuccess) return TT_ERR_CUDA;  // join counters
       return launch_two_sided(tp, x->dtype, rmax, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
     }
   }

@@ -71,8 +71,19 @@ __global__ void __launch_bounds__(256, 1) sweep_two_sided_kernel(const __grid_co
   const T* er = static_cast<const T*>(tp.half[1].e_out);
   const int n = tp.rx * tp.ry;
   double part = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    part = fma(static_cast<double>(__ldcg(el + i)), static_cast<double>(__ldcg(er + i)), part);
+  // eight pairs of loads in flight per thread before the first product
+  const int nt = static_cast<int>(blockDim.x);
+  for (int base = threadIdx.x; base < n; base += 8 * nt) {
+    T a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = base + u * nt;
+      a[u] = i < n ? __ldcg(el + i) : T(0);
+      b[u] = i < n ? __ldcg(er + i) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) part = fma(static_cast<double>(a[u]), static_cast<double>(b[u]), part);
+  }
   part = warp_sum(part);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) s_red[warp] = part;

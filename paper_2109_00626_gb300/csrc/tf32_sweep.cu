@@ -20,20 +20,20 @@
 //
 // Precision.  Every float32 operand x (core slices, E, T) is held as two tf32
 // values hi = rna(x) and lo = x - hi (exact in float32; the tensor core reads
-// lo's top 19 bits).  The hi and lo halves of each core slice are stacked
-// into one M = 128 operand, so each GEMM is two passes (the other operand's
-// hi, then its lo) over K / 8 steps and tensor memory holds rows [0, 64) =
-// slice_hi (hi + lo) and rows [64, 128) = slice_lo (hi + lo): all four
-// products of the split, added by the epilogue (the "3xTF32" scheme, with
-// lo*lo kept since it is free here).  The plain tf32 form runs the hi pass
-// and the upper half only.
+// lo's top 19 bits).  Both operands of every GEMM are stacked: rows 0-63 of
+// an operand hold hi, rows 64-127 lo, so one M = 128, N = 128 product over
+// K / 8 steps leaves the four products hi*hi, hi*lo, lo*hi and lo*lo in the
+// four 64 x 64 quadrants of the accumulator, added by the epilogue (the
+// "3xTF32" scheme, with lo*lo kept since it is free here).  The plain tf32
+// form uses N = 64 (the other operand's hi rows) and the upper half only.
 //
-// Warp roles (288 threads): warps 0-3 epilogue (tensor-memory lane quadrants
+// Warp roles (256 threads, two warps per SM sub-partition so that a thread may
+// hold up to 255 registers): warps 0-3 epilogue (tensor-memory lane quadrants
 // 0-3: combine the two halves, split T into the GEMM 2 operand, the cluster
-// reduction, E' into the GEMM 1 operand, the end of the sweep); warps 4-7
+// reduction, E' into the GEMM 1 operand, the end of the sweep); warps 4-6
 // load and split core slices (global -> registers -> hi / lo swizzled shared
 // tiles, zero padded to 64 x 64; a right-to-left sweep reads its slices with
-// their rank legs swapped); warp 8 allocates tensor memory and one of its
+// their rank legs swapped); warp 7 allocates tensor memory and one of its
 // threads issues every MMA.
 //
 // Scaling: as the CUDA-core sweep, E' is rescaled by an exact power of two
@@ -46,21 +46,22 @@ namespace ttc {
 namespace tf {
 
 constexpr int RM = 64;            // rank tile (ranks above 64 are not taken by this path)
-constexpr int kThreads = 288;     // 9 warps
-constexpr int kLoadTid0 = 128;    // loader threads 128..255 (warps 4-7)
-constexpr int kMmaWarp = 8;
+constexpr int kThreads = 256;     // 8 warps
+constexpr int kLoadTid0 = 128;    // loader threads 128..223 (warps 4-6)
+constexpr int kLoaders = 96;
+constexpr int kLoadIters = (64 * 16 + kLoaders - 1) / kLoaders;  // groups of 4 values per loader thread
+constexpr int kMmaWarp = 7;
 constexpr int NA = 2;             // A-tile buffers (GEMM 2 operand; next mode's A loads during this one)
 constexpr int NB = 1;             // B-tile buffers (GEMM 1 operand; freed as soon as GEMM 1 is done)
 constexpr uint32_t TILE = 32768;  // one operand buffer: 64 x 64 float32 values as hi and lo tf32
-// Stacked operand (a core slice, M = 128): per 32-column K block (16 KB) rows
-// 0-63 hold hi, rows 64-127 lo.  Plain operand (E, T^T; N = 64): hi in the
-// first 16 KB, lo in the second, 8 KB per 32-column K block.
+// Stacked operand (every operand): per 32-column K block (16 KB) rows 0-63
+// hold hi, rows 64-127 lo.
 constexpr int SLD = 68;           // row stride (floats) of the float32 staging buffers
 constexpr int RROWS = RM + 16;    // receive rows: C slots of ceil(64 / C) rows
 constexpr int DROWS = 32;         // reduced rows one CTA owns (C >= 2)
 
-constexpr uint32_t OFF_E = 0;                         // GEMM 1 B operand E (plain)
-constexpr uint32_t OFF_T = OFF_E + TILE;              // GEMM 2 B operand T^T (plain); E' rows during the exchange
+constexpr uint32_t OFF_E = 0;                         // GEMM 1 B operand E
+constexpr uint32_t OFF_T = OFF_E + TILE;              // GEMM 2 B operand T^T; E' rows during the exchange
 constexpr uint32_t OFF_A = OFF_T + TILE;              // NA A tiles
 constexpr uint32_t OFF_B = OFF_A + NA * TILE;         // NB B tiles
 constexpr uint32_t OFF_S = OFF_B + NB * TILE;         // combine scratch / P rows, 64 x SLD floats
@@ -88,15 +89,14 @@ __device__ __forceinline__ float rna_tf32(float x) {
 __device__ __forceinline__ uint32_t kmaj(int m, int k, uint32_t blk) {
   return (k >> 5) * blk + m * 128 + ((((k & 31) >> 2) ^ (m & 7)) << 4) + ((k & 3) << 2);
 }
-// Stacked operand (core slice): hi at row m, lo at row m + 64.
+// Stacked operand: hi at row m, lo at row m + 64 (8192 bytes on).
 __device__ __forceinline__ uint32_t st_off(int m, int k) { return kmaj(m, k, 16384); }
-// Plain operand (E, T^T): hi part; the lo part is 16384 bytes on.
-__device__ __forceinline__ uint32_t pl_off(int n, int k) { return kmaj(n, k, 8192); }
 
-// Instruction descriptor: tf32 x tf32 -> f32, dense, M = 128, N = 64.
-__host__ __device__ constexpr uint32_t idesc_tf32(bool a_mn_major, bool b_mn_major) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((b_mn_major ? 1u : 0u) << 16) |
-         (static_cast<uint32_t>(64 >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+// Instruction descriptor: tf32 x tf32 -> f32, dense, both operands K-major,
+// M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -104,6 +104,24 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 32 lanes x 64 consecutive 32-bit columns of tensor memory (warp-collective),
+// four loads in flight and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[16 * c]), "=r"(r[16 * c + 1]), "=r"(r[16 * c + 2]), "=r"(r[16 * c + 3]), "=r"(r[16 * c + 4]),
+          "=r"(r[16 * c + 5]), "=r"(r[16 * c + 6]), "=r"(r[16 * c + 7]), "=r"(r[16 * c + 8]), "=r"(r[16 * c + 9]),
+          "=r"(r[16 * c + 10]), "=r"(r[16 * c + 11]), "=r"(r[16 * c + 12]), "=r"(r[16 * c + 13]), "=r"(r[16 * c + 14]),
+          "=r"(r[16 * c + 15])
+        : "r"(taddr + 16 * c));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
@@ -125,62 +143,68 @@ struct TfOut {
 // rank index (M of the GEMM), column k = the contracted rank index (K).
 //   out_major == 0: value(m, k) = core[k][i][m]   (core [n_in][I][n_out])
 //   out_major == 1: value(m, k) = core[m][i][k]   (core [n_out][I][n_in])
-// Entries outside n_out x n_in are zero.  128 threads (tl = 0..127).
+// Entries outside n_out x n_in are zero.  96 threads (tl = 0..95), each with
+// kLoadIters groups of 4 values (q = tl + 96 g < 1024): load_regs issues all
+// of a thread's global loads before any is used (so a slice's two tiles are in
+// flight together), then store_tile splits them into hi / lo and writes them.
+//   out_major: group q is row m = q / 16, columns 4 (q % 16) .. + 3
+//              (contiguous in global memory);
+//   in_major:  column k = q % 64, rows 4 (q / 64) .. + 3 (lanes along k: each
+//              4-byte store of a warp covers one row).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void load_tile(unsigned char* tile, const float* __restrict__ core, int i, int I, int n_in,
-                                          int n_out, int out_major, bool x3, int tl) {
-  if (out_major) {
-    // a row of the slice is contiguous in k: thread -> (row m, 4 columns), 16-byte stores
-    const bool vec = (n_in & 3) == 0 && (reinterpret_cast<uintptr_t>(core) & 15) == 0;
-#pragma unroll 2
-    for (int q = tl; q < RM * 16; q += 128) {
-      const int m = q >> 4, k0 = (q & 15) * 4;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      if (m < n_out && k0 < n_in) {
-        const float* src = core + (static_cast<int64_t>(m) * I + i) * n_in + k0;
-        if (vec) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(src));
-          v[0] = t.x;
-          v[1] = t.y;
-          v[2] = t.z;
-          v[3] = t.w;
-        } else {
+struct TileRegs {
+  float4 v[kLoadIters];
+};
+
+__device__ __forceinline__ void load_regs(TileRegs& r, const float* __restrict__ core, int i, int I, int n_in, int n_out,
+                                          int out_major, int tl) {
+  const int inner = out_major ? n_in : n_out;
+  const bool vec = (inner & 3) == 0 && (reinterpret_cast<uintptr_t>(core) & 15) == 0;
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (k0 + e < n_in) v[e] = __ldg(src + e);
-        }
+  for (int g = 0; g < kLoadIters; ++g) {
+    const int q = tl + kLoaders * g;
+    int row, col0, nrow, ncol;  // the run of 4 is along col (contiguous in memory)
+    if (out_major) {
+      row = q >> 4;
+      col0 = (q & 15) * 4;
+      nrow = n_out;
+      ncol = n_in;
+    } else {
+      row = q & 63;
+      col0 = (q >> 6) * 4;
+      nrow = n_in;
+      ncol = n_out;
+    }
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < 1024 && row < nrow && col0 < ncol) {
+      const float* src = core + (static_cast<int64_t>(row) * I + i) * ncol + col0;
+      if (vec) {
+        t = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        t.x = __ldg(src);
+        if (col0 + 1 < ncol) t.y = __ldg(src + 1);
+        if (col0 + 2 < ncol) t.z = __ldg(src + 2);
+        if (col0 + 3 < ncol) t.w = __ldg(src + 3);
       }
-      float4 h;
-      h.x = rna_tf32(v[0]);
-      h.y = rna_tf32(v[1]);
-      h.z = rna_tf32(v[2]);
-      h.w = rna_tf32(v[3]);
+    }
+    r.v[g] = t;
+  }
+}
+
+__device__ __forceinline__ void store_tile(unsigned char* tile, const TileRegs& r, int out_major, bool x3, int tl) {
+#pragma unroll
+  for (int g = 0; g < kLoadIters; ++g) {
+    const int q = tl + kLoaders * g;
+    if (q >= 1024) break;
+    const float v[4] = {r.v[g].x, r.v[g].y, r.v[g].z, r.v[g].w};
+    if (out_major) {
+      const int m = q >> 4, k0 = (q & 15) * 4;
+      const float4 h = make_float4(rna_tf32(v[0]), rna_tf32(v[1]), rna_tf32(v[2]), rna_tf32(v[3]));
       const uint32_t off = st_off(m, k0);
       *reinterpret_cast<float4*>(tile + off) = h;
       if (x3) *reinterpret_cast<float4*>(tile + off + 8192) = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
-    }
-  } else {
-    // a row of the slice is contiguous in m: thread -> (column k, 4 rows); lanes
-    // along k, so each 4-byte store of a warp covers one 128-byte row
-    const bool vec = (n_out & 3) == 0 && (reinterpret_cast<uintptr_t>(core) & 15) == 0;
-#pragma unroll 2
-    for (int q = tl; q < RM * 16; q += 128) {
+    } else {
       const int k = q & 63, m0 = (q >> 6) * 4;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      if (k < n_in && m0 < n_out) {
-        const float* src = core + (static_cast<int64_t>(k) * I + i) * n_out + m0;
-        if (vec) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(src));
-          v[0] = t.x;
-          v[1] = t.y;
-          v[2] = t.z;
-          v[3] = t.w;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (m0 + e < n_out) v[e] = __ldg(src + e);
-        }
-      }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float h = rna_tf32(v[e]);
@@ -228,14 +252,14 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
   const bool emit = p.emit.enabled != 0;
   int bits = 0;
 
-  if (warp == kMmaWarp) tc::tmem_alloc(tmem_slot, 128);
+  if (warp == kMmaWarp) tc::tmem_alloc(tmem_slot, 256);
   if (tid == 0) {
     for (int s = 0; s < NA; ++s) {
-      tc::mbar_init(&a_full[s], 128);
+      tc::mbar_init(&a_full[s], kLoaders);
       tc::mbar_init(&a_empty[s], 1);
     }
     for (int s = 0; s < NB; ++s) {
-      tc::mbar_init(&b_full[s], 128);
+      tc::mbar_init(&b_full[s], kLoaders);
       tc::mbar_init(&b_empty[s], 1);
     }
     tc::mbar_init(e_ready, 128);
@@ -258,27 +282,29 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
   cg::this_cluster().sync();  // barriers of every CTA exist before any peer pushes; E_0 written
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tD1 = tmem, tD2 = tmem + 64;
+  const uint32_t tD1 = tmem, tD2 = tmem + 128;  // 128 columns each
 
-  if (warp >= 4 && warp < 8) {
+  if (warp >= 4 && warp < kMmaWarp) {
     // ---------------- loaders ----------------
     const int tl = tid - kLoadTid0;
     uint32_t ia = 0, ib = 0;
+    TileRegs rb, ra;
     for (int j = 0; j < n_pipe; ++j) {
       const SweepStep& s = p.step[j];
       const int ns = n_slices(s.I, crank, C);
       for (int t = 0; t < ns; ++t) {
         const int i = crank + t * C;
         const int sb = ib % NB, sa = ia % NA;
+        // both tiles of the slice in flight before either buffer is waited for
+        load_regs(rb, static_cast<const float*>(s.gy), i, s.I, s.rin_y, s.rout_y, p.transposed, tl);  // B_i^T: rows v, columns q
+        load_regs(ra, static_cast<const float*>(s.gx), i, s.I, s.rin_x, s.rout_x, p.transposed, tl);  // A_i^T: rows u, columns p
         if (!tc::mbar_wait(&b_empty[sb], ((ib / NB) & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        load_tile(sm + OFF_B + sb * TILE, static_cast<const float*>(s.gy), i, s.I, s.rin_y, s.rout_y, p.transposed,
-                  X3, tl);  // B_i^T: rows v, columns q
+        store_tile(sm + OFF_B + sb * TILE, rb, p.transposed, X3, tl);
         tc::fence_proxy_async();
         tc::mbar_arrive(&b_full[sb]);
         ++ib;
         if (!tc::mbar_wait(&a_empty[sa], ((ia / NA) & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        load_tile(sm + OFF_A + sa * TILE, static_cast<const float*>(s.gx), i, s.I, s.rin_x, s.rout_x, p.transposed,
-                  X3, tl);  // A_i^T: rows u, columns p
+        store_tile(sm + OFF_A + sa * TILE, ra, p.transposed, X3, tl);
         tc::fence_proxy_async();
         tc::mbar_arrive(&a_full[sa]);
         ++ia;
@@ -292,9 +318,9 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
       const int ns = n_slices(em.I, crank, C);
       for (int t = 0; t < ns; ++t) {
         const int sa = ia % NA;
+        load_regs(ra, static_cast<const float*>(em.gx), crank + t * C, em.I, n_in, n_out, em.lead ? 0 : 1, tl);
         if (!tc::mbar_wait(&a_empty[sa], ((ia / NA) & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        load_tile(sm + OFF_A + sa * TILE, static_cast<const float*>(em.gx), crank + t * C, em.I, n_in, n_out,
-                  em.lead ? 0 : 1, X3, tl);
+        store_tile(sm + OFF_A + sa * TILE, ra, em.lead ? 0 : 1, X3, tl);
         tc::fence_proxy_async();
         tc::mbar_arrive(&a_full[sa]);
         ++ia;
@@ -303,7 +329,7 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr uint32_t id = idesc_tf32(false, false);  // both operands K-major
+      constexpr uint32_t id = idesc_tf32(X3 ? 128 : 64);
       const uint32_t sE = tc::su32(sm + OFF_E), sT = tc::su32(sm + OFF_T);
       uint32_t ia = 0, ib = 0, nt = 0;
       for (int j = 0; j <= n_pipe; ++j) {
@@ -323,10 +349,9 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
             if (!tc::mbar_wait(&a_full[sa], (ia / NA) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
             tc::fence_after_sync();
             const uint32_t sA = tc::su32(sm + OFF_A + sa * TILE);
-            for (int pass = 0; pass < (X3 ? 2 : 1); ++pass)
-              for (int kk = 0; kk < kst; ++kk)
-                mma_tf32(tD2, tc::sdesc(sA + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                         tc::sdesc(sT + pass * 16384 + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024), id, (pass | kk) != 0);
+            for (int kk = 0; kk < kst; ++kk)
+              mma_tf32(tD2, tc::sdesc(sA + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+                       tc::sdesc(sT + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), id, kk != 0);
             tc::mma_commit(&a_empty[sa]);
             tc::mma_commit(t_full);
             ++ia;
@@ -342,23 +367,21 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
           if (!tc::mbar_wait(&b_full[sb], (ib / NB) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
           tc::fence_after_sync();
           const uint32_t sB = tc::su32(sm + OFF_B + sb * TILE);
-          // GEMM 1: D1 = [B_hi^T; B_lo^T] (E_hi + E_lo)^T
-          for (int pass = 0; pass < (X3 ? 2 : 1); ++pass)
-            for (int kk = 0; kk < k1; ++kk)
-              mma_tf32(tD1, tc::sdesc(sB + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                       tc::sdesc(sE + pass * 16384 + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024), id, (pass | kk) != 0);
+          // GEMM 1: D1 = [B_hi^T; B_lo^T] [E_hi; E_lo]^T
+          for (int kk = 0; kk < k1; ++kk)
+            mma_tf32(tD1, tc::sdesc(sB + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+                     tc::sdesc(sE + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), id, kk != 0);
           tc::mma_commit(&b_empty[sb]);
           tc::mma_commit(t_full);
           ++ib;
-          // GEMM 2: D2 += [A_hi^T; A_lo^T] (T_hi + T_lo), once T^T is staged
+          // GEMM 2: D2 += [A_hi^T; A_lo^T] [T_hi^T; T_lo^T]^T, once T^T is staged
           if (!tc::mbar_wait(t_ready, nt & 1, abort)) bits |= TT_STATUS_TIMEOUT;
           if (!tc::mbar_wait(&a_full[sa], (ia / NA) & 1, abort)) bits |= TT_STATUS_TIMEOUT;
           tc::fence_after_sync();
           const uint32_t sA = tc::su32(sm + OFF_A + sa * TILE);
-          for (int pass = 0; pass < (X3 ? 2 : 1); ++pass)
-            for (int kk = 0; kk < k2; ++kk)
-              mma_tf32(tD2, tc::sdesc(sA + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
-                       tc::sdesc(sT + pass * 16384 + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024), id, (t | pass | kk) != 0);
+          for (int kk = 0; kk < k2; ++kk)
+            mma_tf32(tD2, tc::sdesc(sA + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024),
+                     tc::sdesc(sT + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024), id, (t | kk) != 0);
           tc::mma_commit(&a_empty[sa]);
           ++ia;
           ++nt;
@@ -372,7 +395,17 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
     }
   } else {
     // ---------------- epilogue (warps 0-3) ----------------
+    // Each warp owns 32 accumulator rows (r = 32 (q & 1) + lane) and half of
+    // the 64 output columns (warps 0, 1 columns 0-31, warps 2, 3 columns
+    // 32-63).  The accumulator is 128 x 128 (x3) or 128 x 64: rows 0-63 come
+    // from the hi rows of the stacked A operand, rows 64-127 from its lo rows;
+    // columns 0-63 from the B operand's hi rows, 64-127 from its lo rows.
+    // Warps 0, 1 read lanes 0-63, warps 2, 3 lanes 64-127; each adds its
+    // column halves and hands the half it does not own to its partner (warp
+    // q ^ 2) through S, so every output is the sum of its four quadrants.
     const int q = warp;  // tensor-memory lane quadrant
+    const int r = 32 * (q & 1) + lane;
+    const int half = q >> 1;
     float* S = reinterpret_cast<float*>(sm + OFF_S);
     float* R = reinterpret_cast<float*>(sm + OFF_R);
     float* D = reinterpret_cast<float*>(sm + OFF_D);
@@ -386,93 +419,109 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
     int nu = 1, nv = 1;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
 
-    // Combine the two halves of accumulator tD into rows [0, 64): returns the
-    // row's 64 values in v (threads of quadrants 0, 1: row 32 q + lane).
-    auto combine = [&](uint32_t tD, float (&v)[64]) {
-      if (X3 && q >= 2) {
-        float w[16];
+    // v = row r, columns 32 half .. + 31 of the sum of tD's quadrants
+    auto combine = [&](uint32_t tD, float (&v)[32]) {
+      float w[64];
+      tmem_ld64(tD + lane_base, w);
+      if (X3) {
+        float w2[64];
+        tmem_ld64(tD + lane_base + 64, w2);
 #pragma unroll
-        for (int c16 = 0; c16 < 4; ++c16) {
-          tc::tmem_ld16(tD + lane_base + c16 * 16, w);
-          float* row = S + (32 * (q - 2) + lane) * SLD + c16 * 16;
+        for (int c = 0; c < 64; ++c) w[c] += w2[c];
+      }
+      // warps 0, 1 pass columns 32-63 of the upper half; warps 2, 3 columns 0-31 of the lower
+      if (half == 0 || X3) {
+        float* dst = S + r * SLD + (half ? 0 : 32);
+        const float* src = w + (half ? 0 : 32);
 #pragma unroll
-          for (int e = 0; e < 16; e += 4) *reinterpret_cast<float4*>(row + e) = make_float4(w[e], w[e + 1], w[e + 2], w[e + 3]);
-        }
+        for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(dst + c) = make_float4(src[c], src[c + 1], src[c + 2], src[c + 3]);
       }
       named_sync(1, 128);
-      if (q < 2) {
-        float w[16];
+      const float* oth = S + r * SLD + 32 * half;
 #pragma unroll
-        for (int c16 = 0; c16 < 4; ++c16) {
-          tc::tmem_ld16(tD + lane_base + c16 * 16, w);
+      for (int c = 0; c < 32; c += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(oth + c);
+        const float o4[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = w[e];
+        for (int e = 0; e < 4; ++e) {
+          if (half == 0) v[c + e] = X3 ? w[c + e] + o4[e] : w[c + e];
+          else v[c + e] = X3 ? o4[e] + w[32 + c + e] : o4[e];
         }
-        if (X3) {
-          const float* row = S + (32 * q + lane) * SLD;
+      }
+    };
+
+    // E' (rows nu, columns nv of src, row stride SLD, times 2^-escale) into
+    // the stacked GEMM 1 B operand; every other entry zero
+    auto build_e = [&](const float* src) {
+      unsigned char* eb = sm + OFF_E;
+      const int j4 = tid & 15, c0 = j4 * 4, m0 = tid >> 4;
+      float4 x[8];
 #pragma unroll
-          for (int c = 0; c < 64; c += 4) {
-            const float4 a = *reinterpret_cast<const float4*>(row + c);
-            v[c] += a.x;
-            v[c + 1] += a.y;
-            v[c + 2] += a.z;
-            v[c + 3] += a.w;
-          }
+      for (int it = 0; it < 8; ++it) {
+        const int m = m0 + 8 * it;
+        x[it] = m < nu ? *reinterpret_cast<const float4*>(src + m * SLD + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int m = m0 + 8 * it;
+        float e4[4] = {x[it].x, x[it].y, x[it].z, x[it].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (c0 + e >= nv) e4[e] = 0.f;
+          else if (escale) e4[e] = mul_pow2<float>(e4[e], -escale);
         }
+        const float4 h = make_float4(rna_tf32(e4[0]), rna_tf32(e4[1]), rna_tf32(e4[2]), rna_tf32(e4[3]));
+        const uint32_t off = st_off(m, c0);
+        *reinterpret_cast<float4*>(eb + off) = h;
+        *reinterpret_cast<float4*>(eb + off + 8192) =
+            X3 ? make_float4(e4[0] - h.x, e4[1] - h.y, e4[2] - h.z, e4[3] - h.w) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
 
     for (int j = 0; j < n_pipe; ++j) {
       const SweepStep& s = p.step[j];
       const int ns = n_slices(s.I, crank, C);
+      const bool last = j + 1 == n_pipe;
       for (int t = 0; t < ns; ++t) {
-        // T^T = D1 rows (v), split into the GEMM 2 B operand (row v, K column p)
+        // T^T = D1 rows (v), split into the stacked GEMM 2 B operand (row v, K column p)
         if (!tc::mbar_wait(t_full, nt & 1, abort)) bits |= TT_STATUS_TIMEOUT;
         tc::fence_after_sync();
-        float v[64];
+        float v[32];
         combine(tD1, v);
-        if (q < 2) {
-          const int r = 32 * q + lane;
-          unsigned char* tb = sm + OFF_T;
+        unsigned char* tb = sm + OFF_T;
 #pragma unroll
-          for (int j4 = 0; j4 < 16; ++j4) {
-            float4 h;
-            h.x = rna_tf32(v[4 * j4]);
-            h.y = rna_tf32(v[4 * j4 + 1]);
-            h.z = rna_tf32(v[4 * j4 + 2]);
-            h.w = rna_tf32(v[4 * j4 + 3]);
-            const uint32_t off = pl_off(r, 4 * j4);
-            *reinterpret_cast<float4*>(tb + off) = h;
-            if (X3)
-              *reinterpret_cast<float4*>(tb + 16384 + off) =
-                  make_float4(v[4 * j4] - h.x, v[4 * j4 + 1] - h.y, v[4 * j4 + 2] - h.z, v[4 * j4 + 3] - h.w);
-          }
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 h = make_float4(rna_tf32(v[4 * j4]), rna_tf32(v[4 * j4 + 1]), rna_tf32(v[4 * j4 + 2]),
+                                       rna_tf32(v[4 * j4 + 3]));
+          const uint32_t off = st_off(r, 32 * half + 4 * j4);
+          *reinterpret_cast<float4*>(tb + off) = h;
+          if (X3)
+            *reinterpret_cast<float4*>(tb + off + 8192) =
+                make_float4(v[4 * j4] - h.x, v[4 * j4 + 1] - h.y, v[4 * j4 + 2] - h.z, v[4 * j4 + 3] - h.w);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
         tc::mbar_arrive(t_ready);
         ++nt;
       }
-      // ---- P of this CTA ----
+      // ---- P of this CTA, rows in S ----
       if (!tc::mbar_wait(p_full, j & 1, abort)) bits |= TT_STATUS_TIMEOUT;
       tc::fence_after_sync();
       nu = s.rout_x;
       nv = s.rout_y;
       {
-        float v[64];
+        float v[32];
         if (ns > 0) {
           combine(tD2, v);
         } else {
           named_sync(1, 128);
 #pragma unroll
-          for (int c = 0; c < 64; ++c) v[c] = 0.f;
+          for (int c = 0; c < 32; ++c) v[c] = 0.f;
         }
-        named_sync(1, 128);  // every quadrant is done reading S before the P rows go there
-        if (q < 2) {
-          float* row = S + (32 * q + lane) * SLD;
+        // this thread read S[r][32 half ..] above and is the only one to write it now
+        float* row = S + r * SLD + 32 * half;
 #pragma unroll
-          for (int c = 0; c < 64; c += 4) *reinterpret_cast<float4*>(row + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-        }
+        for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(row + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
       }
       tc::fence_before_sync();
       named_sync(1, 128);
@@ -513,28 +562,43 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
                          tc::mapa(tc::su32(&xbar[0]), tid));
         }
         if (!tc::mbar_wait(&xbar[0], xph & 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        // owner sum over the C peers, fixed order (deterministic)
+        // owner sum over the C peers, fixed order (deterministic); tpj threads
+        // per 4-column job, each over every tpj-th peer, then a shuffle sum
+        const int jobs = my_rows * 16;
+        const int tpj = jobs <= 32 ? 4 : (jobs <= 64 ? 2 : 1);
+        const int per = 128 / tpj;
+        const int niter = (jobs + per - 1) / per;  // the same for every thread
+        const int sub = tid & (tpj - 1);
         float lmax = 0.f;
         int lbad = 0;
-        const int nq = (nv + 3) / 4;
-        for (int idx = tid; idx < my_rows * nq; idx += 128) {
-          const int vr = idx / nq, c = (idx - vr * nq) * 4;
+        for (int it = 0; it < niter; ++it) {
+          const int job = tid / tpj + it * per;
+          const bool act = job < jobs;
+          const int vr = act ? job >> 4 : 0, c = (job & 15) * 4;
           float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int r = 0; r < C; ++r) {
-            const float4 x = *reinterpret_cast<const float4*>(R + (r * chunk + vr) * SLD + c);
+          for (int rr = sub; act && rr < C; rr += tpj) {
+            const float4 x = *reinterpret_cast<const float4*>(R + (rr * chunk + vr) * SLD + c);
             sum.x += x.x;
             sum.y += x.y;
             sum.z += x.z;
             sum.w += x.w;
           }
-          *reinterpret_cast<float4*>(D + vr * SLD + c) = sum;
-          const float e4[4] = {sum.x, sum.y, sum.z, sum.w};
+          for (int off = 1; off < tpj; off <<= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+            sum.w += __shfl_xor_sync(0xffffffffu, sum.w, off);
+          }
+          if (act && sub == 0) {
+            *reinterpret_cast<float4*>(D + vr * SLD + c) = sum;
+            const float e4[4] = {sum.x, sum.y, sum.z, sum.w};
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (c + e < nv) {
-              if (isfinite(e4[e])) lmax = fmaxf(lmax, fabsf(e4[e]));
-              else lbad = 1;
-            }
+            for (int e = 0; e < 4; ++e)
+              if (c + e < nv) {
+                if (isfinite(e4[e])) lmax = fmaxf(lmax, fabsf(e4[e]));
+                else lbad = 1;
+              }
+          }
         }
         lmax = warp_max(lmax);
         lbad = warp_or(lbad);
@@ -562,33 +626,17 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
         }
         if (!tc::mbar_wait(&xbar[1], xph & 1, abort)) bits |= TT_STATUS_TIMEOUT;
         ++xph;
-        for (int r = 0; r < C; ++r) {
-          gexp = max(gexp, rec[4 * r]);
-          gbad |= rec[4 * r + 1];
+        for (int rr = 0; rr < C; ++rr) {
+          gexp = max(gexp, rec[4 * rr]);
+          gbad |= rec[4 * rr + 1];
         }
       }
       if (gbad) bad = 1;
       escale = (gexp != kNoExpF && (gexp > p.renorm_bits || gexp < -p.renorm_bits)) ? gexp : 0;
       log2s += escale;
-      // ---- E' into the GEMM 1 B operand (row p = u, K column q = v) ----
-      if (j + 1 < n_pipe) {
-        unsigned char* eb = sm + OFF_E;
-        for (int idx = tid; idx < RM * 16; idx += 128) {
-          const int m = idx >> 4, c0 = (idx & 15) * 4;
-          float x[4] = {0.f, 0.f, 0.f, 0.f};
-          if (m < nu)
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (c0 + e < nv) x[e] = escale ? mul_pow2<float>(eraw[m * SLD + c0 + e], -escale) : eraw[m * SLD + c0 + e];
-          float4 h, l;
-          h.x = rna_tf32(x[0]);
-          h.y = rna_tf32(x[1]);
-          h.z = rna_tf32(x[2]);
-          h.w = rna_tf32(x[3]);
-          *reinterpret_cast<float4*>(eb + pl_off(m, c0)) = h;
-          l = X3 ? make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w) : make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(eb + 16384 + pl_off(m, c0)) = l;
-        }
+      // ---- E' into the GEMM 1 operand of the next mode ----
+      if (!last) {
+        build_e(eraw);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         tc::mbar_arrive(e_ready);
@@ -622,8 +670,8 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
         const int m = idx >> 6, c = idx & 63;
         const float x = escale ? mul_pow2<float>(kx[e], -escale) : kx[e];
         const float h = rna_tf32(x);
-        *reinterpret_cast<float*>(tb + pl_off(c, m)) = h;
-        *reinterpret_cast<float*>(tb + 16384 + pl_off(c, m)) = X3 ? x - h : 0.f;
+        *reinterpret_cast<float*>(tb + st_off(c, m)) = h;
+        *reinterpret_cast<float*>(tb + st_off(c, m) + 8192) = X3 ? x - h : 0.f;
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -635,15 +683,16 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
         const int i = crank + t * C;
         if (!tc::mbar_wait(t_full, nt & 1, abort)) bits |= TT_STATUS_TIMEOUT;
         tc::fence_after_sync();
-        float v[64];
+        float v[32];
         combine(tD2, v);
-        if (q < 2) {
-          const int u = 32 * q + lane;
+        {
+          const int u = r;
           if (u < ncol) {
             float* dst = static_cast<float*>(em.c_out) + (static_cast<int64_t>(u) * em.I + i) * em.ry;
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-              if (c < em.ry) {
+            for (int c = 0; c < 32; ++c) {
+              const int y = 32 * half + c;
+              if (y < em.ry) {
                 float val = v[c];
                 if (fold && log2s != 0) {
                   const float v0 = val;
@@ -651,7 +700,7 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
                   if (isfinite(v0) && !isfinite(val)) ebits |= TT_STATUS_OVERFLOW;
                 }
                 if (!isfinite(val)) ebits |= TT_STATUS_NONFINITE;
-                dst[c] = val;
+                dst[y] = val;
               }
             }
           }
@@ -689,7 +738,7 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
   st.nu = stash[2];
   st.nv = stash[3];
   st.log2s = reinterpret_cast<int64_t*>(misc + 56)[0];
-  if (warp == kMmaWarp) tc::tmem_dealloc(tmem, 128);
+  if (warp == kMmaWarp) tc::tmem_dealloc(tmem, 256);
 }
 
 // Final-environment work shared by the kernels: the last mode of a full
@@ -758,13 +807,16 @@ __device__ void tf_finish(const SweepParams& p, const TfOut& o, unsigned char* s
     }
     return;
   }
-  if (crank == 0 && p.e_out != nullptr) {
+  if (p.e_out != nullptr) {
+    // every CTA holds the whole environment: each writes rows u = crank, crank + C, ...
     float* e = static_cast<float*>(p.e_out);
-    for (int idx = tid; idx < st.nu * st.nv; idx += kThreads) {
-      const int u = idx / st.nv, c = idx - u * st.nv;
-      e[idx] = st.escale ? mul_pow2<float>(eraw[u * SLD + c], -st.escale) : eraw[u * SLD + c];
+    const int nrow = st.nu > crank ? (st.nu - 1 - crank) / C + 1 : 0;
+    for (int idx = tid; idx < nrow * st.nv; idx += kThreads) {
+      const int u = crank + (idx / st.nv) * C, c = idx % st.nv;
+      e[u * st.nv + c] = st.escale ? mul_pow2<float>(eraw[u * SLD + c], -st.escale) : eraw[u * SLD + c];
     }
-    if (tid == 0 && p.e_out_log2 != nullptr) *p.e_out_log2 = st.log2s;
+    if (crank == 0 && tid == 0 && p.e_out_log2 != nullptr) *p.e_out_log2 = st.log2s;
+    __threadfence();  // visible to the other cluster before this cluster counts itself done
   }
   if (tid == 0 && crank == 0 && st.bad) set_status(o.status, TT_STATUS_NONFINITE);
 }
@@ -810,7 +862,8 @@ __global__ void __launch_bounds__(kThreads, 1) tf_sweep_kernel(const __grid_cons
 // Full contraction from both ends (as the CUDA-core two-sided kernel): cluster
 // 0 sweeps the leading modes, cluster 1 the trailing ones (slices read with
 // swapped legs), each writes its environment and scale to the workspace, and
-// the cluster that finishes second forms z = sum E_L * F_R in float64.
+// z = sum E_L * F_R is formed in float64 by pairs of CTAs as their rows are
+// ready (no CTA waits for another).
 template <bool X3>
 __global__ void __launch_bounds__(kThreads, 1) tf_two_sided_kernel(const __grid_constant__ TwoSidedParams tp) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -825,49 +878,63 @@ __global__ void __launch_bounds__(kThreads, 1) tf_two_sided_kernel(const __grid_
   const TfOut o{nullptr, nullptr, tp.status, 0};
   TfState st;
   tf_body<X3>(p, o, sm, C, crank, st);
-  tf_finish(p, o, sm, C, crank, st);
-  cluster.sync();
-  if (crank != 0) return;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(tp.counter, 1);
+  tf_finish(p, o, sm, C, crank, st);  // this CTA's rows u = crank, crank + C, ... written and fenced
+  cluster.sync();                     // peers' bulk copies out of this CTA's shared memory are done
+  // The join z = sum E_L * F_R is split over pairs: CTA c of each cluster
+  // wrote rows u = c, c + C, ... of its side; the second of the pair to
+  // arrive forms their partial sum (float64), and the last pair to finish
+  // adds the C partial sums in order.  Workspace: counter[0] pairs done,
+  // counter[1 + c] arrivals of pair c, 16 doubles of partial sums 128 bytes on.
+  int* ctr = tp.counter;
+  double* psum = reinterpret_cast<double*>(reinterpret_cast<char*>(tp.counter) + 128);
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr + 1 + crank, 1);
   __syncthreads();
   if (s_last != 1) return;
   __threadfence();
   const float* el = static_cast<const float*>(tp.half[0].e_out);
   const float* er = static_cast<const float*>(tp.half[1].e_out);
-  const int n = tp.rx * tp.ry;
+  const int nrow = tp.rx > crank ? (tp.rx - 1 - crank) / C + 1 : 0;
   double part = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
+  for (int idx = threadIdx.x; idx < nrow * tp.ry; idx += kThreads) {
+    const int i = (crank + (idx / tp.ry) * C) * tp.ry + idx % tp.ry;
     part = fma(static_cast<double>(__ldcg(el + i)), static_cast<double>(__ldcg(er + i)), part);
+  }
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double z = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) z += s_red[w];
-    const int64_t log2s = __ldcg(tp.half[0].e_out_log2) + __ldcg(tp.half[1].e_out_log2);
-    int st_bits = isfinite(z) ? 0 : TT_STATUS_NONFINITE;
-    if (tp.z_out_log2 != nullptr) {
-      *tp.z_out = z;
-      *tp.z_out_log2 = log2s;
-    } else {
-      double v = z;
-      if (z != 0.0 && isfinite(z)) {
-        const int64_t tot = static_cast<int64_t>(exp2_of(z)) + log2s;
-        if (tot > 1024) {
-          v = z > 0 ? INFINITY : -INFINITY;
-          st_bits |= TT_STATUS_OVERFLOW;
-        } else if (tot < -1074) {
-          v = 0.0;
-        } else {
-          v = ldexp(z, static_cast<int>(log2s));
-        }
-      }
-      *tp.z_out = v;
-    }
-    set_status(tp.status, st_bits);
+    double sum = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) sum += s_red[w];
+    psum[crank] = sum;
+    __threadfence();
+    s_last = atomicAdd(ctr, 1);
   }
+  __syncthreads();
+  if (s_last != C - 1 || threadIdx.x != 0) return;
+  __threadfence();
+  double z = 0.0;
+  for (int c = 0; c < C; ++c) z += __ldcg(psum + c);
+  const int64_t log2s = __ldcg(tp.half[0].e_out_log2) + __ldcg(tp.half[1].e_out_log2);
+  int st_bits = isfinite(z) ? 0 : TT_STATUS_NONFINITE;
+  if (tp.z_out_log2 != nullptr) {
+    *tp.z_out = z;
+    *tp.z_out_log2 = log2s;
+  } else {
+    double v = z;
+    if (z != 0.0 && isfinite(z)) {
+      const int64_t tot = static_cast<int64_t>(exp2_of(z)) + log2s;
+      if (tot > 1024) {
+        v = z > 0 ? INFINITY : -INFINITY;
+        st_bits |= TT_STATUS_OVERFLOW;
+      } else if (tot < -1074) {
+        v = 0.0;
+      } else {
+        v = ldexp(z, static_cast<int>(log2s));
+      }
+    }
+    *tp.z_out = v;
+  }
+  set_status(tp.status, st_bits);
 }
 
 template <typename K>

@@ -14,7 +14,9 @@ joined core C within the per-entry Cauchy-Schwarz scale of the oracle's
 (|Gx| max times the largest sqrt(Gram_x[a, a] Gram_y[b, b]) of K times
 sqrt(rank)): 1e-5 for tf32x3, 8 * 2^-11 * sqrt(2 s) for tf32 (two tf32
 roundings per contracted mode, s modes); small cases against the dense Eq. 8
-within the per-entry scale ||X[., i_F]|| ||Y[., j_F]||.
+within the per-entry scale ||X[., i_F]|| ||Y[., j_F]|| (with nothing
+contracted, C entry by entry: one tf32 rounding, 2^-11, or 2^-20 for the
+split).
 The measured errors are printed (pytest -s).
 """
 import ctypes
@@ -181,6 +183,15 @@ def test_partial_chain_small_dense(prec, mask):
     x64 = [c.astype(np.float64) for c in x]
     y64 = [c.astype(np.float64) for c in y]
     contracted = [k for k in range(5) if mask[k]]
+    if not contracted:
+        # nothing contracted: C is the boundary core of X times K = [1], one
+        # tf32 rounding (nearest) of each entry, or hi + lo with lo truncated
+        want, _ = O.partial_chain(x64, y64, mask)
+        c, w = got[len(x) - 1], want[len(x) - 1]
+        rel = float(np.max(np.abs(c - w) / np.maximum(np.abs(w), 1e-300)))
+        print(f"partial small {''.join(map(str, mask))} {prec}: C entrywise rel={rel:.2e}")
+        assert rel <= (2.0**-11 if prec == "tf32" else 2.0**-20)
+        return
     dense = O.chain_to_dense(got, perm)
     ref = O.tcp(O.tt_to_dense(x64), O.tt_to_dense(y64), contracted)
     eps = dense_cs_eps(dense, ref, x64, y64, contracted)
