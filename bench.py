@@ -777,28 +777,50 @@ def bench_batched(T, dev, args):
     # N > 1: every rank contracts its own LPT shard of the pairs (no exchange)
     subset = S.lpt_shards(costs, world)[rank] if world > 1 else None
     specs, pairs = G.batch4096_device(4096, 0, dev, subset=subset)
-    bat = T.BatchedContraction(pairs)
-    g = bat.graph()
-    setup_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
-    for _ in range(max(3, args.warmup // 4)):
-        g.replay()
-    torch.cuda.synchronize(dev)
     K = max(3, args.steps // 20)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    for a, b in evs:
-        a.record(stream)
-        g.replay()
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+
+    def time_graph(bat):
+        g = bat.graph()
+        for _ in range(max(3, args.warmup // 4)):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        for a, b in evs:
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            t = torch.tensor([t_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_ms = float(t.item())
+        del g
+        return t_ms
+
+    # untuned (the default tile configuration for every pair), then the
+    # autotuner's cache (built here, before timing) and the tuned plan
+    saved = os.environ.pop("TTC_AUTOTUNE_CACHE", None)
+    bat0 = T.BatchedContraction(pairs)
+    ms_untuned = time_graph(bat0)
+    del bat0
+    t_tune = time.perf_counter()
+    cache = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                         f"autotune_f32_rank{rank}.txt")
+    T.autotune("f32", cache)
+    tune_s = time.perf_counter() - t_tune
+    os.environ["TTC_AUTOTUNE_CACHE"] = cache
+    bat = T.BatchedContraction(pairs)
+    setup_s = time.perf_counter() - t0
+    ms = time_graph(bat)
+    if saved is not None:
+        os.environ["TTC_AUTOTUNE_CACHE"] = saved
+    else:
+        os.environ.pop("TTC_AUTOTUNE_CACHE", None)
     achieved = flops / (ms / 1e3) / 1e12
     peak = fp32_simt_peak_tflops()
     hbm = _peaks().get("hbm_gbs", 6683.2)
@@ -824,11 +846,16 @@ def bench_batched(T, dev, args):
             "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm,
         },
         "tiles": {str(int(t)): int(c) for t, c in zip(*np.unique(bat.tiles(), return_counts=True))},
+        "tiles_note": "tile configuration = panel-budget level + 3 x replica-cap index (caps none, 1, 2, 4); "
+                      "chosen per (rank, mode size) bucket by the autotuner, run before timing",
+        "value_untuned": 4096 / (ms_untuned / 1e3),
+        "ms_per_launch_untuned": ms_untuned,
+        "autotune_s": tune_s,
         "setup_s": setup_s,
         "device_status": int(bat.status.item()),
         "gpu_launches_per_replay": 1,
     }
-    del g, bat, pairs
+    del bat, pairs
     torch.cuda.empty_cache()
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_batched()

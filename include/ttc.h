@@ -228,13 +228,17 @@ typedef struct {
  * and size the device tables.  The plan of a contracted mode is its
  * evaluation order (E B_i first or A_i^T E first, whichever a cost model of
  * the kernel rates faster) and how many mode slices one panel of the kernel's
- * products takes; the panel budget is the tile configuration reported by
- * tt_plan_info (0, 1, 2 = a quarter, half or all of the kernel's buffer),
- * autotuned per (rank, mode size) bucket.  Host only, synchronous, allocates
- * host memory (freed by tt_plan_free).  Returns the bytes of the packed
- * device table (*packed_bytes) and of the workspace (*ws_bytes).
- * TT_ERR_TOO_LARGE: a swept rank above 128 (F32) / 64 (F64), or a free core
- * copied into a chain output with a right rank above 4096 (F32) / 2048 (F64). */
+ * products takes.  Each pair gets a tile configuration (reported by
+ * tt_plan_info as 0..11 = panel-budget level + 3 * replica-cap index): the
+ * panel budget is a quarter, half or all of the kernel's buffer (level 0, 1,
+ * 2), the replica cap limits the thread groups that split the second product
+ * of a slice panel to none, 1, 2 or 4; autotuned per (rank, mode size)
+ * bucket (tt_autotune), else 2 (full budget, no cap).  Host only,
+ * synchronous, allocates host memory (freed by tt_plan_free).  Returns the
+ * bytes of the packed device table (*packed_bytes) and of the workspace
+ * (*ws_bytes).  TT_ERR_TOO_LARGE: a swept rank above 128 (F32) / 64 (F64), or
+ * a free core copied into a chain output with a right rank above 4096 (F32) /
+ * 2048 (F64). */
 int tt_batch_plan(const tt_batch* batch, tt_plan** plan, size_t* packed_bytes, size_t* ws_bytes);
 
 /* Write the packed table into host memory `packed_host` (packed_bytes long);
@@ -277,14 +281,16 @@ int tt_plan_info(const tt_plan* plan, int32_t p, int32_t* n_pairs, int32_t* tile
 
 void tt_plan_free(tt_plan* plan);
 
-/* Tile autotuner for the batched launch.  For every (rank bucket <= 32, <= 64,
- * <= 128) x (mode-size bucket <= 8, <= 16, <= 32, > 32) it times each panel
- * budget level (0, 1, 2) on a synthetic batch of order-6 pairs filling the
- * GPU, and writes the fastest as text lines
- * "dtype rank_bucket mode_bucket level" to `cache_path`.  tt_batch_plan reads
- * the file named by the environment variable TTC_AUTOTUNE_CACHE (without it,
- * level 2 is used).  Synchronous; unlike every other call it allocates (and
- * frees) device memory and must not be called during stream capture. */
+/* Tile autotuner for the batched launch.  For every (rank bucket <= 16, <= 32,
+ * <= 64, <= 128) x (mode-size bucket <= 4, <= 8, <= 16, <= 32, > 32) it times
+ * each of the 12 tile configurations (see tt_batch_plan) on a batch of
+ * order-6 pairs of that rank and mode size filling the GPU, with seeded
+ * random cores (the median of three launches after a warm-up), and writes the
+ * fastest as text lines "dtype rank_bucket mode_bucket config" to
+ * `cache_path`.  tt_batch_plan reads the file named by the environment
+ * variable TTC_AUTOTUNE_CACHE (without it, configuration 2 is used).
+ * Synchronous; unlike every other call it allocates (and frees) device memory
+ * and must not be called during stream capture. */
 int tt_autotune(int dtype, const char* cache_path);
 
 /* ---------------------------------------------------------------------------
@@ -334,6 +340,16 @@ const char* tt_error_string(int code);
 /* Number of kernel launches the library has enqueued since load (all calls,
  * all threads); used to report how many of this library's kernels ran. */
 uint64_t tt_launch_count(void);
+
+/* Self-test of the device-side bounded waits (the paper has no counterpart):
+ * one CTA runs the bounded mbarrier wait that the pipelined kernels use, with
+ * a limit of `limit_cycles` SM clock cycles (0 .. 10^9, the kernels' own
+ * limit), on a barrier whose phase completes before the wait (complete != 0)
+ * or never does (complete == 0).  A wait that runs out sets TT_STATUS_TIMEOUT
+ * in *status_dev (device int32); nothing asynchronous is in flight, so the
+ * kernel returns normally either way.  TT_ERR_ARG for a NULL status or a limit
+ * out of range. */
+int tt_selftest_wait(int complete, int64_t limit_cycles, int32_t* status_dev, tt_stream stream);
 
 #ifdef __cplusplus
 }

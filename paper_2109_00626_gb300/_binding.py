@@ -41,6 +41,7 @@ EXPORTS = [
     "tt_contract_backward_k",
     "tt_error_string",
     "tt_launch_count",
+    "tt_selftest_wait",
 ]
 
 
@@ -107,6 +108,7 @@ def lib():
     L.tt_error_string.argtypes = [c_int]
     L.tt_error_string.restype = ctypes.c_char_p
     L.tt_launch_count.argtypes = []
+    L.tt_selftest_wait.argtypes = [c_int, ctypes.c_int64, c_void_p, c_void_p]
     L.tt_launch_count.restype = c_uint64
     _lib = L
     return L

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -25,28 +26,38 @@ struct tt_plan {
 
 namespace ttc {
 
-// Autotuned panel-budget level per (dtype, rank bucket, mode bucket); -1 = not tuned.
+// Autotuned tile configuration (plan_engine_steps) per (dtype, rank bucket,
+// mode bucket); -1 = not tuned.
+constexpr int kRankBuckets = 4, kModeBuckets = 5;
 struct TuneTable {
-  int tile[2][3][4];
+  int cfg[2][kRankBuckets][kModeBuckets];
   bool loaded = false;
+  char path[512] = {0};  // the cache file it was read from ("" = none)
 };
 
-static int rank_bucket(int r) { return r <= 32 ? 0 : (r <= 64 ? 1 : 2); }
-static int mode_bucket(int I) { return I <= 8 ? 0 : (I <= 16 ? 1 : (I <= 32 ? 2 : 3)); }
+static int rank_bucket(int r) { return r <= 16 ? 0 : (r <= 32 ? 1 : (r <= 64 ? 2 : 3)); }
+static int mode_bucket(int I) { return I <= 4 ? 0 : (I <= 8 ? 1 : (I <= 16 ? 2 : (I <= 32 ? 3 : 4))); }
+static const int kRankOf[kRankBuckets] = {16, 32, 64, 128};  // representative sizes the tuner times
+static const int kModeOf[kModeBuckets] = {4, 8, 16, 32, 48};
 
+// Read again whenever TTC_AUTOTUNE_CACHE names another file (or after tt_autotune).
 static TuneTable& tune_table() {
   static TuneTable t;
+  const char* path = getenv("TTC_AUTOTUNE_CACHE");
+  if (t.loaded && strncmp(t.path, path != nullptr ? path : "", sizeof(t.path) - 1) != 0) t.loaded = false;
   if (!t.loaded) {
-    for (auto& a : t.tile)
+    for (auto& a : t.cfg)
       for (auto& b : a)
         for (int& c : b) c = -1;
-    const char* path = getenv("TTC_AUTOTUNE_CACHE");
+    snprintf(t.path, sizeof(t.path), "%s", path != nullptr ? path : "");
     if (path != nullptr) {
       FILE* f = fopen(path, "r");
       if (f != nullptr) {
-        int d, rb, ib, tl;
-        while (fscanf(f, "%d %d %d %d", &d, &rb, &ib, &tl) == 4)
-          if (d >= 0 && d < 2 && rb >= 0 && rb < 3 && ib >= 0 && ib < 4 && tl >= 0 && tl < 3) t.tile[d][rb][ib] = tl;
+        int d, rb, ib, cfg;
+        while (fscanf(f, "%d %d %d %d", &d, &rb, &ib, &cfg) == 4)
+          if (d >= 0 && d < 2 && rb >= 0 && rb < kRankBuckets && ib >= 0 && ib < kModeBuckets && cfg >= 0 &&
+              cfg < kTileConfigs)
+            t.cfg[d][rb][ib] = cfg;
         fclose(f);
       }
     }
@@ -55,12 +66,12 @@ static TuneTable& tune_table() {
   return t;
 }
 
-// Panel-budget level of a pair's engine plan (see plan_engine_steps): the
-// autotuned value of its (rank, mode) bucket, else the full budget.
-static int choose_level(const SweepParams& p, int dtype) {
+// Tile configuration of a pair's engine plan: the autotuned value of its
+// (rank, mode) bucket, else the default (full panel budget, no replica cap).
+static int choose_config(const SweepParams& p, int dtype) {
   const int d = dtype == TT_F64 ? 1 : 0;
-  const int tuned = tune_table().tile[d][rank_bucket(sweep_max_rank(p))][mode_bucket(sweep_max_mode(p))];
-  return tuned >= 0 ? tuned : 2;
+  const int tuned = tune_table().cfg[d][rank_bucket(sweep_max_rank(p))][mode_bucket(sweep_max_mode(p))];
+  return tuned >= 0 ? tuned : kDefaultTileConfig;
 }
 
 }  // namespace ttc
@@ -108,7 +119,7 @@ int tt_batch_plan(const tt_batch* b, tt_plan** plan_out, size_t* packed_bytes, s
       delete plan;
       return rc;
     }
-    plan->tile[i] = choose_level(plan->table[i], plan->dtype);
+    plan->tile[i] = choose_config(plan->table[i], plan->dtype);
     plan_engine_steps(plan->table[i], plan->dtype, plan->tile[i]);
     plan->cost[i] = sweep_flops(plan->table[i]);
   }
@@ -180,9 +191,6 @@ int tt_autotune(int dtype, const char* cache_path) {
   if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_DTYPE;
   const int d = dtype == TT_F64 ? 1 : 0;
   const int eb = dtype == TT_F64 ? 8 : 4;
-  const int nlevels = 3;
-  const int rank_of[3] = {32, 64, 128};
-  const int mode_of[4] = {8, 16, 32, 48};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -211,18 +219,40 @@ int tt_autotune(int dtype, const char* cache_path) {
       cudaEventCreate(&e1) != cudaSuccess) {
     rc = TT_ERR_CUDA;
   }
-  for (int rb = 0; rb < 3 && rc == TT_OK; ++rb) {
-    if (dtype == TT_F64 && rb == 2) break;  // float64 ranks stop at 64
-    for (int ib = 0; ib < 4 && rc == TT_OK; ++ib) {
-      const int R = dtype == TT_F64 ? std::min(rank_of[rb], 64) : rank_of[rb];
-      const int I = mode_of[ib];
-      // one synthetic pair (zeros: the timing does not depend on values)
+  for (int rb = 0; rb < kRankBuckets && rc == TT_OK; ++rb) {
+    if (dtype == TT_F64 && kRankOf[rb] > 64) break;  // float64 ranks stop at 64
+    for (int ib = 0; ib < kModeBuckets && rc == TT_OK; ++ib) {
+      const int R = kRankOf[rb];
+      const int I = kModeOf[ib];
+      // one synthetic pair per CTA slot: seeded values (a 64-bit linear
+      // congruential stream, uniform in [-1, 1) / sqrt(I R)), the same for X and Y
       const size_t core_elems = static_cast<size_t>(R) * I * R;
       const size_t bytes = core_elems * eb * order;
-      if (cudaMalloc(&cores, bytes) != cudaSuccess || cudaMemset(cores, 0, bytes) != cudaSuccess) {
+      if (cudaMalloc(&cores, bytes) != cudaSuccess) {
         rc = TT_ERR_CUDA;
         release();
         break;
+      }
+      {
+        std::vector<double> h64;
+        std::vector<float> h32;
+        uint64_t st = 0x2109006260ull + 977ull * (rb * kModeBuckets + ib);
+        const double sc = 1.0 / std::sqrt(static_cast<double>(I) * R);
+        const size_t n = core_elems * order;
+        if (eb == 8) h64.resize(n);
+        else h32.resize(n);
+        for (size_t e = 0; e < n; ++e) {
+          st = st * 6364136223846793005ull + 1442695040888963407ull;
+          const double v = (static_cast<double>(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * sc;
+          if (eb == 8) h64[e] = v;
+          else h32[e] = static_cast<float>(v);
+        }
+        if (cudaMemcpy(cores, eb == 8 ? static_cast<void*>(h64.data()) : static_cast<void*>(h32.data()), bytes,
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+          rc = TT_ERR_CUDA;
+          release();
+          break;
+        }
       }
       int32_t modes[order], ranks[order + 1];
       void* ptrs[order];
@@ -237,8 +267,6 @@ int tt_autotune(int dtype, const char* cache_path) {
       build_full(&x, &x, nullptr, nullptr, nullptr, &p);
       std::vector<SweepParams> tab(npairs, p);
       std::vector<int32_t> ord(npairs), tl(npairs);
-      std::vector<SweepParams> lvl_tab(nlevels, p);
-      for (int t = 0; t < nlevels; ++t) plan_engine_steps(lvl_tab[t], dtype, t);
       std::iota(ord.begin(), ord.end(), 0);
       if (cudaMalloc(&dev_table, sizeof(SweepParams) * npairs + 8 * npairs + 256) != cudaSuccess ||
           cudaMalloc(&counter, 256) != cudaSuccess || cudaMalloc(&out, sizeof(double) * npairs) != cudaSuccess) {
@@ -249,13 +277,16 @@ int tt_autotune(int dtype, const char* cache_path) {
       char* tb = static_cast<char*>(dev_table);
       cudaMemcpy(tb + sizeof(SweepParams) * npairs, ord.data(), 4 * npairs, cudaMemcpyHostToDevice);
       float best_ms = 1e30f;
-      int best = nlevels - 1;
-      for (int t = 0; t < nlevels; ++t) {
-        std::fill(tab.begin(), tab.end(), lvl_tab[t]);
+      int best = kDefaultTileConfig;
+      std::vector<SweepParams> cfg_tab(1, p);
+      for (int cfg = 0; cfg < kTileConfigs && rc == TT_OK; ++cfg) {
+        cfg_tab[0] = p;
+        plan_engine_steps(cfg_tab[0], dtype, cfg);
+        std::fill(tab.begin(), tab.end(), cfg_tab[0]);
         cudaMemcpy(tb, tab.data(), sizeof(SweepParams) * npairs, cudaMemcpyHostToDevice);
-        std::fill(tl.begin(), tl.end(), t);
+        std::fill(tl.begin(), tl.end(), cfg);
         cudaMemcpy(tb + sizeof(SweepParams) * npairs + 4 * npairs, tl.data(), 4 * npairs, cudaMemcpyHostToDevice);
-        float ms_sum = 0.f;
+        float times[4];
         for (int rep = 0; rep < 4; ++rep) {
           cudaMemsetAsync(counter, 0, 8, s);
           cudaEventRecord(e0, s);
@@ -264,21 +295,21 @@ int tt_autotune(int dtype, const char* cache_path) {
                          0, counter, out, nullptr, nullptr, dtype, 0, s);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0) ms_sum += ms;
+          cudaEventElapsedTime(&times[rep], e0, e1);
         }
         if (cudaGetLastError() != cudaSuccess) {
           rc = TT_ERR_CUDA;
           break;
         }
-        if (ms_sum < best_ms) {
-          best_ms = ms_sum;
-          best = t;
+        // median of the three launches after the first
+        std::sort(times + 1, times + 4);
+        if (times[2] < best_ms) {
+          best_ms = times[2];
+          best = cfg;
         }
       }
       release();
-      // a bucket is written only when every level of it was timed without error
+      // a bucket is written only when every configuration of it was timed without error
       if (rc == TT_OK) fprintf(f, "%d %d %d %d\n", d, rb, ib, best);
     }
   }

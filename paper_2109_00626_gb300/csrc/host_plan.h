@@ -516,8 +516,10 @@ inline int merged_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask, 
 //
 // For every contracted mode but the float64 last one, choose the evaluation
 // order (0: E B_i first, 1: A_i^T E first) and the slices per panel g that
-// minimise a model of the engine's time (eng_mode_cost).  `level` (0..2, the
-// autotuned knob) caps the T panel at 1/4, 1/2 or all of the engine's budget.
+// minimise a model of the engine's time (eng_mode_cost).  The two autotuned
+// knobs: `level` (0..2) caps the T panel at 1/4, 1/2 or all of the engine's
+// budget, `rcap` (0 = none, else 1, 2, 4) caps the replica thread groups
+// that split the second product.
 inline int eng_r4(int v) { return (v + 3) & ~3; }
 inline int eng_pow2_floor(int v) { return v <= 1 ? 1 : pow2_floor(v); }
 
@@ -547,7 +549,7 @@ inline int eng_gmax(const EngGeom& eg, int m, int n, int u, int I, int budget) {
 // I slices in panels of g: one or two 4x4 tiles per thread (as the engine
 // picks), k (GEMM1) and m (GEMM2, per slice of a replica group) steps per
 // panel, plus a fixed cost per streamed chunk.
-inline double eng_mode_cost(const EngGeom& eg, bool f64, int m, int k, int n, int u, int I, int g) {
+inline double eng_mode_cost(const EngGeom& eg, bool f64, int m, int k, int n, int u, int I, int g, int rcap = 0) {
   const int NT = kEngThreads;
   constexpr double kChunk = 200.0;  // stage hand-off and pipeline bubble per streamed chunk
   const int n_pad = eng_r4(n), u_pad = eng_r4(u), m_pad = eng_r4(m);
@@ -558,6 +560,7 @@ inline double eng_mode_cost(const EngGeom& eg, bool f64, int m, int k, int n, in
   int rep = std::min(g, NT / 32);
   rep = std::min(rep, std::max(1, NT / tiles2));
   rep = std::min(rep, std::max(1, eg.tbuf / (eng_r8(u) * eng_r8(n))));
+  if (rcap > 0) rep = std::min(rep, rcap);
   rep = eng_pow2_floor(rep);
   const int ntr = NT / rep;
   const bool one = f64 || (tiles1 <= NT && tiles2 <= ntr);  // one 4x4 tile per thread, else two
@@ -573,7 +576,17 @@ inline double eng_mode_cost(const EngGeom& eg, bool f64, int m, int k, int n, in
   return t;
 }
 
-inline void plan_engine_steps(SweepParams& p, int dtype, int level) {
+// Tile configuration codes of the batched engine: level + 3 * rcap index.
+constexpr int kTileConfigs = 12;
+constexpr int kDefaultTileConfig = 2;  // full panel budget, no replica cap
+inline int config_level(int cfg) { return cfg % 3; }
+inline int config_rcap(int cfg) {
+  static const int caps[4] = {0, 1, 2, 4};
+  return caps[(cfg / 3) & 3];
+}
+
+inline void plan_engine_steps(SweepParams& p, int dtype, int cfg) {
+  const int level = config_level(cfg), rcap = config_rcap(cfg);
   const EngGeom eg = eng_geom(dtype);
   const bool f64 = dtype == TT_F64;
   const int budget = eg.tiles_cap >> (2 - std::max(0, std::min(2, level)));
@@ -583,6 +596,7 @@ inline void plan_engine_steps(SweepParams& p, int dtype, int level) {
     SweepStep& st = p.step[j];
     st.ord = 0;
     st.g = 1;
+    st.rcap = rcap;
     if (j >= n_modes) continue;
     double best = 1e300;
     for (int ord = 0; ord < 2; ++ord) {
@@ -590,7 +604,7 @@ inline void plan_engine_steps(SweepParams& p, int dtype, int level) {
       const int n = ord == 0 ? st.rout_y : st.rout_x, u = ord == 0 ? st.rout_x : st.rout_y;
       const int gmax = eng_gmax(eg, m, n, u, st.I, budget);
       auto consider = [&](int g) {
-        const double c = eng_mode_cost(eg, f64, m, k, n, u, st.I, g);
+        const double c = eng_mode_cost(eg, f64, m, k, n, u, st.I, g, rcap);
         if (c < best) {
           best = c;
           st.ord = ord;

@@ -404,6 +404,7 @@ __device__ void run_pair(const SweepParams& p, const SweepOut& o, unsigned char*
       int rep = min(G.g, NT / 32);  // replica groups of whole warps
       rep = min(rep, max(1, NT / tiles2));
       rep = min(rep, max(1, L::TBUF / (r8(G.u) * r8(G.n))));
+      if (st.rcap > 0) rep = min(rep, st.rcap);  // autotuned cap
       G.rep = pow2_floor_d(rep);
       const int ntr = NT / G.rep;
       // tiles1 <= r8(m) r8(W) / 16 <= 2 NT and tiles2 <= 2 NT / rep by the limits above

@@ -102,13 +102,16 @@ __device__ __forceinline__ bool mbar_try(void* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity.  Gives up (returns false)
-// after about half a second, or at once when *abort is set (by another role
-// of the CTA that already gave up), so a broken pipeline ends quickly.
-__device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, volatile int* abort) {
+// after `limit` SM cycles (by default 10^9, about half a second), or at once
+// when *abort is set (by another role of the CTA that already gave up), so a
+// broken pipeline ends quickly.
+constexpr long long kWaitLimit = 1000000000LL;
+__device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, volatile int* abort,
+                                          long long limit = kWaitLimit) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (*abort || clock64() - t0 > 1000000000LL) {
+    if (*abort || clock64() - t0 > limit) {
       *abort = 1;
       return false;
     }

@@ -33,9 +33,11 @@ struct SweepStep {
   int rin_x, rout_x;  // p range, u range
   int rin_y, rout_y;  // q range, v range
   // Batched engine only (filled by plan_engine_steps): evaluation order
-  // (0: T_i = E B_i first, 1: U_i = A_i^T E first) and slices per panel.
+  // (0: T_i = E B_i first, 1: U_i = A_i^T E first), slices per panel, and a
+  // cap on the replica thread groups of the second product (0 = none).
   int ord;
   int g;
+  int rcap;
 };
 
 // Geometry limits of the per-CTA engine of the batched launch (pair_engine.cuh);

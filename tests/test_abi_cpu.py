@@ -236,7 +236,7 @@ def test_batch_plan_on_the_host(L):
         t = ctypes.c_int32(-1)
         for p in range(len(specs)):
             assert L.tt_plan_info(plan, p, ctypes.byref(n), ctypes.byref(t)) == 0
-            assert n.value == len(specs) and t.value in (0, 1, 2)
+            assert n.value == len(specs) and t.value == 2  # no tuning cache: full budget, no replica cap
         assert L.tt_plan_info(plan, len(specs), None, ctypes.byref(t)) == -1
         buf = (ctypes.c_uint8 * pb)()
         assert L.tt_batch_pack(plan, buf, pb) == 0
@@ -296,6 +296,15 @@ def test_batched_entries_reject_missing_buffers(L):
         assert L.tt_contract_batched(plan, packed, out, None, st, ws, wb - 1, None) == -6  # too small
     finally:
         L.tt_plan_free(plan)
+
+
+def test_selftest_wait_arguments(L):
+    """The bounded-wait self-test rejects a NULL status and a limit outside
+    0 .. 10^9 cycles before launching anything."""
+    st = ctypes.c_void_p(0x3000)
+    assert L.tt_selftest_wait(0, 1000, None, None) == -1
+    assert L.tt_selftest_wait(0, -1, st, None) == -1
+    assert L.tt_selftest_wait(0, 10**9 + 1, st, None) == -1
 
 
 def test_tf32_forms_rejections(L):

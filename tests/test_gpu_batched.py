@@ -213,14 +213,35 @@ def test_autotune_cache(tmp_path, monkeypatch):
     T.autotune("f32", path)
     lines = open(path).read().split("\n")
     rows = [list(map(int, ln.split())) for ln in lines if ln.strip()]
-    assert len(rows) == 12
-    for d, rb, ib, level in rows:
-        assert d == 0 and 0 <= level <= 2
+    assert len(rows) == 20  # 4 rank buckets x 5 mode-size buckets
+    for d, rb, ib, cfg in rows:
+        assert d == 0 and 0 <= rb < 4 and 0 <= ib < 5 and 0 <= cfg < 12
     pairs = _uneven_pairs(8, 5)
     dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
     bat = T.BatchedContraction(dev)
     bat()
     torch.cuda.synchronize()
+    _check(pairs, bat, 1e-5)
+
+
+@pytest.mark.parametrize("cfg", range(12))
+def test_every_tile_configuration(tmp_path, monkeypatch, cfg):
+    """Every tile configuration the autotuner can choose (panel-budget level
+    and replica cap), forced on every bucket through a cache file, gives the
+    oracle's results on uneven pairs of ranks up to 128."""
+    path = str(tmp_path / f"cfg{cfg}.txt")
+    with open(path, "w") as f:
+        for rb in range(4):
+            for ib in range(5):
+                f.write(f"0 {rb} {ib} {cfg}\n")
+    monkeypatch.setenv("TTC_AUTOTUNE_CACHE", path)
+    pairs = _uneven_pairs(12, 40 + cfg, rmax=128, nmax=5)
+    dev = [(to_dev(x), to_dev(y), m) for x, y, m in pairs]
+    bat = T.BatchedContraction(dev)
+    assert set(bat.tiles()) == {cfg}
+    bat()
+    torch.cuda.synchronize()
+    assert int(bat.status.item()) == 0
     _check(pairs, bat, 1e-5)
 
 
