@@ -208,6 +208,35 @@ int tt_contract_partial_k(const tt_desc* x, const tt_desc* y, const uint8_t* mas
                           const tt_desc* z, int64_t* z_log2_dev, int32_t* status_dev, void* ws,
                           size_t ws_bytes, tt_stream stream);
 
+/* Partial contraction of TTs of different orders over mode pairs: mode
+ * xmodes[t] of X (order N) is contracted with mode ymodes[t] of Y (order M),
+ * t < n_pairs (Eq. 8 applied to each pair, e.g. Example 1's x_3^2).  The
+ * xmodes form a block at one end of X, the ymodes one at one end of Y, and
+ * walking both trains from those ends inward meets the pairs in the same
+ * order (leading against leading, leading against trailing, ...); else
+ * TT_ERR_LAYOUT.  Result: one TT (chain layout) of (N - s) + (M - s) cores,
+ * s = n_pairs: an operand whose block is the trailing one is read backwards
+ * with its rank legs swapped, so both blocks lead; K is the environment over
+ * the pairs; the cores are X's free cores walked from its far end back
+ * (legs swapped), C = X's boundary core joined with K, then Y's free cores
+ * (Algorithm 2 steps 4-6).  When X has no free mode the roles exchange: Y's
+ * free cores walked back, the last of them joined with K^T.
+ * tt_pairs_shape (host only, synchronous) reports the output shape and
+ * z_perm: axis p of the represented tensor is axis z_perm[p] of Eq. 8's Z
+ * (X's free modes ascending, then Y's).  Arrays hold N + M (+1 for ranks)
+ * entries.  Mode sizes must agree on every pair (TT_ERR_SHAPE); repeated or
+ * out-of-range modes, n_pairs < 1, or every mode of both operands contracted
+ * (use tt_contract_full): TT_ERR_ARG.
+ * tt_contract_pairs: `z` describes caller-allocated output cores of exactly
+ * that shape, same dtype; z_log2_dev as in tt_contract_partial.  Precision:
+ * TT_P_NATIVE (F64/F32), TT_P_TF32 and TT_P_TF32X3 (F32, ranks <= 64).
+ * Asynchronous on `stream`; no allocation. */
+int tt_pairs_shape(const tt_desc* x, const tt_desc* y, int n_pairs, const int32_t* xmodes, const int32_t* ymodes,
+                   int32_t* z_order, int32_t* z_modes, int32_t* z_ranks, int32_t* z_perm);
+int tt_contract_pairs(const tt_desc* x, const tt_desc* y, int n_pairs, const int32_t* xmodes,
+                      const int32_t* ymodes, int prec, const tt_desc* z, int64_t* z_log2_dev,
+                      int32_t* status_dev, tt_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Batched contraction of many independent pairs in one persistent launch.
  * ------------------------------------------------------------------------- */

@@ -19,14 +19,17 @@ from ._binding import (  # noqa: F401
     PREC,
     Desc,
     FullContraction,
+    PairsContraction,
     PartialContraction,
     TTError,
     contract_full,
+    contract_pairs,
     contract_partial,
     error_string,
     launch_count,
     lib,
     partial_k,
+    pairs_shape,
     partial_shape,
     workspace_bytes,
 )

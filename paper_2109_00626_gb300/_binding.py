@@ -42,6 +42,8 @@ EXPORTS = [
     "tt_error_string",
     "tt_launch_count",
     "tt_selftest_wait",
+    "tt_pairs_shape",
+    "tt_contract_pairs",
 ]
 
 
@@ -109,6 +111,8 @@ def lib():
     L.tt_error_string.restype = ctypes.c_char_p
     L.tt_launch_count.argtypes = []
     L.tt_selftest_wait.argtypes = [c_int, ctypes.c_int64, c_void_p, c_void_p]
+    L.tt_pairs_shape.argtypes = [D, D, c_int, I32, I32, I32, I32, I32, I32]
+    L.tt_contract_pairs.argtypes = [D, D, c_int, I32, I32, c_int, D, c_void_p, c_void_p, c_void_p]
     L.tt_launch_count.restype = c_uint64
     _lib = L
     return L
@@ -325,6 +329,68 @@ class PartialContraction:
         )
         check(rc, "tt_contract_partial")
         return self.z
+
+
+def pairs_shape(xd, yd, pairs):
+    """tt_pairs_shape: (modes, ranks, perm) of the chain-layout result of
+    contracting mode pairs[t][0] of X with mode pairs[t][1] of Y."""
+    n = xd.desc.order + yd.desc.order
+    s = len(pairs)
+    xm = (c_int32 * max(s, 1))(*[int(a) for a, _ in pairs])
+    ym = (c_int32 * max(s, 1))(*[int(b) for _, b in pairs])
+    order = c_int32(0)
+    modes = (c_int32 * n)()
+    ranks = (c_int32 * (n + 1))()
+    perm = (c_int32 * n)()
+    check(lib().tt_pairs_shape(xd.ref, yd.ref, s, xm, ym, ctypes.byref(order), modes, ranks, perm), "tt_pairs_shape")
+    o = order.value
+    return list(modes[:o]), list(ranks[: o + 1]), list(perm[:o])
+
+
+class PairsContraction:
+    """Pre-marshalled contraction of TTs of (possibly) different orders over
+    end-block mode pairs (tt_contract_pairs); output cores allocated once."""
+
+    def __init__(self, x, y, pairs, prec="native", split=False):
+        import torch
+
+        self.xd, self.yd = Desc(x), Desc(y)
+        self.pairs = [(int(a), int(b)) for a, b in pairs]
+        s = len(self.pairs)
+        self._xm = (c_int32 * max(s, 1))(*[a for a, _ in self.pairs])
+        self._ym = (c_int32 * max(s, 1))(*[b for _, b in self.pairs])
+        self.prec = PREC[prec]
+        dev = x[0].device
+        modes, ranks, perm = pairs_shape(self.xd, self.yd, self.pairs)
+        self.perm = perm
+        self.z = [torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=dev) for t in range(len(modes))]
+        self.zd = Desc(self.z)
+        self.log2 = torch.zeros(1, dtype=torch.int64, device=dev) if split else None
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def __call__(self, stream=None):
+        rc = lib().tt_contract_pairs(
+            self.xd.ref,
+            self.yd.ref,
+            len(self.pairs),
+            self._xm,
+            self._ym,
+            self.prec,
+            self.zd.ref,
+            c_void_p(self.log2.data_ptr()) if self.log2 is not None else None,
+            c_void_p(self.status.data_ptr()),
+            _stream_ptr(stream),
+        )
+        check(rc, "tt_contract_pairs")
+        return self.z
+
+
+def contract_pairs(x, y, pairs, prec="native", stream=None):
+    """Contract mode pairs[t][0] of X with pairs[t][1] of Y (end blocks, any
+    orders); returns (cores, perm) of the chain-layout result."""
+    op = PairsContraction(x, y, pairs, prec)
+    op(stream)
+    return op.z, op.perm
 
 
 def contract_full(x, y, prec="native", split=False, stream=None):

@@ -81,6 +81,7 @@ inline int pow2_floor(int v) {
 inline void fill_left(SweepParams& p, const tt_desc* x, const tt_desc* y, int k0, int k1) {
   p.n_steps = k1 - k0;
   p.transposed = 0;
+  p.transposed_y = 0;
   for (int j = 0; j < p.n_steps; ++j) {
     const int k = k0 + j;
     SweepStep& st = p.step[j];
@@ -98,6 +99,7 @@ inline void fill_left(SweepParams& p, const tt_desc* x, const tt_desc* y, int k0
 inline void fill_right(SweepParams& p, const tt_desc* x, const tt_desc* y, int k0, int k1) {
   p.n_steps = k1 - k0;
   p.transposed = 1;
+  p.transposed_y = 1;
   for (int j = 0; j < p.n_steps; ++j) {
     const int k = k1 - 1 - j;
     SweepStep& st = p.step[j];

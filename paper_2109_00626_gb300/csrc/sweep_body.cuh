@@ -360,7 +360,8 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       const int cols = prod.which == 0 ? st.rout_y : st.rout_x;
       const T* core = static_cast<const T*>(prod.which == 0 ? st.gy : st.gx);
       const int r0 = prod.c * Cfg::KC;
-      load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, p.transposed, r0, min(Cfg::KC, rows - r0));
+      load_rows_async<T, LD, NT>(dst, core, prod.i, st.I, rows, cols, prod.which == 0 ? p.transposed_y : p.transposed,
+                                 r0, min(Cfg::KC, rows - r0));
       ++Lp;
       it_next<Cfg::KC>(prod, sst, n_pipe, crank, C);
     }
@@ -690,7 +691,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
     double part = 0.0;
     for (int i = crank; i < I; i += C) {
       for (int q = tid; q < st.rin_y; q += NT)
-        bvec[q] = p.transposed ? ldg(gy + static_cast<int64_t>(i) * st.rin_y + q)
+        bvec[q] = p.transposed_y ? ldg(gy + static_cast<int64_t>(i) * st.rin_y + q)
                                : ldg(gy + static_cast<int64_t>(q) * I + i);
       for (int a = tid; a < st.rin_x; a += NT)
         avec[a] = p.transposed ? ldg(gx + static_cast<int64_t>(i) * st.rin_x + a)

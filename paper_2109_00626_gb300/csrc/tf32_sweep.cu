@@ -296,10 +296,10 @@ __device__ void tf_body(const SweepParams& p, const TfOut& o, unsigned char* sm,
         const int i = crank + t * C;
         const int sb = ib % NB, sa = ia % NA;
         // both tiles of the slice in flight before either buffer is waited for
-        load_regs(rb, static_cast<const float*>(s.gy), i, s.I, s.rin_y, s.rout_y, p.transposed, tl);  // B_i^T: rows v, columns q
+        load_regs(rb, static_cast<const float*>(s.gy), i, s.I, s.rin_y, s.rout_y, p.transposed_y, tl);  // B_i^T: rows v, columns q
         load_regs(ra, static_cast<const float*>(s.gx), i, s.I, s.rin_x, s.rout_x, p.transposed, tl);  // A_i^T: rows u, columns p
         if (!tc::mbar_wait(&b_empty[sb], ((ib / NB) & 1) ^ 1, abort)) bits |= TT_STATUS_TIMEOUT;
-        store_tile(sm + OFF_B + sb * TILE, rb, p.transposed, X3, tl);
+        store_tile(sm + OFF_B + sb * TILE, rb, p.transposed_y, X3, tl);
         tc::fence_proxy_async();
         tc::mbar_arrive(&b_full[sb]);
         ++ib;
@@ -758,7 +758,7 @@ __device__ void tf_finish(const SweepParams& p, const TfOut& o, unsigned char* s
     double part = 0.0;
     for (int i = crank; i < s.I; i += C) {
       for (int qq = tid; qq < s.rin_y; qq += kThreads)
-        bvec[qq] = p.transposed ? __ldg(gy + static_cast<int64_t>(i) * s.rin_y + qq) : __ldg(gy + static_cast<int64_t>(qq) * s.I + i);
+        bvec[qq] = p.transposed_y ? __ldg(gy + static_cast<int64_t>(i) * s.rin_y + qq) : __ldg(gy + static_cast<int64_t>(qq) * s.I + i);
       __syncthreads();
       for (int a = tid; a < s.rin_x; a += kThreads) {
         float t = 0.f;

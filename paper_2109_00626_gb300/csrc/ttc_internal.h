@@ -93,7 +93,9 @@ struct EmitParams {
 
 struct SweepParams {
   int n_steps;            // contracted modes in the sweep (may be 0 for an emission only)
-  int transposed;         // 1 = right-to-left (slices read with swapped legs)
+  int transposed;         // 1 = X's slices read with swapped legs (right-to-left sweep)
+  int transposed_y;       // the same for Y (equal to `transposed` except for mode pairs
+                          // that walk one operand forwards and the other backwards)
   int final_scalar;       // 1 = the last step ends at a 1x1 environment summed in float64
   int renorm_bits;
   SweepStep step[kMaxOrder];

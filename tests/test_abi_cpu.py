@@ -298,6 +298,62 @@ def test_batched_entries_reject_missing_buffers(L):
         L.tt_plan_free(plan)
 
 
+def _pairs_shape(L, x, y, pairs):
+    n = x.desc.order + y.desc.order
+    xm = (ctypes.c_int32 * len(pairs))(*[a for a, _ in pairs])
+    ym = (ctypes.c_int32 * len(pairs))(*[b for _, b in pairs])
+    order = ctypes.c_int32(0)
+    modes = (ctypes.c_int32 * n)()
+    ranks = (ctypes.c_int32 * (n + 1))()
+    perm = (ctypes.c_int32 * n)()
+    rc = L.tt_pairs_shape(x.ref, y.ref, len(pairs), xm, ym, ctypes.byref(order), modes, ranks, perm)
+    o = order.value
+    return rc, list(modes[:o]), list(ranks[: o + 1]), list(perm[:o])
+
+
+def test_pairs_shape_on_the_host(L):
+    """tt_pairs_shape: the chain's mode sizes are X's free modes walked back,
+    then Y's (Y's walked back when X has none), perm a permutation of Eq. 8's
+    axes consistent with the sizes; the oracle's layout where X has free
+    modes; rejections before anything is enqueued."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2109_00626_gb300 import inputs as G
+
+    cases = [([2, 3, 4, 5], [4, 6, 7], [(2, 0)]),   # not an end block of X
+             ([2, 3, 4, 5], [5, 6, 7], [(3, 0)]),
+             ([2, 3, 4, 5], [6, 5, 4], [(3, 1), (2, 2)]),
+             ([3, 4], [3, 4, 5, 6], [(0, 0), (1, 1)]),
+             ([5, 4, 3], [3, 4], [(2, 0), (1, 1)])]
+    for mx, my, pairs in cases:
+        rng = np.random.default_rng(1)
+        rx = [1] + [3] * (len(mx) - 1) + [1]
+        ry = [1] + [2] * (len(my) - 1) + [1]
+        x, y = FakeDesc(mx, rx), FakeDesc(my, ry)
+        rc, modes, ranks, perm = _pairs_shape(L, x, y, pairs)
+        try:
+            oc, operm = O.partial_chain_pairs(G.random_tt(rng, mx, rx, np.float64),
+                                              G.random_tt(rng, my, ry, np.float64), pairs)
+        except ValueError:
+            assert rc == -4, (pairs, rc)  # TT_ERR_LAYOUT
+            continue
+        assert rc == 0
+        fx = [m for k, m in enumerate(mx) if k not in {a for a, _ in pairs}]
+        fy = [m for k, m in enumerate(my) if k not in {b for _, b in pairs}]
+        eq8 = fx + fy
+        assert sorted(perm) == list(range(len(eq8)))
+        assert [eq8[pm] for pm in perm] == modes
+        assert ranks[0] == 1 and ranks[-1] == 1
+        if len(fx) > 0:
+            assert modes == [c.shape[1] for c in oc] and perm == operm
+            assert ranks[:-1] == [c.shape[0] for c in oc]
+    x, y = FakeDesc([2, 3], [1, 2, 1]), FakeDesc([3, 2], [1, 2, 1])
+    assert _pairs_shape(L, x, y, [(0, 1), (1, 0)])[0] == -1   # every mode of both: a full contraction
+    assert _pairs_shape(L, x, y, [(1, 0), (1, 1)])[0] == -1   # a mode paired twice
+    assert _pairs_shape(L, x, FakeDesc([4, 2], [1, 2, 1]), [(1, 0)])[0] == -2  # sizes differ
+
+
 def test_selftest_wait_arguments(L):
     """The bounded-wait self-test rejects a NULL status and a limit outside
     0 .. 10^9 cycles before launching anything."""
