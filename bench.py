@@ -37,11 +37,10 @@ from paper_2109_00626_gb300 import inputs as G  # noqa: E402
 from paper_2109_00626_gb300 import workload as W  # noqa: E402
 
 # DRAM bytes read + written by one launch of sweep_two_sided_kernel<float,64> on
-# this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2; see
-# profiles/two_sided_order10_r64.md).  Reset to None whenever that kernel changes:
-# the capture there (4287616 bytes) predates its exponents read from IEEE bits
-# and the checkpoint stores added to the shared sweep body.
-TWO_SIDED_TRAFFIC = None
+# this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2; the
+# capture is in profiles/launches_order10_r64_step.md).  Reset to None whenever
+# that kernel or the sweep body changes.
+TWO_SIDED_TRAFFIC = 4288000
 
 METRIC = "TT contractions/s (order-10, I=16, R=64, fp32: full + partial over modes 1-6)"
 UNIT = "contractions/s"

@@ -313,10 +313,12 @@ void tt_plan_free(tt_plan* plan);
 /* Tile autotuner for the batched launch.  For every (rank bucket <= 16, <= 32,
  * <= 64, <= 128) x (mode-size bucket <= 4, <= 8, <= 16, <= 32, > 32) it times
  * each of the 12 tile configurations (see tt_batch_plan) on a batch of
- * order-6 pairs of that rank and mode size filling the GPU, with seeded
- * random cores (the median of three launches after a warm-up), and writes the
- * fastest as text lines "dtype rank_bucket mode_bucket config" to
- * `cache_path`.  tt_batch_plan reads the file named by the environment
+ * order-6 full contractions of that rank and mode size filling the GPU (two
+ * per SM), with seeded random cores that are distinct per pair up to 2 GiB
+ * (so they stream from memory, not from L2), the median of three launches
+ * after a warm-up; a configuration other than 2 is chosen only when it is at
+ * least 3 % faster than configuration 2.  Writes text lines
+ * "dtype rank_bucket mode_bucket config" to `cache_path`.  tt_batch_plan reads the file named by the environment
  * variable TTC_AUTOTUNE_CACHE (without it, configuration 2 is used).
  * Synchronous; unlike every other call it allocates (and frees) device memory
  * and must not be called during stream capture. */
