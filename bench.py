@@ -562,6 +562,7 @@ def run_ours(args):
             "bf16x3": lambda: bench_bf16(T, dev, args, "bf16x3"),
             "backward": lambda: bench_backward(T, dev, args),
             "merged": lambda: bench_merged(T, dev, args),
+            "dense_ttcp": lambda: bench_dense_ttcp(T, dev, args),
         }
         wanted = list(runners) if args.forms == "all" else [f for f in args.forms.split(",") if f]
         for name in wanted:
@@ -939,6 +940,71 @@ def bench_merged(T, dev, args):
         "device_status": status,
         "l2": "flushed before each contraction",
     }
+
+
+EXAMPLE2_Y = [(20, 20, 20), (20, 20, 20, 5), (20, 20, 20, 5, 4)]
+
+
+def bench_dense_ttcp(T, dev, args):
+    """Dense-input contraction (Alg. 2 on dense operands): Example 2's
+    X x_1^1 Y with X in R^{20x20x20} and Y of 20^3, 20^3 x 5 and
+    20^3 x 5 x 4, Gaussian, float32, eps = 1e-6 (full ranks): both TT-SVDs
+    and the contraction of the leading pair, timed end to end with CUDA
+    events (the call reads the chosen ranks back to size the contraction);
+    beside it the float64 oracle (its TT decomposition of both operands and
+    the chain contraction) on one host thread, and the accuracy of the GPU
+    result against Eq. 8 on the dense tensors."""
+    import time as _time
+
+    import torch
+
+    import oracle as O
+
+    rng = np.random.default_rng(2109)
+    xh = rng.standard_normal((20, 20, 20)).astype(np.float32)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "Example 2 shapes: X 20^3 x_1^1 Y (Y = 20^3, 20^3x5, 20^3x5x4), Gaussian, float32, "
+                       "eps 1e-6; TT-SVD of both operands on the GPU, then the leading-pair chain contraction",
+           "cases": []}
+    status = 0
+    for ys in EXAMPLE2_Y:
+        yh = rng.standard_normal(ys).astype(np.float32)
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.from_numpy(yh).to(dev)
+        for _ in range(2):
+            z, perm = T.contract_dense_pairs(x, y, [(0, 0)], 1e-6)
+        torch.cuda.synchronize(dev)
+        R = 5
+        ts = []
+        for _ in range(R):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            z, perm = T.contract_dense_pairs(x, y, [(0, 0)], 1e-6)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        got = O.chain_to_dense([c.detach().cpu().numpy().astype(np.float64) for c in z], perm)
+        want = O.tcp_pairs(xh.astype(np.float64), yh.astype(np.float64), [(0, 0)])
+        rel = float(np.linalg.norm(got - want) / (np.linalg.norm(xh) * np.linalg.norm(yh)))
+        case = {"y_shape": list(ys), "ms": ms, "value": 1.0 / (ms / 1e3), "unit": "dense contractions/s",
+                "ranks_z": [int(c.shape[0]) for c in z] + [1], "err_rel_frobenius": rel}
+        if not args.no_cpu_baseline:
+            t0 = _time.perf_counter()
+            xc = O.tt_svd(xh.astype(np.float64), 1e-6)
+            yc = O.tt_svd(yh.astype(np.float64), 1e-6)
+            O.partial_chain_pairs(xc, yc, [(0, 0)])
+            dt = _time.perf_counter() - t0
+            case["cpu_baseline"] = {"value": 1.0 / dt, "unit": "dense contractions/s", "cores": 1, "kind": "oracle",
+                                    "sample": "one call: numpy float64 TT decomposition of both operands and the "
+                                              "chain contraction"}
+        out["cases"].append(case)
+    out["value"] = statistics.mean(c["value"] for c in out["cases"])
+    out["unit"] = "dense contractions/s (mean over the three shapes)"
+    out["roofline"] = {"bound": "latency", "note": "one CTA runs each decomposition (dependent Jacobi rounds); "
+                                                   "a few MB of data, no roofline fraction is meaningful"}
+    out["device_status"] = status
+    return out
 
 
 _TC_RESULTS = {}  # precision form -> (mantissa, exponent) of its last z, for the accuracy report

@@ -237,6 +237,38 @@ int tt_contract_pairs(const tt_desc* x, const tt_desc* y, int n_pairs, const int
                       const int32_t* ymodes, int prec, const tt_desc* z, int64_t* z_log2_dev,
                       int32_t* status_dev, tt_stream stream);
 
+/* TT decomposition of a dense tensor: the TT-SVD of Section II (Algorithm 1),
+ * whose result satisfies ||X - TT(X)||_F <= eps ||X||_F.  x_dev: device,
+ * row-major, modes[0] x ... x modes[order-1] (F64 or F32).  Modes are taken
+ * left to right: at mode k the unfactored part is a matrix of
+ * (r_{k-1} I_k) rows; its SVD (one-sided Jacobi, in the storage type, singular
+ * values and norms in float64) keeps the smallest rank r_k >= 1 whose dropped
+ * singular values have 2-norm <= eps ||X||_F / sqrt(order - 1), then at most
+ * max_rank (0: no cap); core k is the r_k leading left singular vectors
+ * (left-orthonormal for k < order - 1), the last core carries the rest.
+ * tt_svd_workspace (host only): cap_ranks[order + 1] = the largest ranks the
+ * call can return (min of the two unfolding sizes, capped by max_rank) and
+ * *ws_bytes; TT_ERR_TOO_LARGE when the shorter side of an unfolding exceeds
+ * 512 or the tensor exceeds 2^31 - 1 entries.  tt_svd: cores_dev[k] holds at
+ * least cap_ranks[k] * modes[k] * cap_ranks[k+1] elements and receives core k
+ * contiguous with its chosen ranks, [r_k][I_k][r_{k+1}]; the chosen ranks go
+ * to ranks_dev[order + 1] (device int32; read them after the stream has
+ * reached the call).  A non-finite norm sets TT_STATUS_NONFINITE and writes no
+ * core.  One CTA runs the decomposition (latency-bound: meant for tensors of
+ * up to a few million entries).  Asynchronous on `stream`; no allocation. */
+int tt_svd_workspace(int order, const int32_t* modes, int dtype, int32_t max_rank, int32_t* cap_ranks,
+                     size_t* ws_bytes);
+int tt_svd(const void* x_dev, int order, const int32_t* modes, int dtype, double eps, int32_t max_rank,
+           void* const* cores_dev, int32_t* ranks_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
+           tt_stream stream);
+
+/* Dense mode permutation (Alg. 2 steps 1-2: the paired modes brought to the
+ * front before the decomposition): out has axis t = axis axes[t] of in
+ * (both device, row-major, F64 or F32, distinct buffers).  TT_ERR_ARG for a
+ * repeated or out-of-range axis.  Asynchronous on `stream`; no allocation. */
+int tt_dense_permute(const void* in_dev, int order, const int32_t* modes, const int32_t* axes, int dtype,
+                     void* out_dev, tt_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Batched contraction of many independent pairs in one persistent launch.
  * ------------------------------------------------------------------------- */

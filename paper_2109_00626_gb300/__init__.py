@@ -22,6 +22,8 @@ from ._binding import (  # noqa: F401
     PairsContraction,
     PartialContraction,
     TTError,
+    Decomposition,
+    contract_dense_pairs,
     contract_full,
     contract_pairs,
     contract_partial,
@@ -31,5 +33,8 @@ from ._binding import (  # noqa: F401
     partial_k,
     pairs_shape,
     partial_shape,
+    dense_permute,
+    svd_workspace,
+    tt_decompose,
     workspace_bytes,
 )

@@ -44,6 +44,9 @@ EXPORTS = [
     "tt_selftest_wait",
     "tt_pairs_shape",
     "tt_contract_pairs",
+    "tt_svd_workspace",
+    "tt_svd",
+    "tt_dense_permute",
 ]
 
 
@@ -113,6 +116,10 @@ def lib():
     L.tt_selftest_wait.argtypes = [c_int, ctypes.c_int64, c_void_p, c_void_p]
     L.tt_pairs_shape.argtypes = [D, D, c_int, I32, I32, I32, I32, I32, I32]
     L.tt_contract_pairs.argtypes = [D, D, c_int, I32, I32, c_int, D, c_void_p, c_void_p, c_void_p]
+    L.tt_svd_workspace.argtypes = [c_int, I32, c_int, c_int32, I32, POINTER(c_size_t)]
+    L.tt_svd.argtypes = [c_void_p, c_int, I32, c_int, ctypes.c_double, c_int32, POINTER(c_void_p), c_void_p, c_void_p,
+                         c_void_p, c_size_t, c_void_p]
+    L.tt_dense_permute.argtypes = [c_void_p, c_int, I32, I32, c_int, c_void_p, c_void_p]
     L.tt_launch_count.restype = c_uint64
     _lib = L
     return L
@@ -389,6 +396,105 @@ def contract_pairs(x, y, pairs, prec="native", stream=None):
     """Contract mode pairs[t][0] of X with pairs[t][1] of Y (end blocks, any
     orders); returns (cores, perm) of the chain-layout result."""
     op = PairsContraction(x, y, pairs, prec)
+    op(stream)
+    return op.z, op.perm
+
+
+def svd_workspace(modes, dtype, max_rank=0):
+    """tt_svd_workspace: (cap_ranks, ws_bytes) of decomposing a dense tensor of
+    the given modes."""
+    n = len(modes)
+    md = (c_int32 * n)(*[int(v) for v in modes])
+    cap = (c_int32 * (n + 1))()
+    ws = c_size_t(0)
+    check(lib().tt_svd_workspace(n, md, int(dtype), int(max_rank), cap, ctypes.byref(ws)), "tt_svd_workspace")
+    return list(cap), ws.value
+
+
+class Decomposition:
+    """Pre-marshalled TT-SVD of dense tensors of one shape and dtype
+    (tt_svd): workspace, core buffers at their largest ranks and the rank and
+    status words allocated once.  ``__call__(x)`` enqueues the decomposition;
+    ``cores()`` reads the chosen ranks (a device-to-host copy: it waits for the
+    call) and returns views of the cores at those ranks."""
+
+    def __init__(self, modes, dtype, eps, max_rank=0, device=None):
+        import torch
+
+        self.modes = [int(v) for v in modes]
+        self.tdtype = dtype
+        self.code = TT_F64 if dtype == torch.float64 else TT_F32
+        if dtype not in (torch.float64, torch.float32):
+            raise TypeError(f"unsupported dtype {dtype}")
+        self.eps = float(eps)
+        self.max_rank = int(max_rank)
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.cap, nbytes = svd_workspace(self.modes, self.code, self.max_rank)
+        self.ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+        n = len(self.modes)
+        self.buf = [torch.empty(self.cap[k] * self.modes[k] * self.cap[k + 1], dtype=dtype, device=dev) for k in range(n)]
+        self._ptrs = (c_void_p * n)(*[b.data_ptr() for b in self.buf])
+        self._modes = (c_int32 * n)(*self.modes)
+        self.ranks = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def __call__(self, x, stream=None):
+        if list(x.shape) != self.modes or x.dtype != self.tdtype or not x.is_contiguous():
+            raise ValueError("tensor does not match the decomposition's modes / dtype, or is not contiguous")
+        rc = lib().tt_svd(c_void_p(x.data_ptr()), len(self.modes), self._modes, self.code, self.eps, self.max_rank,
+                          self._ptrs, c_void_p(self.ranks.data_ptr()), c_void_p(self.status.data_ptr()),
+                          c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream_ptr(stream))
+        check(rc, "tt_svd")
+
+    def cores(self):
+        r = [int(v) for v in self.ranks.cpu().tolist()]
+        return [self.buf[k][: r[k] * self.modes[k] * r[k + 1]].view(r[k], self.modes[k], r[k + 1])
+                for k in range(len(self.modes))]
+
+
+def tt_decompose(x, eps, max_rank=0, stream=None):
+    """TT cores of the dense CUDA tensor x with ||x - TT||_F <= eps ||x||_F
+    (tt_svd; waits for the call to read the ranks)."""
+    op = Decomposition(list(x.shape), x.dtype, eps, max_rank, x.device)
+    op(x.contiguous(), stream)
+    cores = op.cores()
+    if int(op.status.item()) != 0:
+        raise ValueError("tt_svd: the tensor holds a non-finite value (TT_STATUS_NONFINITE)")
+    return cores
+
+
+def dense_permute(x, axes, out=None, stream=None):
+    """out = x with axis t = axis axes[t] of x (tt_dense_permute)."""
+    import torch
+
+    n = x.dim()
+    axes = [int(a) for a in axes]
+    if out is None:
+        out = torch.empty([x.shape[a] for a in axes], dtype=x.dtype, device=x.device)
+    md = (c_int32 * n)(*[int(v) for v in x.shape])
+    ax = (c_int32 * n)(*axes)
+    check(lib().tt_dense_permute(c_void_p(x.data_ptr()), n, md, ax, _dtype_code(x), c_void_p(out.data_ptr()),
+                                 _stream_ptr(stream)), "tt_dense_permute")
+    return out
+
+
+def contract_dense_pairs(x, y, pairs, eps, prec="native", max_rank=0, stream=None):
+    """Eq. 8 over mode pairs of two dense CUDA tensors by way of TTs (Alg. 2):
+    each operand's paired modes are brought to the front in pair order
+    (tt_dense_permute), both are decomposed with accuracy eps (tt_svd), and
+    the leading blocks are contracted (tt_contract_pairs).  Returns (cores,
+    perm) of the chain-layout result; its represented tensor is within
+    (eps_x + eps_y + eps_x eps_y) ||x|| ||y|| of Eq. 8's Z in Frobenius norm,
+    plus rounding."""
+    pairs = [(int(a), int(b)) for a, b in pairs]
+    s = len(pairs)
+    ax = [a for a, _ in pairs] + [k for k in range(x.dim()) if k not in {a for a, _ in pairs}]
+    ay = [b for _, b in pairs] + [k for k in range(y.dim()) if k not in {b for _, b in pairs}]
+    xp = x.contiguous() if ax == list(range(x.dim())) else dense_permute(x.contiguous(), ax, stream=stream)
+    yp = y.contiguous() if ay == list(range(y.dim())) else dense_permute(y.contiguous(), ay, stream=stream)
+    xc = tt_decompose(xp, eps, max_rank, stream)
+    yc = tt_decompose(yp, eps, max_rank, stream)
+    op = PairsContraction(xc, yc, [(t, t) for t in range(s)], prec)
     op(stream)
     return op.z, op.perm
 

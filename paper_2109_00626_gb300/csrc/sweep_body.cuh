@@ -287,6 +287,15 @@ __device__ __forceinline__ void it_next(ChunkIt& it, const SweepStep* steps, int
   it_settle<KCV>(it, steps, n_pipe, crank);
 }
 
+// A chain emission whose K fits one pipeline chunk gets its first boundary-core
+// slice loaded during the last mode of the sweep (sweep_body issues it,
+// sweep_tail only waits for it).
+template <int KCV>
+__device__ __forceinline__ bool emit_prefetched(const SweepParams& p, int crank) {
+  return p.emit.enabled && !p.final_scalar && p.n_steps > 0 && p.step[p.n_steps - 1].rout_x <= KCV &&
+         crank < p.emit.I;
+}
+
 // Where results and device status go (per call; the batched kernel points
 // these at its per-pair slots).
 struct SweepOut {
@@ -328,6 +337,7 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int n_pipe = p.final_scalar ? p.n_steps - 1 : p.n_steps;
+  const bool emit_prefetch = emit_prefetched<Cfg::KC>(p, crank);
 
   int64_t log2s = 0;
   int bad = 0;
@@ -444,6 +454,16 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
       }
     }
     __syncthreads();  // every thread is done reading Es / Ts of this mode
+    if (j == n_pipe - 1 && emit_prefetch) {
+      // the first slice of the boundary core this CTA joins with K after the
+      // sweep (every chunk of the ring has been consumed, so stage 0 is free):
+      // its load overlaps the cluster exchange of the last mode
+      const EmitParams& em = p.emit;
+      const T* gx = static_cast<const T*>(em.gx);
+      if (em.lead) load_rows_async<T, LD, NT>(stage0, gx, crank, em.I, em.ra, em.rb, 0, 0, st.rout_x);
+      else load_rows_async<T, LD, NT>(stage0, gx, crank, em.I, em.rb, em.ra, 1, 0, st.rout_x);
+      cp_async_commit();
+    }
 
     const int nu = st.rout_x, nv = st.rout_y;
     if (!CL || C == 1) {
@@ -787,6 +807,7 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
     T* cout = static_cast<T*>(em.c_out);
     const int nu = em.lead ? em.rb : em.ra;
     const bool fold = em.z_log2_out == nullptr && log2s != 0;
+    const bool pre = emit_prefetched<Cfg::KC>(p, crank);
     int ebits = 0;
     constexpr int NS = Cfg::NS;
     for (int i = crank; i < em.I; i += C) {
@@ -800,9 +821,11 @@ __device__ __forceinline__ void sweep_tail(const SweepParams& p, const SweepOut&
       for (int r0 = 0; r0 < kx; r0 += Cfg::KC) {
         const int kc = min(Cfg::KC, kx - r0);
         __syncthreads();
-        if (em.lead) load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.ra, em.rb, 0, r0, kc);
-        else load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.rb, em.ra, 1, r0, kc);
-        cp_async_commit();
+        if (!(pre && i == crank)) {  // else the sweep's last mode already issued this load
+          if (em.lead) load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.ra, em.rb, 0, r0, kc);
+          else load_rows_async<T, LD, NT>(stage0, gx, i, em.I, em.rb, em.ra, 1, r0, kc);
+          cp_async_commit();
+        }
         cp_async_wait<0>();
         __syncthreads();
 #pragma unroll

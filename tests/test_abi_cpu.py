@@ -393,6 +393,48 @@ def _ws(L, op, x, y, mask=None, layout="chain", prec="native"):
     return rc, nb.value
 
 
+def test_svd_workspace_and_rejections(L):
+    """tt_svd_workspace: the largest ranks a TT-SVD can return (the shorter
+    side of each unfolding, capped by max_rank) for Example 2's shapes and
+    the limits; tt_svd and tt_dense_permute reject bad arguments before they
+    enqueue (fake device pointers, never dereferenced)."""
+    assert T.svd_workspace([20, 20, 20], B.TT_F64)[0] == [1, 20, 20, 1]
+    assert T.svd_workspace([20, 20, 20, 5], B.TT_F32)[0] == [1, 20, 100, 5, 1]
+    assert T.svd_workspace([20, 20, 20, 5, 4], B.TT_F32)[0] == [1, 20, 400, 20, 4, 1]
+    assert T.svd_workspace([20, 20, 20, 5, 4], B.TT_F32, max_rank=8)[0] == [1, 8, 8, 8, 4, 1]
+    assert T.svd_workspace([7], B.TT_F64)[0] == [1, 1]
+    cap, ws = T.svd_workspace([3, 5, 2], B.TT_F64)
+    assert cap == [1, 3, 2, 1]
+    # two copies of the tensor, the 3 x 3 rotations, singular values and order
+    assert ws == 2 * 256 + 256 + 256 + 256
+    cap = (ctypes.c_int32 * 8)()
+    ws = ctypes.c_size_t(0)
+    md = (ctypes.c_int32 * 2)(600, 600)
+    assert L.tt_svd_workspace(2, md, B.TT_F32, 0, cap, ctypes.byref(ws)) == -5   # 600 x 600 unfolding
+    assert L.tt_svd_workspace(2, md, B.TT_F32, 100, cap, ctypes.byref(ws)) == -5  # the cap does not shrink the SVD
+    assert L.tt_svd_workspace(2, md, B.TT_BF16, 0, cap, ctypes.byref(ws)) == -3
+    md0 = (ctypes.c_int32 * 2)(4, 0)
+    assert L.tt_svd_workspace(2, md0, B.TT_F32, 0, cap, ctypes.byref(ws)) == -2
+    assert L.tt_svd_workspace(0, md0, B.TT_F32, 0, cap, ctypes.byref(ws)) == -1
+    md = (ctypes.c_int32 * 3)(4, 5, 6)
+    cores = (ctypes.c_void_p * 3)(0x1000, 0x2000, 0x3000)
+    fake = ctypes.c_void_p(0x4000)
+    need = T.svd_workspace([4, 5, 6], B.TT_F32)[1]
+    assert L.tt_svd(None, 3, md, B.TT_F32, 1e-3, 0, cores, fake, fake, fake, need, None) == -1
+    assert L.tt_svd(fake, 3, md, B.TT_F32, -1.0, 0, cores, fake, fake, fake, need, None) == -1
+    assert L.tt_svd(fake, 3, md, B.TT_F32, float("nan"), 0, cores, fake, fake, fake, need, None) == -1
+    assert L.tt_svd(fake, 3, md, B.TT_F32, 1e-3, 0, cores, fake, fake, fake, need - 1, None) == -6
+    nul = (ctypes.c_void_p * 3)(0x1000, None, 0x3000)
+    assert L.tt_svd(fake, 3, md, B.TT_F32, 1e-3, 0, nul, fake, fake, fake, need, None) == -1
+    ax = (ctypes.c_int32 * 3)(2, 0, 2)
+    assert L.tt_dense_permute(fake, 3, md, ax, B.TT_F32, ctypes.c_void_p(0x5000), None) == -1
+    ax = (ctypes.c_int32 * 3)(2, 0, 3)
+    assert L.tt_dense_permute(fake, 3, md, ax, B.TT_F32, ctypes.c_void_p(0x5000), None) == -1
+    ax = (ctypes.c_int32 * 3)(2, 0, 1)
+    assert L.tt_dense_permute(fake, 3, md, ax, B.TT_F32, fake, None) == -1  # in place
+    assert L.tt_dense_permute(fake, 3, md, ax, B.TT_BF16, ctypes.c_void_p(0x5000), None) == -3
+
+
 def test_workspace_queries_and_their_limits(L):
     """tt_workspace_bytes per operation, and the conditions the header states
     for each path (host only)."""

@@ -371,6 +371,27 @@ def test_tt_svd_exact_and_truncated(rng):
     np.testing.assert_allclose(O.tt_to_dense(O.tt_svd(w)), w, rtol=0, atol=1e-13)
 
 
+def test_tt_svd_taken_left_to_right(rng):
+    """The decomposition taken from the left (the order the GPU kernel uses)
+    is the oracle's right-to-left one on the reversed axes, reversed back:
+    it reconstructs the tensor within eps ||X||, its first rank is the one
+    the SVD of the first unfolding I_1 x rest gives for the threshold
+    eps ||X|| / sqrt(N - 1), and its cores 0 .. N-2 are left-orthonormal."""
+    x = rng.standard_normal((6, 5, 4, 3))
+    n = x.ndim
+    for eps in (0.0, 0.1, 0.4):
+        t = O.reverse_tt(O.tt_svd(np.transpose(x, tuple(range(n - 1, -1, -1))), eps))
+        assert np.linalg.norm(O.tt_to_dense(t) - x) <= eps * np.linalg.norm(x) * (1 + 1e-12) + 1e-12
+        sv = np.linalg.svd(x.reshape(6, -1), compute_uv=False)
+        tol = eps * np.linalg.norm(x) / np.sqrt(n - 1)
+        tails = np.sqrt(np.cumsum(sv[::-1] ** 2))[::-1]  # tails[r] = ||sv[r:]||
+        r1 = next((r for r in range(1, len(sv)) if tails[r] <= tol), len(sv))
+        assert t[0].shape[2] == r1
+        for g in t[:-1]:
+            m = g.reshape(-1, g.shape[2])
+            np.testing.assert_allclose(m.T @ m, np.eye(m.shape[1]), rtol=0, atol=1e-12)
+
+
 def test_reverse_tt_reverses_modes(rng):
     x = _rand_tt(rng, [3, 4, 2, 5], [1, 2, 3, 4, 1])
     d = O.tt_to_dense(x)
