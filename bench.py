@@ -563,6 +563,7 @@ def run_ours(args):
             "backward": lambda: bench_backward(T, dev, args),
             "merged": lambda: bench_merged(T, dev, args),
             "dense_ttcp": lambda: bench_dense_ttcp(T, dev, args),
+            "factored": lambda: bench_factored(T, dev, args),
         }
         wanted = list(runners) if args.forms == "all" else [f for f in args.forms.split(",") if f]
         for name in wanted:
@@ -939,6 +940,64 @@ def bench_merged(T, dev, args):
         },
         "device_status": status,
         "l2": "flushed before each contraction",
+    }
+
+
+FACTORED_MASK = [1, 0, 0, 1, 1, 1, 0, 0]
+
+
+def bench_factored(T, dev, args):
+    """General-S partial contraction at rank 64 in factored form: order 8,
+    modes 16, ranks 64, float32, S = {0, 3, 4, 5} (the left environment of mode
+    0 and the 4096 x 4096 transfer matrix of the interior run 3-5; the merged
+    layout's cores would hold 4096 x 16 x 16 x 4096 entries).  CUDA events on
+    the launching stream, L2 flushed before each call."""
+    import torch
+
+    x, y = G.pair(3, [16] * 8, G.tt_ranks(8, 64), G.tt_ranks(8, 64), np.float32)
+    xd = [torch.from_numpy(c).to(dev) for c in x]
+    yd = [torch.from_numpy(c).to(dev) for c in y]
+    op = T.FactoredContraction(xd, yd, FACTORED_MASK)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        op(stream)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for r in range(5):
+        flush.fill_(float(r))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        op(stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    rx = [c.shape[0] for c in x] + [1]
+    ry = [c.shape[0] for c in y] + [1]
+    flops = W.factored_flops([16] * 8, rx, ry, FACTORED_MASK)
+    peak = fp32_simt_peak_tflops()
+    out_bytes = sum(r[0].numel() * 4 + r[1].numel() * 8 for r in op.runs() if r is not None)
+    return {
+        "workload": "order-8 TT pair, modes 16, ranks 64, float32; partial contraction over S = {0, 3, 4, 5} "
+                    "in factored form (left environment + 4096 x 4096 transfer matrix)",
+        "value": 1.0 / (ms / 1e3),
+        "unit": "contractions/s",
+        "ms_per_contraction": ms,
+        "alg_flops": flops,
+        "out_bytes": out_bytes,
+        "roofline": {
+            "kernel": "transfer_kernel<float> (the interior run's rows)",
+            "bound": "alu",
+            "achieved": flops / (ms / 1e3) / 1e12,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": flops / (ms / 1e3) / 1e12 / peak,
+            "note": "flops = 4096 basis sweeps of the run (the first mode from a unit environment) + the left "
+                    "environment; fp32 FMA peak derived",
+        },
+        "device_status": int(op.status.item()),
+        "l2": "flushed before each call",
     }
 
 

@@ -237,6 +237,49 @@ int tt_contract_pairs(const tt_desc* x, const tt_desc* y, int n_pairs, const int
                       const int32_t* ymodes, int prec, const tt_desc* z, int64_t* z_log2_dev,
                       int32_t* status_dev, tt_stream stream);
 
+/* Partial contraction over any contracted set S (Eq. 8 applied to each k in
+ * S) in factored form: the merged (TT-matrix) result kept as its Kronecker
+ * factors.  With f_0 < ... < f_{m-1} the free positions,
+ *   Z[i_F; j_F] = T_0 W_{f_0}[i_0, j_0] T_1 ... W_{f_{m-1}}[i_{m-1}, j_{m-1}] T_m,
+ *   W_f[i, j][(a, b), (a', b')] = Gx_f[a][i][a'] Gy_f[b][j][b']  (pair index a R^y + b),
+ * i_F in X's free modes, j_F in Y's (Eq. 8's order).  W_f is the operands'
+ * own free cores (never formed or copied); T_t is the contracted run between
+ * free positions as a matrix over pair indices: T_0 = the left environment
+ * of the modes before f_0 (1 x R^x R^y at f_0), T_m = the right environment
+ * of the modes after f_{m-1} (R^x R^y at f_{m-1}+1 x 1), and T_t for
+ * 0 < t < m the transfer matrix of the modes strictly between f_{t-1} and
+ * f_t: row (a, b) is the run swept from the basis environment e_a e_b^T,
+ * R^x R^y at f_{t-1}+1 x R^x R^y at f_t.  A run with no mode is the identity
+ * and stores nothing (rows = cols = 0).  Row r of T_t is stored as mantissas
+ * scaled by 2^{log2_t[r]} (int64; an all-zero row has a large negative
+ * scale).  Caps: ranks as tt_contract_full, every T_t at most 2^30 entries
+ * (TT_ERR_TOO_LARGE); S = all modes: TT_ERR_ARG.
+ * tt_factored_shape (host only) fills `f`: the free positions, each T_t's
+ * shape and its byte offsets in one output arena (entries, then rows + 1
+ * int64: the row scales and a scratch slot), and the arena size.
+ * f->ws_bytes: the device workspace tt_contract_factored needs (0 unless an
+ * interior run has R^x R^y >= 256 rows: those are swept for all rows at once
+ * as plain GEMMs on cuBLAS, float32 / float64 arithmetic, in chunks that bound
+ * the intermediate; smaller runs use one CTA per row).
+ * tt_contract_factored: out_dev = a device arena of f->bytes (16-byte
+ * aligned); `f` must be the shape of these operands and S (TT_ERR_SHAPE);
+ * ws of at least f->ws_bytes (TT_ERR_WS).  The runs are computed one after
+ * another on `stream`; no allocation, except that the first call on a device
+ * that takes the GEMM path creates the library's cuBLAS handle for it. */
+typedef struct {
+  int32_t n_free;
+  int32_t free_pos[TT_MAX_ORDER];
+  int32_t rows[TT_MAX_ORDER + 1];
+  int32_t cols[TT_MAX_ORDER + 1];
+  size_t off_t[TT_MAX_ORDER + 1];
+  size_t off_log2[TT_MAX_ORDER + 1];
+  size_t bytes;
+  size_t ws_bytes;
+} tt_factored;
+int tt_factored_shape(const tt_desc* x, const tt_desc* y, const uint8_t* mask, tt_factored* f);
+int tt_contract_factored(const tt_desc* x, const tt_desc* y, const uint8_t* mask, const tt_factored* f,
+                         void* out_dev, int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream);
+
 /* TT decomposition of a dense tensor: the TT-SVD of Section II (Algorithm 1),
  * whose result satisfies ||X - TT(X)||_F <= eps ||X||_F.  x_dev: device,
  * row-major, modes[0] x ... x modes[order-1] (F64 or F32).  Modes are taken

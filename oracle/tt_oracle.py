@@ -40,6 +40,10 @@ two_sum / two_product / dot2_dd / absorb_left_dd / contract_full_dd
 partial_chain          end-block S -> chain TT (Algorithm 2 steps 4-6)
 partial_merged         any S -> TT-matrix of merged cores
 chain_to_dense / merged_to_dense   dense reconstruction + un-permutation
+transfer_matrix / partial_factored / factored_to_dense
+                       any S in factored form: the contracted runs as
+                       matrices over pair indices, the free cores as the
+                       Kronecker factors of the merged cores (Eq. 8)
 grad_sweep / grad_full / grad_partial_chain   gradients by the L/F formulas
 tt_svd                 a TT of a dense tensor within eps ||X||_F (Section II)
 reverse_tt             the same TT with its modes in reverse order
@@ -76,6 +80,9 @@ __all__ = [
     "partial_merged",
     "chain_to_dense",
     "merged_to_dense",
+    "transfer_matrix",
+    "partial_factored",
+    "factored_to_dense",
     "grad_sweep",
     "grad_full",
     "grad_partial_chain",
@@ -405,6 +412,69 @@ def merged_to_dense(cores, perm):
         acc = g.reshape(i_dim * j_dim, r2) if acc is None else np.tensordot(acc, g, axes=([acc.ndim - 1], [0]))
     zr = acc.reshape(dims)
     return np.transpose(zr, np.argsort(perm))
+
+
+def transfer_matrix(gx, gy):
+    """One contracted mode as a matrix over pair indices (a R^y + b):
+    T[(a,b), (a',b')] = sum_i Gx[a,i,a'] Gy[b,i,b'] (Eq. 8's sum over the
+    shared index, written for every left pair (a,b) at once)."""
+    gx, gy = np.asarray(gx, dtype=np.float64), np.asarray(gy, dtype=np.float64)
+    rx, _, rx2 = gx.shape
+    ry, _, ry2 = gy.shape
+    return np.einsum("aiu,biv->abuv", gx, gy).reshape(rx * ry, rx2 * ry2)
+
+
+def partial_factored(xc, yc, mask):
+    """Partial contraction over any S in factored form.
+
+    With free positions f_0 < ... < f_{m-1},
+      Z[i_F; j_F] = T_0 W_{f_0}[i_0, j_0] T_1 ... W_{f_{m-1}} T_m,
+      W_f[i, j][(a,b), (a',b')] = Gx_f[a,i,a'] Gy_f[b,j,b'],
+    T_t the product of the transfer matrices of the contracted modes between
+    free positions (T_0 a 1 x R^xR^y row: the modes before f_0 starting from
+    the rank-1 end; T_m a column: the modes after f_{m-1}); None for a run
+    with no mode (the identity).  Returns (free positions, [T_0 .. T_m])."""
+    xc, yc = _f64(xc), _f64(yc)
+    n = len(xc)
+    free = [k for k in range(n) if not mask[k]]
+    if not free:
+        raise ValueError("all modes contracted: use contract_full")
+    m = len(free)
+    runs = []
+    for t in range(m + 1):
+        k0 = 0 if t == 0 else free[t - 1] + 1
+        k1 = n if t == m else free[t]
+        if k1 <= k0:
+            runs.append(None)
+            continue
+        acc = transfer_matrix(xc[k0], yc[k0])
+        for k in range(k0 + 1, k1):
+            acc = acc @ transfer_matrix(xc[k], yc[k])
+        runs.append(acc)
+    return free, runs
+
+
+def factored_to_dense(xc, yc, free, runs):
+    """Dense Z in Eq. 8 order (X's free modes, then Y's) from the factored
+    form: the chain T_0 W_{f_0} T_1 ... T_m multiplied out."""
+    xc, yc = _f64(xc), _f64(yc)
+    m = len(free)
+    acc = np.ones((1, 1))  # rows: (i_0, j_0, ..., i_{t-1}, j_{t-1}); columns: the pair index
+    dims = []
+    for t, f in enumerate(free):
+        if runs[t] is not None:
+            acc = acc @ runs[t]
+        gx, gy = xc[f], yc[f]
+        rx, i_dim, rx2 = gx.shape
+        ry, j_dim, ry2 = gy.shape
+        w = np.einsum("aiu,bjv->abijuv", gx, gy).reshape(rx * ry, i_dim * j_dim * rx2 * ry2)
+        acc = (acc @ w).reshape(-1, rx2 * ry2)
+        dims += [i_dim, j_dim]
+    if runs[m] is not None:
+        acc = acc @ runs[m]
+    zr = acc.reshape(dims)
+    order = [2 * t for t in range(m)] + [2 * t + 1 for t in range(m)]
+    return np.transpose(zr, order)
 
 
 # --------------------------------------------------------------------------

@@ -23,7 +23,9 @@ from ._binding import (  # noqa: F401
     PartialContraction,
     TTError,
     Decomposition,
+    FactoredContraction,
     contract_dense_pairs,
+    contract_factored,
     contract_full,
     contract_pairs,
     contract_partial,

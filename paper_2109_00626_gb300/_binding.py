@@ -47,7 +47,24 @@ EXPORTS = [
     "tt_svd_workspace",
     "tt_svd",
     "tt_dense_permute",
+    "tt_factored_shape",
+    "tt_contract_factored",
 ]
+
+
+class TTFactored(ctypes.Structure):
+    """tt_factored: free positions, run-matrix shapes and arena offsets."""
+
+    _fields_ = [
+        ("n_free", c_int32),
+        ("free_pos", c_int32 * 64),
+        ("rows", c_int32 * 65),
+        ("cols", c_int32 * 65),
+        ("off_t", c_size_t * 65),
+        ("off_log2", c_size_t * 65),
+        ("bytes", c_size_t),
+        ("ws_bytes", c_size_t),
+    ]
 
 
 class TTDesc(ctypes.Structure):
@@ -120,6 +137,9 @@ def lib():
     L.tt_svd.argtypes = [c_void_p, c_int, I32, c_int, ctypes.c_double, c_int32, POINTER(c_void_p), c_void_p, c_void_p,
                          c_void_p, c_size_t, c_void_p]
     L.tt_dense_permute.argtypes = [c_void_p, c_int, I32, I32, c_int, c_void_p, c_void_p]
+    L.tt_factored_shape.argtypes = [D, D, U8, POINTER(TTFactored)]
+    L.tt_contract_factored.argtypes = [D, D, U8, POINTER(TTFactored), c_void_p, c_void_p, c_void_p, c_size_t,
+                                       c_void_p]
     L.tt_launch_count.restype = c_uint64
     _lib = L
     return L
@@ -398,6 +418,59 @@ def contract_pairs(x, y, pairs, prec="native", stream=None):
     op = PairsContraction(x, y, pairs, prec)
     op(stream)
     return op.z, op.perm
+
+
+class FactoredContraction:
+    """Pre-marshalled partial contraction over any S in factored form
+    (tt_contract_factored): the output arena allocated once.  After a call,
+    ``runs()`` gives, for t = 0 .. m, None for an empty run (the identity) or
+    (T_t, log2_t): the run matrix's mantissas (rows x cols) and its int64 row
+    scales, views into the arena."""
+
+    def __init__(self, x, y, mask):
+        import torch
+
+        self.xd, self.yd = Desc(x), Desc(y)
+        self.mask = [int(v) for v in mask]
+        self._mask = (c_uint8 * len(self.mask))(*self.mask)
+        self.f = TTFactored()
+        check(lib().tt_factored_shape(self.xd.ref, self.yd.ref, self._mask, ctypes.byref(self.f)), "tt_factored_shape")
+        dev = x[0].device
+        self.dtype = x[0].dtype
+        self.arena = torch.empty(self.f.bytes, dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(max(self.f.ws_bytes, 1), dtype=torch.uint8, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.free_pos = list(self.f.free_pos[: self.f.n_free])
+
+    def __call__(self, stream=None):
+        rc = lib().tt_contract_factored(self.xd.ref, self.yd.ref, self._mask, ctypes.byref(self.f),
+                                        c_void_p(self.arena.data_ptr()), c_void_p(self.status.data_ptr()),
+                                        c_void_p(self.ws.data_ptr()), self.f.ws_bytes, _stream_ptr(stream))
+        check(rc, "tt_contract_factored")
+
+    def runs(self):
+        import torch
+
+        eb = torch.finfo(self.dtype).bits // 8
+        out = []
+        for t in range(self.f.n_free + 1):
+            r, c = self.f.rows[t], self.f.cols[t]
+            if r == 0:
+                out.append(None)
+                continue
+            o, ol = self.f.off_t[t], self.f.off_log2[t]
+            tm = self.arena[o: o + r * c * eb].view(self.dtype).view(r, c)
+            lg = self.arena[ol: ol + r * 8].view(torch.int64)
+            out.append((tm, lg))
+        return out
+
+
+def contract_factored(x, y, mask, stream=None):
+    """Partial contraction over S = {k: mask[k]} in factored form; returns
+    (free positions, runs) as FactoredContraction.runs()."""
+    op = FactoredContraction(x, y, mask)
+    op(stream)
+    return op.free_pos, op.runs()
 
 
 def svd_workspace(modes, dtype, max_rank=0):

@@ -72,3 +72,26 @@ def partial_chain_bytes(modes, rx, ry, mask, elem_bytes):
             else:
                 wr += ex
     return (rd + wr) * elem_bytes
+
+
+def factored_flops(modes, rx, ry, mask):
+    """Work of the factored form over S: each environment run is one sweep;
+    an interior run between free positions is swept once from every basis
+    environment e_a e_b^T of its left pair rank (its first mode from a unit
+    environment costs I R^x' R^y' multiply-adds)."""
+    n = len(modes)
+    free = [k for k in range(n) if not mask[k]]
+    tot = 0
+    for t in range(len(free) + 1):
+        k0 = 0 if t == 0 else free[t - 1] + 1
+        k1 = n if t == len(free) else free[t]
+        if k1 <= k0:
+            continue
+        if t == 0 or t == len(free):
+            tot += sum(mode_flops(rx[k], rx[k + 1], ry[k], ry[k + 1], modes[k]) for k in range(k0, k1))
+            continue
+        rows = rx[k0] * ry[k0]
+        per = 2 * modes[k0] * rx[k0 + 1] * ry[k0 + 1]
+        per += sum(mode_flops(rx[k], rx[k + 1], ry[k], ry[k + 1], modes[k]) for k in range(k0 + 1, k1))
+        tot += rows * per
+    return tot

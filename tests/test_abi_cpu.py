@@ -435,6 +435,45 @@ def test_svd_workspace_and_rejections(L):
     assert L.tt_dense_permute(fake, 3, md, ax, B.TT_BF16, ctypes.c_void_p(0x5000), None) == -3
 
 
+def test_factored_shape_on_the_host(L):
+    """tt_factored_shape: free positions, run shapes over pair indices (an
+    empty run is 0 x 0), arena offsets; rejections before anything is
+    enqueued."""
+    x = FakeDesc([3, 4, 5, 4, 3], [1, 2, 3, 4, 2, 1])
+    y = FakeDesc([3, 4, 5, 4, 3], [1, 3, 2, 2, 3, 1])
+    f = B.TTFactored()
+    assert L.tt_factored_shape(x.ref, y.ref, _mask([1, 0, 1, 1, 0]), ctypes.byref(f)) == 0
+    assert f.n_free == 2 and list(f.free_pos[:2]) == [1, 4]
+    # T_0: 1 x (2*3); T_1: modes 2..3, (3*2) x (2*3); T_2: none (mode 4 is free and last)
+    assert (f.rows[0], f.cols[0]) == (1, 6)
+    assert (f.rows[1], f.cols[1]) == (6, 6)
+    assert (f.rows[2], f.cols[2]) == (0, 0)
+    assert f.off_t[0] == 0 and f.off_log2[0] == 256 and f.off_t[1] == 512 and f.off_log2[1] == 768
+    assert f.bytes == 1024
+    assert L.tt_factored_shape(x.ref, y.ref, _mask([0, 1, 1, 1, 1]), ctypes.byref(f)) == 0
+    assert (f.rows[0], f.rows[1], f.cols[1]) == (0, 2 * 3, 1)
+    assert L.tt_factored_shape(x.ref, y.ref, _mask([1, 1, 1, 1, 1]), ctypes.byref(f)) == -1
+    y_bad = FakeDesc([3, 4, 6, 4, 3], [1, 3, 2, 2, 3, 1])
+    assert L.tt_factored_shape(x.ref, y_bad.ref, _mask([1, 0, 1, 1, 0]), ctypes.byref(f)) == -2
+    big = FakeDesc([3, 4, 5, 4, 3], [1, 200, 3, 4, 2, 1])
+    assert L.tt_factored_shape(big.ref, y.ref, _mask([1, 0, 1, 1, 0]), ctypes.byref(f)) == -5
+    # the contraction checks its shape against the operands and S
+    assert L.tt_factored_shape(x.ref, y.ref, _mask([1, 0, 1, 1, 0]), ctypes.byref(f)) == 0
+    out = ctypes.c_void_p(0x10000)
+    st = ctypes.c_void_p(0x20000)
+    assert f.ws_bytes == 0  # runs of fewer than 256 pair rows need no workspace
+    assert L.tt_contract_factored(x.ref, y.ref, _mask([1, 1, 0, 1, 0]), ctypes.byref(f), out, st, None, 0, None) == -2
+    assert L.tt_contract_factored(x.ref, y.ref, _mask([1, 0, 1, 1, 0]), ctypes.byref(f), None, st, None, 0, None) == -1
+    # a rank-64 interior run goes through the GEMM path and needs its workspace
+    x64 = FakeDesc([16] * 5, [1, 64, 64, 64, 64, 1])
+    assert L.tt_factored_shape(x64.ref, x64.ref, _mask([0, 1, 1, 0, 0]), ctypes.byref(f)) == 0
+    assert (f.rows[1], f.cols[1]) == (4096, 4096)
+    # two environment buffers of 4096 x 4096 floats and a chunk of 2^26 floats of the intermediate
+    assert f.ws_bytes == 2 * 4096 * 4096 * 4 + (1 << 26) * 4
+    assert L.tt_contract_factored(x64.ref, x64.ref, _mask([0, 1, 1, 0, 0]), ctypes.byref(f), out, st, None, 0,
+                                  None) == -6
+
+
 def test_workspace_queries_and_their_limits(L):
     """tt_workspace_bytes per operation, and the conditions the header states
     for each path (host only)."""

@@ -187,3 +187,28 @@ def test_tt_svd_pin_catches_a_dropped_direction(monkeypatch):
     assert np.abs(O.tt_to_dense(O.tt_svd(x)) - x).max() < 1e-12
     monkeypatch.setattr(T, "tt_svd", _svd_keep_one_too_few)
     assert np.abs(T.tt_to_dense(T.tt_svd(x)) - x).max() > 1e-3
+
+
+def _transfer_pairs_swapped(gx, gy):
+    """The pair index taken as b R^x + a on the right only."""
+    rx, _, rx2 = gx.shape
+    ry, _, ry2 = gy.shape
+    return np.einsum("aiu,biv->abvu", gx, gy).reshape(rx * ry, rx2 * ry2)
+
+
+def _transfer_drop_last_slice(gx, gy):
+    rx, _, rx2 = gx.shape
+    ry, _, ry2 = gy.shape
+    return np.einsum("aiu,biv->abuv", gx[:, :-1], gy[:, :-1]).reshape(rx * ry, rx2 * ry2)
+
+
+@pytest.mark.parametrize("mutant", [_transfer_pairs_swapped, _transfer_drop_last_slice])
+def test_factored_pin_catches_transfer_mutants(mutant, monkeypatch):
+    x, y = G.pair(15, [2, 3, 2, 3, 2], [1, 2, 3, 2, 2, 1], [1, 3, 2, 2, 2, 1], np.float64)
+    mask = [0, 1, 1, 0, 1]
+    want = O.tcp(O.tt_to_dense(x), O.tt_to_dense(y), [1, 2, 4])
+    f, runs = O.partial_factored(x, y, mask)
+    assert np.abs(O.factored_to_dense(x, y, f, runs) - want).max() < 1e-13
+    monkeypatch.setattr(T, "transfer_matrix", mutant)
+    f, runs = T.partial_factored(x, y, mask)
+    assert np.abs(T.factored_to_dense(x, y, f, runs) - want).max() > 1e-6

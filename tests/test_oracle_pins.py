@@ -607,3 +607,60 @@ def test_contract_full_dd_under_cancellation(rng):
     exact = float(_exact_full(x, y))
     assert abs(O.contract_full_dd(x, y) - exact) <= 2 * U64 * abs(exact)
     assert abs(O.contract_full(x, y) - exact) > 1e3 * U64 * abs(exact)  # the case does need compensation
+
+
+@pytest.mark.parametrize("mask", [[1, 0, 1, 1, 0], [0, 1, 0, 1, 0], [1, 1, 0, 0, 1], [0, 0, 0, 0, 0],
+                                  [1, 1, 1, 1, 0], [0, 1, 1, 1, 1], [1, 0, 0, 0, 1]])
+def test_factored_form_against_brute_force(mask):
+    """The factored form multiplied out equals Eq. 8 computed entry by entry
+    on the dense tensors, for interior, end, alternating and empty sets; and
+    it agrees with the merged layout's cores (the same Z)."""
+    rng = np.random.default_rng(sum(v << k for k, v in enumerate(mask)) + 3)
+    x = _rand_tt(rng, [3, 2, 3, 2, 2], [1, 2, 3, 2, 2, 1])
+    y = _rand_tt(rng, [3, 2, 3, 2, 2], [1, 3, 2, 2, 3, 1])
+    dx, dy = O.tt_to_dense(x), O.tt_to_dense(y)
+    sset = [k for k in range(5) if mask[k]]
+    free = [k for k in range(5) if not mask[k]]
+    want = np.zeros([dx.shape[k] for k in free] + [dy.shape[k] for k in free])
+    for idx in itertools.product(*[range(dx.shape[k]) for k in free]):
+        for jdx in itertools.product(*[range(dy.shape[k]) for k in free]):
+            tot = 0.0
+            for sdx in itertools.product(*[range(dx.shape[k]) for k in sset]):
+                ix, iy = [0] * 5, [0] * 5
+                for k, v in zip(free, idx):
+                    ix[k] = v
+                for k, v in zip(free, jdx):
+                    iy[k] = v
+                for k, v in zip(sset, sdx):
+                    ix[k] = iy[k] = v
+                tot += dx[tuple(ix)] * dy[tuple(iy)]
+            want[idx + jdx] = tot
+    f, runs = O.partial_factored(x, y, mask)
+    assert f == free and len(runs) == len(free) + 1
+    np.testing.assert_allclose(O.factored_to_dense(x, y, f, runs), want, rtol=0, atol=1e-13)
+    cores, perm = O.partial_merged(x, y, mask)
+    np.testing.assert_allclose(O.merged_to_dense(cores, perm), want, rtol=0, atol=1e-13)
+
+
+def test_transfer_matrix_entries_and_runs(rng):
+    """A mode's transfer matrix entry by entry (sum over the shared index of
+    one X entry times one Y entry, pair index a R^y + b); a run's matrix is
+    the product, so row (a, b) is the run swept from e_a e_b^T; the left and
+    right environments are its end rows and columns."""
+    gx = rng.standard_normal((2, 3, 4))
+    gy = rng.standard_normal((3, 3, 2))
+    t = O.transfer_matrix(gx, gy)
+    for a, b, u, v in itertools.product(range(2), range(3), range(4), range(2)):
+        assert abs(t[a * 3 + b, u * 2 + v] - sum(gx[a, i, u] * gy[b, i, v] for i in range(3))) < 1e-14
+    x = _rand_tt(rng, [2, 3, 2, 3], [1, 2, 3, 2, 1])
+    y = _rand_tt(rng, [2, 3, 2, 3], [1, 3, 2, 2, 1])
+    f, runs = O.partial_factored(x, y, [0, 1, 1, 0])
+    e = np.zeros((2, 3))
+    e[1, 2] = 1.0
+    row = O.absorb_left(O.absorb_left(e, x[1], y[1]), x[2], y[2]).ravel()
+    np.testing.assert_allclose(runs[1][1 * 3 + 2], row, rtol=0, atol=1e-14)
+    assert runs[0] is None and runs[2] is None
+    f, runs = O.partial_factored(x, y, [1, 0, 1, 1])
+    np.testing.assert_allclose(runs[0].ravel(), O.left_envs(x[:1], y[:1])[-1].ravel(), rtol=0, atol=1e-14)
+    assert len(runs) == 2
+    np.testing.assert_allclose(runs[1].ravel(), O.right_envs(x[2:], y[2:])[0].ravel(), rtol=0, atol=1e-14)
