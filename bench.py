@@ -564,6 +564,7 @@ def run_ours(args):
             "merged": lambda: bench_merged(T, dev, args),
             "dense_ttcp": lambda: bench_dense_ttcp(T, dev, args),
             "factored": lambda: bench_factored(T, dev, args),
+            "random_sets": lambda: bench_random_sets(T, dev, args),
         }
         wanted = list(runners) if args.forms == "all" else [f for f in args.forms.split(",") if f]
         for name in wanted:
@@ -999,6 +1000,70 @@ def bench_factored(T, dev, args):
         "device_status": int(op.status.item()),
         "l2": "flushed before each call",
     }
+
+
+def bench_random_sets(T, dev, args, n_pairs=512):
+    """The batch's secondary run over truly random contracted sets: 512 pairs
+    of order U{4..12}, modes U{2..32}, ranks U{4..16}, float32, S = a random
+    set of floor(N/2) modes at any positions, factored output (the merged
+    layout's Kronecker factors; the merged cores themselves would reach
+    256 x 32 x 32 x 256 entries).  One contraction call per pair, all issued on
+    one stream between two CUDA events (not one persistent launch: each call
+    is its own few launches); beside it the float64 oracle on a sample of
+    pairs on one host thread."""
+    import time as _time
+
+    import torch
+
+    import oracle as O
+
+    pairs = [G.random_sets_pair(p) for p in range(n_pairs)]
+    ops = []
+    for mask, x, y in pairs:
+        xd = [torch.from_numpy(c).to(dev) for c in x]
+        yd = [torch.from_numpy(c).to(dev) for c in y]
+        ops.append(T.FactoredContraction(xd, yd, mask))
+    stream = torch.cuda.current_stream(dev)
+    for op in ops:
+        op(stream)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for r in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for op in ops:
+            op(stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    flops = sum(W.factored_flops([c.shape[1] for c in x_], [c.shape[0] for c in x_] + [1],
+                                 [c.shape[0] for c in y_] + [1], m) for m, x_, y_ in pairs)
+    status = 0
+    for op in ops:
+        status |= int(op.status.item())
+    out = {
+        "workload": "512 TT pairs, order U{4..12}, modes U{2..32}, ranks U{4..16}, float32; partial contraction "
+                    "over a random set of floor(N/2) modes (any positions), factored output; one call per pair "
+                    "on one stream",
+        "value": n_pairs / (ms / 1e3),
+        "unit": "contractions/s",
+        "ms_per_batch": ms,
+        "alg_flops": flops,
+        "gflops": flops / (ms / 1e3) / 1e9,
+        "device_status": status,
+    }
+    if not args.no_cpu_baseline:
+        t0 = _time.perf_counter()
+        k = 0
+        while k < n_pairs and _time.perf_counter() - t0 < 5.0:
+            m, x_, y_ = pairs[k]
+            O.partial_factored(x_, y_, m)
+            k += 1
+        dt = _time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": k / dt, "unit": "contractions/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the first {k} pairs, numpy float64 transfer matrices, one thread"}
+    return out
 
 
 EXAMPLE2_Y = [(20, 20, 20), (20, 20, 20, 5), (20, 20, 20, 5, 4)]

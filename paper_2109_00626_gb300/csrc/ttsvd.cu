@@ -17,8 +17,9 @@
 // S V^T's first r rows carry on to mode k + 1.
 //
 // One CTA of 1024 threads runs the whole decomposition (the steps depend on
-// each other's ranks); the matrices live in the caller's workspace, in L2 for
-// the sizes this is meant for.  Wide matrices (rows < columns) are
+// each other's ranks); the matrices live in the caller's workspace, and an SVD
+// whose vectors and accumulated rotations fit in 200 KB is swept in shared
+// memory.  Wide matrices (rows < columns) are
 // orthogonalised by rows in place; tall ones are first transposed so their
 // columns become contiguous rows.
 #include <math.h>
@@ -48,7 +49,10 @@ struct SvdParams {
   int64_t numel;
   double eps;
   int max_rank;        // 0: no cap
+  size_t smem_bytes;   // dynamic shared memory: an SVD whose vectors and rotations fit runs there
 };
+
+constexpr size_t kSvdSmemCap = 200 * 1024;
 
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
@@ -153,6 +157,7 @@ __device__ int jacobi_rows(T* __restrict__ W, T* __restrict__ Qt, int p, int L, 
 
 template <typename T>
 __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_constant__ SvdParams p) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[kSvdWarps];
   __shared__ int s_rot, s_r;
   __shared__ T tile[32 * 33];
@@ -191,9 +196,22 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
       transpose_rows<T>(oth, cur, m, n, tile);
       W = oth;
     }
-    for (int e = tid; e < pp * pp; e += kSvdThreads) Qt[e] = (e / pp == e % pp) ? T(1) : T(0);
+    // the Jacobi sweeps run in shared memory when the vectors and the
+    // rotations fit (every round then costs shared-memory, not L2, latency)
+    const int64_t wl = static_cast<int64_t>(pp) * L;
+    const bool local = static_cast<size_t>(wl + static_cast<int64_t>(pp) * pp) * sizeof(T) <= p.smem_bytes;
+    T* Wj = local ? reinterpret_cast<T*>(dsm) : W;
+    T* Qj = local ? Wj + wl : Qt;
+    if (local)
+      for (int64_t e = tid; e < wl; e += kSvdThreads) Wj[e] = W[e];
+    for (int e = tid; e < pp * pp; e += kSvdThreads) Qj[e] = (e / pp == e % pp) ? T(1) : T(0);
     __syncthreads();
-    jacobi_rows<T>(W, Qt, pp, L, &s_rot);
+    jacobi_rows<T>(Wj, Qj, pp, L, &s_rot);
+    if (local) {
+      for (int64_t e = tid; e < wl; e += kSvdThreads) W[e] = Wj[e];
+      for (int e = tid; e < pp * pp; e += kSvdThreads) Qt[e] = Qj[e];
+      __syncthreads();
+    }
     // singular values: the row norms (float64 sums), warp per row
     const int lane = tid & 31, warp = tid >> 5;
     for (int i = warp; i < pp; i += kSvdWarps) {
@@ -379,9 +397,29 @@ extern "C" int tt_svd(const void* x_dev, int order, const int32_t* modes, int dt
   p.numel = numel;
   p.eps = eps;
   p.max_rank = max_rank;
+  // shared memory for the largest SVD that fits (sizes bounded by the caps)
+  size_t smem = 0;
+  {
+    int64_t tail = numel;
+    for (int k = 0; k + 1 < order; ++k) {
+      tail /= modes[k];
+      const int64_t rows = static_cast<int64_t>(cap[k]) * modes[k];
+      const int64_t ps = std::min<int64_t>(rows, tail);
+      const size_t b = static_cast<size_t>(rows * tail + ps * ps) * eb;
+      if (b <= kSvdSmemCap) smem = std::max(smem, b);
+    }
+  }
+  p.smem_bytes = smem;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (dtype == TT_F64) ttsvd_kernel<double><<<1, kSvdThreads, 0, s>>>(p);
-  else ttsvd_kernel<float><<<1, kSvdThreads, 0, s>>>(p);
+  cudaError_t err = dtype == TT_F64 ? cudaFuncSetAttribute(ttsvd_kernel<double>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           static_cast<int>(smem))
+                                    : cudaFuncSetAttribute(ttsvd_kernel<float>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           static_cast<int>(smem));
+  if (err != cudaSuccess) return TT_ERR_CUDA;
+  if (dtype == TT_F64) ttsvd_kernel<double><<<1, kSvdThreads, smem, s>>>(p);
+  else ttsvd_kernel<float><<<1, kSvdThreads, smem, s>>>(p);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }

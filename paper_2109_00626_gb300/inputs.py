@@ -183,6 +183,24 @@ def batch_pair(p: int, seed: int = 0, dtype=np.float32):
     return spec, x, y
 
 
+def random_sets_pair(p: int, seed: int = 0, dtype=np.float32):
+    """Pair ``p`` of the random-contracted-set batch: order U{4..12}, mode
+    sizes U{2..32} shared by the pair, internal ranks U{4..16} per bond and
+    operand, and S = a uniformly drawn set of floor(N/2) modes (any
+    positions).  Stream default_rng([seed, 1, p]); shape first, then the
+    cores of X and Y."""
+    rng = np.random.default_rng([seed, 1, p])
+    n = int(rng.integers(4, 13))
+    modes = [int(v) for v in rng.integers(2, 33, size=n)]
+    rx = [1] + [int(v) for v in rng.integers(4, 17, size=n - 1)] + [1]
+    ry = [1] + [int(v) for v in rng.integers(4, 17, size=n - 1)] + [1]
+    sset = set(int(v) for v in rng.choice(n, size=n // 2, replace=False))
+    mask = [1 if k in sset else 0 for k in range(n)]
+    x = random_tt(rng, modes, rx, dtype)
+    y = random_tt(rng, modes, ry, dtype)
+    return mask, x, y
+
+
 def to_bf16_f32(a: np.ndarray) -> np.ndarray:
     """Round float32 values to bfloat16 (round to nearest even), kept as float32.
 

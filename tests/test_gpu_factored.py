@@ -183,3 +183,23 @@ def test_factored_gemm_path_ragged(dtype):
             err = np.max(np.abs(g - w) / _run_scale(x64, y64, t, free, 6))
             print(f"gemm path {''.join(map(str, mask))} run {t} {g.shape}: err {err:.2e}")
             assert err <= TOL[dtype]
+
+
+def test_random_sets_batch_sampled():
+    """Pairs of the random-contracted-set batch (order U{4..12}, modes
+    U{2..32}, ranks U{4..16}, S a random set of floor(N/2) modes at any
+    positions, as timed by the benchmark): every run against the oracle."""
+    for p in range(0, 512, 64):
+        mask, x, y = G.random_sets_pair(p)
+        n = len(x)
+        free, runs = _gpu_runs(x, y, mask)
+        x64 = [c.astype(np.float64) for c in x]
+        y64 = [c.astype(np.float64) for c in y]
+        want_free, want = O.partial_factored(x64, y64, mask)
+        assert free == want_free
+        for t, (g, w) in enumerate(zip(runs, want)):
+            assert (g is None) == (w is None)
+            if g is None:
+                continue
+            err = np.max(np.abs(g - w) / _run_scale(x64, y64, t, free, n))
+            assert err <= 1e-5, (p, t, err)
