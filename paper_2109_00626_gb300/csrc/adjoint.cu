@@ -51,7 +51,7 @@ struct AdjCfg {
 template <typename T, int TM, int LD>
 __device__ __forceinline__ void op_acc(T (&acc)[TM][TM], const T* __restrict__ A, const T* __restrict__ B, int K, int m0,
                                        int n0) {
-#pragma unroll 4
+#pragma unroll 16
   for (int k = 0; k < K; ++k) {
     T av[TM], bv[TM];
     ld_vec<T, TM>(av, A + k * LD + m0);
