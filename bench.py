@@ -565,6 +565,7 @@ def run_ours(args):
             "dense_ttcp": lambda: bench_dense_ttcp(T, dev, args),
             "factored": lambda: bench_factored(T, dev, args),
             "random_sets": lambda: bench_random_sets(T, dev, args),
+            "round": lambda: bench_round(T, dev, args),
         }
         wanted = list(runners) if args.forms == "all" else [f for f in args.forms.split(",") if f]
         for name in wanted:
@@ -1064,6 +1065,64 @@ def bench_random_sets(T, dev, args, n_pairs=512):
         out["cpu_baseline"] = {"value": k / dt, "unit": "contractions/s", "cores": 1, "kind": "oracle",
                                "sample": f"the first {k} pairs, numpy float64 transfer matrices, one thread"}
     return out
+
+
+def bench_round(T, dev, args):
+    """TT rounding of a merged-layout result: order-5 operands, modes 8, ranks
+    8, float32, S = {1, 3}: merged cores of ranks up to 64 and modes 8 x 8,
+    rounded at eps 1e-4 (tt_round on the GPU, CUDA events around the call
+    and the read of the new ranks); the error of the rounded result against
+    Eq. 8 on the dense operands and the float64 oracle's rounding timed
+    beside it."""
+    import time as _time
+
+    import torch
+
+    import oracle as O
+
+    x, y = G.pair(6, [8] * 5, G.tt_ranks(5, 8), G.tt_ranks(5, 8), np.float32)
+    mask = [0, 1, 0, 1, 0]
+    xd = [torch.from_numpy(c).to(dev) for c in x]
+    yd = [torch.from_numpy(c).to(dev) for c in y]
+    op = T.PartialContraction(xd, yd, mask, layout="merged")
+    op()
+    torch.cuda.synchronize(dev)
+    eps = 1e-4
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        out = T.round_merged(op.z, eps)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = T.round_merged(op.z, eps)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    ms = statistics.median(ts)
+    got = O.merged_to_dense([c.cpu().numpy().astype(np.float64).reshape(c.shape[0], 8, 8, c.shape[2]) for c in out],
+                            op.perm)
+    want = O.tcp(O.tt_to_dense([c.astype(np.float64) for c in x]), O.tt_to_dense([c.astype(np.float64) for c in y]),
+                 [1, 3])
+    res = {
+        "workload": "merged result of an order-5 pair (modes 8, ranks 8, float32, S = {1, 3}): cores of ranks "
+                    "up to 64 and modes 8 x 8, TT-rounded at eps 1e-4",
+        "ms": ms,
+        "value": 1.0 / (ms / 1e3),
+        "unit": "roundings/s",
+        "ranks_in": [int(c.shape[0]) for c in op.z] + [1],
+        "ranks_out": [int(c.shape[0]) for c in out] + [1],
+        "err_rel_frobenius": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+        "roofline": {"bound": "latency", "note": "one CTA runs both sweeps of single-core Jacobi SVDs"},
+    }
+    if not args.no_cpu_baseline:
+        flat = [c.cpu().numpy().astype(np.float64) for c in op.z]
+        t0 = _time.perf_counter()
+        O.tt_round(flat, eps)
+        res["cpu_baseline"] = {"value": 1.0 / (_time.perf_counter() - t0), "unit": "roundings/s", "cores": 1,
+                               "kind": "oracle", "sample": "one rounding, numpy float64 (QR and SVD), one thread"}
+    return res
 
 
 EXAMPLE2_Y = [(20, 20, 20), (20, 20, 20, 5), (20, 20, 20, 5, 4)]

@@ -305,6 +305,22 @@ int tt_svd(const void* x_dev, int order, const int32_t* modes, int dtype, double
            void* const* cores_dev, int32_t* ranks_dev, int32_t* status_dev, void* ws, size_t ws_bytes,
            tt_stream stream);
 
+/* TT rounding: the tensor x represents, re-expressed with smaller ranks
+ * within eps ||X||_F (the TT-SVD's truncation rule of Section II applied to a
+ * TT, e.g. a merged-layout result viewed as a TT of modes I J).  One CTA runs
+ * two sweeps of single-core SVDs (one-sided Jacobi, the storage type): right
+ * to left making the cores right-orthonormal (only exactly-zero singular
+ * values dropped), then left to right keeping, per core, the smallest rank
+ * whose dropped singular values have 2-norm <= eps ||X||_F / sqrt(order - 1),
+ * then at most max_rank (0: no cap).  cores_out[k] (device) holds at least
+ * x's core k (ranks never grow) and receives core k contiguous with the new
+ * ranks, which go to ranks_dev[order + 1] (device int32).  F64 / F32; every
+ * unfolding's shorter side <= 512 (TT_ERR_TOO_LARGE).  tt_round_workspace
+ * (host only) gives the workspace.  Asynchronous on `stream`; no allocation. */
+int tt_round_workspace(const tt_desc* x, int32_t max_rank, size_t* ws_bytes);
+int tt_round(const tt_desc* x, double eps, int32_t max_rank, void* const* cores_out, int32_t* ranks_dev,
+             int32_t* status_dev, void* ws, size_t ws_bytes, tt_stream stream);
+
 /* Dense mode permutation (Alg. 2 steps 1-2: the paired modes brought to the
  * front before the decomposition): out has axis t = axis axes[t] of in
  * (both device, row-major, F64 or F32, distinct buffers).  TT_ERR_ARG for a

@@ -46,6 +46,7 @@ transfer_matrix / partial_factored / factored_to_dense
                        Kronecker factors of the merged cores (Eq. 8)
 grad_sweep / grad_full / grad_partial_chain   gradients by the L/F formulas
 tt_svd                 a TT of a dense tensor within eps ||X||_F (Section II)
+tt_round               a TT re-expressed with truncated ranks within eps ||X||_F
 reverse_tt             the same TT with its modes in reverse order
 tcp_pairs              Eq. 8 over several (n, m) pairs, operands of any orders
 partial_chain_pairs    end-block pairs of TTs of different orders -> chain TT
@@ -83,6 +84,7 @@ __all__ = [
     "transfer_matrix",
     "partial_factored",
     "factored_to_dense",
+    "tt_round",
     "grad_sweep",
     "grad_full",
     "grad_partial_chain",
@@ -585,6 +587,41 @@ def tt_svd(x, eps=0.0):
         rest = u[:, :keep] * sv[:keep]
         right_rank = keep
     cores[0] = rest.reshape(1, dims[0], right_rank)
+    return cores
+
+
+def tt_round(cores, eps=0.0):
+    """TT rounding: the tensor the TT represents, re-expressed with ranks
+    chosen by the TT-SVD's truncation rule (Section II) so that the result is
+    within eps ||X||_F.
+
+    First the cores are made right-orthonormal from the right: core k's
+    transposed unfolding (I_k R_{k+1}) x R_k = Q R (QR), core k becomes Q^T and
+    R^T is multiplied into core k-1; then ||X||_F = ||G_0||_F.  Then from the
+    left each core's unfolding (R_k I_k) x R_{k+1} = U S V^T keeps the
+    smallest rank r >= 1 whose dropped singular values have 2-norm
+    <= eps ||X||_F / sqrt(N - 1); the core becomes U's r columns and the r rows
+    of S V^T are multiplied into core k+1.  The parts dropped at the N-1 steps
+    are orthogonal, so the total error is at most eps ||X||_F."""
+    cores = [np.array(c, dtype=np.float64) for c in cores]
+    n = len(cores)
+    for k in range(n - 1, 0, -1):
+        r0, i_dim, r1 = cores[k].shape
+        q, r = np.linalg.qr(cores[k].reshape(r0, i_dim * r1).T)
+        cores[k] = q.T.reshape(-1, i_dim, r1)
+        cores[k - 1] = np.einsum("aib,cb->aic", cores[k - 1], r)
+    if n == 1:
+        return cores
+    tol = eps * np.linalg.norm(cores[0]) / np.sqrt(n - 1)
+    for k in range(n - 1):
+        r0, i_dim, r1 = cores[k].shape
+        u, sv, vt = np.linalg.svd(cores[k].reshape(r0 * i_dim, r1), full_matrices=False)
+        dropped = np.sqrt(np.cumsum(sv[::-1] ** 2))[::-1]  # dropped[r] = ||sv[r:]||
+        keep = len(sv)
+        while keep > 1 and dropped[keep - 1] <= tol:
+            keep -= 1
+        cores[k] = u[:, :keep].reshape(r0, i_dim, keep)
+        cores[k + 1] = np.einsum("ab,bic->aic", sv[:keep, None] * vt[:keep], cores[k + 1])
     return cores
 
 

@@ -24,6 +24,9 @@ from ._binding import (  # noqa: F401
     TTError,
     Decomposition,
     FactoredContraction,
+    Rounding,
+    round_merged,
+    tt_round,
     contract_dense_pairs,
     contract_factored,
     contract_full,

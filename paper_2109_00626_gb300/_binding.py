@@ -49,6 +49,8 @@ EXPORTS = [
     "tt_dense_permute",
     "tt_factored_shape",
     "tt_contract_factored",
+    "tt_round_workspace",
+    "tt_round",
 ]
 
 
@@ -137,6 +139,9 @@ def lib():
     L.tt_svd.argtypes = [c_void_p, c_int, I32, c_int, ctypes.c_double, c_int32, POINTER(c_void_p), c_void_p, c_void_p,
                          c_void_p, c_size_t, c_void_p]
     L.tt_dense_permute.argtypes = [c_void_p, c_int, I32, I32, c_int, c_void_p, c_void_p]
+    L.tt_round_workspace.argtypes = [D, c_int32, POINTER(c_size_t)]
+    L.tt_round.argtypes = [D, ctypes.c_double, c_int32, POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_size_t,
+                           c_void_p]
     L.tt_factored_shape.argtypes = [D, D, U8, POINTER(TTFactored)]
     L.tt_contract_factored.argtypes = [D, D, U8, POINTER(TTFactored), c_void_p, c_void_p, c_void_p, c_size_t,
                                        c_void_p]
@@ -523,6 +528,60 @@ class Decomposition:
         r = [int(v) for v in self.ranks.cpu().tolist()]
         return [self.buf[k][: r[k] * self.modes[k] * r[k + 1]].view(r[k], self.modes[k], r[k + 1])
                 for k in range(len(self.modes))]
+
+
+class Rounding:
+    """Pre-marshalled TT rounding (tt_round) of TTs of one shape: workspace,
+    output buffers (at the input's ranks) and rank / status words allocated
+    once.  ``__call__()`` enqueues; ``cores()`` reads the new ranks (waits for
+    the call) and returns views of the rounded cores."""
+
+    def __init__(self, cores, eps, max_rank=0):
+        import torch
+
+        self.xd = Desc(cores)
+        self.eps = float(eps)
+        self.max_rank = int(max_rank)
+        ws = c_size_t(0)
+        check(lib().tt_round_workspace(self.xd.ref, self.max_rank, ctypes.byref(ws)), "tt_round_workspace")
+        dev = cores[0].device
+        self.modes = [int(c.shape[1]) for c in cores]
+        self.ws = torch.empty(max(ws.value, 1), dtype=torch.uint8, device=dev)
+        self.buf = [torch.empty(c.numel(), dtype=c.dtype, device=dev) for c in cores]
+        self._ptrs = (c_void_p * len(cores))(*[b.data_ptr() for b in self.buf])
+        self.ranks = torch.zeros(len(cores) + 1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def __call__(self, stream=None):
+        rc = lib().tt_round(self.xd.ref, self.eps, self.max_rank, self._ptrs, c_void_p(self.ranks.data_ptr()),
+                            c_void_p(self.status.data_ptr()), c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                            _stream_ptr(stream))
+        check(rc, "tt_round")
+
+    def cores(self):
+        r = [int(v) for v in self.ranks.cpu().tolist()]
+        return [self.buf[k][: r[k] * self.modes[k] * r[k + 1]].view(r[k], self.modes[k], r[k + 1])
+                for k in range(len(self.modes))]
+
+
+def tt_round(cores, eps, max_rank=0, stream=None):
+    """TT rounding of the CUDA cores within eps ||X||_F (tt_round; waits for
+    the call to read the new ranks)."""
+    op = Rounding([c.contiguous() for c in cores], eps, max_rank)
+    op(stream)
+    out = op.cores()
+    if int(op.status.item()) != 0:
+        raise ValueError("tt_round: the TT holds a non-finite value (TT_STATUS_NONFINITE)")
+    return out
+
+
+def round_merged(cores, eps, max_rank=0, stream=None):
+    """TT rounding of merged-layout cores, (r, I J, r') as the library writes
+    them or (r, I, J, r'): rounded as a TT of modes I J, returned in the
+    shape given."""
+    flat = [c if c.dim() == 3 else c.reshape(c.shape[0], c.shape[1] * c.shape[2], c.shape[3]) for c in cores]
+    out = tt_round(flat, eps, max_rank, stream)
+    return [o if c.dim() == 3 else o.view(o.shape[0], c.shape[1], c.shape[2], o.shape[2]) for o, c in zip(out, cores)]
 
 
 def tt_decompose(x, eps, max_rank=0, stream=None):

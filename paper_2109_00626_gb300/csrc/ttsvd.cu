@@ -5,12 +5,7 @@
 //
 // The decomposition walks the modes left to right.  At mode k the part of X
 // not yet factored is a matrix C of (r_{k-1} I_k) rows and prod_{j>k} I_j
-// columns.  Its SVD C = U S V^T is taken with a one-sided Jacobi method
-// (Hestenes 1958): the p = min(rows, columns) vectors of the shorter side are
-// made mutually orthogonal by plane rotations, swept in the round-robin
-// order of the circle method (p / 2 disjoint pairs per round), each rotation
-// also applied to an accumulated orthogonal p x p matrix.  The norms of the
-// orthogonalised vectors are the singular values.  Ranks are kept by the
+// columns.  Its SVD C = U S V^T (one-sided Jacobi, svd_common.cuh) keeps the
 // truncation rule of the TT-SVD: the smallest r >= 1 whose dropped singular
 // values have 2-norm <= eps ||X||_F / sqrt(N - 1), capped by an optional
 // maximum rank.  Core k is U's first r columns (left-orthonormal cores), and
@@ -19,20 +14,14 @@
 // One CTA of 1024 threads runs the whole decomposition (the steps depend on
 // each other's ranks); the matrices live in the caller's workspace, and an SVD
 // whose vectors and accumulated rotations fit in 200 KB is swept in shared
-// memory.  Wide matrices (rows < columns) are
-// orthogonalised by rows in place; tall ones are first transposed so their
-// columns become contiguous rows.
+// memory.
 #include <math.h>
 #include <string.h>
 
 #include "host_plan.h"
+#include "svd_common.cuh"
 
 namespace ttc {
-
-constexpr int kSvdThreads = 1024;
-constexpr int kSvdWarps = kSvdThreads / 32;
-constexpr int kSvdMaxP = 512;       // the shorter side of an unfolding
-constexpr int kSvdMaxSweeps = 40;   // a bound on the Jacobi sweeps of one SVD
 
 struct SvdParams {
   const void* x;
@@ -51,109 +40,6 @@ struct SvdParams {
   int max_rank;        // 0: no cap
   size_t smem_bytes;   // dynamic shared memory: an SVD whose vectors and rotations fit runs there
 };
-
-constexpr size_t kSvdSmemCap = 200 * 1024;
-
-template <typename T>
-__device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the block (every thread gets it).
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum_t(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < kSvdWarps; ++w) s += red[w];
-  return s;
-}
-
-// dst (n x m) = src (m x n)^T through 32 x 33 shared-memory tiles.
-template <typename T>
-__device__ void transpose_rows(T* __restrict__ dst, const T* __restrict__ src, int m, int n, T* tile) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int b0 = 0; b0 < m; b0 += 32)
-    for (int b1 = 0; b1 < n; b1 += 32) {
-      const int r = b0 + ty, c = b1 + tx;
-      if (r < m && c < n) tile[ty * 33 + tx] = src[static_cast<int64_t>(r) * n + c];
-      __syncthreads();
-      const int r2 = b1 + ty, c2 = b0 + tx;
-      if (r2 < n && c2 < m) dst[static_cast<int64_t>(r2) * m + c2] = tile[tx * 33 + ty];
-      __syncthreads();
-    }
-}
-
-// Pair i of round t of the circle method over P (even) indices.
-__device__ __forceinline__ void rr_pair(int P, int t, int i, int& a, int& b) {
-  if (i == 0) {
-    a = P - 1;
-    b = t;
-  } else {
-    a = (t + i) % (P - 1);
-    b = (t - i + P - 1) % (P - 1);
-  }
-}
-
-// One-sided Jacobi on the p rows (length L) of W, rotations also applied to
-// the rows of Qt (p x p).  Returns the number of sweeps taken.
-template <typename T>
-__device__ int jacobi_rows(T* __restrict__ W, T* __restrict__ Qt, int p, int L, int* s_rot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const T tol = T(8) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08));
-  const int P = (p + 1) & ~1;
-  int sweep = 0;
-  for (; sweep < kSvdMaxSweeps; ++sweep) {
-    if (threadIdx.x == 0) *s_rot = 0;
-    __syncthreads();
-    for (int t = 0; t < P - 1; ++t) {
-      for (int i = warp; i < P / 2; i += kSvdWarps) {
-        int a, b;
-        rr_pair(P, t, i, a, b);
-        if (a >= p || b >= p) continue;  // the dummy index of an odd p
-        T* wa = W + static_cast<int64_t>(a) * L;
-        T* wb = W + static_cast<int64_t>(b) * L;
-        T al = T(0), be = T(0), ga = T(0);
-        for (int e = lane; e < L; e += 32) {
-          const T u = wa[e], v = wb[e];
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
-        }
-        al = warp_sum_t(al);
-        be = warp_sum_t(be);
-        ga = warp_sum_t(ga);
-        if (ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        // rotation that zeroes the inner product of the two new rows:
-        // t^2 + 2 zeta t - 1 = 0, the root of modulus <= 1
-        const T zeta = (be - al) / (T(2) * ga);
-        const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + tn * tn), s = c * tn;
-        for (int e = lane; e < L; e += 32) {
-          const T u = wa[e], v = wb[e];
-          wa[e] = c * u - s * v;
-          wb[e] = s * u + c * v;
-        }
-        T* qa = Qt + static_cast<int64_t>(a) * p;
-        T* qb = Qt + static_cast<int64_t>(b) * p;
-        for (int e = lane; e < p; e += 32) {
-          const T u = qa[e], v = qb[e];
-          qa[e] = c * u - s * v;
-          qb[e] = s * u + c * v;
-        }
-        if (lane == 0) *s_rot = 1;
-      }
-      __syncthreads();
-    }
-    if (*s_rot == 0) break;
-    __syncthreads();
-  }
-  return sweep;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_constant__ SvdParams p) {
@@ -183,6 +69,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
   const double delta2 = N > 1 ? p.eps * p.eps * nrm2 / (N - 1) : 0.0;
   if (tid == 0) p.ranks_out[0] = 1;
 
+  const SvdShared<T> sh{red, &s_rot, &s_r, tile, dsm, p.smem_bytes};
   int r_prev = 1;
   int64_t tail = p.numel;  // prod_{j >= k} I_j
   for (int k = 0; k + 1 < N; ++k) {
@@ -190,95 +77,15 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
     const int m = r_prev * p.modes[k];
     const int n = static_cast<int>(tail);
     const bool wide = m < n;
-    const int pp = wide ? m : n, L = wide ? n : m;
-    T* W = cur;
-    if (!wide) {
-      transpose_rows<T>(oth, cur, m, n, tile);
-      W = oth;
-    }
-    // the Jacobi sweeps run in shared memory when the vectors and the
-    // rotations fit (every round then costs shared-memory, not L2, latency)
-    const int64_t wl = static_cast<int64_t>(pp) * L;
-    const bool local = static_cast<size_t>(wl + static_cast<int64_t>(pp) * pp) * sizeof(T) <= p.smem_bytes;
-    T* Wj = local ? reinterpret_cast<T*>(dsm) : W;
-    T* Qj = local ? Wj + wl : Qt;
-    if (local)
-      for (int64_t e = tid; e < wl; e += kSvdThreads) Wj[e] = W[e];
-    for (int e = tid; e < pp * pp; e += kSvdThreads) Qj[e] = (e / pp == e % pp) ? T(1) : T(0);
-    __syncthreads();
-    jacobi_rows<T>(Wj, Qj, pp, L, &s_rot);
-    if (local) {
-      for (int64_t e = tid; e < wl; e += kSvdThreads) W[e] = Wj[e];
-      for (int e = tid; e < pp * pp; e += kSvdThreads) Qt[e] = Qj[e];
-      __syncthreads();
-    }
-    // singular values: the row norms (float64 sums), warp per row
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int i = warp; i < pp; i += kSvdWarps) {
-      double s2 = 0.0;
-      const T* w = W + static_cast<int64_t>(i) * L;
-      for (int e = lane; e < L; e += 32) s2 += static_cast<double>(w[e]) * static_cast<double>(w[e]);
-      s2 = warp_sum_t(s2);
-      if (lane == 0) p.sig[i] = sqrt(s2);
-    }
-    __syncthreads();
-    // order, largest first (ties by index): position of value i
-    for (int i = tid; i < pp; i += kSvdThreads) {
-      const double si = p.sig[i];
-      int pos = 0;
-      for (int j = 0; j < pp; ++j) {
-        const double sj = p.sig[j];
-        pos += (sj > si || (sj == si && j < i)) ? 1 : 0;
-      }
-      p.ord[pos] = i;
-    }
-    __syncthreads();
-    // rank: the smallest r >= 1 whose dropped values have squared 2-norm <= delta^2
-    if (tid == 0) {
-      int r = pp;
-      double dropped = 0.0;
-      while (r > 1) {
-        const double s = p.sig[p.ord[r - 1]];
-        if (dropped + s * s > delta2) break;
-        dropped += s * s;
-        --r;
-      }
-      if (p.max_rank > 0 && r > p.max_rank) r = p.max_rank;
-      s_r = r;
-      p.ranks_out[k + 1] = r;
-    }
-    __syncthreads();
-    const int r = s_r;
-    T* core = static_cast<T*>(p.cores[k]);  // m x r
+    // core k = U's columns; S V^T carries on (a wide M is read while S V^T is
+    // written, so that goes to the other buffer)
+    const int r = svd_factor<T>(cur, oth, Qt, p.sig, p.ord, m, n, delta2, p.max_rank, static_cast<T*>(p.cores[k]),
+                                wide ? oth : cur, sh);
+    if (tid == 0) p.ranks_out[k + 1] = r;
     if (wide) {
-      // U = Q: core[i][t] = Qt[ord t][i]; S V^T = the rows of W in order
-      for (int e = tid; e < m * r; e += kSvdThreads) {
-        const int i = e / r, t = e - i * r;
-        core[e] = Qt[static_cast<int64_t>(p.ord[t]) * pp + i];
-      }
-      for (int64_t e = tid; e < static_cast<int64_t>(r) * n; e += kSvdThreads) {
-        const int t = static_cast<int>(e / n);
-        const int64_t j = e - static_cast<int64_t>(t) * n;
-        oth[e] = W[static_cast<int64_t>(p.ord[t]) * n + j];
-      }
-      __syncthreads();
       T* sw = cur;
       cur = oth;
       oth = sw;
-    } else {
-      // W = S U^T row by row: core[i][t] = W[ord t][i] / sigma; S V^T = sigma Qt rows
-      for (int e = tid; e < m * r; e += kSvdThreads) {
-        const int i = e / r, t = e - i * r;
-        const int o = p.ord[t];
-        const double s = p.sig[o];
-        core[e] = s > 0.0 ? static_cast<T>(static_cast<double>(W[static_cast<int64_t>(o) * m + i]) / s) : T(0);
-      }
-      for (int e = tid; e < r * n; e += kSvdThreads) {
-        const int t = e / n, j = e - t * n;
-        const int o = p.ord[t];
-        cur[e] = static_cast<T>(p.sig[o] * static_cast<double>(Qt[static_cast<int64_t>(o) * pp + j]));
-      }
-      __syncthreads();
     }
     r_prev = r;
   }

@@ -474,6 +474,26 @@ def test_factored_shape_on_the_host(L):
                                   None) == -6
 
 
+def test_round_workspace_and_rejections(L):
+    """tt_round_workspace and tt_round's argument checks (host only)."""
+    x = FakeDesc([4, 3, 5], [1, 3, 4, 1])
+    ws = ctypes.c_size_t(0)
+    assert L.tt_round_workspace(x.ref, 0, ctypes.byref(ws)) == 0 and ws.value > 0
+    assert L.tt_round_workspace(x.ref, -1, ctypes.byref(ws)) == -1
+    xb = FakeDesc([4, 3, 5], [1, 3, 4, 1], dtype=B.TT_BF16)
+    assert L.tt_round_workspace(xb.ref, 0, ctypes.byref(ws)) == -3
+    big = FakeDesc([4, 600, 4], [1, 600, 600, 1])
+    assert L.tt_round_workspace(big.ref, 0, ctypes.byref(ws)) == -5
+    L.tt_round_workspace(x.ref, 0, ctypes.byref(ws))
+    outs = (ctypes.c_void_p * 3)(0x1000, 0x2000, 0x3000)
+    fake = ctypes.c_void_p(0x4000)
+    assert L.tt_round(x.ref, 0.1, 0, outs, fake, fake, fake, ws.value - 1, None) == -6
+    assert L.tt_round(x.ref, -0.1, 0, outs, fake, fake, fake, ws.value, None) == -1
+    assert L.tt_round(x.ref, 0.1, 0, outs, None, fake, fake, ws.value, None) == -1
+    nul = (ctypes.c_void_p * 3)(0x1000, None, 0x3000)
+    assert L.tt_round(x.ref, 0.1, 0, nul, fake, fake, fake, ws.value, None) == -1
+
+
 def test_workspace_queries_and_their_limits(L):
     """tt_workspace_bytes per operation, and the conditions the header states
     for each path (host only)."""

@@ -212,3 +212,38 @@ def test_factored_pin_catches_transfer_mutants(mutant, monkeypatch):
     monkeypatch.setattr(T, "transfer_matrix", mutant)
     f, runs = T.partial_factored(x, y, mask)
     assert np.abs(T.factored_to_dense(x, y, f, runs) - want).max() > 1e-6
+
+
+def _round_without_orthogonalising(cores, eps=0.0):
+    """Truncation from the left without the right-orthonormal sweep first."""
+    cores = [np.array(c, dtype=np.float64) for c in cores]
+    n = len(cores)
+    nrm = math.sqrt(T.contract_full(cores, cores))
+    tol = eps * nrm / np.sqrt(n - 1)
+    for k in range(n - 1):
+        r0, i_dim, r1 = cores[k].shape
+        u, sv, vt = np.linalg.svd(cores[k].reshape(r0 * i_dim, r1), full_matrices=False)
+        dropped = np.sqrt(np.cumsum(sv[::-1] ** 2))[::-1]
+        keep = len(sv)
+        while keep > 1 and dropped[keep - 1] <= tol:
+            keep -= 1
+        cores[k] = u[:, :keep].reshape(r0, i_dim, keep)
+        cores[k + 1] = np.einsum("ab,bic->aic", sv[:keep, None] * vt[:keep], cores[k + 1])
+    return cores
+
+
+def test_round_pin_catches_missing_orthogonalisation(monkeypatch):
+    """Without the right-orthonormal sweep the kept ranks are not the TT-SVD's
+    (and the error bound can break): the rank pin sees it."""
+    rng = np.random.default_rng(31)
+    y = G.random_tt(rng, [4, 3, 5, 3, 4], [1, 4, 8, 7, 4, 1], np.float64)
+    for c in y:
+        c *= rng.uniform(0.2, 5.0)
+    dy = O.tt_to_dense(y)
+    eps = 0.2
+    want = [c.shape[0] for c in O.reverse_tt(O.tt_svd(np.transpose(dy, (4, 3, 2, 1, 0)), eps))]
+    assert [c.shape[0] for c in O.tt_round(y, eps)] == want
+    monkeypatch.setattr(T, "tt_round", _round_without_orthogonalising)
+    t = T.tt_round(y, eps)
+    err = np.linalg.norm(T.tt_to_dense(t) - dy) / np.linalg.norm(dy)
+    assert [c.shape[0] for c in t] != want or err > eps

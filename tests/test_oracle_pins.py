@@ -664,3 +664,55 @@ def test_transfer_matrix_entries_and_runs(rng):
     np.testing.assert_allclose(runs[0].ravel(), O.left_envs(x[:1], y[:1])[-1].ravel(), rtol=0, atol=1e-14)
     assert len(runs) == 2
     np.testing.assert_allclose(runs[1].ravel(), O.right_envs(x[2:], y[2:])[0].ravel(), rtol=0, atol=1e-14)
+
+
+def _tt_sum(a, b):
+    """The TT of A + B: block-diagonal interior cores (ranks add)."""
+    n = len(a)
+    out = []
+    for k, (ga, gb) in enumerate(zip(a, b)):
+        ra, i_dim, ra2 = ga.shape
+        rb, _, rb2 = gb.shape
+        if n == 1:
+            out.append(ga + gb)
+        elif k == 0:
+            out.append(np.concatenate([ga, gb], axis=2))
+        elif k == n - 1:
+            out.append(np.concatenate([ga, gb], axis=0))
+        else:
+            g = np.zeros((ra + rb, i_dim, ra2 + rb2))
+            g[:ra, :, :ra2] = ga
+            g[ra:, :, ra2:] = gb
+            out.append(g)
+    return out
+
+
+def test_tt_round_recovers_ranks_and_bounds_the_error(rng):
+    """Rounding X + X (ranks doubled, the tensor 2X of the original ranks)
+    recovers the original ranks with eps ~ 0 and the same tensor; on a random
+    TT the error stays within eps ||X||_F; the cores come out left-orthonormal
+    except the last; and the ranks equal those of the TT-SVD of the dense
+    tensor taken left to right at the same eps (the same singular values),
+    unless a threshold lies within 1e-6 of a tail of them."""
+    x = _rand_tt(rng, [4, 3, 5, 3, 4], [1, 3, 4, 4, 2, 1])
+    d = O.tt_to_dense(x)
+    r = O.tt_round(_tt_sum(x, x), 1e-12)
+    assert [c.shape[0] for c in r] + [1] == [1, 3, 4, 4, 2, 1]
+    np.testing.assert_allclose(O.tt_to_dense(r), 2 * d, rtol=0, atol=1e-12 * np.abs(d).max())
+    y = _rand_tt(rng, [4, 3, 5, 3, 4], [1, 4, 8, 7, 4, 1])
+    dy = O.tt_to_dense(y)
+    for eps in (0.02, 0.2, 0.5):
+        t = O.tt_round(y, eps)
+        assert np.linalg.norm(O.tt_to_dense(t) - dy) <= eps * np.linalg.norm(dy) * (1 + 1e-12)
+        for g in t[:-1]:
+            m = g.reshape(-1, g.shape[2])
+            np.testing.assert_allclose(m.T @ m, np.eye(m.shape[1]), rtol=0, atol=1e-12)
+        ltr = O.reverse_tt(O.tt_svd(np.transpose(dy, (4, 3, 2, 1, 0)), eps))
+        near = False
+        tol = eps * np.linalg.norm(dy) / 2.0
+        for k in range(4):
+            sv = np.linalg.svd(dy.reshape(int(np.prod(dy.shape[: k + 1])), -1), compute_uv=False)
+            tails = np.sqrt(np.cumsum(sv[::-1] ** 2))[::-1]
+            near |= bool(np.min(np.abs(tails - tol)) <= 1e-6 * tol)
+        if not near:
+            assert [c.shape[0] for c in t] == [c.shape[0] for c in ltr]
