@@ -71,7 +71,9 @@ __device__ __forceinline__ void rr_pair(int P, int t, int i, int& a, int& b) {
 template <typename T>
 __device__ int jacobi_rows(T* __restrict__ W, T* __restrict__ Qt, int p, int L, int* s_rot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const T tol = T(8) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08));
+  // a pair counts as orthogonal once |<a, b>| <= 4 u sqrt(L) |a| |b|: the
+  // rounding of an L-term dot product, below which rotations only chase noise
+  const T tol = T(4) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08)) * sqrt(T(L > 1 ? L : 1));
   const int P = (p + 1) & ~1;
   int sweep = 0;
   for (; sweep < kSvdMaxSweeps; ++sweep) {
