@@ -1379,6 +1379,28 @@ def run_profile_case(case):
             full()
             part()
         status = full.status | part.status
+    elif case == "dense_ttcp":
+        rng = np.random.default_rng(2109)
+        x = torch.from_numpy(rng.standard_normal((20, 20, 20)).astype(np.float32)).to(dev)
+        y = torch.from_numpy(rng.standard_normal((20, 20, 20, 5)).astype(np.float32)).to(dev)
+        for _ in range(2):
+            T.contract_dense_pairs(x, y, [(0, 0)], 1e-6)
+        status = torch.zeros(1, dtype=torch.int32)
+    elif case == "factored":
+        x, y = G.pair(3, [16] * 8, G.tt_ranks(8, 64), G.tt_ranks(8, 64), np.float32)
+        op = T.FactoredContraction([torch.from_numpy(c).to(dev) for c in x], [torch.from_numpy(c).to(dev) for c in y],
+                                   FACTORED_MASK)
+        for _ in range(2):
+            op()
+        status = op.status
+    elif case == "round":
+        x, y = G.pair(6, [8] * 5, G.tt_ranks(5, 8), G.tt_ranks(5, 8), np.float32)
+        op = T.PartialContraction([torch.from_numpy(c).to(dev) for c in x], [torch.from_numpy(c).to(dev) for c in y],
+                                  [0, 1, 0, 1, 0], layout="merged")
+        op()
+        for _ in range(2):
+            T.round_merged(op.z, 1e-4)
+        status = op.status
     elif case == "batched512":
         _, pairs = G.batch4096_device(512, 0, dev)
         op = T.BatchedContraction(pairs)
@@ -1406,7 +1428,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--forms", default="all", help="comma-separated subset of the secondary forms to run (default all)")
-    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "order10_tf32x3", "backward", "merged"],
+    ap.add_argument("--profile-case", choices=["tc_native", "tc_x3", "batched512", "order10", "order10_tf32x3", "backward",
+                                               "merged", "dense_ttcp", "factored", "round"],
                     default=None,
                     help="run a small case twice for an ncu capture and exit (no JSON line)")
     ap.add_argument("--measure-peaks", action="store_true",
