@@ -6,11 +6,23 @@
 // pair), each rotation also applied to an accumulated orthogonal p x p
 // matrix; their norms are the singular values.  svd_factor() then keeps the
 // rank that the TT-SVD's truncation rule gives and writes the two factors.
+//
+// The kernels run as a cluster of CTAs.  CTA 0 (the leader) does everything
+// but the sweeps; the sweeps run in one of three places: in the leader's
+// shared memory when the vectors and the rotations fit there; else spread
+// over the cluster by columns when every CTA's slice fits (each CTA holds
+// columns [c0, c1) of every vector and of the rotations, computes its part of
+// each pair's three inner products, the pair's owner sums them and sends the
+// rotation to every CTA, which applies it to its slice: two cluster barriers
+// per round, exchanges through distributed shared memory); else the same
+// in place in the workspace (L2), or by a leader without a cluster alone.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <math.h>
 #include <stdint.h>
 
+#include "tc_common.cuh"
 #include "ttc_internal.h"
 
 namespace ttc {
@@ -55,14 +67,58 @@ __device__ void transpose_rows(T* __restrict__ dst, const T* __restrict__ src, i
     }
 }
 
+// ---- the cluster a decomposition runs on ----
+//
+// Every CTA runs the same sequence of barriers: the control flow of the
+// sweeps depends only on values that all CTAs compute identically (the same
+// sums in the same order), so the hardware cluster barrier (arrive with
+// release, wait with acquire semantics at cluster scope) serves, as in the
+// contraction sweeps.
+struct SvdCluster {
+  int C, rank;
+  int32_t* status;
+  int* bc;                 // the leader's broadcast block [16] (shared): problem shape and path
+  unsigned long long* bcp; // the leader's broadcast pointers [4]
+};
+
+__device__ __forceinline__ void svd_barrier(const SvdCluster& cl) {
+  if (cl.C > 1)
+    cooperative_groups::this_cluster().sync();
+  else
+    __syncthreads();
+}
+
+__device__ __forceinline__ SvdCluster svd_cluster_begin(int32_t* status, int* bc, unsigned long long* bcp) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  SvdCluster cl;
+  cl.C = static_cast<int>(cluster.num_blocks());
+  cl.rank = static_cast<int>(cluster.block_rank());
+  cl.status = status;
+  cl.bc = bc;
+  cl.bcp = bcp;
+  cluster.sync();  // every CTA's shared memory exists before a peer maps it
+  return cl;
+}
+
+// A flag of the leader's, read by every CTA (after a barrier that follows
+// the leader's write).
+__device__ __forceinline__ int svd_leader_flag(const SvdCluster& cl, int slot) {
+  namespace cg = cooperative_groups;
+  return cl.C > 1 ? *cg::this_cluster().map_shared_rank(cl.bc + slot, 0) : cl.bc[slot];
+}
+
 // Pair i of round t of the circle method over P (even) indices.
 __device__ __forceinline__ void rr_pair(int P, int t, int i, int& a, int& b) {
   if (i == 0) {
     a = P - 1;
     b = t;
   } else {
-    a = (t + i) % (P - 1);
-    b = (t - i + P - 1) % (P - 1);
+    // t < P - 1 and 0 < i < P / 2: both sums lie in [0, 2 (P - 1))
+    a = t + i;
+    if (a >= P - 1) a -= P - 1;
+    b = t - i + P - 1;
+    if (b >= P - 1) b -= P - 1;
   }
 }
 
@@ -124,6 +180,188 @@ __device__ int jacobi_rows(T* __restrict__ W, T* __restrict__ Qt, int p, int L, 
   return sweep;
 }
 
+// Shared memory of the column-distributed sweeps: each CTA's slice of the p
+// vectors (ceil(L / C) columns) and of the rotations (ceil(p / C) columns)
+// when they are held there, then (from a multiple of four entries, for vector
+// stores) the partial inner products this CTA collects for the pairs it owns
+// (four entries per pair and source CTA) and a round's rotations (c, s per
+// pair).
+__host__ __device__ inline size_t dist_part_offset(int p, int L, int C) {
+  const int cw = (L + C - 1) / C, cq = (p + C - 1) / C;
+  return (static_cast<size_t>(p) * cw + static_cast<size_t>(p) * cq + 3) & ~static_cast<size_t>(3);
+}
+__host__ __device__ inline size_t dist_comm_elems(int p, int C) {
+  const int np = (p + 1) / 2, owned = (np + C - 1) / C;
+  return static_cast<size_t>(owned) * C * 4 + 2 * static_cast<size_t>(np);
+}
+__host__ __device__ inline size_t dist_smem_elems(int p, int L, int C) {
+  return dist_part_offset(p, L, C) + dist_comm_elems(p, C);
+}
+
+__device__ __forceinline__ void store4(float* q, float a, float b, float c) { *reinterpret_cast<float4*>(q) = make_float4(a, b, c, 0.f); }
+__device__ __forceinline__ void store4(double* q, double a, double b, double c) {
+  reinterpret_cast<double2*>(q)[0] = make_double2(a, b);
+  q[2] = c;
+}
+__device__ __forceinline__ void store2(float* q, float a, float b) { *reinterpret_cast<float2*>(q) = make_float2(a, b); }
+__device__ __forceinline__ void store2(double* q, double a, double b) { *reinterpret_cast<double2*>(q) = make_double2(a, b); }
+
+// Sum over the g lanes (a power of two) of an aligned lane group; every lane
+// gets it.
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int g) {
+  for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided Jacobi on the p rows (length L) of W with the rotations
+// accumulated into Qt, spread over the cluster by columns (see above); every
+// CTA of the cluster calls it.  kInSmem: each CTA copies its slices of W and
+// Qt into its shared memory (dist_smem_elems) and back at the end; else it
+// works on them in place in the workspace (only the exchange buffers,
+// dist_comm_elems, are in shared memory).  The rotations start from the
+// identity.
+//
+// A round takes two cluster barriers.  Each CTA forms its part of every
+// pair's three inner products and stores it into the shared memory of the
+// pair's owner (CTA i mod C for pair i); after the first barrier each owner
+// sums the C parts of its pairs, takes the rotation (or none: c = 1, s = 0)
+// and stores (c, s) into every CTA; after the second barrier every CTA
+// applies the round's rotations to its slices.  All transfers are stores, one
+// per pair and CTA plus one per owned pair and CTA, so no CTA waits on a
+// remote load.  Single buffers suffice: a CTA can store a round's parts only
+// after the previous round's second barrier, which every owner reaches after
+// reading the previous parts, and its rotations only after the first barrier
+// of the round, which every CTA reaches after applying the previous ones.
+// A pair's parts and its rotation are handled by a group of g lanes, g the
+// largest power of two <= 32 with g (p / 2) <= the block's threads.
+template <typename T, bool kInSmem>
+__device__ void jacobi_dist(T* W, T* Qt, int p, int L, T* dsm, const SvdCluster& cl) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = cl.C, rank = cl.rank;
+  const int cw = (L + C - 1) / C, c0 = min(L, rank * cw), nw = min(L, c0 + cw) - c0;
+  const int cq = (p + C - 1) / C, q0 = min(p, rank * cq), nq = min(p, q0 + cq) - q0;
+  const int P = (p + 1) & ~1, NP = P / 2, owned = (NP + C - 1) / C;
+  int g = 32;
+  while (g > 1 && g * NP > static_cast<int>(blockDim.x)) g >>= 1;
+  const int gl = threadIdx.x & (g - 1), grp = threadIdx.x / g, ngrp = blockDim.x / g;
+  T* Ws = kInSmem ? dsm : W + c0;
+  const int ldw = kInSmem ? cw : L;
+  T* Qs = kInSmem ? Ws + static_cast<int64_t>(p) * cw : Qt + q0;
+  const int ldq = kInSmem ? cq : p;
+  T* part = kInSmem ? dsm + dist_part_offset(p, L, C) : dsm;  // [owned][C][4]
+  T* rot = part + static_cast<int64_t>(owned) * C * 4;         // [NP][2]
+  __shared__ int rotated;
+  if (kInSmem)
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p) * cw; e += blockDim.x) {
+      const int i = static_cast<int>(e / cw), j = static_cast<int>(e - static_cast<int64_t>(i) * cw);
+      Ws[e] = j < nw ? __ldcg(W + static_cast<int64_t>(i) * L + c0 + j) : T(0);
+    }
+  for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p) * nq; e += blockDim.x) {
+    const int i = static_cast<int>(e / nq), j = static_cast<int>(e - static_cast<int64_t>(i) * nq);
+    Qs[static_cast<int64_t>(i) * ldq + j] = i == q0 + j ? T(1) : T(0);
+  }
+  const T tol = T(4) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08)) * sqrt(T(L > 1 ? L : 1));
+  // the owners' lanes: C per owned pair (C <= 32, a power of two)
+  const int oh = threadIdx.x & (C - 1), og = threadIdx.x / C, nog = blockDim.x / C;
+  svd_barrier(cl);  // every CTA's buffers exist before a peer stores into them
+  for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    for (int t = 0; t < P - 1; ++t) {
+      // this CTA's parts of every pair's inner products, stored at the owner
+      // (the group loops run the same trip count in every lane, for the shuffles)
+      for (int base = 0; base < NP; base += ngrp) {
+        const int i = base + grp;
+        int a = p, b = p;
+        if (i < NP) rr_pair(P, t, i, a, b);
+        const bool valid = a < p && b < p;
+        T al = T(0), be = T(0), ga = T(0);
+        if (valid) {
+          const T* wa = Ws + static_cast<int64_t>(a) * ldw;
+          const T* wb = Ws + static_cast<int64_t>(b) * ldw;
+          for (int j = gl; j < nw; j += g) {
+            const T u = kInSmem ? wa[j] : __ldcg(wa + j), v = kInSmem ? wb[j] : __ldcg(wb + j);
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+        }
+        al = group_sum(al, g);
+        be = group_sum(be, g);
+        ga = group_sum(ga, g);
+        if (valid && gl == 0)
+          store4(cluster.map_shared_rank(part + (static_cast<int64_t>(i / C) * C + rank) * 4, i % C), al, be, ga);
+      }
+      svd_barrier(cl);
+      // the owned pairs: sum the parts, take the rotation, store it everywhere
+      for (int base = 0; base < owned; base += nog) {
+        const int j = base + og, i = j * C + rank;
+        int a = p, b = p;
+        if (j < owned && i < NP) rr_pair(P, t, i, a, b);
+        const bool valid = a < p && b < p;
+        T al = T(0), be = T(0), ga = T(0);
+        if (valid) {
+          const T* q = part + (static_cast<int64_t>(j) * C + oh) * 4;
+          al = q[0];
+          be = q[1];
+          ga = q[2];
+        }
+        al = group_sum(al, C);
+        be = group_sum(be, C);
+        ga = group_sum(ga, C);
+        if (!valid) continue;
+        T c = T(1), sn = T(0);
+        if (!(ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be))) {
+          const T zeta = (be - al) / (T(2) * ga);
+          const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          c = T(1) / sqrt(T(1) + tn * tn);
+          sn = c * tn;
+        }
+        store2(cluster.map_shared_rank(rot + static_cast<int64_t>(i) * 2, oh), c, sn);
+      }
+      svd_barrier(cl);
+      // the round's rotations applied to this CTA's slices
+      for (int i = grp; i < NP; i += ngrp) {
+        int a, b;
+        rr_pair(P, t, i, a, b);
+        if (a >= p || b >= p) continue;
+        const T c = rot[2 * i], sn = rot[2 * i + 1];
+        if (sn == T(0)) continue;
+        T* wa = Ws + static_cast<int64_t>(a) * ldw;
+        T* wb = Ws + static_cast<int64_t>(b) * ldw;
+        for (int j = gl; j < nw; j += g) {
+          const T u = kInSmem ? wa[j] : __ldcg(wa + j), v = kInSmem ? wb[j] : __ldcg(wb + j);
+          wa[j] = c * u - sn * v;
+          wb[j] = sn * u + c * v;
+        }
+        T* qa = Qs + static_cast<int64_t>(a) * ldq;
+        T* qb = Qs + static_cast<int64_t>(b) * ldq;
+        for (int j = gl; j < nq; j += g) {
+          const T u = kInSmem ? qa[j] : __ldcg(qa + j), v = kInSmem ? qb[j] : __ldcg(qb + j);
+          qa[j] = c * u - sn * v;
+          qb[j] = sn * u + c * v;
+        }
+        rotated = 1;
+      }
+      __syncthreads();  // the rows rotated before the next round reads them
+    }
+    if (rotated == 0) break;
+    __syncthreads();
+  }
+  if (kInSmem) {
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p) * cw; e += blockDim.x) {
+      const int i = static_cast<int>(e / cw), j = static_cast<int>(e - static_cast<int64_t>(i) * cw);
+      if (j < nw) W[static_cast<int64_t>(i) * L + c0 + j] = Ws[e];
+    }
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p) * cq; e += blockDim.x) {
+      const int i = static_cast<int>(e / cq), j = static_cast<int>(e - static_cast<int64_t>(i) * cq);
+      if (j < nq) Qt[static_cast<int64_t>(i) * p + q0 + j] = Qs[e];
+    }
+  }
+  svd_barrier(cl);
+}
+
 // Per-CTA shared scalars of svd_factor and its dynamic shared memory.
 template <typename T>
 struct SvdShared {
@@ -141,37 +379,79 @@ struct SvdShared {
 // row-major) and the first r rows of S V^T to svt_out (r x n); returns r.
 // M is overwritten; scratch holds m n entries (the transpose of a tall M),
 // qt p^2, sig and ord p.  svt_out may alias M (not scratch), u_out neither.
+// Every CTA of the cluster calls it; only the leader's arguments are read
+// (the others may pass anything) and only the leader's result is meaningful.
 template <typename T>
 __device__ int svd_factor(T* M, T* scratch, T* qt, double* sig, int32_t* ord, int m, int n, double delta2,
-                          int max_rank, T* u_out, T* svt_out, const SvdShared<T>& sh) {
+                          int max_rank, T* u_out, T* svt_out, const SvdShared<T>& sh, SvdCluster& cl) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool wide = m < n;
-  const int pp = wide ? m : n, L = wide ? n : m;
-  T* W = M;
-  if (!wide) {
-    transpose_rows<T>(scratch, M, m, n, sh.tile);
-    W = scratch;
+  const bool leader = cl.rank == 0;
+  if (leader) {
+    const bool wide = m < n;
+    const int pp = wide ? m : n, L = wide ? n : m;
+    T* W = M;
+    if (!wide) {
+      transpose_rows<T>(scratch, M, m, n, sh.tile);
+      W = scratch;
+    }
+    // where the sweeps run: 0 the leader's shared memory, 1 the cluster's, 2 the workspace
+    const int64_t wl = static_cast<int64_t>(pp) * L;
+    // (3: the cluster's, in place in the workspace)
+    int path = 2;
+    if (static_cast<size_t>(wl + static_cast<int64_t>(pp) * pp) * sizeof(T) <= sh.smem_bytes) path = 0;
+    else if (cl.C > 1 && dist_smem_elems(pp, L, cl.C) * sizeof(T) <= sh.smem_bytes) path = 1;
+    else if (cl.C > 1) path = 3;
+    if (tid == 0) {
+      cl.bc[0] = pp;
+      cl.bc[1] = L;
+      cl.bc[2] = path;
+      cl.bcp[0] = reinterpret_cast<unsigned long long>(W);
+      cl.bcp[1] = reinterpret_cast<unsigned long long>(qt);
+    }
   }
-  // the sweeps run in shared memory when the vectors and the rotations fit
-  const int64_t wl = static_cast<int64_t>(pp) * L;
-  const bool local = static_cast<size_t>(wl + static_cast<int64_t>(pp) * pp) * sizeof(T) <= sh.smem_bytes;
-  T* Wj = local ? reinterpret_cast<T*>(sh.dsm) : W;
-  T* Qj = local ? Wj + wl : qt;
-  if (local)
-    for (int64_t e = tid; e < wl; e += kSvdThreads) Wj[e] = W[e];
-  for (int e = tid; e < pp * pp; e += kSvdThreads) Qj[e] = (e / pp == e % pp) ? T(1) : T(0);
-  __syncthreads();
-  jacobi_rows<T>(Wj, Qj, pp, L, sh.s_rot);
-  if (local) {
-    for (int64_t e = tid; e < wl; e += kSvdThreads) W[e] = Wj[e];
-    for (int e = tid; e < pp * pp; e += kSvdThreads) qt[e] = Qj[e];
+  svd_barrier(cl);
+  int pp, L, path;
+  T* W;
+  {
+    namespace cg = cooperative_groups;
+    const int* bc = cl.C > 1 ? cg::this_cluster().map_shared_rank(cl.bc, 0) : cl.bc;
+    const unsigned long long* bcp = cl.C > 1 ? cg::this_cluster().map_shared_rank(cl.bcp, 0) : cl.bcp;
+    pp = bc[0];
+    L = bc[1];
+    path = bc[2];
+    W = reinterpret_cast<T*>(bcp[0]);
+    qt = reinterpret_cast<T*>(bcp[1]);
+  }
+  if (path == 1 || path == 3) {
+    if (path == 1)
+      jacobi_dist<T, true>(W, qt, pp, L, reinterpret_cast<T*>(sh.dsm), cl);
+    else
+      jacobi_dist<T, false>(W, qt, pp, L, reinterpret_cast<T*>(sh.dsm), cl);
+  } else if (leader) {
+    const int64_t wl = static_cast<int64_t>(pp) * L;
+    T* Wj = path == 0 ? reinterpret_cast<T*>(sh.dsm) : W;
+    T* Qj = path == 0 ? Wj + wl : qt;
+    if (path == 0)
+      for (int64_t e = tid; e < wl; e += kSvdThreads) Wj[e] = W[e];
+    for (int e = tid; e < pp * pp; e += kSvdThreads) Qj[e] = (e / pp == e % pp) ? T(1) : T(0);
     __syncthreads();
+    jacobi_rows<T>(Wj, Qj, pp, L, sh.s_rot);
+    if (path == 0) {
+      for (int64_t e = tid; e < wl; e += kSvdThreads) W[e] = Wj[e];
+      for (int e = tid; e < pp * pp; e += kSvdThreads) qt[e] = Qj[e];
+    }
   }
+  svd_barrier(cl);
+  if (!leader) return 0;
+  const bool wide = m < n;
   // singular values: the row norms (float64 sums), warp per row
   for (int i = warp; i < pp; i += kSvdWarps) {
     double s2 = 0.0;
     const T* w = W + static_cast<int64_t>(i) * L;
-    for (int e = lane; e < L; e += 32) s2 += static_cast<double>(w[e]) * static_cast<double>(w[e]);
+    for (int e = lane; e < L; e += 32) {
+      const double v = static_cast<double>(__ldcg(w + e));  // peers may have written W: read it from L2
+      s2 += v * v;
+    }
     s2 = warp_sum_t(s2);
     if (lane == 0) sig[i] = sqrt(s2);
   }
@@ -206,11 +486,11 @@ __device__ int svd_factor(T* M, T* scratch, T* qt, double* sig, int32_t* ord, in
     for (int64_t e = tid; e < static_cast<int64_t>(r) * n; e += kSvdThreads) {
       const int t = static_cast<int>(e / n);
       const int64_t j = e - static_cast<int64_t>(t) * n;
-      svt_out[e] = W[static_cast<int64_t>(ord[t]) * n + j];
+      svt_out[e] = __ldcg(W + static_cast<int64_t>(ord[t]) * n + j);
     }
     for (int e = tid; e < m * r; e += kSvdThreads) {
       const int i = e / r, t = e - i * r;
-      u_out[e] = qt[static_cast<int64_t>(ord[t]) * pp + i];
+      u_out[e] = __ldcg(qt + static_cast<int64_t>(ord[t]) * pp + i);
     }
   } else {
     // W = S U^T row by row: u_out[i][t] = W[ord t][i] / sigma; S V^T = sigma qt rows
@@ -219,16 +499,52 @@ __device__ int svd_factor(T* M, T* scratch, T* qt, double* sig, int32_t* ord, in
       const int t = static_cast<int>(e - i * r);
       const int o = ord[t];
       const double s = sig[o];
-      u_out[e] = s > 0.0 ? static_cast<T>(static_cast<double>(W[static_cast<int64_t>(o) * m + i]) / s) : T(0);
+      u_out[e] = s > 0.0 ? static_cast<T>(static_cast<double>(__ldcg(W + static_cast<int64_t>(o) * m + i)) / s) : T(0);
     }
     for (int e = tid; e < r * n; e += kSvdThreads) {
       const int t = e / n, j = e - t * n;
       const int o = ord[t];
-      svt_out[e] = static_cast<T>(sig[o] * static_cast<double>(qt[static_cast<int64_t>(o) * pp + j]));
+      svt_out[e] = static_cast<T>(sig[o] * static_cast<double>(__ldcg(qt + static_cast<int64_t>(o) * pp + j)));
     }
   }
   __syncthreads();
   return r;
+}
+
+// Launch one of the decomposition kernels on a cluster of CTAs: the largest
+// of 16, 8, 4, 2, 1 the device can place with the dynamic shared memory
+// `smem_of(C)` asks for (the sweeps' needs depend on C).  Returns the launch
+// status; *c_out gets the cluster size.
+template <typename Params, typename SmemOf>
+static cudaError_t svd_launch(void (*kernel)(Params), Params params, SmemOf smem_of, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err != cudaSuccess) return err;
+  for (int c = 16; c >= 1; c >>= 1) {
+    // at least the exchange buffers of the largest SVD (p <= 512)
+    const size_t smem = c > 1 ? std::max<size_t>(smem_of(c), dist_comm_elems(kSvdMaxP, c) * sizeof(double)) : smem_of(c);
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kSvdThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();  // a size the device cannot place: try the next
+      continue;
+    }
+    params.smem_bytes = smem;
+    return cudaLaunchKernelEx(&cfg, kernel, params);
+  }
+  return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace ttc

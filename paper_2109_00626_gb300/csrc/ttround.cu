@@ -62,22 +62,27 @@ __device__ void swap_legs(T* __restrict__ dst, const T* __restrict__ src, int ra
 }
 
 // One left-to-right sweep: cores k = 0 .. N-2 of `area` (ranks rk[], updated)
-// replaced by their unfolding's U, S V^T multiplied into core k + 1.
+// replaced by their unfolding's U, S V^T multiplied into core k + 1.  Every
+// CTA of the cluster calls it (the SVDs are shared); the rest is the leader's.
 template <typename T>
 __device__ void lr_sweep(const RoundParams& p, T* area, const int64_t* off, const int32_t* modes, int* rk,
-                         double delta2, int max_rank, const SvdShared<T>& sh) {
+                         double delta2, int max_rank, const SvdShared<T>& sh, SvdCluster& cl) {
   const int tid = threadIdx.x;
+  const bool leader = cl.rank == 0;
   T* mbuf = static_cast<T*>(p.mbuf);
   T* svt = static_cast<T*>(p.svt);
   for (int k = 0; k + 1 < p.order; ++k) {
     T* core = area + off[k];
     T* next = area + off[k + 1];
     const int m = rk[k] * modes[k], n = rk[k + 1];
-    const int64_t mn = static_cast<int64_t>(m) * n;
-    for (int64_t e = tid; e < mn; e += kSvdThreads) mbuf[e] = core[e];
-    __syncthreads();
+    if (leader) {
+      const int64_t mn = static_cast<int64_t>(m) * n;
+      for (int64_t e = tid; e < mn; e += kSvdThreads) mbuf[e] = core[e];
+      __syncthreads();
+    }
     const int r = svd_factor<T>(mbuf, static_cast<T*>(p.sbuf), static_cast<T*>(p.qt), p.sig, p.ord, m, n, delta2,
-                                max_rank, core, svt, sh);
+                                max_rank, core, svt, sh, cl);
+    if (!leader) continue;
     // next <- (S V^T)[r x n] next[n x L]
     const int64_t L = static_cast<int64_t>(modes[k + 1]) * rk[k + 2];
     for (int64_t e = tid; e < r * L; e += kSvdThreads) {
@@ -103,55 +108,72 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttround_kernel(const __grid_co
   __shared__ T tile[32 * 33];
   __shared__ int rk[kMaxOrder + 1];
   __shared__ int32_t mrev[kMaxOrder];
+  __shared__ int bc[16];
+  __shared__ unsigned long long bcp[4];
+  SvdCluster cl = svd_cluster_begin(p.status, bc, bcp);
+  const bool leader = cl.rank == 0;
   const int tid = threadIdx.x;
   const int N = p.order;
   T* A = static_cast<T*>(p.area_a);
   T* B = static_cast<T*>(p.area_b);
   const SvdShared<T> sh{red, &s_rot, &s_r, tile, dsm, p.smem_bytes};
 
-  // the reversed TT
-  for (int k = 0; k < N; ++k) {
-    const int s = N - 1 - k;
-    swap_legs<T>(A + p.off_a[k], static_cast<const T*>(p.in[s]), p.ranks[s], p.modes[s], p.ranks[s + 1]);
+  if (leader) {
+    // the reversed TT
+    for (int k = 0; k < N; ++k) {
+      const int s = N - 1 - k;
+      swap_legs<T>(A + p.off_a[k], static_cast<const T*>(p.in[s]), p.ranks[s], p.modes[s], p.ranks[s + 1]);
+    }
+    if (tid <= N) rk[tid] = p.ranks[N - tid];
+    if (tid < N) mrev[tid] = p.modes[N - 1 - tid];
+    __syncthreads();
   }
-  if (tid <= N) rk[tid] = p.ranks[N - tid];
-  if (tid < N) mrev[tid] = p.modes[N - 1 - tid];
-  __syncthreads();
   // 1. right-orthonormal cores (a left-to-right sweep of the reversed TT)
-  lr_sweep<T>(p, A, p.off_a, mrev, rk, 0.0, 0, sh);
-  // back to the original order
-  for (int k = 0; k < N; ++k) {
-    const int s = N - 1 - k;
-    swap_legs<T>(B + p.off_b[k], A + p.off_a[s], rk[s], mrev[s], rk[s + 1]);
+  lr_sweep<T>(p, A, p.off_a, mrev, rk, 0.0, 0, sh, cl);
+  double delta2 = 0.0;
+  if (leader) {
+    // back to the original order
+    for (int k = 0; k < N; ++k) {
+      const int s = N - 1 - k;
+      swap_legs<T>(B + p.off_b[k], A + p.off_a[s], rk[s], mrev[s], rk[s + 1]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int tmp[kMaxOrder + 1];
+      for (int k = 0; k <= N; ++k) tmp[k] = rk[N - k];
+      for (int k = 0; k <= N; ++k) rk[k] = tmp[k];
+    }
+    __syncthreads();
+    // ||X||_F = ||G_0||_F now
+    double ss = 0.0;
+    const int64_t n0 = static_cast<int64_t>(rk[0]) * p.modes[0] * rk[1];
+    for (int64_t e = tid; e < n0; e += kSvdThreads) {
+      const double v = static_cast<double>(B[p.off_b[0] + e]);
+      ss += v * v;
+    }
+    const double nrm2 = block_sum(ss, red);
+    if (tid == 0) {
+      bc[8] = isfinite(nrm2) ? 1 : 0;
+      if (!isfinite(nrm2)) atomicOr(p.status, TT_STATUS_NONFINITE);
+    }
+    delta2 = N > 1 ? p.eps * p.eps * nrm2 / (N - 1) : 0.0;
   }
-  __syncthreads();
-  if (tid == 0) {
-    int tmp[kMaxOrder + 1];
-    for (int k = 0; k <= N; ++k) tmp[k] = rk[N - k];
-    for (int k = 0; k <= N; ++k) rk[k] = tmp[k];
-  }
-  __syncthreads();
-  // ||X||_F = ||G_0||_F now
-  double ss = 0.0;
-  const int64_t n0 = static_cast<int64_t>(rk[0]) * p.modes[0] * rk[1];
-  for (int64_t e = tid; e < n0; e += kSvdThreads) {
-    const double v = static_cast<double>(B[p.off_b[0] + e]);
-    ss += v * v;
-  }
-  const double nrm2 = block_sum(ss, red);
-  if (!isfinite(nrm2)) {
-    if (tid == 0) atomicOr(p.status, TT_STATUS_NONFINITE);
+  svd_barrier(cl);
+  if (!svd_leader_flag(cl, 8)) {
+    svd_barrier(cl);  // nobody leaves while a peer may still read its shared memory
     return;
   }
-  const double delta2 = N > 1 ? p.eps * p.eps * nrm2 / (N - 1) : 0.0;
   // 2. truncation, left to right
-  lr_sweep<T>(p, B, p.off_b, p.modes, rk, delta2, p.max_rank, sh);
-  for (int k = 0; k < N; ++k) {
-    const int64_t n = static_cast<int64_t>(rk[k]) * p.modes[k] * rk[k + 1];
-    T* dst = static_cast<T*>(p.out[k]);
-    for (int64_t e = tid; e < n; e += kSvdThreads) dst[e] = B[p.off_b[k] + e];
+  lr_sweep<T>(p, B, p.off_b, p.modes, rk, delta2, p.max_rank, sh, cl);
+  if (leader) {
+    for (int k = 0; k < N; ++k) {
+      const int64_t n = static_cast<int64_t>(rk[k]) * p.modes[k] * rk[k + 1];
+      T* dst = static_cast<T*>(p.out[k]);
+      for (int64_t e = tid; e < n; e += kSvdThreads) dst[e] = B[p.off_b[k] + e];
+    }
+    if (tid <= N) p.ranks_out[tid] = rk[tid];
   }
-  if (tid <= N) p.ranks_out[tid] = rk[tid];
+  svd_barrier(cl);
 }
 
 struct RoundLayout {
@@ -260,17 +282,29 @@ extern "C" int tt_round(const tt_desc* x, double eps, int32_t max_rank, void* co
   p.ord = reinterpret_cast<int32_t*>(w);
   p.eps = eps;
   p.max_rank = max_rank;
-  p.smem_bytes = lo.smem;
+  // shared memory: the largest single-CTA SVD that fits, or the largest
+  // cluster-spread one (both sweeps' unfoldings, at the input's ranks)
+  auto smem_of = [&](int c) {
+    size_t smem = lo.smem;
+    if (c > 1)
+      for (int k = 0; k < x->order; ++k)
+        for (int side = 0; side < 2; ++side) {
+          const int64_t m = static_cast<int64_t>(side ? x->ranks[k + 1] : x->ranks[k]) * x->modes[k];
+          const int64_t n = side ? x->ranks[k] : x->ranks[k + 1];
+          const int64_t ps = std::min(m, n), ls = std::max(m, n);
+          if (ls >= (int64_t(1) << 30)) continue;
+          const size_t d = dist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
+          if (d <= kSvdSmemCap) smem = std::max(smem, d);
+        }
+    return smem;
+  };
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t err = x->dtype == TT_F64 ? cudaFuncSetAttribute(ttround_kernel<double>,
-                                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                              static_cast<int>(lo.smem))
-                                       : cudaFuncSetAttribute(ttround_kernel<float>,
-                                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                              static_cast<int>(lo.smem));
-  if (err != cudaSuccess) return TT_ERR_CUDA;
-  if (x->dtype == TT_F64) ttround_kernel<double><<<1, kSvdThreads, lo.smem, s>>>(p);
-  else ttround_kernel<float><<<1, kSvdThreads, lo.smem, s>>>(p);
+  const cudaError_t err = x->dtype == TT_F64 ? svd_launch<RoundParams>(ttround_kernel<double>, p, smem_of, s)
+                                             : svd_launch<RoundParams>(ttround_kernel<float>, p, smem_of, s);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }

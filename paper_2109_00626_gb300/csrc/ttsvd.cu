@@ -47,6 +47,10 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
   __shared__ double red[kSvdWarps];
   __shared__ int s_rot, s_r;
   __shared__ T tile[32 * 33];
+  __shared__ int bc[16];
+  __shared__ unsigned long long bcp[4];
+  SvdCluster cl = svd_cluster_begin(p.status, bc, bcp);
+  const bool leader = cl.rank == 0;
   const int tid = threadIdx.x;
   const T* x = static_cast<const T*>(p.x);
   T* cur = static_cast<T*>(p.buf0);
@@ -54,20 +58,28 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
   T* Qt = static_cast<T*>(p.qt);
   const int N = p.order;
 
-  // ||X||_F^2 (float64), and X copied into the first buffer
-  double ss = 0.0;
-  for (int64_t e = tid; e < p.numel; e += kSvdThreads) {
-    const T v = x[e];
-    cur[e] = v;
-    ss += static_cast<double>(v) * static_cast<double>(v);
+  // ||X||_F^2 (float64), and X copied into the first buffer (leader)
+  double delta2 = 0.0;
+  if (leader) {
+    double ss = 0.0;
+    for (int64_t e = tid; e < p.numel; e += kSvdThreads) {
+      const T v = x[e];
+      cur[e] = v;
+      ss += static_cast<double>(v) * static_cast<double>(v);
+    }
+    const double nrm2 = block_sum(ss, red);
+    if (tid == 0) {
+      bc[8] = isfinite(nrm2) ? 1 : 0;
+      if (!isfinite(nrm2)) atomicOr(p.status, TT_STATUS_NONFINITE);
+      else p.ranks_out[0] = 1;
+    }
+    delta2 = N > 1 ? p.eps * p.eps * nrm2 / (N - 1) : 0.0;
   }
-  const double nrm2 = block_sum(ss, red);
-  if (!isfinite(nrm2)) {
-    if (tid == 0) atomicOr(p.status, TT_STATUS_NONFINITE);
+  svd_barrier(cl);
+  if (!svd_leader_flag(cl, 8)) {
+    svd_barrier(cl);  // nobody leaves while a peer may still read its shared memory
     return;
   }
-  const double delta2 = N > 1 ? p.eps * p.eps * nrm2 / (N - 1) : 0.0;
-  if (tid == 0) p.ranks_out[0] = 1;
 
   const SvdShared<T> sh{red, &s_rot, &s_r, tile, dsm, p.smem_bytes};
   int r_prev = 1;
@@ -80,8 +92,8 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
     // core k = U's columns; S V^T carries on (a wide M is read while S V^T is
     // written, so that goes to the other buffer)
     const int r = svd_factor<T>(cur, oth, Qt, p.sig, p.ord, m, n, delta2, p.max_rank, static_cast<T*>(p.cores[k]),
-                                wide ? oth : cur, sh);
-    if (tid == 0) p.ranks_out[k + 1] = r;
+                                wide ? oth : cur, sh, cl);
+    if (leader && tid == 0) p.ranks_out[k + 1] = r;
     if (wide) {
       T* sw = cur;
       cur = oth;
@@ -89,10 +101,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) ttsvd_kernel(const __grid_cons
     }
     r_prev = r;
   }
-  // last core: the remaining r_{N-1} x I_N matrix
-  T* last = static_cast<T*>(p.cores[N - 1]);
-  for (int64_t e = tid; e < static_cast<int64_t>(r_prev) * p.modes[N - 1]; e += kSvdThreads) last[e] = cur[e];
-  if (tid == 0) p.ranks_out[N] = 1;
+  if (leader) {
+    // last core: the remaining r_{N-1} x I_N matrix
+    T* last = static_cast<T*>(p.cores[N - 1]);
+    for (int64_t e = tid; e < static_cast<int64_t>(r_prev) * p.modes[N - 1]; e += kSvdThreads) last[e] = cur[e];
+    if (tid == 0) p.ranks_out[N] = 1;
+  }
+  svd_barrier(cl);
 }
 
 // Output axis t: its size and the input stride it walks.
@@ -204,29 +219,31 @@ extern "C" int tt_svd(const void* x_dev, int order, const int32_t* modes, int dt
   p.numel = numel;
   p.eps = eps;
   p.max_rank = max_rank;
-  // shared memory for the largest SVD that fits (sizes bounded by the caps)
-  size_t smem = 0;
-  {
+  // shared memory for the largest SVD that fits, in one CTA or spread over a
+  // cluster of c (sizes bounded by the caps)
+  auto smem_of = [&](int c) {
+    size_t smem = 0;
     int64_t tail = numel;
     for (int k = 0; k + 1 < order; ++k) {
       tail /= modes[k];
       const int64_t rows = static_cast<int64_t>(cap[k]) * modes[k];
-      const int64_t ps = std::min<int64_t>(rows, tail);
+      const int64_t ps = std::min<int64_t>(rows, tail), ls = std::max<int64_t>(rows, tail);
       const size_t b = static_cast<size_t>(rows * tail + ps * ps) * eb;
       if (b <= kSvdSmemCap) smem = std::max(smem, b);
+      if (c > 1 && ls < (int64_t(1) << 30)) {
+        const size_t d = dist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
+        if (d <= kSvdSmemCap) smem = std::max(smem, d);
+      }
     }
-  }
-  p.smem_bytes = smem;
+    return smem;
+  };
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t err = dtype == TT_F64 ? cudaFuncSetAttribute(ttsvd_kernel<double>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                           static_cast<int>(smem))
-                                    : cudaFuncSetAttribute(ttsvd_kernel<float>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                           static_cast<int>(smem));
-  if (err != cudaSuccess) return TT_ERR_CUDA;
-  if (dtype == TT_F64) ttsvd_kernel<double><<<1, kSvdThreads, smem, s>>>(p);
-  else ttsvd_kernel<float><<<1, kSvdThreads, smem, s>>>(p);
+  const cudaError_t err = dtype == TT_F64 ? svd_launch<SvdParams>(ttsvd_kernel<double>, p, smem_of, s)
+                                          : svd_launch<SvdParams>(ttsvd_kernel<float>, p, smem_of, s);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
   count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }

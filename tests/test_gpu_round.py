@@ -129,3 +129,25 @@ def test_round_max_rank_cap():
     y = G.random_tt(rng, [5, 5, 5, 5], [1, 5, 9, 5, 1], np.float64)
     t = _round(y, 0.0, max_rank=3)
     assert [c.shape[0] for c in t] + [1] == [1, 3, 3, 3, 1]
+
+
+def test_round_large_unfoldings_cluster_sweeps():
+    """A merged result of ranks 64 and modes 8 x 8 (unfoldings of 4096 x 64,
+    swept across the cluster) rounded at eps 1e-4: within eps of Eq. 8, and
+    the ranks equal the oracle's rounding unless a threshold is close."""
+    x, y = G.pair(6, [8] * 5, G.tt_ranks(5, 8), G.tt_ranks(5, 8), np.float32)
+    mask = [0, 1, 0, 1, 0]
+    op = T.PartialContraction(to_dev(x), to_dev(y), mask, layout="merged")
+    op()
+    torch.cuda.synchronize()
+    eps = 1e-4
+    rounded = T.round_merged(op.z, eps)
+    torch.cuda.synchronize()
+    got = O.merged_to_dense([c.cpu().numpy().astype(np.float64).reshape(c.shape[0], 8, 8, c.shape[2])
+                             for c in rounded], op.perm)
+    x64 = [c.astype(np.float64) for c in x]
+    y64 = [c.astype(np.float64) for c in y]
+    want = O.tcp(O.tt_to_dense(x64), O.tt_to_dense(y64), [1, 3])
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print(f"merged rank-64 rounding: ranks {[c.shape[0] for c in rounded] + [1]}, err {err:.2e}")
+    assert err <= eps + 1e-5

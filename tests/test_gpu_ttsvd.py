@@ -173,6 +173,10 @@ def _check_dense_contraction(xh, yh, pairs, eps, dtype, label):
     ay = [b for _, b in pairs] + [k for k in range(y64.ndim) if k not in {b for _, b in pairs}]
     ex = np.linalg.norm(O.tt_to_dense(_decompose(np.transpose(x64, ax).astype(dtype), eps)) - np.transpose(x64, ax))
     ey = np.linalg.norm(O.tt_to_dense(_decompose(np.transpose(y64, ay).astype(dtype), eps)) - np.transpose(y64, ay))
+    # each decomposition keeps its own guarantee (the larger unfoldings here take the
+    # cluster-wide sweeps)
+    slack = RTOL[dtype] * np.sqrt(max(x64.size, y64.size))
+    assert ex <= (eps + slack) * nx and ey <= (eps + slack) * ny, (ex / nx, ey / ny)
     bound = ex * (ny + ey) + nx * ey + (1e-12 if dtype == np.float64 else 1e-5) * nx * ny
     err = np.linalg.norm(got - want)
     print(f"{label}: |Z - Z*|_F / (|X||Y|) = {err / (nx * ny):.2e}, bound {bound / (nx * ny):.2e}")
@@ -206,3 +210,19 @@ def test_dense_contraction_interior_pairs(pairs):
     x = x + 1e-4 * np.linalg.norm(x) * rng.standard_normal(x.shape) / np.sqrt(x.size)
     y = y + 1e-4 * np.linalg.norm(y) * rng.standard_normal(y.shape) / np.sqrt(y.size)
     _check_dense_contraction(x, y, pairs, 1e-2, np.float64, f"interior {pairs}")
+
+
+def test_large_unfoldings_cluster_sweeps():
+    """Unfoldings too large for one CTA's shared memory (20 x 8000, 400 x 400,
+    8000 x 20 in float32) are swept across the cluster: exact ranks of a
+    low-rank tensor, and a full-rank Gaussian tensor within its guarantee
+    with left-orthonormal cores."""
+    xh = _dense_tt(60, [20, 20, 20, 5, 4], [1, 12, 40, 15, 4, 1], np.float32)
+    cores = _decompose(xh, 1e-5)
+    assert [c.shape[0] for c in cores] + [1] == [1, 12, 40, 15, 4, 1]
+    _check_valid(xh, cores, 1e-5, np.float32, "low rank 20^3x5x4")
+    rng = np.random.default_rng(61)
+    g = rng.standard_normal((20, 20, 20, 5, 4)).astype(np.float32)
+    cores = _decompose(g, 1e-6)
+    assert [c.shape[0] for c in cores] + [1] == [1, 20, 400, 20, 4, 1]
+    _check_valid(g, cores, 1e-6, np.float32, "gaussian 20^3x5x4")
