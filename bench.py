@@ -1114,7 +1114,9 @@ def bench_round(T, dev, args):
         "ranks_in": [int(c.shape[0]) for c in op.z] + [1],
         "ranks_out": [int(c.shape[0]) for c in out] + [1],
         "err_rel_frobenius": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-        "roofline": {"bound": "latency", "note": "one CTA runs both sweeps of single-core Jacobi SVDs"},
+        "roofline": {"bound": "latency", "note": "one cluster launch runs both sweeps of per-core Jacobi SVDs "
+                                                "(dependent rounds; unfoldings too large for one CTA spread over "
+                                                "16 CTAs, two cluster barriers per round)"},
     }
     if not args.no_cpu_baseline:
         flat = [c.cpu().numpy().astype(np.float64) for c in op.z]
@@ -1184,7 +1186,8 @@ def bench_dense_ttcp(T, dev, args):
         out["cases"].append(case)
     out["value"] = statistics.mean(c["value"] for c in out["cases"])
     out["unit"] = "dense contractions/s (mean over the three shapes)"
-    out["roofline"] = {"bound": "latency", "note": "one CTA runs each decomposition (dependent Jacobi rounds); "
+    out["roofline"] = {"bound": "latency", "note": "one cluster launch runs each decomposition, X's and Y's "
+                                                   "concurrently on two streams (dependent Jacobi rounds); "
                                                    "a few MB of data, no roofline fraction is meaningful"}
     out["device_status"] = status
     return out
@@ -1382,7 +1385,7 @@ def run_profile_case(case):
     elif case == "dense_ttcp":
         rng = np.random.default_rng(2109)
         x = torch.from_numpy(rng.standard_normal((20, 20, 20)).astype(np.float32)).to(dev)
-        y = torch.from_numpy(rng.standard_normal((20, 20, 20, 5)).astype(np.float32)).to(dev)
+        y = torch.from_numpy(rng.standard_normal((20, 20, 20, 5, 4)).astype(np.float32)).to(dev)
         for _ in range(2):
             T.contract_dense_pairs(x, y, [(0, 0)], 1e-6)
         status = torch.zeros(1, dtype=torch.int32)

@@ -297,8 +297,11 @@ int tt_contract_factored(const tt_desc* x, const tt_desc* y, const uint8_t* mask
  * contiguous with its chosen ranks, [r_k][I_k][r_{k+1}]; the chosen ranks go
  * to ranks_dev[order + 1] (device int32; read them after the stream has
  * reached the call).  A non-finite norm sets TT_STATUS_NONFINITE and writes no
- * core.  One CTA runs the decomposition (latency-bound: meant for tensors of
- * up to a few million entries).  Asynchronous on `stream`; no allocation. */
+ * core.  One cluster launch runs the decomposition (up to 16 CTAs: an SVD
+ * whose vectors and rotations fit one CTA's shared memory runs there, larger
+ * ones are spread over the cluster by columns; latency-bound: meant for
+ * tensors of up to a few million entries).  Asynchronous on `stream`; no
+ * allocation. */
 int tt_svd_workspace(int order, const int32_t* modes, int dtype, int32_t max_rank, int32_t* cap_ranks,
                      size_t* ws_bytes);
 int tt_svd(const void* x_dev, int order, const int32_t* modes, int dtype, double eps, int32_t max_rank,
@@ -307,8 +310,9 @@ int tt_svd(const void* x_dev, int order, const int32_t* modes, int dtype, double
 
 /* TT rounding: the tensor x represents, re-expressed with smaller ranks
  * within eps ||X||_F (the TT-SVD's truncation rule of Section II applied to a
- * TT, e.g. a merged-layout result viewed as a TT of modes I J).  One CTA runs
- * two sweeps of single-core SVDs (one-sided Jacobi, the storage type): right
+ * TT, e.g. a merged-layout result viewed as a TT of modes I J).  One cluster
+ * launch (SVDs as in tt_svd) runs two sweeps of single-core SVDs (one-sided
+ * Jacobi, the storage type): right
  * to left making the cores right-orthonormal (only exactly-zero singular
  * values dropped), then left to right keeping, per core, the smallest rank
  * whose dropped singular values have 2-norm <= eps ||X||_F / sqrt(order - 1),

@@ -584,6 +584,20 @@ def round_merged(cores, eps, max_rank=0, stream=None):
     return [o if c.dim() == 3 else o.view(o.shape[0], c.shape[1], c.shape[2], o.shape[2]) for o, c in zip(out, cores)]
 
 
+_side_streams = {}
+
+
+def _side_stream(device):
+    """A second stream per device for independent work of one call."""
+    import torch
+
+    key = torch.device(device).index
+    if key not in _side_streams:
+        with torch.cuda.device(key):
+            _side_streams[key] = torch.cuda.Stream()
+    return _side_streams[key]
+
+
 def tt_decompose(x, eps, max_rank=0, stream=None):
     """TT cores of the dense CUDA tensor x with ||x - TT||_F <= eps ||x||_F
     (tt_svd; waits for the call to read the ranks)."""
@@ -622,10 +636,24 @@ def contract_dense_pairs(x, y, pairs, eps, prec="native", max_rank=0, stream=Non
     s = len(pairs)
     ax = [a for a, _ in pairs] + [k for k in range(x.dim()) if k not in {a for a, _ in pairs}]
     ay = [b for _, b in pairs] + [k for k in range(y.dim()) if k not in {b for _, b in pairs}]
-    xp = x.contiguous() if ax == list(range(x.dim())) else dense_permute(x.contiguous(), ax, stream=stream)
-    yp = y.contiguous() if ay == list(range(y.dim())) else dense_permute(y.contiguous(), ay, stream=stream)
-    xc = tt_decompose(xp, eps, max_rank, stream)
-    yc = tt_decompose(yp, eps, max_rank, stream)
+    import torch
+
+    cur = torch.cuda.current_stream(x.device) if stream is None else stream
+    xp = x.contiguous() if ax == list(range(x.dim())) else dense_permute(x.contiguous(), ax, stream=cur)
+    yp = y.contiguous() if ay == list(range(y.dim())) else dense_permute(y.contiguous(), ay, stream=cur)
+    # the two decompositions are independent: Y's runs on a second stream,
+    # forked from and joined back into the caller's
+    dx = Decomposition(list(xp.shape), xp.dtype, eps, max_rank, xp.device)
+    dy = Decomposition(list(yp.shape), yp.dtype, eps, max_rank, yp.device)
+    side = _side_stream(x.device)
+    side.wait_stream(cur)
+    dx(xp, cur)
+    dy(yp, side)
+    cur.wait_stream(side)
+    cur.synchronize()  # the chosen ranks size the contraction
+    xc, yc = dx.cores(), dy.cores()
+    if int(dx.status.item()) != 0 or int(dy.status.item()) != 0:
+        raise ValueError("tt_svd: the tensor holds a non-finite value (TT_STATUS_NONFINITE)")
     op = PairsContraction(xc, yc, [(t, t) for t in range(s)], prec)
     op(stream)
     return op.z, op.perm
