@@ -430,11 +430,10 @@ int tt_autotune(int dtype, const char* cache_path);
  *                    cotangent of every output core (device, same shapes as
  *                    the output), cot_dev ignored.
  *   gx, gy           caller-allocated gradient cores, shapes of x and y.
- *   ckpt_stride      left environments are stored every `ckpt_stride` modes
- *                    and recomputed inside each segment during the backward
- *                    sweep (0 = choose ceil(sqrt(N))): ceil(N/c) + c
- *                    environments of workspace for one extra forward sweep;
- *                    1 = store all N and recompute nothing.
+ *   ckpt_stride      >= 0, not otherwise used: every left environment is
+ *                    kept (N of them, and N right environments: the
+ *                    gradients of all modes are formed by one launch after
+ *                    the backward sweep; TT_ERR_ARG when negative).
  * For a full contraction, dz/dGx_k[:,i,:] = L_k Gy_k[:,i,:] F_{k+1}^T and
  * dz/dGy_k[:,i,:] = L_k^T Gx_k[:,i,:] F_{k+1}, where L_k / F_{k+1} are the left
  * / right environments; a chain-layout partial contraction reduces to this with
@@ -451,7 +450,7 @@ int tt_contract_backward(const tt_desc* x, const tt_desc* y, const uint8_t* mask
 /* tt_contract_backward of a chain-layout partial contraction run with
  * tt_contract_partial_k: `ws` is the workspace that call filled (same x, y,
  * mask), so K is not swept again and, for a leading block, the adjoint starts
- * from the stored checkpoints (default checkpoint stride).  Arguments as
+ * from the left environments that call stored.  Arguments as
  * tt_contract_backward (mask required, TT_LAYOUT_CHAIN). */
 int tt_contract_backward_k(const tt_desc* x, const tt_desc* y, const uint8_t* mask, int prec,
                            const tt_desc* dz, const tt_desc* gx, const tt_desc* gy,

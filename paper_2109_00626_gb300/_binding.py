@@ -832,7 +832,9 @@ def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, lay
     chain-layout partial contraction (``dz`` = cotangents of the output cores)
     with respect to every core of x and y.  Returns (gx, gy, status).
     ``fwd_ws``: the workspace :func:`partial_k` filled in the forward pass
-    (tt_contract_backward_k: K and the checkpoints are not computed again)."""
+    (tt_contract_backward_k: K and the left environments are not computed
+    again).  ``ckpt_stride`` is passed through (>= 0; every environment is
+    kept whatever its value)."""
     import torch
 
     xd, yd = Desc(x), Desc(y)
@@ -842,8 +844,6 @@ def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, lay
     dev = x[0].device
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     nb = workspace_bytes(TT_OP_BACKWARD, xd, yd, mask, layout)
-    if ckpt_stride:
-        nb = max(nb, (len(x) + 1 + 4) * _env_bytes(x, y) + 8192)
     ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
     m = _mask_arr(mask) if mask is not None else None
     dzd = Desc(dz) if dz is not None else None
@@ -874,12 +874,6 @@ def backward(x, y, mask=None, cot=None, dz=None, ckpt_stride=0, stream=None, lay
     )
     check(rc, "tt_contract_backward")
     return gx, gy, status
-
-
-def _env_bytes(x, y):
-    rx = max([int(c.shape[0]) for c in x] + [int(c.shape[2]) for c in x])
-    ry = max([int(c.shape[0]) for c in y] + [int(c.shape[2]) for c in y])
-    return rx * ry * x[0].element_size()
 
 
 def _autograd():

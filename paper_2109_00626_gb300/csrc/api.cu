@@ -420,11 +420,11 @@ static int contract_chain(const tt_desc* x, const tt_desc* y, const uint8_t* mas
     p.e_out = bws + bp->off_k;
     p.e_out_log2 = reinterpret_cast<int64_t*>(bws + bp->off_klog2);
     if (cp.side == 0 && cp.s > 0) {
-      const int c = bp->stride_for(cp.s);
+      // every left environment L_0 .. L_{s-1} of the block
       p.ckpt = bws + bp->off_ckpt;
       p.ckpt_log2 = reinterpret_cast<int64_t*>(bws + bp->off_ckpt_log2);
-      p.ckpt_stride = c;
-      p.ckpt_n = (cp.s + c - 1) / c;
+      p.ckpt_stride = 1;
+      p.ckpt_n = cp.s;
       p.ckpt_elems = bp->env_elems;
     }
   }
@@ -476,20 +476,101 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   const int eb = elem_bytes(x->dtype);
   const int n = x->order;
 
-  AdjointParams ap;
-  memset(&ap, 0, sizeof(ap));
-  ap.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
-  ap.status = status_dev;
-  ap.env_elems = bp.env_elems;
-  ap.ckpt = w + bp.off_ckpt;
-  ap.seg = w + bp.off_seg;
-  ap.ckpt_log2 = reinterpret_cast<int64_t*>(w + bp.off_ckpt_log2);
-  ap.seg_log2 = reinterpret_cast<int64_t*>(w + bp.off_seg_log2);
-  auto fill_block = [&](int k0, int k1) {
-    ap.n = k1 - k0;
-    ap.stride = bp.stride_for(ap.n);
-    int mi = 1;
-    for (int j = 0; j < ap.n; ++j) {
+  const int renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+  char* const lenv = w + bp.off_ckpt;
+  int64_t* const lenv_log2 = reinterpret_cast<int64_t*>(w + bp.off_ckpt_log2);
+  char* const fenv = w + bp.off_fenv;
+  int64_t* const fenv_log2 = reinterpret_cast<int64_t*>(w + bp.off_fenv_log2);
+  const int64_t env_bytes = bp.env_elems * eb;
+  // Adjoint of the sweep over modes [k0, k1): L_1..L_{nb-1} by a left-to-right
+  // sweep from the left seed (unless the forward sweep stored them),
+  // F_{nb-1}..F_1 by a right-to-left sweep from the right seed, each storing
+  // the environment before every mode, then the gradients of every slice.
+  // leg-swapped copies of the block's cores [bp.k0, bp.k1) (the copy tasks,
+  // and where each copy lands)
+  const void* swx[kMaxOrder];
+  const void* swy[kMaxOrder];
+  SwapParams sp;
+  memset(&sp, 0, sizeof(sp));
+  {
+    char* q = w + bp.off_swap;
+    for (int k = bp.k0; k < bp.k1; ++k)
+      for (int side = 0; side < 2; ++side) {
+        const tt_desc* d = side == 0 ? x : y;
+        CopyTask& t = sp.copy[sp.n_copies++];
+        t.src = d->cores[k];
+        t.dst = q;
+        t.r0 = d->ranks[k];
+        t.I = d->modes[k];
+        t.r1 = d->ranks[k + 1];
+        t.swap = 1;
+        (side == 0 ? swx : swy)[k - bp.k0] = q;
+        q += swap_core_bytes(d, k);
+      }
+  }
+  bool swapped = false;  // set once the copies are enqueued
+  auto adjoint_block = [&](int k0, int k1, const void* l_seed, const void* f_seed, int seed_parts, const double* cot,
+                           bool l_given) -> int {
+    const int nb = k1 - k0;
+    if (!swapped && launch_swap_copies(sp, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
+    if (nb > 1 && !l_given) {
+      SweepParams lp;
+      memset(&lp, 0, sizeof(lp));
+      fill_left(lp, x, y, k0, k1 - 1);
+      lp.rx0 = x->ranks[k0];
+      lp.ry0 = y->ranks[k0];
+      lp.e_seed = l_seed;
+      lp.e_seed_parts = seed_parts;
+      lp.renorm_bits = renorm_bits;
+      lp.ckpt = lenv;
+      lp.ckpt_log2 = lenv_log2;
+      lp.ckpt_stride = 1;
+      lp.ckpt_n = nb - 1;
+      lp.ckpt_elems = bp.env_elems;
+      lp.e_out = lenv + (nb - 1) * env_bytes;
+      lp.e_out_log2 = lenv_log2 + (nb - 1);
+      lp.status = status_dev;
+      const int r = launch_sweep(lp, x->dtype, s);
+      if (r != TT_OK) return r;
+    }
+    if (nb > 1) {
+      // F_{k+1} lands at slot k - k0 and its scale at slot nb - 1 - (k - k0);
+      // the sweep runs left to right over the leg-swapped cores in reverse
+      // order (E' = sum_i Gx_i E Gy_i^T)
+      SweepParams rp;
+      memset(&rp, 0, sizeof(rp));
+      rp.n_steps = nb - 1;
+      for (int j = 0; j < nb - 1; ++j) {
+        const int k = k1 - 1 - j;
+        SweepStep& st = rp.step[j];
+        st.gx = swx[k - k0];
+        st.gy = swy[k - k0];
+        st.I = x->modes[k];
+        st.rin_x = x->ranks[k + 1];
+        st.rout_x = x->ranks[k];
+        st.rin_y = y->ranks[k + 1];
+        st.rout_y = y->ranks[k];
+      }
+      rp.rx0 = x->ranks[k1];
+      rp.ry0 = y->ranks[k1];
+      rp.e_seed = f_seed;
+      rp.e_seed_parts = seed_parts;
+      rp.renorm_bits = renorm_bits;
+      rp.ckpt = fenv + (nb - 1) * env_bytes;
+      rp.ckpt_log2 = fenv_log2;
+      rp.ckpt_stride = 1;
+      rp.ckpt_n = nb - 1;
+      rp.ckpt_elems = -bp.env_elems;
+      rp.e_out = fenv;
+      rp.e_out_log2 = fenv_log2 + (nb - 1);
+      rp.status = status_dev;
+      const int r = launch_sweep(rp, x->dtype, s);
+      if (r != TT_OK) return r;
+    }
+    AdjointParams ap;
+    memset(&ap, 0, sizeof(ap));
+    ap.n = nb;
+    for (int j = 0; j < nb; ++j) {
       const int k = k0 + j;
       AdjStep& st = ap.step[j];
       st.gx = x->cores[k];
@@ -501,9 +582,20 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
       st.rx2 = x->ranks[k + 1];
       st.ry = y->ranks[k];
       st.ry2 = y->ranks[k + 1];
-      mi = std::max(mi, st.I);
+      st.gxs = swx[j];
+      ap.total_slices += st.I;
     }
-    ap.cluster = pow2_floor(std::min(16, mi));
+    ap.l_seed = l_seed;
+    ap.f_seed = f_seed;
+    ap.seed_parts = seed_parts;
+    ap.cot = cot;
+    ap.lenv = lenv;
+    ap.lenv_log2 = lenv_log2;
+    ap.fenv = fenv;
+    ap.fenv_log2 = fenv_log2;
+    ap.env_elems = bp.env_elems;
+    ap.status = status_dev;
+    return launch_adjoint_grads(ap, x->dtype, bp.rmax, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   };
 
   if (mask == nullptr && bp.r1) {
@@ -528,16 +620,14 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     rp.llog = reinterpret_cast<int64_t*>(w + bp.off_llog);
     rp.flog = reinterpret_cast<int64_t*>(w + bp.off_flog);
     rp.vstride = bp.vstride;
-    rp.renorm_bits = ap.renorm_bits;
+    rp.renorm_bits = renorm_bits;
     rp.cot = cot_dev;
     rp.status = status_dev;
     return launch_adjoint_r1(rp, x->dtype, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   if (mask == nullptr) {
     if (cot_dev == nullptr) return TT_ERR_ARG;
-    fill_block(0, n);
-    ap.cot = cot_dev;
-    return launch_adjoint(ap, x->dtype, bp.rmax, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+    return adjoint_block(0, n, nullptr, nullptr, 1, cot_dev, false);
   }
 
   const ChainPlan& cp = bp.cp;
@@ -559,7 +649,7 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     }
     p.rx0 = 1;
     p.ry0 = 1;
-    p.renorm_bits = ap.renorm_bits;
+    p.renorm_bits = renorm_bits;
     p.e_out = w + bp.off_k;
     p.e_out_log2 = reinterpret_cast<int64_t*>(w + bp.off_klog2);
     p.status = status_dev;
@@ -608,21 +698,18 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
       add(dz->cores[m + q], gy->cores[k], y->ranks[k + 1], y->modes[k], y->ranks[k], 1);
     }
   }
+  if (sS > 0 && cap.n_copies + sp.n_copies <= kMaxCopies) {
+    // the leg-swapped copies ride along with the free-core copies
+    for (int t = 0; t < sp.n_copies; ++t) cap.copy[cap.n_copies++] = sp.copy[t];
+    swapped = true;
+  }
   if (launch_chain_adjoint(cap, x->dtype, s) != cudaSuccess) return TT_ERR_CUDA;
-  (void)eb;
   // 3. adjoint of the sweep over the contracted block, seeded with dK (the
-  //    sum of the chain adjoint's partials)
+  //    sum of the chain adjoint's partials); for a leading block the forward
+  //    pass of tt_contract_partial_k stored the left environments
   if (sS > 0) {
-    ap.seed_parts = cap.dk_parts;
-    if (cp.side == 0) {
-      fill_block(0, sS);
-      ap.f_seed = dkbuf;
-      ap.ckpt_given = from_forward;  // the forward sweep stored the left checkpoints
-    } else {
-      fill_block(m, n);
-      ap.l_seed = dkbuf;
-    }
-    if (launch_adjoint(ap, x->dtype, bp.rmax, s) != cudaSuccess) return TT_ERR_CUDA;
+    if (cp.side == 0) return adjoint_block(0, sS, nullptr, dkbuf, cap.dk_parts, nullptr, from_forward != 0);
+    return adjoint_block(m, n, dkbuf, nullptr, cap.dk_parts, nullptr, false);
   }
   return TT_OK;
 }

@@ -347,12 +347,6 @@ inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
   return TT_OK;
 }
 
-inline int isqrt_ceil(int n) {
-  int c = 1;
-  while (c * c < n) ++c;
-  return c;
-}
-
 // Workspace layout of tt_contract_backward.
 struct BackwardPlan {
   ChainPlan cp;
@@ -361,19 +355,23 @@ struct BackwardPlan {
   size_t off_lvec = 0, off_fvec = 0, off_llog = 0, off_flog = 0;
   int64_t vstride = 1;
   int rmax = 1;
-  int user_stride = 0;
   int64_t env_elems = 1;
-  size_t off_k = 0, off_klog2 = 0, off_dk = 0, off_ckpt = 0, off_seg = 0, off_ckpt_log2 = 0, off_seg_log2 = 0;
+  // Every left environment L_0..L_{N-1} of the block (written by the forward
+  // sweep, or by the adjoint's own forward pass) and every right environment
+  // F_1..F_N (written by the backward walk): the gradients of all modes are
+  // then formed by one launch over every (mode, slice), off the walk's
+  // critical path.  2N environments of R^x R^y elements.
+  size_t off_k = 0, off_klog2 = 0, off_dk = 0, off_ckpt = 0, off_ckpt_log2 = 0, off_fenv = 0, off_fenv_log2 = 0;
+  // leg-swapped copies of the block's cores (X then Y, mode by mode, each
+  // 256-byte aligned): the right-to-left sweep and the gradients read them
+  size_t off_swap = 0;
+  int k0 = 0, k1 = 0;  // the block
   size_t ws_bytes = 0;
-  // Left environments stored every c modes (default ceil(sqrt(N))): the
-  // backward walk recomputes each segment from its checkpoint, so the
-  // workspace holds ceil(N/c) + c environments instead of N.  c = 1 stores
-  // every one and recomputes nothing.
-  int stride_for(int nmodes) const {
-    const int c = user_stride > 0 ? user_stride : isqrt_ceil(nmodes);
-    return std::max(1, std::min(c, nmodes));
-  }
 };
+
+inline size_t swap_core_bytes(const tt_desc* d, int k) {
+  return align256(static_cast<size_t>(d->ranks[k]) * d->modes[k] * d->ranks[k + 1] * elem_bytes(d->dtype));
+}
 
 inline int adjoint_rank_cap(int dtype) { return dtype == TT_F64 ? 32 : 64; }
 
@@ -385,7 +383,6 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   if (x->dtype == TT_BF16) return TT_ERR_UNSUPPORTED;
   if (stride < 0) return TT_ERR_ARG;
   const int n = x->order;
-  bp->user_stride = stride;
   bp->partial = mask != nullptr;
   int nblock = n;
   if (mask != nullptr) {
@@ -419,8 +416,6 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
   if (mask != nullptr && rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
   const int eb = elem_bytes(x->dtype);
   bp->env_elems = static_cast<int64_t>(max_rank(x)) * max_rank(y);
-  const int c = bp->stride_for(nblock);
-  const int nseg = (nblock + c - 1) / c;
   size_t off = 0;
   if (mask != nullptr) {
     bp->off_k = off;
@@ -431,13 +426,25 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     off += align256(static_cast<size_t>(kDkGroups) * bp->cp.kx * bp->cp.ky * eb);  // partial sums of dK
   }
   bp->off_ckpt = off;
-  off += align256(static_cast<size_t>(nseg) * bp->env_elems * eb);
-  bp->off_seg = off;
-  off += align256(static_cast<size_t>(c) * bp->env_elems * eb);
+  off += align256(static_cast<size_t>(nblock) * bp->env_elems * eb);
   bp->off_ckpt_log2 = off;
-  off += align256(sizeof(int64_t) * nseg);
-  bp->off_seg_log2 = off;
-  off += align256(sizeof(int64_t) * c);
+  off += align256(sizeof(int64_t) * nblock);
+  bp->off_fenv = off;
+  off += align256(static_cast<size_t>(nblock) * bp->env_elems * eb);
+  bp->off_fenv_log2 = off;
+  off += align256(sizeof(int64_t) * nblock);
+  if (mask == nullptr) {
+    bp->k0 = 0;
+    bp->k1 = n;
+  } else if (bp->cp.side == 0) {
+    bp->k0 = 0;
+    bp->k1 = bp->cp.s;
+  } else {
+    bp->k0 = bp->cp.m;
+    bp->k1 = n;
+  }
+  bp->off_swap = off;
+  for (int k = bp->k0; k < bp->k1; ++k) off += swap_core_bytes(x, k) + swap_core_bytes(y, k);
   bp->ws_bytes = off;
   return TT_OK;
 }

@@ -342,8 +342,19 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
   int64_t log2s = 0;
   int bad = 0;
 
-  // ---- start environment: [1] (the trains start and end with rank 1) ----
-  if (tid == 0) Es[0] = T(1);
+  // ---- start environment: [1] (the trains start and end with rank 1), or
+  //      a given one (the sum of its parts, added in order) ----
+  if (p.e_seed != nullptr) {
+    const int ry0 = p.ry0;
+    sum_parts<T, NT>(static_cast<const T*>(p.e_seed), p.rx0 * ry0, p.e_seed_parts > 1 ? p.e_seed_parts : 1,
+                     [&](int idx, T e) {
+                       const int u = idx / ry0, v = idx - u * ry0;
+                       Es[v * LD + u] = e;
+                     });
+    if (p.e_seed_log2 != nullptr) log2s = *p.e_seed_log2;
+  } else if (tid == 0) {
+    Es[0] = T(1);
+  }
 
   for (int q = tid; q < p.n_steps; q += NT) sst[q] = p.step[q];
   if constexpr (Cfg::PUSH) {
@@ -681,17 +692,18 @@ __device__ __forceinline__ bool sweep_body(const SweepParams& p, const SweepOut&
 
   };
   for (int j = 0; j < n_pipe; ++j) {
-    if (p.ckpt != nullptr && crank == 0 && j % p.ckpt_stride == 0 && j / p.ckpt_stride < p.ckpt_n) {
+    if (p.ckpt != nullptr && j % p.ckpt_stride == 0 && j / p.ckpt_stride < p.ckpt_n) {
       // checkpoint: the environment before mode j (read before this mode's
-      // products; nothing writes Es until its exchange)
+      // products; nothing writes Es until its exchange).  Every CTA holds
+      // all of E: each stores a 1/C share, so no CTA lags the exchange.
       const int g = j / p.ckpt_stride;
       const int rxk = j == 0 ? p.rx0 : sst[j - 1].rout_x, ryk = j == 0 ? p.ry0 : sst[j - 1].rout_y;
       T* dst = static_cast<T*>(p.ckpt) + g * p.ckpt_elems;
-      for (int idx = tid; idx < rxk * ryk; idx += NT) {
+      for (int idx = crank * NT + tid; idx < rxk * ryk; idx += NT * C) {
         const int u = idx / ryk, v = idx - u * ryk;
         dst[idx] = Es[v * LD + u];
       }
-      if (tid == 0) p.ckpt_log2[g] = log2s;
+      if (tid == 0 && crank == 0) p.ckpt_log2[g] = log2s;
     }
     const SweepStep& sj = sst[j];
     const int need1 = ((sj.rin_x + 3) >> 2) * ((sj.rout_y + 3) >> 2);

@@ -154,4 +154,34 @@ __device__ __forceinline__ int warp_or(int v) {
   return v;
 }
 
+// Elements [0, n) of the sum of `parts` consecutive arrays of n elements
+// (added in order: part 0, then 1, ...), each handed to f(idx, value) by the
+// block's NT threads.  A thread keeps 16 elements' loads of a part in flight,
+// so the sum costs about `parts` memory latencies, not one per element and part.
+template <typename T, int NT, typename F>
+__device__ __forceinline__ void sum_parts(const T* __restrict__ src, int n, int parts, F f) {
+  constexpr int B = 16;
+  for (int base = threadIdx.x; base < n; base += NT * B) {
+    T acc[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int idx = base + u * NT;
+      acc[u] = idx < n ? src[idx] : T(0);
+    }
+    for (int g = 1; g < parts; ++g) {
+      const T* sg = src + static_cast<int64_t>(g) * n;
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int idx = base + u * NT;
+        if (idx < n) acc[u] += sg[idx];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int idx = base + u * NT;
+      if (idx < n) f(idx, acc[u]);
+    }
+  }
+}
+
 }  // namespace ttc

@@ -112,7 +112,12 @@ struct SweepParams {
   void* ckpt;
   int64_t* ckpt_log2;
   int ckpt_stride, ckpt_n;
-  int64_t ckpt_elems;
+  int64_t ckpt_elems;     // may be negative (environments stored in reverse order)
+  // optional start environment instead of [1]: [rx0][ry0] row-major, the sum
+  // of e_seed_parts consecutive such matrices, its scale in *e_seed_log2
+  const void* e_seed;
+  const int64_t* e_seed_log2;
+  int e_seed_parts;
 };
 
 // Full contraction as two half sweeps meeting in the middle (sweep.cu):
@@ -136,27 +141,28 @@ struct AdjStep {
   void* dgx;
   void* dgy;
   int I, rx, rx2, ry, ry2;
+  const void* gxs;  // optional leg-swapped copy of gx, [rx2][I][rx]
 };
 
+// Gradients of an adjoint block from its stored environments (adjoint.cu):
+// L_k for k >= 1 at lenv + k env_elems (scale lenv_log2[k]), F_{k+1} for
+// k <= n - 2 at fenv + k env_elems (scale fenv_log2[n - 1 - k], the order a
+// right-to-left sweep writes them in); L_0 and F_n are the seeds.
 struct AdjointParams {
   int n;                 // modes in the block
-  int stride;            // checkpoint stride c
-  int cluster;           // requested cluster size
-  int renorm_bits;
-  int need_f0;           // 1 = also reduce the right environment left of the block
   AdjStep step[kMaxOrder];
-  const void* l_seed;    // optional left seed [rx(0)][ry(0)] (NULL = [1])
+  const void* l_seed;    // L_0 [rx(0)][ry(0)] (NULL = [1])
   const int64_t* l_seed_log2;
-  int ckpt_given;        // 1: the checkpoints are already in ckpt / ckpt_log2 (written by the forward sweep)
-  const void* f_seed;    // optional right seed [rx2(n-1)][ry2(n-1)] (NULL = [1])
+  const void* f_seed;    // F_n [rx2(n-1)][ry2(n-1)] (NULL = [1])
   const int64_t* f_seed_log2;
   int seed_parts;        // a seed is the sum of this many consecutive matrices (0 or 1 = one)
   const double* cot;     // optional scalar multiplier (device)
-  void* ckpt;            // ceil(n/c) environments
-  int64_t* ckpt_log2;
-  void* seg;             // c environments
-  int64_t* seg_log2;
+  const void* lenv;
+  const int64_t* lenv_log2;
+  const void* fenv;
+  const int64_t* fenv_log2;
   int64_t env_elems;     // elements per stored environment
+  int total_slices;      // sum of step[k].I (blocks of the launch)
   int32_t* status;
 };
 
@@ -302,7 +308,16 @@ cudaError_t launch_kron0(const KronParams& p, int which, int dtype, cudaStream_t
 cudaError_t launch_transfer(const TransferParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_scaled_gemm(const ScaledGemmParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_zrows(const ZRowsParams& p, bool prod, int dtype, cudaStream_t s);
-cudaError_t launch_adjoint(const AdjointParams& p, int dtype, int rmax, cudaStream_t s);
+cudaError_t launch_adjoint_grads(const AdjointParams& p, int dtype, int rmax, cudaStream_t s);
+
+// Leg-swapped copies of whole cores (dst[r1][I][r0] = src[r0][I][r1]) as copy
+// jobs (copy_jobs.cuh): lets a right-to-left environment sweep read its
+// slices as a left-to-right one does, 16 bytes a copy.
+struct SwapParams {
+  int n_copies, n_jobs;
+  CopyTask copy[kMaxCopies];
+};
+cudaError_t launch_swap_copies(const SwapParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_chain_adjoint(const ChainAdjParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepParams& p, int rmax, int cluster, cudaStream_t s);
