@@ -1,31 +1,30 @@
 // Adjoint of a full contraction whose second operand has every rank 1.  The
 // sum of a TT's entries is its contraction with the all-ones rank-1 TT -- the
 // usual way a partial contraction is reduced to a loss -- and with one operand
-// of rank 1 the environments are vectors (y_k[i] = Gy_k[0][i][0]):
-//   L_0 = 1,  L_{k+1}[a'] = sum_{a,i} L_k[a] y_k[i] Gx_k[a][i][a']
-//   F_N = 1,  F_k[a]      = sum_{i,a'} Gx_k[a][i][a'] y_k[i] F_{k+1}[a']
-// and, z being linear in each core (Eq. 9), the gradients are
+// of rank 1 the environments are vectors (y_k[i] = Gy_k[0][i][0]).  With the
+// folded cores M_k = sum_i y_k[i] Gx_k[:, i, :] (rx x rx2 matrices),
+//   L_0 = 1,  L_{k+1} = L_k M_k          (row vectors)
+//   F_N = 1,  F_k     = M_k F_{k+1}      (column vectors)
+// z = L_N = F_0, and, z being linear in each core (Eq. 9), the gradients are
 //   dGx_k[a][i][a'] = g L_k[a] y_k[i] F_{k+1}[a']
 //   dGy_k[0][i][0]  = g sum_{a,a'} L_k[a] Gx_k[a][i][a'] F_{k+1}[a'].
-// One launch sweeps L and F at the same time (a cluster each), each mode a
-// matrix-vector product over one core read once, and keeps every vector with
-// a power-of-two scale (no checkpoints: the vectors are small); a second
-// launch writes the gradients, one block per (k, i).
-#include <cooperative_groups.h>
-
+// Three launches: the fold of every core at once (the cores are read once,
+// by every SM), the two chains of vector-matrix products (one block each,
+// on the folded cores, which sit in L2), and the gradients, one block per
+// (k, i).  Every vector is kept with a power-of-two scale (no checkpoints:
+// the vectors are small).  The forward value alone takes the fold and the
+// left chain.
 #include "ttc_device.cuh"
 #include "ttc_internal.h"
-
-namespace cg = cooperative_groups;
 
 namespace ttc {
 
 namespace {
 
 constexpr int kR1Threads = 512;
-constexpr int kR1Cluster = 8;  // CTAs per sweep direction
 constexpr int kR1Warps = kR1Threads / 32;
 constexpr int kNoExpR1 = -(1 << 30);
+constexpr int kFoldThreads = 256;
 
 // Block-wide max of an exponent and OR of a flag (every thread gets both).
 // One barrier: callers alternate `red` between two buffers, so the previous
@@ -47,154 +46,183 @@ __device__ __forceinline__ void block_max_or_r1(int& e, int& bad, int* red) {
   }
 }
 
-// Cluster of kR1Cluster CTAs per direction (blocks [0, C): L, [C, 2C): F).
-// Per mode each CTA forms part of the next vector from its share of the core
-// (L: a share of the rows (a, i), summed into partial columns; F: a share of
-// the rows a, each a full dot product), a cluster barrier makes the parts
-// visible, and every CTA gathers the whole vector from its peers (in rank
-// order: the same sum everywhere), so all CTAs take the same rescaling
-// decision.  The parts alternate between two buffers by mode parity, so one
-// barrier per mode suffices: a peer reads parts of mode k before it reaches
-// the barrier of mode k + 1, and they are overwritten in mode k + 2.
+// M_k[a][c] = sum_i y_k[i] Gx_k[a][i][c] (i in order); with mtbuf set also
+// M_k^T[c][a].  A block takes fold_rows(k) = max(1, 256 / rx2) rows of one
+// core, a thread per (row, column), so narrow cores keep every lane busy.
+__host__ __device__ inline int fold_rows(int rx2) { return rx2 >= kFoldThreads ? 1 : kFoldThreads / rx2; }
+
 template <typename T>
-__global__ void __launch_bounds__(kR1Threads) r1_sweep_kernel(const __grid_constant__ AdjR1Params p) {
+__global__ void __launch_bounds__(kFoldThreads) r1_fold_kernel(const __grid_constant__ AdjR1Params p) {
+  int k = 0, b = static_cast<int>(blockIdx.x);
+  while (k + 1 < p.n) {
+    const int nb = (p.step[k].rx + fold_rows(p.step[k].rx2) - 1) / fold_rows(p.step[k].rx2);
+    if (b < nb) break;
+    b -= nb;
+    ++k;
+  }
+  const AdjStep& st = p.step[k];
+  const int I = st.I, R = st.rx, R2 = st.rx2, fr = fold_rows(R2);
+  const T* y = static_cast<const T*>(st.gy);
+  T* m = static_cast<T*>(p.mbuf) + p.moff[k];
+  T* mt = p.mtbuf != nullptr ? static_cast<T*>(p.mtbuf) + p.moff[k] : nullptr;
+  const int q = static_cast<int>(threadIdx.x) / (fr > 1 ? R2 : kFoldThreads);  // row of this block
+  const int a = b * fr + q;
+  if (q >= fr || a >= R) return;
+  const T* gx = static_cast<const T*>(st.gx) + static_cast<int64_t>(a) * I * R2;
+  for (int c = fr > 1 ? static_cast<int>(threadIdx.x) % R2 : static_cast<int>(threadIdx.x); c < R2;
+       c += fr > 1 ? R2 : kFoldThreads) {
+    T acc = T(0);
+#pragma unroll 4
+    for (int i = 0; i < I; ++i) acc = fma(ldg(y + i), ldg(gx + static_cast<int64_t>(i) * R2 + c), acc);
+    m[static_cast<int64_t>(a) * R2 + c] = acc;
+    if (mt != nullptr) mt[static_cast<int64_t>(c) * R + a] = acc;
+  }
+}
+
+// The chains: block 0 forms L_1..L_N (out = in M_k: A = M_k, [R][R2]),
+// block 1 F_{N-1}..F_0 (out = M_k in: A = M_k^T, [R2][R]).  Each output
+// entry is summed by G threads over strided rows of A (rows g, g + G, ...;
+// neighbouring threads take neighbouring entries, so the loads of A are
+// coalesced), then its G parts are added in order.
+template <typename T>
+__global__ void __launch_bounds__(kR1Threads) r1_chain_kernel(const __grid_constant__ AdjR1Params p) {
   extern __shared__ __align__(16) unsigned char r1_smem[];
   T* cur = reinterpret_cast<T*>(r1_smem);  // [kR1MaxRank] the current vector
   T* nxt = cur + kR1MaxRank;                // [kR1MaxRank] the next vector
-  T* parts = nxt + kR1MaxRank;              // [2][kR1MaxRank] this CTA's part, by mode parity
-  T* tmp = parts + 2 * kR1MaxRank;          // [16 / sizeof(T)][kR1Threads] per-thread partial columns
-  __shared__ int red[2][2 * kR1Warps];  // block reductions, alternating by mode parity
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = static_cast<int>(cluster.num_blocks());
-  const int crank = static_cast<int>(cluster.block_rank());
-  const bool left = blockIdx.x < static_cast<unsigned>(C);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  T* part = nxt + kR1MaxRank;               // [kR1Threads] partial sums
+  __shared__ int red[2][2 * kR1Warps];
+  __shared__ double zr[kR1Warps];
+  const bool left = blockIdx.x == 0;
+  const int tid = threadIdx.x;
   const int n = p.n;
   int bad = 0;
   T* vecs = static_cast<T*>(left ? p.lvec : p.fvec);
   int64_t* scl = left ? p.llog : p.flog;
   int64_t lg = 0;
   if (tid == 0) cur[0] = T(1);
-  if (crank == 0 && tid == 0) {
+  if (!p.fwd && tid == 0) {
     vecs[static_cast<int64_t>(left ? 0 : n) * p.vstride] = T(1);
     scl[left ? 0 : n] = 0;
   }
   __syncthreads();
-  for (int step = 0; step < n; ++step) {
+  const int steps = p.fwd ? n - 1 : n;  // the forward value's last step is summed in float64
+  // A step whose matrix has <= kR1Threads columns and <= kPre rows per thread
+  // has its loads issued during the step before (registers `pre`), so the
+  // chain waits on no memory latency but the first
+  constexpr int kPre = 16;
+  auto geo = [&](int step, const T*& A, int& rows, int& cols) {
     const int k = left ? step : n - 1 - step;
     const AdjStep& st = p.step[k];
-    const T* gx = static_cast<const T*>(st.gx);
-    const T* y = static_cast<const T*>(st.gy);
-    const int R = st.rx, I = st.I, R2 = st.rx2;
-    T* part = parts + (step & 1) * kR1MaxRank;
-    int nout;  // length of the next vector
-    if (left) {
-      // L_{k+1}[a'] = sum over rows r = (a, i) of L_k[a] y_k[i] Gx_k[r][a'], rows
-      // [r0, r1) here; 16-byte loads along a row when it allows
-      nout = R2;
-      const int rows = R * I, r0 = static_cast<int>(static_cast<int64_t>(rows) * crank / C),
-                r1 = static_cast<int>(static_cast<int64_t>(rows) * (crank + 1) / C);
-      constexpr int VW = 16 / static_cast<int>(sizeof(T));
-      const bool vec = R2 % VW == 0 && (reinterpret_cast<uintptr_t>(gx) & 15) == 0;
-      const int w = vec ? VW : 1;
-      for (int c0 = 0; c0 < R2; c0 += kR1Threads * w) {
-        if (c0 > 0) __syncthreads();  // the previous pass has read tmp
-        const int nc = min(kR1Threads, (R2 - c0 + w - 1) / w);  // column units of this pass
-        const int G = max(1, kR1Threads / nc);                   // row groups
-        const int col = tid % nc, grp = tid / nc;
-        T acc[VW];
+    rows = left ? st.rx : st.rx2;
+    cols = left ? st.rx2 : st.rx;
+    A = static_cast<const T*>(left ? p.mbuf : p.mtbuf) + p.moff[k];
+    return cols <= kR1Threads && (rows + kR1Threads / cols - 1) / (kR1Threads / cols) <= kPre;
+  };
+  auto prefetch = [&](const T* A, int rows, int cols, T (&pre)[kPre]) {
+    const int G = kR1Threads / cols, c = tid % cols, g = tid / cols;
 #pragma unroll
-        for (int q = 0; q < VW; ++q) acc[q] = T(0);
-        if (grp < G) {
-          int a = (r0 + grp) / I, i = (r0 + grp) - ((r0 + grp) / I) * I;
-          const int da = G / I, di = G - da * I;
-#pragma unroll 4
-          for (int r = r0 + grp; r < r1; r += G) {
-            const T wgt = cur[a] * ldg(y + i);
-            const T* src = gx + static_cast<int64_t>(r) * R2 + c0 + col * w;
-            if (vec) {
-              T v[VW];
-              ld_vec<T, VW>(v, src);
-#pragma unroll
-              for (int q = 0; q < VW; ++q) acc[q] = fma(wgt, v[q], acc[q]);
-            } else {
-              acc[0] = fma(wgt, ldg(src), acc[0]);
-            }
-            a += da;
-            i += di;
-            if (i >= I) {
-              i -= I;
-              ++a;
-            }
-          }
-        }
-        for (int q = 0; q < w; ++q) tmp[q * kR1Threads + tid] = acc[q];
-        __syncthreads();
-        for (int u = tid; u < nc * w; u += kR1Threads) {  // column unit u / w, lane u % w
-          const int cu = u / w, q = u - cu * w;
-          if (c0 + cu * w + q < R2) {
-            T sum = T(0);
-            for (int g = 0; g < G; ++g) sum += tmp[q * kR1Threads + g * nc + cu];
-            part[c0 + cu * w + q] = sum;
-          }
-        }
-      }
-    } else {
-      // F_k[a] = sum_{i,a'} Gx_k[a][i][a'] y_k[i] F_{k+1}[a'] for rows a in [a0, a1)
-      nout = R;
-      const int a0 = R * crank / C, a1 = R * (crank + 1) / C;
-      for (int a = a0 + warp; a < a1; a += kR1Warps) {
-        const T* row = gx + static_cast<int64_t>(a) * I * R2;
-        T acc = T(0);
-#pragma unroll 4
-        for (int i = 0; i < I; ++i) {
-          const T yi = ldg(y + i);
-          for (int c = lane; c < R2; c += 32) acc = fma(ldg(row + static_cast<int64_t>(i) * R2 + c) * yi, cur[c], acc);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) part[a] = acc;
-      }
+    for (int j = 0; j < kPre; ++j) {
+      const int r = g + j * G;
+      pre[j] = (g < G && r < rows) ? ldg(A + static_cast<int64_t>(r) * cols + c) : T(0);
     }
-    cluster.sync();  // every CTA's part of this mode is visible (and this CTA's threads are in step)
-    // gather the whole vector (each thread keeps its own entries in nxt) and
-    // its largest binary exponent
+  };
+  T pre[kPre];
+  {
+    const T* A0;
+    int r0, c0;
+    if (steps > 0 && geo(0, A0, r0, c0)) prefetch(A0, r0, c0, pre);
+  }
+  for (int step = 0; step < steps; ++step) {
+    const int k = left ? step : n - 1 - step;
+    const T* A;
+    int rows, cols;
+    const bool fast = geo(step, A, rows, cols);
     int e = kNoExpR1, lbad = 0;
-    if (left) {
-      for (int c = tid; c < nout; c += kR1Threads) {
+    for (int c0 = 0; c0 < cols; c0 += kR1Threads) {
+      const int nc = min(kR1Threads, cols - c0);
+      const int G = max(1, kR1Threads / nc);
+      const int c = tid % nc, g = tid / nc;
+      T acc = T(0);
+      if (fast) {
+#pragma unroll
+        for (int j = 0; j < kPre; ++j) {
+          const int r = g + j * G;
+          if (g < G && r < rows) acc = fma(cur[r], pre[j], acc);
+        }
+        const T* An;
+        int rn, cn;
+        if (step + 1 < steps && geo(step + 1, An, rn, cn)) prefetch(An, rn, cn, pre);
+      } else if (g < G) {
+#pragma unroll 8
+        for (int r = g; r < rows; r += G) acc = fma(cur[r], ldg(A + static_cast<int64_t>(r) * cols + c0 + c), acc);
+      }
+      __syncthreads();  // the previous pass has read `part`
+      part[tid] = acc;
+      __syncthreads();
+      if (tid < nc) {
         T sum = T(0);
-        for (int r = 0; r < C; ++r) sum += *cluster.map_shared_rank(part + c, r);
-        nxt[c] = sum;
+        for (int q = 0; q < G; ++q) sum += part[q * nc + tid];
         if (!isfinite(sum)) lbad = 1;
         else if (sum != T(0)) e = max(e, exp2_bits(sum));
-      }
-    } else {
-      for (int a = tid; a < nout; a += kR1Threads) {
-        // rows [R r / C, R (r + 1) / C) belong to rank r
-        int o = min(C - 1, static_cast<int>((static_cast<int64_t>(a) * C + C - 1) / R));
-        while (o > 0 && a < R * o / C) --o;
-        while (o + 1 < C && a >= R * (o + 1) / C) ++o;
-        const T v = *cluster.map_shared_rank(part + a, o);
-        nxt[a] = v;
-        if (!isfinite(v)) lbad = 1;
-        else if (v != T(0)) e = max(e, exp2_bits(v));
+        nxt[c0 + tid] = sum;
       }
     }
-    block_max_or_r1(e, lbad, red[step & 1]);
+    block_max_or_r1(e, lbad, red[step & 1]);  // also: every thread is past its reads of cur
     if (lbad) bad = 1;
     const int sh = (e != kNoExpR1 && (e > p.renorm_bits || e < -p.renorm_bits)) ? e : 0;
     lg += sh;
     const int64_t vk = left ? k + 1 : k;
-    for (int a = tid; a < nout; a += kR1Threads) {  // the same entries this thread gathered
-      const T v = sh ? mul_pow2<T>(nxt[a], -sh) : nxt[a];
-      cur[a] = v;
-      if (crank == 0) vecs[vk * p.vstride + a] = v;
+    for (int c = tid; c < cols; c += kR1Threads) {
+      const T v = sh ? mul_pow2<T>(nxt[c], -sh) : nxt[c];
+      cur[c] = v;
+      if (!p.fwd) vecs[vk * p.vstride + c] = v;
     }
-    if (crank == 0 && tid == 0) scl[vk] = lg;
-    __syncthreads();  // cur is complete before the next mode reads it
+    if (!p.fwd && tid == 0) scl[vk] = lg;
+    if (!fast && step + 1 < steps) {  // a fast step after a slow one: its loads now
+      const T* An;
+      int rn, cn;
+      if (geo(step + 1, An, rn, cn)) prefetch(An, rn, cn, pre);
+    }
+    __syncthreads();  // cur is complete before the next step reads it
   }
-  if (bad && tid == 0 && crank == 0) set_status(p.status, TT_STATUS_NONFINITE);
-  cluster.sync();  // peers' parts stay readable until everyone is done
+  if (p.fwd && left) {
+    // z = L_{N-1} M_{N-1} (a 1 x 1 result), summed in float64
+    const AdjStep& st = p.step[n - 1];
+    const T* A = static_cast<const T*>(p.mbuf) + p.moff[n - 1];
+    double s = 0.0;
+    for (int r = tid; r < st.rx; r += kR1Threads) s = fma(static_cast<double>(cur[r]), static_cast<double>(A[r]), s);
+    s = warp_sum(s);
+    if ((tid & 31) == 0) zr[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double z = 0.0;
+      for (int w = 0; w < kR1Warps; ++w) z += zr[w];
+      int st_bits = (isfinite(z) && !bad) ? 0 : TT_STATUS_NONFINITE;
+      if (p.z_out_log2 != nullptr) {
+        *p.z_out = z;
+        *p.z_out_log2 = lg;
+      } else {
+        // the scale folded in: infinity (and TT_STATUS_OVERFLOW) beyond the
+        // float64 range, zero below it
+        double v = z;
+        if (z != 0.0 && isfinite(z)) {
+          const int64_t tot = static_cast<int64_t>(exp2_of(z)) + lg;
+          if (tot > 1024) {
+            v = z > 0 ? INFINITY : -INFINITY;
+            st_bits |= TT_STATUS_OVERFLOW;
+          } else if (tot < -1074) {
+            v = 0.0;
+          } else {
+            v = ldexp(z, static_cast<int>(lg));
+          }
+        }
+        *p.z_out = v;
+      }
+      if (st_bits) set_status(p.status, st_bits);
+    }
+    return;
+  }
+  if (bad && tid == 0) set_status(p.status, TT_STATUS_NONFINITE);
 }
 
 // One block per (i, k): dGx_k[:, i, :] and dGy_k[0][i][0].
@@ -254,38 +282,48 @@ __global__ void __launch_bounds__(256) r1_grad_kernel(const __grid_constant__ Ad
 
 }  // namespace
 
+static cudaError_t r1_fold(const AdjR1Params& p, int dtype, cudaStream_t s) {
+  int blocks = 0;
+  for (int k = 0; k < p.n; ++k) blocks += (p.step[k].rx + fold_rows(p.step[k].rx2) - 1) / fold_rows(p.step[k].rx2);
+  count_launch();
+  if (dtype == TT_F64) r1_fold_kernel<double><<<blocks, kFoldThreads, 0, s>>>(p);
+  else r1_fold_kernel<float><<<blocks, kFoldThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+static cudaError_t r1_chains(const AdjR1Params& p, int dtype, int nblocks, cudaStream_t s) {
+  const size_t esz = dtype == TT_F64 ? 8 : 4;
+  const size_t smem = (2 * static_cast<size_t>(kR1MaxRank) + kR1Threads) * esz;
+  const void* k = dtype == TT_F64 ? reinterpret_cast<const void*>(r1_chain_kernel<double>)
+                                  : reinterpret_cast<const void*>(r1_chain_kernel<float>);
+  const cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  count_launch();
+  if (dtype == TT_F64) r1_chain_kernel<double><<<nblocks, kR1Threads, smem, s>>>(p);
+  else r1_chain_kernel<float><<<nblocks, kR1Threads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_r1(const AdjR1Params& p, int dtype, cudaStream_t s) {
+  if (p.mbuf == nullptr || p.mtbuf == nullptr) return cudaErrorInvalidValue;
+  cudaError_t err = r1_fold(p, dtype, s);
+  if (err == cudaSuccess) err = r1_chains(p, dtype, 2, s);
+  if (err != cudaSuccess) return err;
   int imax = 1;
   for (int k = 0; k < p.n; ++k) imax = std::max(imax, p.step[k].I);
-  const size_t esz = dtype == TT_F64 ? 8 : 4;
-  const size_t smem = (4 * static_cast<size_t>(kR1MaxRank) + (16 / esz) * kR1Threads) * esz;
-  const void* sweep = dtype == TT_F64 ? reinterpret_cast<const void*>(r1_sweep_kernel<double>)
-                                      : reinterpret_cast<const void*>(r1_sweep_kernel<float>);
-  cudaError_t err = cudaFuncSetAttribute(sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (err != cudaSuccess) return err;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * kR1Cluster);
-  cfg.blockDim = dim3(kR1Threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kR1Cluster;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  count_launch(2);
-  if (dtype == TT_F64) {
-    err = cudaLaunchKernelEx(&cfg, r1_sweep_kernel<double>, p);
-    if (err != cudaSuccess) return err;
-    r1_grad_kernel<double><<<dim3(imax, p.n), 256, 0, s>>>(p);
-  } else {
-    err = cudaLaunchKernelEx(&cfg, r1_sweep_kernel<float>, p);
-    if (err != cudaSuccess) return err;
-    r1_grad_kernel<float><<<dim3(imax, p.n), 256, 0, s>>>(p);
-  }
+  count_launch();
+  if (dtype == TT_F64) r1_grad_kernel<double><<<dim3(imax, p.n), 256, 0, s>>>(p);
+  else r1_grad_kernel<float><<<dim3(imax, p.n), 256, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_full_r1(const AdjR1Params& p, int dtype, cudaStream_t s) {
+  if (p.mbuf == nullptr || p.z_out == nullptr || !p.fwd) return cudaErrorInvalidValue;
+  AdjR1Params q = p;
+  q.mtbuf = nullptr;  // the left chain alone: no transposes
+  cudaError_t err = r1_fold(q, dtype, s);
+  if (err == cudaSuccess) err = r1_chains(q, dtype, 1, s);
+  return err;
 }
 
 }  // namespace ttc

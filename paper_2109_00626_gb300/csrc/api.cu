@@ -276,6 +276,7 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
     }
     if (prec != TT_P_NATIVE && prec != TT_P_TF32X3 && prec != TT_P_TF32) return TT_ERR_UNSUPPORTED;
     if (x->order >= 2) *bytes = two_sided_layout(x, y).bytes;  // both-ends sweep
+    if (prec == TT_P_NATIVE && full_is_r1(x, y)) *bytes = std::max(*bytes, full_r1_bytes(x));
     return TT_OK;
   }
   if (op == TT_OP_PARTIAL) {
@@ -337,6 +338,30 @@ int tt_contract_full(const tt_desc* x, const tt_desc* y, int prec, double* out_d
       }
     }
     return launch_tf32_sweep(p, x3, C, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
+  if (full_is_r1(x, y) && ws != nullptr && ws_bytes >= full_r1_bytes(x)) {
+    // Y of rank 1: fold X's cores with y, then one chain of vector-matrix products
+    AdjR1Params rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.n = x->order;
+    for (int k = 0; k < x->order; ++k) {
+      AdjStep& st = rp.step[k];
+      st.gx = x->cores[k];
+      st.gy = y->cores[k];
+      st.I = x->modes[k];
+      st.rx = x->ranks[k];
+      st.rx2 = x->ranks[k + 1];
+      st.ry = 1;
+      st.ry2 = 1;
+    }
+    r1_fold_layout(x, rp.moff);
+    rp.mbuf = ws;
+    rp.renorm_bits = x->dtype == TT_F64 ? kRenormBitsF64 : kRenormBitsF32;
+    rp.fwd = 1;
+    rp.z_out = out_dev;
+    rp.z_out_log2 = out_log2_dev;
+    rp.status = status_dev;
+    return launch_full_r1(rp, x->dtype, s) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   if (rmax > rank_cap(x->dtype)) return TT_ERR_TOO_LARGE;
   if (x->order >= 2 && ws != nullptr) {
@@ -620,6 +645,9 @@ static int backward_impl(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     rp.llog = reinterpret_cast<int64_t*>(w + bp.off_llog);
     rp.flog = reinterpret_cast<int64_t*>(w + bp.off_flog);
     rp.vstride = bp.vstride;
+    rp.mbuf = w + bp.off_m;
+    rp.mtbuf = w + bp.off_mt;
+    r1_fold_layout(x, rp.moff);
     rp.renorm_bits = renorm_bits;
     rp.cot = cot_dev;
     rp.status = status_dev;

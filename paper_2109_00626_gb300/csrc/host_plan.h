@@ -348,11 +348,31 @@ inline int check_same_shape(const tt_desc* a, const tt_desc* g) {
 }
 
 // Workspace layout of tt_contract_backward.
+// Where the folded cores of a rank-1 contraction go (adjoint_r1.cu): M_k at
+// element offset moff[k], 16-byte aligned; returns the total elements.
+inline int64_t r1_fold_layout(const tt_desc* x, int64_t* moff) {
+  int64_t off = 0;
+  for (int k = 0; k < x->order; ++k) {
+    if (moff != nullptr) moff[k] = off;
+    off += (static_cast<int64_t>(x->ranks[k]) * x->ranks[k + 1] + 3) & ~static_cast<int64_t>(3);
+  }
+  return off;
+}
+
+// The full contraction of a Y of rank 1 (the sum of a TT's entries and the
+// like) folds X's cores with y and runs one chain of vector-matrix products.
+inline bool full_is_r1(const tt_desc* x, const tt_desc* y) {
+  return max_rank(y) == 1 && max_rank(x) <= kR1MaxRank && x->dtype != TT_BF16;
+}
+inline size_t full_r1_bytes(const tt_desc* x) {
+  return align256(static_cast<size_t>(r1_fold_layout(x, nullptr)) * elem_bytes(x->dtype));
+}
+
 struct BackwardPlan {
   ChainPlan cp;
   int partial = 0;
   int r1 = 0;  // full contraction with Y of rank 1 everywhere: vector adjoint (adjoint_r1.cu)
-  size_t off_lvec = 0, off_fvec = 0, off_llog = 0, off_flog = 0;
+  size_t off_lvec = 0, off_fvec = 0, off_llog = 0, off_flog = 0, off_m = 0, off_mt = 0;
   int64_t vstride = 1;
   int rmax = 1;
   int64_t env_elems = 1;
@@ -409,6 +429,11 @@ inline int backward_plan(const tt_desc* x, const tt_desc* y, const uint8_t* mask
     off1 += align256(sizeof(int64_t) * (n + 1));
     bp->off_flog = off1;
     off1 += align256(sizeof(int64_t) * (n + 1));
+    const size_t mbytes = align256(static_cast<size_t>(r1_fold_layout(x, nullptr)) * eb1);
+    bp->off_m = off1;
+    off1 += mbytes;
+    bp->off_mt = off1;
+    off1 += mbytes;
     bp->ws_bytes = off1;
     return TT_OK;
   }

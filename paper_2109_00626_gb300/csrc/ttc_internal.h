@@ -180,8 +180,19 @@ struct AdjR1Params {
   int renorm_bits;
   const double* cot;         // scalar multiplier (device; NULL = 1)
   int32_t* status;
+  // the folded cores M_k = sum_i y_k[i] Gx_k[:, i, :] ([rx][rx2] at
+  // mbuf + moff[k]) and their transposes (at mtbuf + moff[k]; the adjoint only)
+  void* mbuf;
+  void* mtbuf;
+  int64_t moff[kMaxOrder];
+  // forward only: z = L_n, written as a float64 value (and exponent)
+  int fwd;
+  double* z_out;
+  int64_t* z_out_log2;       // optional; if NULL the scale is folded into *z_out
 };
 cudaError_t launch_adjoint_r1(const AdjR1Params& p, int dtype, cudaStream_t s);
+// <X, Y> for a Y of rank 1: fold, then one chain of vector-matrix products.
+cudaError_t launch_full_r1(const AdjR1Params& p, int dtype, cudaStream_t s);
 
 // Most slice groups dK is split into (each group's partial sum is written
 // separately and the adjoint adds them as it loads its seed).
