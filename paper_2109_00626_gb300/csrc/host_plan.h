@@ -360,9 +360,10 @@ inline int64_t r1_fold_layout(const tt_desc* x, int64_t* moff) {
 }
 
 // The full contraction of a Y of rank 1 (the sum of a TT's entries and the
-// like) folds X's cores with y and runs one chain of vector-matrix products.
+// like; order >= 2) folds X's cores with y and runs one chain of
+// vector-matrix products.
 inline bool full_is_r1(const tt_desc* x, const tt_desc* y) {
-  return max_rank(y) == 1 && max_rank(x) <= kR1MaxRank && x->dtype != TT_BF16;
+  return x->order >= 2 && max_rank(y) == 1 && max_rank(x) <= kR1MaxRank && x->dtype != TT_BF16;
 }
 inline size_t full_r1_bytes(const tt_desc* x) {
   return align256(static_cast<size_t>(r1_fold_layout(x, nullptr)) * elem_bytes(x->dtype));

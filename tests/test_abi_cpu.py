@@ -502,6 +502,10 @@ def test_workspace_queries_and_their_limits(L):
     assert rc == 0 and nb > 0                        # the two-sided sweep's meeting environments
     one = FakeDesc([5], [1, 1])
     assert _ws(L, B.TT_OP_FULL, one, one) == (0, 0)  # order 1: one sweep, nothing to meet
+    # a Y of rank 1 (the sum of x's entries): room for x's cores folded with y
+    ones = FakeDesc([16] * 10, [1] * 11)
+    rc, nb = _ws(L, B.TT_OP_FULL, x, ones)
+    assert rc == 0 and nb >= 4 * (64 + 8 * 64 * 64 + 64)
     assert _ws(L, B.TT_OP_PARTIAL, x, x, [1] * 6 + [0] * 4) == (0, 0)  # chain: K stays on chip
     # tensor-core forms: bfloat16 storage, or float32 storage with bf16 / bf16x3 products
     xb = FakeDesc([32] * 4, [1, 256, 128, 256, 1], dtype=B.TT_BF16)
