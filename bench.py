@@ -1003,15 +1003,20 @@ def bench_factored(T, dev, args):
     }
 
 
+RS_STREAMS = 8  # streams the random-set batch's independent calls are dealt over
+
+
 def bench_random_sets(T, dev, args, n_pairs=512):
     """The batch's secondary run over truly random contracted sets: 512 pairs
     of order U{4..12}, modes U{2..32}, ranks U{4..16}, float32, S = a random
     set of floor(N/2) modes at any positions, factored output (the merged
     layout's Kronecker factors; the merged cores themselves would reach
-    256 x 32 x 32 x 256 entries).  One contraction call per pair, all issued on
-    one stream between two CUDA events (not one persistent launch: each call
-    is its own few launches); beside it the float64 oracle on a sample of
-    pairs on one host thread."""
+    256 x 32 x 32 x 256 entries).  One contraction call per pair (each call
+    its own few launches, none using more than one cluster), dealt round-robin
+    over RS_STREAMS streams forked from and joined back into the timing
+    stream between two CUDA events, so independent pairs share the GPU; also
+    the same calls captured once in a CUDA graph and replayed; beside it the
+    float64 oracle on a sample of pairs on one host thread."""
     import time as _time
 
     import torch
@@ -1025,19 +1030,54 @@ def bench_random_sets(T, dev, args, n_pairs=512):
         yd = [torch.from_numpy(c).to(dev) for c in y]
         ops.append(T.FactoredContraction(xd, yd, mask))
     stream = torch.cuda.current_stream(dev)
-    for op in ops:
-        op(stream)
+    lanes = [torch.cuda.Stream(dev) for _ in range(RS_STREAMS)]
+
+    def run_all(base):
+        for ln in lanes:
+            ln.wait_stream(base)
+        for q, op in enumerate(ops):
+            op(lanes[q % RS_STREAMS])
+        for ln in lanes:
+            base.wait_stream(ln)
+
+    run_all(stream)  # first calls (and per-stream library handles) outside the timing
     torch.cuda.synchronize(dev)
     ts = []
     for r in range(3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for op in ops:
-            op(stream)
+        run_all(stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
         ts.append(a.elapsed_time(b))
     ms = statistics.median(ts)
+    # the same 512 calls captured once in a CUDA graph and replayed: the
+    # device time of the batch without the host's per-call launch overhead
+    graph_ms = None
+    try:
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        run_all(side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            run_all(side)
+        g.replay()
+        torch.cuda.synchronize(dev)
+        gts = []
+        for r in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            gts.append(a.elapsed_time(b))
+        graph_ms = statistics.median(gts)
+        del g
+    except RuntimeError as e:  # a call the capture refuses: report the eager number alone
+        graph_ms = None
+        print(f"random_sets: graph capture failed: {e}", file=sys.stderr)
     flops = sum(W.factored_flops([c.shape[1] for c in x_], [c.shape[0] for c in x_] + [1],
                                  [c.shape[0] for c in y_] + [1], m) for m, x_, y_ in pairs)
     status = 0
@@ -1045,11 +1085,13 @@ def bench_random_sets(T, dev, args, n_pairs=512):
         status |= int(op.status.item())
     out = {
         "workload": "512 TT pairs, order U{4..12}, modes U{2..32}, ranks U{4..16}, float32; partial contraction "
-                    "over a random set of floor(N/2) modes (any positions), factored output; one call per pair "
-                    "on one stream",
+                    "over a random set of floor(N/2) modes (any positions), factored output; one call per pair, "
+                    f"dealt round-robin over {RS_STREAMS} streams",
         "value": n_pairs / (ms / 1e3),
         "unit": "contractions/s",
         "ms_per_batch": ms,
+        "ms_per_batch_graph": graph_ms,
+        "value_graph": n_pairs / (graph_ms / 1e3) if graph_ms else None,
         "alg_flops": flops,
         "gflops": flops / (ms / 1e3) / 1e9,
         "device_status": status,

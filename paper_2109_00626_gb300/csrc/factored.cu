@@ -22,7 +22,9 @@
 #include <limits.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "host_plan.h"
 #include "ttc_device.cuh"
@@ -104,21 +106,28 @@ __global__ void renorm_rows_kernel(T* __restrict__ e, int64_t n_row, int rows, i
   }
 }
 
-// One cuBLAS handle per device, created on the first GEMM-path call (it
-// allocates cuBLAS's own workspace) and used under a lock.
+// One cuBLAS handle per (device, stream), created on the first GEMM-path
+// call on that stream (it allocates cuBLAS's own workspace, so that first
+// call belongs outside a stream capture) and bound to the stream for good:
+// calls on different streams may run at the same time without sharing a
+// cuBLAS workspace.  The table is guarded by a lock.
 static std::mutex g_blas_mu;
-static cublasHandle_t g_blas[64];
+static std::map<std::pair<int, cudaStream_t>, cublasHandle_t> g_blas;
 
-static cublasHandle_t blas_handle() {
+static cublasHandle_t blas_handle(cudaStream_t s) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (g_blas[dev] == nullptr) {
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    if (cublasSetMathMode(h, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    g_blas[dev] = h;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  const auto key = std::make_pair(dev, s);
+  auto it = g_blas.find(key);
+  if (it != g_blas.end()) return it->second;
+  cublasHandle_t h = nullptr;
+  if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+  if (cublasSetMathMode(h, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) {
+    cublasDestroy(h);
+    return nullptr;
   }
-  return g_blas[dev];
+  g_blas.emplace(key, h);
+  return h;
 }
 
 // Row-major C (M x N) = E (M x K) Gy (K x N): column-major C^T = Gy^T E^T.
@@ -193,8 +202,8 @@ static int gemm_run(const tt_desc* x, const tt_desc* y, int k0, int k1, int rows
   }
   if (k1 == k0 + 1) return TT_OK;
   std::lock_guard<std::mutex> lock(g_blas_mu);
-  cublasHandle_t h = blas_handle();
-  if (h == nullptr || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return TT_ERR_CUDA;
+  cublasHandle_t h = blas_handle(s);
+  if (h == nullptr) return TT_ERR_CUDA;
   T* cur = eb0;
   T* nxt = eb1;
   for (int k = k0 + 1; k < k1; ++k) {
