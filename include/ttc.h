@@ -264,8 +264,10 @@ int tt_contract_pairs(const tt_desc* x, const tt_desc* y, int n_pairs, const int
  * tt_contract_factored: out_dev = a device arena of f->bytes (16-byte
  * aligned); `f` must be the shape of these operands and S (TT_ERR_SHAPE);
  * ws of at least f->ws_bytes (TT_ERR_WS).  The runs are computed one after
- * another on `stream`; no allocation, except that the first call on a device
- * that takes the GEMM path creates the library's cuBLAS handle for it. */
+ * another on `stream`; no allocation, except that the first call on a
+ * stream that takes the GEMM path creates a cuBLAS handle bound to that
+ * stream (so that call belongs outside a stream capture); calls on different
+ * streams may run concurrently. */
 typedef struct {
   int32_t n_free;
   int32_t free_pos[TT_MAX_ORDER];
