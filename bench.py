@@ -40,7 +40,7 @@ from paper_2109_00626_gb300 import workload as W  # noqa: E402
 # this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2; the
 # capture is in profiles/launches_order10_r64_step.md).  Reset to None whenever
 # that kernel or the sweep body changes.
-TWO_SIDED_TRAFFIC = 4288000
+TWO_SIDED_TRAFFIC = 4299776
 
 METRIC = "TT contractions/s (order-10, I=16, R=64, fp32: full + partial over modes 1-6)"
 UNIT = "contractions/s"
