@@ -243,3 +243,51 @@ def test_order1_full_and_outer_product(dt, I):
     _, perm = O.partial_chain(x, y, [0])
     dense = O.chain_to_dense(got, perm)
     np.testing.assert_array_equal(dense, np.outer(x[0].reshape(-1).astype(np.float64), y[0].reshape(-1).astype(np.float64)))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize(
+    "rx,scale",
+    [([1, 8, 8, 8, 1], 0), ([1, 64, 600, 64, 1], 0), ([1, 1024, 17, 1024, 1], 0), ([1, 16, 16, 16, 1], 40)],
+)
+def test_full_rank1_y_fold_and_chain(dt, rx, scale):
+    """A Y of rank 1 (the sum of a TT's entries is the case y = ones) takes
+    the fold-and-chain path: z against the oracle for ranks of X up to 1024
+    (vectors longer than a block: several passes per step), a mode of size 1,
+    cores scaled by 2^40 each (renormalised on the way), and the split output
+    (mantissa, log2) against the folded one."""
+    rng = np.random.default_rng(sum(rx) + scale)
+    modes = [3, 16, 1, 7]
+    x = G.random_tt(rng, modes, rx, dt)
+    if scale:
+        x = [c * dt(2.0**scale) for c in x]
+    y = G.random_tt(rng, modes, [1] * 5, dt)
+    z, st = _full(x, y)
+    assert st == 0
+    want = O.contract_full(x, y)
+    eps = abs(z - want) / norm_scale(x, y)
+    print(f"rank-1 y {dt.__name__} {rx[1:-1]} 2^{scale}: eps {eps:.2e}")
+    assert eps <= TOL[dt], (z, want, eps)
+    m, e, st2 = _full(x, y, split=True)
+    assert st2 == 0
+    assert m * 2.0**e == z
+
+
+def test_full_rank1_y_sum_of_entries_and_overflow():
+    """y = ones: z is the sum of X's entries (dense brute force); scaled past
+    the float64 range, the folded output overflows with TT_STATUS_OVERFLOW
+    while the split output stays finite."""
+    rng = np.random.default_rng(5)
+    modes = [4, 3, 5]
+    x = G.random_tt(rng, modes, [1, 6, 7, 1], np.float64)
+    ones = [np.ones((1, i, 1)) for i in modes]
+    z, st = _full(x, ones)
+    assert st == 0
+    want = O.tt_to_dense(x).sum()
+    assert abs(z - want) <= 1e-12 * np.abs(O.tt_to_dense(x)).sum()
+    xs = [c * 2.0**400 for c in x]
+    z, st = _full(xs, ones)
+    assert st & 2 and np.isinf(z)
+    m, e, st = _full(xs, ones, split=True)
+    assert st == 0 and np.isfinite(m)
+    assert abs(m * 2.0 ** (e - 1200) - want) <= 1e-12 * np.abs(O.tt_to_dense(x)).sum()
