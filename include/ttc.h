@@ -197,9 +197,9 @@ int tt_contract_partial(const tt_desc* x, const tt_desc* y, const uint8_t* mask,
 /* The chain-layout partial contraction that also leaves, in `ws`, what its
  * backward pass (tt_contract_backward_k with the same ws) would otherwise
  * recompute: K, the environment over the contracted block (Algorithm 2 step
- * 4), with its scale, and for a leading block the adjoint's checkpoints of the
- * left environments (every ceil(sqrt(s)) modes; the backward still re-sweeps
- * each segment from them).
+ * 4), with its scale, and for a leading block every left environment of the
+ * block (L_0 .. L_{s-1}, with their scales), which the adjoint's gradient
+ * launch reads.
  *   ws, ws_bytes  device workspace of at least tt_workspace_bytes(TT_OP_BACKWARD,
  *                 x, y, mask, TT_LAYOUT_CHAIN, prec) bytes, owned by the caller,
  *                 kept unchanged until the backward call (TT_ERR_WS if short).

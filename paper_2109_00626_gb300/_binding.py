@@ -809,8 +809,8 @@ def autotune(dtype="f32", cache_path=None):
 
 def partial_k(x, y, mask, z, stream=None):
     """Chain-layout partial contraction into the output cores ``z`` that also
-    fills a backward workspace (K and, for a leading block, the adjoint's
-    checkpoints; tt_contract_partial_k).  Returns (ws, status); pass ``ws`` to
+    fills a backward workspace (K and, for a leading block, every left
+    environment of the block; tt_contract_partial_k).  Returns (ws, status); pass ``ws`` to
     :func:`backward` as ``fwd_ws``."""
     import torch
 
@@ -909,7 +909,7 @@ def _autograd():
             modes, ranks, _ = partial_shape(Desc(x), Desc(y), mask, "chain")
             z = [torch.empty((ranks[t], modes[t], ranks[t + 1]), dtype=x[0].dtype, device=x[0].device)
                  for t in range(len(modes))]
-            fws, _ = partial_k(x, y, mask, z)  # K and checkpoints kept for the backward pass
+            fws, _ = partial_k(x, y, mask, z)  # K and the left environments kept for the backward pass
             ctx.nx = nx
             ctx.mask = list(mask)
             ctx.save_for_backward(*x, *y, fws)
