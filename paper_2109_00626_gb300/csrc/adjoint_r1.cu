@@ -10,10 +10,10 @@
 //   dGy_k[0][i][0]  = g sum_{a,a'} L_k[a] Gx_k[a][i][a'] F_{k+1}[a'].
 // Three launches: the fold of every core at once (the cores are read once,
 // by every SM), the two chains of vector-matrix products (one block each,
-// on the folded cores, which sit in L2), and the gradients, one block per
-// (k, i).  Every vector is kept with a power-of-two scale (no checkpoints:
-// the vectors are small).  The forward value alone takes the fold and the
-// left chain.
+// on the folded cores, which sit in L2; a 128-thread kernel when every rank
+// is at most 64), and the gradients, one block per (k, i).  Every vector is
+// kept with a power-of-two scale (no checkpoints: the vectors are small).
+// The forward value alone takes the fold and the left chain.
 #include "ttc_device.cuh"
 #include "ttc_internal.h"
 
@@ -225,6 +225,125 @@ __global__ void __launch_bounds__(kR1Threads) r1_chain_kernel(const __grid_const
   if (bad && tid == 0) set_status(p.status, TT_STATUS_NONFINITE);
 }
 
+// The chains when every rank is at most 64: 128 threads, output column c of
+// a step taken by the 16-lane half-warps of warp c / 16, lane half h summing
+// rows h, h + 2, ... of A (32 registers, loaded during the step before), the
+// halves joined by one shuffle; two block barriers a step.  Same sums and
+// scaling rules as r1_chain_kernel.
+constexpr int kC64Threads = 128;
+template <typename T>
+__global__ void __launch_bounds__(kC64Threads) r1_chain64_kernel(const __grid_constant__ AdjR1Params p) {
+  __shared__ T cur[64];
+  __shared__ T nxt[64];
+  __shared__ int wred[2][8];
+  __shared__ double zr[4];
+  const bool left = blockIdx.x == 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = warp * 16 + (lane & 15), h = lane >> 4;
+  const int n = p.n;
+  int bad = 0;
+  T* vecs = static_cast<T*>(left ? p.lvec : p.fvec);
+  int64_t* scl = left ? p.llog : p.flog;
+  int64_t lg = 0;
+  if (tid < 64) cur[tid] = tid == 0 ? T(1) : T(0);
+  if (!p.fwd && tid == 0) {
+    vecs[static_cast<int64_t>(left ? 0 : n) * p.vstride] = T(1);
+    scl[left ? 0 : n] = 0;
+  }
+  const int steps = p.fwd ? n - 1 : n;  // the forward value's last step is summed in float64
+  T pre[32];
+  auto fetch = [&](int step) {
+    const int k = left ? step : n - 1 - step;
+    const AdjStep& st = p.step[k];
+    const int rows = left ? st.rx : st.rx2, cols = left ? st.rx2 : st.rx;
+    const T* A = static_cast<const T*>(left ? p.mbuf : p.mtbuf) + p.moff[k];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int r = h + 2 * j;
+      pre[j] = (r < rows && c < cols) ? ldg(A + static_cast<int64_t>(r) * cols + c) : T(0);
+    }
+  };
+  if (steps > 0) fetch(0);
+  __syncthreads();
+  for (int step = 0; step < steps; ++step) {
+    const int k = left ? step : n - 1 - step;
+    const AdjStep& st = p.step[k];
+    const int cols = left ? st.rx2 : st.rx;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc = fma(cur[h + 2 * j], pre[j], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (step + 1 < steps) fetch(step + 1);  // the next matrix's loads during this step's reductions
+    int e = kNoExpR1, lbad = 0;
+    if (h == 0 && c < cols) {
+      nxt[c] = acc;
+      if (!isfinite(acc)) lbad = 1;
+      else if (acc != T(0)) e = exp2_bits(acc);
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+    lbad = __reduce_or_sync(0xffffffffu, lbad);
+    if (lane == 0) {
+      wred[step & 1][warp] = e;
+      wred[step & 1][4 + warp] = lbad;
+    }
+    __syncthreads();  // nxt complete, every thread past its reads of cur
+    e = kNoExpR1;
+    lbad = 0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      e = max(e, wred[step & 1][w]);
+      lbad |= wred[step & 1][4 + w];
+    }
+    if (lbad) bad = 1;
+    const int sh = (e != kNoExpR1 && (e > p.renorm_bits || e < -p.renorm_bits)) ? e : 0;
+    lg += sh;
+    if (tid < 64) {
+      const T v = tid < cols ? (sh ? mul_pow2<T>(nxt[tid], -sh) : nxt[tid]) : T(0);
+      cur[tid] = v;
+      if (!p.fwd && tid < cols) vecs[static_cast<int64_t>(left ? k + 1 : k) * p.vstride + tid] = v;
+    }
+    if (!p.fwd && tid == 0) scl[left ? k + 1 : k] = lg;
+    __syncthreads();  // cur is complete before the next step reads it
+  }
+  if (p.fwd && left) {
+    // z = L_{N-1} M_{N-1} (a 1 x 1 result), summed in float64
+    const AdjStep& st = p.step[n - 1];
+    const T* A = static_cast<const T*>(p.mbuf) + p.moff[n - 1];
+    double s = 0.0;
+    for (int r = tid; r < st.rx; r += kC64Threads) s = fma(static_cast<double>(cur[r]), static_cast<double>(A[r]), s);
+    s = warp_sum(s);
+    if (lane == 0) zr[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      const double z = zr[0] + zr[1] + zr[2] + zr[3];
+      int st_bits = (isfinite(z) && !bad) ? 0 : TT_STATUS_NONFINITE;
+      if (p.z_out_log2 != nullptr) {
+        *p.z_out = z;
+        *p.z_out_log2 = lg;
+      } else {
+        // the scale folded in: infinity (and TT_STATUS_OVERFLOW) beyond the
+        // float64 range, zero below it
+        double v = z;
+        if (z != 0.0 && isfinite(z)) {
+          const int64_t tot = static_cast<int64_t>(exp2_of(z)) + lg;
+          if (tot > 1024) {
+            v = z > 0 ? INFINITY : -INFINITY;
+            st_bits |= TT_STATUS_OVERFLOW;
+          } else if (tot < -1074) {
+            v = 0.0;
+          } else {
+            v = ldexp(z, static_cast<int>(lg));
+          }
+        }
+        *p.z_out = v;
+      }
+      if (st_bits) set_status(p.status, st_bits);
+    }
+    return;
+  }
+  if (bad && tid == 0) set_status(p.status, TT_STATUS_NONFINITE);
+}
+
 // One block per (i, k): dGx_k[:, i, :] and dGy_k[0][i][0].
 template <typename T>
 __global__ void __launch_bounds__(256) r1_grad_kernel(const __grid_constant__ AdjR1Params p) {
@@ -292,6 +411,14 @@ static cudaError_t r1_fold(const AdjR1Params& p, int dtype, cudaStream_t s) {
 }
 
 static cudaError_t r1_chains(const AdjR1Params& p, int dtype, int nblocks, cudaStream_t s) {
+  bool small = true;
+  for (int k = 0; k < p.n; ++k) small = small && p.step[k].rx <= 64 && p.step[k].rx2 <= 64;
+  if (small) {
+    count_launch();
+    if (dtype == TT_F64) r1_chain64_kernel<double><<<nblocks, kC64Threads, 0, s>>>(p);
+    else r1_chain64_kernel<float><<<nblocks, kC64Threads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   const size_t esz = dtype == TT_F64 ? 8 : 4;
   const size_t smem = (2 * static_cast<size_t>(kR1MaxRank) + kR1Threads) * esz;
   const void* k = dtype == TT_F64 ? reinterpret_cast<const void*>(r1_chain_kernel<double>)
