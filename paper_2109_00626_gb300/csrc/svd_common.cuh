@@ -362,6 +362,151 @@ __device__ void jacobi_dist(T* W, T* Qt, int p, int L, T* dsm, const SvdCluster&
   svd_barrier(cl);
 }
 
+// ---- row-distributed sweeps ----
+//
+// For many vectors of moderate length (p large, L moderate) the vectors
+// themselves are spread over the cluster: CTA c holds the pair slots
+// [k0, k1) of the round-robin tournament, each slot a "top" and a "bottom"
+// vector (its W row followed by its Qt row, L + p entries, in shared
+// memory).  A round rotates every slot's pair locally (whole dot products,
+// no reduction across CTAs); then every vector but the one in top slot 0
+// moves one place along the cycle top 1 -> top 2 -> ... -> top NP-1 ->
+// bottom NP-1 -> ... -> bottom 0 -> top 1, so each CTA sends its last top
+// vector to the next CTA and its first bottom vector to the previous one
+// (distributed shared memory, receive buffers alternating by round parity)
+// and renames the rest in place: one cluster barrier per round.  After the
+// P - 1 rounds of a sweep every vector is back in its first place and every
+// pair has met once.  Needs at least two slots per CTA (NP >= 2 C); taken
+// for vectors no longer than 4 p.
+__host__ __device__ inline int rowdist_slots(int NP, int C, int rank) {
+  return (rank + 1) * NP / C - rank * NP / C;
+}
+__host__ __device__ inline size_t rowdist_smem_elems(int p, int L, int C) {
+  const int NP = (p + 1) / 2;
+  // long vectors with few per CTA leave most warps idle: the column split
+  // serves those better (a 4096 x 64 unfolding: 12.3 vs 10.2 ms a rounding)
+  if (C < 2 || NP / C < 2 || L > 4 * p) return 0;
+  const int nsmax = (NP + C - 1) / C;
+  return static_cast<size_t>(2 * nsmax + 4) * (static_cast<size_t>(L) + p);
+}
+constexpr int kRowDistMaxSlots = kSvdMaxP / 2;
+
+template <typename T>
+__device__ void jacobi_rowdist(T* W, T* Qt, int p, int L, T* dsm, const SvdCluster& cl) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = cl.C, rank = cl.rank;
+  const int P = (p + 1) & ~1, NP = P / 2;
+  const int k0 = rank * NP / C, ns = rowdist_slots(NP, C, rank);
+  const int Lp = L + p;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  __shared__ int topb[kRowDistMaxSlots], botb[kRowDistMaxSlots];
+  __shared__ int rflag[2];
+  auto buf = [&](int b) { return dsm + static_cast<int64_t>(b) * Lp; };
+  // slot s starts with vectors 2 (k0 + s) (top) and 2 (k0 + s) + 1 (bottom) in buffers 2 s, 2 s + 1
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    topb[s] = 2 * s;
+    botb[s] = 2 * s + 1;
+  }
+  for (int64_t e = threadIdx.x; e < static_cast<int64_t>(2 * ns) * Lp; e += blockDim.x) {
+    const int b = static_cast<int>(e / Lp), j = static_cast<int>(e - static_cast<int64_t>(b) * Lp);
+    const int v = 2 * k0 + b;
+    T val = T(0);
+    if (v < p) val = j < L ? __ldcg(W + static_cast<int64_t>(v) * L + j) : (j - L == v ? T(1) : T(0));
+    dsm[e] = val;
+  }
+  const T tol = T(4) * (sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08)) * sqrt(T(L > 1 ? L : 1));
+  const int ns_next = rank + 1 < C ? rowdist_slots(NP, C, rank + 1) : 0;
+  const int ns_prev = rank > 0 ? rowdist_slots(NP, C, rank - 1) : 0;
+  int parity = 0;
+  svd_barrier(cl);
+  for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
+    int rotated = 0;  // thread-local: a rotation this thread's warp took
+    for (int t = 0; t < P - 1; ++t) {
+      // this CTA's pairs
+      for (int s = warp; s < ns; s += nwarps) {
+        T* wa = buf(topb[s]);
+        T* wb = buf(botb[s]);
+        T al = T(0), be = T(0), ga = T(0);
+        for (int j = lane; j < L; j += 32) {
+          const T u = wa[j], v = wb[j];
+          al = fma(u, u, al);
+          be = fma(v, v, be);
+          ga = fma(u, v, ga);
+        }
+        al = warp_sum_t(al);
+        be = warp_sum_t(be);
+        ga = warp_sum_t(ga);
+        if (ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        const T zeta = (be - al) / (T(2) * ga);
+        const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + tn * tn), sn = c * tn;
+        for (int j = lane; j < Lp; j += 32) {  // the W row and the Qt row
+          const T u = wa[j], v = wb[j];
+          wa[j] = c * u - sn * v;
+          wb[j] = sn * u + c * v;
+        }
+        rotated = 1;
+      }
+      __syncthreads();
+      // the two vectors leaving this CTA, into the neighbours' receive buffers
+      const int out_top = topb[ns - 1], out_bot = botb[0];
+      if (rank + 1 < C) {
+        const T* src = buf(out_top);
+        T* dst = cluster.map_shared_rank(dsm + static_cast<int64_t>(2 * ns_next + parity) * Lp, rank + 1);
+        for (int j = threadIdx.x; j < Lp; j += blockDim.x) dst[j] = src[j];
+      }
+      if (rank > 0) {
+        const T* src = buf(out_bot);
+        T* dst = cluster.map_shared_rank(dsm + static_cast<int64_t>(2 * ns_prev + 2 + parity) * Lp, rank - 1);
+        for (int j = threadIdx.x; j < Lp; j += blockDim.x) dst[j] = src[j];
+      }
+      svd_barrier(cl);  // every send has landed (and every thread has read topb / botb)
+      if (threadIdx.x == 0) {
+        // the vectors that stay move one slot by renaming their buffers; the
+        // two sent away free theirs for the two that arrived
+        for (int k = ns - 2; k >= (rank == 0 ? 1 : 0); --k) topb[k + 1] = topb[k];
+        if (rank == 0) topb[1] = out_bot;  // topb[0] stays
+        else topb[0] = out_bot;             // filled from the previous CTA below
+        for (int k = 1; k < ns; ++k) botb[k - 1] = botb[k];
+        botb[ns - 1] = out_top;  // stays here on the last CTA, filled from the next CTA elsewhere
+      }
+      if (rank > 0) {
+        const T* src = buf(2 * ns + parity);
+        T* dst = buf(out_bot);
+        for (int j = threadIdx.x; j < Lp; j += blockDim.x) dst[j] = src[j];
+      }
+      if (rank + 1 < C) {
+        const T* src = buf(2 * ns + 2 + parity);
+        T* dst = buf(out_top);
+        for (int j = threadIdx.x; j < Lp; j += blockDim.x) dst[j] = src[j];
+      }
+      parity ^= 1;
+      __syncthreads();
+    }
+    // any rotation anywhere in the cluster this sweep?  (flags alternate by
+    // sweep parity, so a peer's next write waits behind two barriers)
+    rotated = __syncthreads_or(rotated);
+    if (threadIdx.x == 0) rflag[sweep & 1] = rotated;
+    svd_barrier(cl);
+    int any = 0;
+    for (int r = 0; r < C; ++r) any |= *cluster.map_shared_rank(&rflag[sweep & 1], r);
+    if (!any) break;
+  }
+  // every vector is back in its first slot: write W and Qt rows
+  for (int s = 0; s < ns; ++s)
+    for (int h = 0; h < 2; ++h) {
+      const int v = 2 * (k0 + s) + h;
+      if (v >= p) continue;
+      const T* src = buf(h == 0 ? topb[s] : botb[s]);
+      for (int j = threadIdx.x; j < Lp; j += blockDim.x) {
+        if (j < L) W[static_cast<int64_t>(v) * L + j] = src[j];
+        else Qt[static_cast<int64_t>(v) * p + (j - L)] = src[j];
+      }
+    }
+  svd_barrier(cl);
+}
+
 // Per-CTA shared scalars of svd_factor and its dynamic shared memory.
 template <typename T>
 struct SvdShared {
@@ -394,11 +539,14 @@ __device__ int svd_factor(T* M, T* scratch, T* qt, double* sig, int32_t* ord, in
       transpose_rows<T>(scratch, M, m, n, sh.tile);
       W = scratch;
     }
-    // where the sweeps run: 0 the leader's shared memory, 1 the cluster's, 2 the workspace
+    // where the sweeps run: 0 the leader's shared memory; 4 the cluster's,
+    // vectors spread over the CTAs; 1 the cluster's, columns spread; 3 the
+    // same in place in the workspace; 2 the leader alone in the workspace
     const int64_t wl = static_cast<int64_t>(pp) * L;
-    // (3: the cluster's, in place in the workspace)
+    const size_t rd = rowdist_smem_elems(pp, L, cl.C);
     int path = 2;
     if (static_cast<size_t>(wl + static_cast<int64_t>(pp) * pp) * sizeof(T) <= sh.smem_bytes) path = 0;
+    else if (cl.C > 1 && rd > 0 && rd * sizeof(T) <= sh.smem_bytes) path = 4;
     else if (cl.C > 1 && dist_smem_elems(pp, L, cl.C) * sizeof(T) <= sh.smem_bytes) path = 1;
     else if (cl.C > 1) path = 3;
     if (tid == 0) {
@@ -422,8 +570,10 @@ __device__ int svd_factor(T* M, T* scratch, T* qt, double* sig, int32_t* ord, in
     W = reinterpret_cast<T*>(bcp[0]);
     qt = reinterpret_cast<T*>(bcp[1]);
   }
-  if (path == 1 || path == 3) {
-    if (path == 1)
+  if (path == 1 || path == 3 || path == 4) {
+    if (path == 4)
+      jacobi_rowdist<T>(W, qt, pp, L, reinterpret_cast<T*>(sh.dsm), cl);
+    else if (path == 1)
       jacobi_dist<T, true>(W, qt, pp, L, reinterpret_cast<T*>(sh.dsm), cl);
     else
       jacobi_dist<T, false>(W, qt, pp, L, reinterpret_cast<T*>(sh.dsm), cl);

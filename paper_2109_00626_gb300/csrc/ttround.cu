@@ -295,6 +295,8 @@ extern "C" int tt_round(const tt_desc* x, double eps, int32_t max_rank, void* co
           if (ls >= (int64_t(1) << 30)) continue;
           const size_t d = dist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
           if (d <= kSvdSmemCap) smem = std::max(smem, d);
+          const size_t rd = rowdist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
+          if (rd <= kSvdSmemCap) smem = std::max(smem, rd);
         }
     return smem;
   };

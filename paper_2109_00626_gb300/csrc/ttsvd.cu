@@ -233,6 +233,8 @@ extern "C" int tt_svd(const void* x_dev, int order, const int32_t* modes, int dt
       if (c > 1 && ls < (int64_t(1) << 30)) {
         const size_t d = dist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
         if (d <= kSvdSmemCap) smem = std::max(smem, d);
+        const size_t rd = rowdist_smem_elems(static_cast<int>(ps), static_cast<int>(ls), c) * eb;
+        if (rd <= kSvdSmemCap) smem = std::max(smem, rd);
       }
     }
     return smem;

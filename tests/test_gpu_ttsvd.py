@@ -226,3 +226,22 @@ def test_large_unfoldings_cluster_sweeps():
     cores = _decompose(g, 1e-6)
     assert [c.shape[0] for c in cores] + [1] == [1, 20, 400, 20, 4, 1]
     _check_valid(g, cores, 1e-6, np.float32, "gaussian 20^3x5x4")
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape", [(20, 20, 20, 20), (333, 400)])
+def test_square_unfoldings_vector_split_sweeps(shape, dtype):
+    """Unfoldings with many vectors of moderate length (400 x 400 of a 20^4
+    tensor; 333 x 400, an odd count of vectors, so the tournament carries an
+    empty one) are swept with the vectors spread over the cluster: a Gaussian
+    tensor within its guarantee with left-orthonormal cores, and a low-rank
+    one of the same shape at its exact ranks."""
+    rng = np.random.default_rng(sum(shape))
+    g = rng.standard_normal(shape).astype(dtype)
+    eps = 1e-10 if dtype == np.float64 else 1e-6
+    cores = _decompose(g, eps)
+    _check_valid(g, cores, eps, dtype, f"gaussian {shape} {np.dtype(dtype).name}")
+    ranks = [1] + [min(7 + 3 * k, 60) for k in range(len(shape) - 1)] + [1]
+    xh = _dense_tt(70 + len(shape), list(shape), ranks, dtype)
+    cores = _decompose(xh, eps if dtype == np.float64 else 1e-5)
+    assert [c.shape[0] for c in cores] + [1] == ranks
