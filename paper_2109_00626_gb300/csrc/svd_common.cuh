@@ -8,9 +8,11 @@
 // rank that the TT-SVD's truncation rule gives and writes the two factors.
 //
 // The kernels run as a cluster of CTAs.  CTA 0 (the leader) does everything
-// but the sweeps; the sweeps run in one of three places: in the leader's
-// shared memory when the vectors and the rotations fit there; else spread
-// over the cluster by columns when every CTA's slice fits (each CTA holds
+// but the sweeps; the sweeps run in one of these places: in the leader's
+// shared memory when the vectors and the rotations fit there; else, for many
+// vectors of moderate length, with the vectors themselves spread over the
+// cluster (jacobi_rowdist below); else spread over the cluster by columns
+// when every CTA's slice fits (each CTA holds
 // columns [c0, c1) of every vector and of the rotations, computes its part of
 // each pair's three inner products, the pair's owner sums them and sends the
 // rotation to every CTA, which applies it to its slice: two cluster barriers
