@@ -25,6 +25,7 @@ import json  # noqa: E402
 import math  # noqa: E402
 import statistics  # noqa: E402
 import subprocess  # noqa: E402
+import tempfile  # noqa: E402
 import sys  # noqa: E402
 import time  # noqa: E402
 
@@ -812,8 +813,7 @@ def bench_batched(T, dev, args):
     ms_untuned = time_graph(bat0)
     del bat0
     t_tune = time.perf_counter()
-    cache = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                         f"autotune_f32_rank{rank}.txt")
+    cache = os.path.join(tempfile.gettempdir(), f"ttc_autotune_f32_rank{rank}.txt")
     T.autotune("f32", cache)
     tune_s = time.perf_counter() - t_tune
     os.environ["TTC_AUTOTUNE_CACHE"] = cache

@@ -98,7 +98,7 @@ def test_factored_small_against_dense(mask, dtype):
 
 
 def test_factored_order8_rank16_random_sets():
-    """The merged layout's survey size (order 8, modes 8, ranks 16, float32)
+    """The merged layout's order-8 size (order 8, modes 8, ranks 16, float32)
     over random sets of four modes: every run matrix against the oracle."""
     x, y = G.pair(13, [8] * 8, G.tt_ranks(8, 16), G.tt_ranks(8, 16), np.float32)
     x64 = [c.astype(np.float64) for c in x]
