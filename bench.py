@@ -63,7 +63,7 @@ def fp32_simt_peak_tflops():
 
 
 def measure_peaks():
-    """Reference peaks the driver does not measure: cuBLAS SGEMM with TF32 off
+    """Reference peaks beside the measured HBM copy and bf16 GEMM: cuBLAS SGEMM with TF32 off
     (the float32 FMA pipe) and DGEMM, square n x n, timed with CUDA events
     after warm-up; one JSON line.  Context for the float32 roofline, whose
     denominator stays the derived FMA peak."""
