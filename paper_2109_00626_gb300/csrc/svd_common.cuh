@@ -404,6 +404,8 @@ __device__ void jacobi_rowdist(T* W, T* Qt, int p, int L, T* dsm, const SvdClust
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   __shared__ int topb[kRowDistMaxSlots], botb[kRowDistMaxSlots];
   __shared__ int rflag[2];
+  __shared__ T pairsum[15 * 2 * 3];  // dual mode: each pair's two halves of its three sums
+  const bool dual = 2 * ns <= nwarps && ns <= 15;  // named barriers 1..15
   auto buf = [&](int b) { return dsm + static_cast<int64_t>(b) * Lp; };
   // slot s starts with vectors 2 (k0 + s) (top) and 2 (k0 + s) + 1 (bottom) in buffers 2 s, 2 s + 1
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
@@ -425,30 +427,73 @@ __device__ void jacobi_rowdist(T* W, T* Qt, int p, int L, T* dsm, const SvdClust
   for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
     int rotated = 0;  // thread-local: a rotation this thread's warp took
     for (int t = 0; t < P - 1; ++t) {
-      // this CTA's pairs
-      for (int s = warp; s < ns; s += nwarps) {
-        T* wa = buf(topb[s]);
-        T* wb = buf(botb[s]);
-        T al = T(0), be = T(0), ga = T(0);
-        for (int j = lane; j < L; j += 32) {
-          const T u = wa[j], v = wb[j];
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
+      // this CTA's pairs: two warps a pair when there are warps enough (their
+      // halves of the dot products met through shared memory at a named
+      // barrier of the pair's 64 threads), else one
+      if (dual) {
+        const int s = warp >> 1, half = warp & 1, gl = half * 32 + lane;
+        if (s < ns) {
+          T* wa = buf(topb[s]);
+          T* wb = buf(botb[s]);
+          T al = T(0), be = T(0), ga = T(0);
+          for (int j = gl; j < L; j += 64) {
+            const T u = wa[j], v = wb[j];
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+          al = warp_sum_t(al);
+          be = warp_sum_t(be);
+          ga = warp_sum_t(ga);
+          T* pr = pairsum + (s * 2 + half) * 3;
+          if (lane == 0) {
+            pr[0] = al;
+            pr[1] = be;
+            pr[2] = ga;
+          }
+          asm volatile("bar.sync %0, 64;" ::"r"(1 + s) : "memory");
+          const T* qo = pairsum + (s * 2 + (half ^ 1)) * 3;
+          // the same sum in both warps: lower half first
+          al = half == 0 ? al + qo[0] : qo[0] + al;
+          be = half == 0 ? be + qo[1] : qo[1] + be;
+          ga = half == 0 ? ga + qo[2] : qo[2] + ga;
+          if (!(ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be))) {
+            const T zeta = (be - al) / (T(2) * ga);
+            const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+            const T c = T(1) / sqrt(T(1) + tn * tn), sn = c * tn;
+            for (int j = gl; j < Lp; j += 64) {  // the W row and the Qt row
+              const T u = wa[j], v = wb[j];
+              wa[j] = c * u - sn * v;
+              wb[j] = sn * u + c * v;
+            }
+            rotated = 1;
+          }
         }
-        al = warp_sum_t(al);
-        be = warp_sum_t(be);
-        ga = warp_sum_t(ga);
-        if (ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        const T zeta = (be - al) / (T(2) * ga);
-        const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + tn * tn), sn = c * tn;
-        for (int j = lane; j < Lp; j += 32) {  // the W row and the Qt row
-          const T u = wa[j], v = wb[j];
-          wa[j] = c * u - sn * v;
-          wb[j] = sn * u + c * v;
+      } else {
+        for (int s = warp; s < ns; s += nwarps) {
+          T* wa = buf(topb[s]);
+          T* wb = buf(botb[s]);
+          T al = T(0), be = T(0), ga = T(0);
+          for (int j = lane; j < L; j += 32) {
+            const T u = wa[j], v = wb[j];
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+          al = warp_sum_t(al);
+          be = warp_sum_t(be);
+          ga = warp_sum_t(ga);
+          if (ga == T(0) || al == T(0) || be == T(0) || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+          const T zeta = (be - al) / (T(2) * ga);
+          const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + tn * tn), sn = c * tn;
+          for (int j = lane; j < Lp; j += 32) {  // the W row and the Qt row
+            const T u = wa[j], v = wb[j];
+            wa[j] = c * u - sn * v;
+            wb[j] = sn * u + c * v;
+          }
+          rotated = 1;
         }
-        rotated = 1;
       }
       __syncthreads();
       // the two vectors leaving this CTA, into the neighbours' receive buffers
