@@ -117,8 +117,13 @@ int tt_workspace_bytes(int op, const tt_desc* x, const tt_desc* y, const uint8_t
  *                workspace of tt_workspace_bytes(TT_OP_FULL) bytes and order
  *                >= 2, the environment is swept from both ends at once and
  *                the halves meet in the middle (half the dependent steps);
- *                with ws NULL or smaller the contraction runs as one sweep.
- *                The tensor-core forms need their workspace (TT_ERR_WS).
+ *                when every rank of Y is 1 (the sum of X's entries, and the
+ *                like; X's ranks <= 1024) X's cores are instead folded with
+ *                y into matrices M_k = sum_i y_k[i] X_k[:, i, :] in the
+ *                workspace and z is a chain of vector-matrix products, its
+ *                last one in float64; with ws NULL or smaller the
+ *                contraction runs as one sweep.  The tensor-core forms need
+ *                their workspace (TT_ERR_WS).
  *   out_dev      device double.  If out_log2_dev is NULL it receives z;
  *                otherwise it receives a mantissa m and *out_log2_dev an int64 e
  *                with z = m * 2^e (use this form when |z| may leave the double
