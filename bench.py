@@ -752,6 +752,15 @@ def bench_step_prec(T, dev, args, prec):
             }
         except Exception as e:  # a report, never a reason to lose the measurement line
             out["accuracy"] = {"error": repr(e)[:200]}
+        if "order10_step" not in _ORACLE_TIMES:
+            def oracle_step():
+                O.contract_full(x, y)
+                O.partial_chain(x, y, MASK)
+
+            t = _oracle_once(oracle_step, "contractions/s", "one step (full + partial over modes 1-6), numpy float64")
+            t["value"] *= 2  # two contractions a step, as the form's value counts them
+            _ORACLE_TIMES["order10_step"] = t
+        out["cpu_baseline"] = _ORACLE_TIMES["order10_step"]
     return out
 
 
@@ -921,7 +930,14 @@ def bench_merged(T, dev, args):
     status = 0
     for op in ops:
         status |= int(op.status.item())
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        extra["cpu_baseline"] = _oracle_once(lambda: O.partial_merged(x, y, masks[0]), "contractions/s",
+                                             "one contraction over the first set, numpy float64 merged cores")
     return {
+        **extra,
         "workload": "order-6 TT pair, modes 8, ranks 16, float32; partial contraction over a random S, |S| = 3, "
                     "merged layout; eight seeded draws of S timed in turn",
         "sets": ["".join(str(v) for v in m) for m in masks],
@@ -946,6 +962,15 @@ def bench_merged(T, dev, args):
 
 
 FACTORED_MASK = [1, 0, 0, 1, 1, 1, 0, 0]
+
+
+def _oracle_once(fn, unit, sample):
+    """The float64 oracle timed beside a GPU form: one call of fn on one host
+    thread (OPENBLAS_NUM_THREADS=1), as a rate in the form's unit."""
+    t0 = time.perf_counter()
+    fn()
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
 
 
 def bench_factored(T, dev, args):
@@ -980,7 +1005,14 @@ def bench_factored(T, dev, args):
     flops = W.factored_flops([16] * 8, rx, ry, FACTORED_MASK)
     peak = fp32_simt_peak_tflops()
     out_bytes = sum(r[0].numel() * 4 + r[1].numel() * 8 for r in op.runs() if r is not None)
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        extra["cpu_baseline"] = _oracle_once(lambda: O.partial_factored(x, y, FACTORED_MASK), "contractions/s",
+                                             "one contraction, numpy float64 transfer matrices (4096 x 4096)")
     return {
+        **extra,
         "workload": "order-8 TT pair, modes 16, ranks 64, float32; partial contraction over S = {0, 3, 4, 5} "
                     "in factored form (left environment + 4096 x 4096 transfer matrix)",
         "value": 1.0 / (ms / 1e3),
@@ -1236,6 +1268,7 @@ def bench_dense_ttcp(T, dev, args):
 
 
 _TC_RESULTS = {}  # precision form -> (mantissa, exponent) of its last z, for the accuracy report
+_ORACLE_TIMES = {}  # workload -> the oracle's timing, shared by the forms that run it
 
 
 def bench_bf16(T, dev, args, prec):
@@ -1276,7 +1309,16 @@ def bench_bf16(T, dev, args, prec):
     achieved = flops * nprod / (ms / 1e3) / 1e12
     del op, xd, yd, flush
     torch.cuda.empty_cache()
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        if "order16" not in _ORACLE_TIMES:
+            _ORACLE_TIMES["order16"] = _oracle_once(lambda: O.contract_full(x, y), "contractions/s",
+                                                    "one contraction of the float32 cores, numpy float64 sweep")
+        extra["cpu_baseline"] = _ORACLE_TIMES["order16"]
     return {
+        **extra,
         "workload": "order-16 TT pair, modes 32, ranks 256, log-normal core scales (sigma 1); full contraction on tcgen05 tensor cores" + (", bf16 cores, fp32 sums, fp64 final sum" if prec == "native" else ", fp32 cores split into hi+lo bf16, 3 products per step"),
         "value": 1.0 / (ms / 1e3),
         "unit": "contractions/s",
@@ -1352,6 +1394,20 @@ def bench_backward(T, dev, args):
     torch.cuda.synchronize(dev)
     graph_ms = a.elapsed_time(b) / K
     del g
+    extra = {}
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        def oracle_step():
+            zo, _ = O.partial_chain(x, y, mask)
+            ones = [np.ones((1, c.shape[1], 1)) for c in zo]
+            O.contract_full(zo, ones)
+            dz, _ = O.grad_full(zo, ones)
+            O.grad_partial_chain(x, y, mask, dz)
+
+        extra["cpu_baseline"] = _oracle_once(oracle_step, "gradient evaluations/s",
+                                             "one step (partial contraction, its sum, the gradients of every "
+                                             "core), numpy float64")
     modes, r = [16] * 12, G.tt_ranks(12, 64)
     fwd = W.partial_chain_flops(modes, r, r, mask)
     # adjoint: five products per contracted mode (U, dGx, W, dGy, next F), counted without recompute
@@ -1367,16 +1423,18 @@ def bench_backward(T, dev, args):
         "gflops": (fwd + bwd) / (graph_ms / 1e3) / 1e9,
         "alg_flops": fwd + bwd,
         "roofline": {
-            "kernel": "adjoint_kernel<float,64>",
+            "kernel": "whole gradient step (sweep_cluster_kernel: the forward partial and the right-environment "
+                      "sweep; adjoint_grads_kernel; the rank-1 chains of the sum)",
             "bound": "alu",
             "achieved": (fwd + bwd) / (graph_ms / 1e3) / 1e12,
             "peak": fp32_simt_peak_tflops(),
             "unit": "TFLOP/s",
             "frac": (fwd + bwd) / (graph_ms / 1e3) / 1e12 / fp32_simt_peak_tflops(),
-            "note": "latency-bound single instance (one cluster of 16 SMs); forward + adjoint products, recompute "
-            "not counted; timed as a CUDA-graph replay of the whole step (value_eager / ms_per_step_eager: the same "
-            "step launched from Python through torch.autograd)",
+            "note": "latency-bound single instance (environment sweeps on clusters of 16 SMs); forward + adjoint "
+            "products (five per contracted mode); timed as a CUDA-graph replay of the whole step "
+            "(value_eager / ms_per_step_eager: the same step launched from Python through torch.autograd)",
         },
+        **extra,
     }
 
 
