@@ -1035,7 +1035,7 @@ def bench_factored(T, dev, args):
     }
 
 
-RS_STREAMS = 8  # streams the random-set batch's independent calls are dealt over
+RS_STREAMS = 16  # streams the random-set batch's independent calls are dealt over
 
 
 def bench_random_sets(T, dev, args, n_pairs=512):
