@@ -534,6 +534,12 @@ def test_workspace_queries_and_their_limits(L):
     assert _ws(L, B.TT_OP_BACKWARD, wide, wide)[0] == -5
     rc, nb = _ws(L, B.TT_OP_BACKWARD, wide, ones)
     assert rc == 0 and nb > 0
+    # the order-12 rank-64 gradient step: every left and right environment of
+    # the 8-mode block and leg-swapped copies of its 16 cores fit (float32)
+    x12 = FakeDesc([16] * 12, [1] + [64] * 11 + [1])
+    rc, nb = _ws(L, B.TT_OP_BACKWARD, x12, x12, [1] * 8 + [0] * 4)
+    env, core = 64 * 64 * 4, 64 * 16 * 64 * 4
+    assert rc == 0 and nb >= 2 * 8 * env + 2 * 7 * core + 2 * 16 * 64 * 4  # the first cores have rank 1 on the left
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
