@@ -661,8 +661,9 @@ def contract_dense_pairs(x, y, pairs, eps, prec="native", max_rank=0, stream=Non
 
 def contract_full(x, y, prec="native", split=False, stream=None):
     """<X, Y> on the device.  Returns a float64 CUDA tensor of shape (1,), or
-    (mantissa, log2) tensors with split=True.  Raises on argument errors;
-    device status bits are returned by ``contract_full_status``."""
+    (mantissa, log2) tensors with split=True.  Raises on argument errors; for
+    the device status bits (TT_STATUS_*) use :class:`FullContraction`, whose
+    ``status`` tensor they land in."""
     op = FullContraction(x, y, prec, split)
     op(stream)
     if split:
