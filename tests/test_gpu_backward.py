@@ -79,6 +79,8 @@ def test_full_grad_cotangent_scaling_and_euler():
 
 @pytest.mark.parametrize("stride", [1, 2, 3, 10])
 def test_full_grad_order10_fp32_checkpoint_strides(stride):
+    """The order-10 gradients for every value of the checkpoint-stride
+    argument (accepted and ignored: every environment is kept)."""
     x, y = G.order10_r64(0)
     xd, yd = to_dev(x), to_dev(y)
     cot = torch.tensor([1.0], dtype=torch.float64, device="cuda")
@@ -192,7 +194,7 @@ def test_partial_grad_uneven_ranks_fp32(lead):
 def test_partial_k_kept_for_backward(dt, lead):
     """tt_contract_partial_k writes the same output cores as the plain partial
     contraction and fills a backward workspace (K; for a leading block also
-    the adjoint's checkpoints, stored by the forward sweep); the backward pass
+    every left environment, stored by the forward sweep); the backward pass
     that starts from it gives the oracle's gradients, like the one that
     recomputes everything."""
     rng = np.random.default_rng(51 if lead else 53)
@@ -202,7 +204,7 @@ def test_partial_k_kept_for_backward(dt, lead):
     ry = [1, 12, r, 17, r - 3, 9, 11, r, 3, 1]
     x = G.random_tt(rng, modes, rx, dt)
     y = G.random_tt(rng, modes, ry, dt)
-    mask = [1] * 7 + [0] * 2 if lead else [0] * 2 + [1] * 7  # seven modes: three checkpoint segments
+    mask = [1] * 7 + [0] * 2 if lead else [0] * 2 + [1] * 7  # seven contracted modes
     xd, yd = to_dev(x), to_dev(y)
     ref = T.PartialContraction(xd, yd, mask)
     ref()
